@@ -1,0 +1,402 @@
+/*
+ * mphf_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of the cascading-bit-array
+ * minimal perfect hash function (BBhash) of Limasset, Rizk, Chikhi and
+ * Peterlongo, "Fast and scalable minimal perfect hashing for massive key
+ * sets" (arXiv 1702.03154).  It exists to check the CUDA library against:
+ * only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no source with the CUDA path.
+ *
+ * The oracle follows the paper's algorithms step by step, in the paper's
+ * notation (F_d, A_d, C_d, h_d, gamma, last = L-1), with the conventions the
+ * paper leaves open fixed as follows:
+ *
+ *   mix(z)      the SplitMix64 finalizer (Steele, Lea, Flood, OOPSLA 2014);
+ *               the paper only asks for an "xor-shift based" hash (Sec. 3.3).
+ *   s_d         level seed  = mix(mix(seed) + d).
+ *   h_d(x)      = mix(x XOR s_d).
+ *   position    p = floor(h_d(x) * m_d / 2^64) (Lemire's fastrange reduction,
+ *               in place of "mod" in Algorithms 1-3).
+ *   m_d = |A_d| = |C_d| = max(64, ceil(gamma * |F_d|) rounded up to a multiple
+ *               of 64), gamma >= 1 real (Sec. 2.2.4); ceil(gamma*n) is taken
+ *               from one IEEE-754 double multiply.
+ *   indices     0-based: [0, N) instead of the paper's [1, N] (Sec. 1).
+ *   rank        exclusive: rank(g) = number of ones of A in bits [0, g)
+ *               (Sec. 2.2.3), checkpointed every 512 bits with 64-bit
+ *               counters (Sec. 3.1): rank[b] = ones in bits [0, 512 b).
+ *   levels      L levels numbered 0 .. L-1 (D = 25 by default, Sec. 3.5);
+ *               keys still colliding after level L-1 go to the fallback.
+ *   fallback    the "regular hash table" of Sec. 3.5 is a sorted array of
+ *               the leftover keys; key at sorted position i gets index
+ *               N - n_fb + i (the range Algorithm 1 gives it).
+ *   duplicates  identical keys collide at every level, so they reach the
+ *               fallback; two equal neighbours there -> ORACLE_EDUPLICATE.
+ *   non-members Algorithm 3 run as is: the first level whose bit is 1 gives
+ *               the rank, else a fallback hit, else UINT64_MAX.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL 1
+#define ORACLE_ENOMEM 2
+#define ORACLE_EDUPLICATE 3
+
+#define ORACLE_MAX_LEVELS 64
+#define ORACLE_RANK_BLOCK 512 /* Sec. 3.1: one 64-bit counter every 512 bits */
+
+/* Optional test hook: replaces the position of key x at level d (must be < m). */
+typedef uint64_t (*oracle_pos_hook)(void *user, uint32_t level, uint64_t key, uint64_t m);
+
+typedef struct oracle_mphf {
+    uint64_t N;
+    double gamma;
+    uint32_t L;          /* level budget */
+    uint32_t L_used;     /* levels actually built ("last" + 1) */
+    uint64_t seed;
+    uint64_t n[ORACLE_MAX_LEVELS + 1]; /* n[d] = |F_d|; n[L_used] = |fallback| */
+    uint64_t m[ORACLE_MAX_LEVELS];     /* |A_d| in bits */
+    uint64_t off[ORACLE_MAX_LEVELS];   /* first bit of A_d inside A */
+    uint64_t s[ORACLE_MAX_LEVELS];     /* level seeds s_d */
+    uint64_t M;                        /* total bits of A = sum m_d */
+    unsigned char *bitA;               /* A as one byte per bit, M entries */
+    unsigned char *bitC[ORACLE_MAX_LEVELS]; /* C_d kept for the invariant checks */
+    uint64_t *rank;                    /* ceil(M / 512) checkpoints */
+    uint64_t n_fb;
+    uint64_t *fb;                      /* sorted leftover keys */
+    oracle_pos_hook hook;
+    void *hook_user;
+} oracle_mphf;
+
+/* ---- hash pieces ------------------------------------------------------- */
+
+/* SplitMix64 finalizer: the published mixing function of SplitMix64. */
+uint64_t oracle_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* s_d: seed of the level-d hash function h_d (Sec. 2.1, "a new hash function h_1"). */
+uint64_t oracle_level_seed(uint64_t seed, uint32_t d)
+{
+    return oracle_mix(oracle_mix(seed) + (uint64_t)d);
+}
+
+/* h_d(x) (Sec. 3.3). */
+uint64_t oracle_hash(uint64_t x, uint64_t s_d)
+{
+    return oracle_mix(x ^ s_d);
+}
+
+/* Reduction of a 64-bit hash onto [0, m): floor(h * m / 2^64). */
+uint64_t oracle_fastrange(uint64_t h, uint64_t m)
+{
+    return (uint64_t)(((unsigned __int128)h * (unsigned __int128)m) >> 64);
+}
+
+/* |A_d| for |F_d| = n keys (Sec. 2.2.4: |A_d| = gamma |F_d|). */
+uint64_t oracle_level_bits(uint64_t n, double gamma)
+{
+    double t = gamma * (double)n;
+    uint64_t c = (uint64_t)t;
+    if ((double)c < t)
+        c += 1;                      /* ceil(gamma * n) */
+    c = (c + 63) / 64 * 64;          /* whole 64-bit words */
+    if (c < 64)
+        c = 64;
+    return c;
+}
+
+static uint64_t position(const oracle_mphf *h, uint32_t d, uint64_t x)
+{
+    if (h->hook)
+        return h->hook(h->hook_user, d, x, h->m[d]);
+    return oracle_fastrange(oracle_hash(x, h->s[d]), h->m[d]);
+}
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+void oracle_free(oracle_mphf *h)
+{
+    if (!h)
+        return;
+    free(h->bitA);
+    for (uint32_t d = 0; d < ORACLE_MAX_LEVELS; d++)
+        free(h->bitC[d]);
+    free(h->rank);
+    free(h->fb);
+    free(h);
+}
+
+/*
+ * Algorithm 2 (ArrayFill) for level d: hash every key of F into A_d / C_d,
+ * read as an if / else-if chain on (A[p], C[p]) so that exactly one branch
+ * fires per key, which is what the three implications of Sec. 2.2.1 state:
+ *   (0,0) -> A=1;   (1,0) -> A=0, C=1;   (0,1) -> skip.
+ */
+static void array_fill(const oracle_mphf *h, uint32_t d, const uint64_t *F, uint64_t n,
+                       unsigned char *A, unsigned char *C)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = position(h, d, F[i]);
+        if (A[p] == 0 && C[p] == 0) {
+            A[p] = 1;
+        } else if (A[p] == 1 && C[p] == 0) {
+            A[p] = 0;
+            C[p] = 1;
+        } else {
+            /* A[p] == 0 and C[p] == 1: skip.  (1,1) never happens. */
+        }
+    }
+}
+
+/*
+ * Algorithm 1 (MPHF construction) followed by the rank checkpoints of
+ * Sec. 3.1 and the fallback table of Sec. 3.5.
+ */
+int oracle_build_hooked(const uint64_t *keys, uint64_t N, double gamma, uint32_t L, uint64_t seed,
+                        oracle_pos_hook hook, void *hook_user, oracle_mphf **out)
+{
+    *out = NULL;
+    if (!(gamma >= 1.0) || isinf(gamma) || L < 1 || L > ORACLE_MAX_LEVELS || (N > 0 && !keys))
+        return ORACLE_EINVAL;
+    oracle_mphf *h = (oracle_mphf *)calloc(1, sizeof(oracle_mphf));
+    if (!h)
+        return ORACLE_ENOMEM;
+    h->N = N;
+    h->gamma = gamma;
+    h->L = L;
+    h->seed = seed;
+    h->hook = hook;
+    h->hook_user = hook_user;
+
+    /* F_0 = the key set; F_{i+1} gets the keys of F_i whose bit ended at 0. */
+    uint64_t *F = (uint64_t *)malloc((N ? N : 1) * sizeof(uint64_t));
+    uint64_t *Fnext = (uint64_t *)malloc((N ? N : 1) * sizeof(uint64_t));
+    unsigned char **Alev = (unsigned char **)calloc(ORACLE_MAX_LEVELS, sizeof(unsigned char *));
+    if (!F || !Fnext || !Alev) {
+        free(F); free(Fnext); free(Alev); oracle_free(h);
+        return ORACLE_ENOMEM;
+    }
+    if (N)
+        memcpy(F, keys, N * sizeof(uint64_t));
+    uint64_t n = N;
+    uint32_t i = 0;
+    uint64_t off = 0;
+    while (n > 0 && i < L) {           /* "while F_i not empty and i <= last" */
+        h->n[i] = n;
+        h->s[i] = oracle_level_seed(seed, i);
+        h->m[i] = oracle_level_bits(n, gamma);
+        h->off[i] = off;
+        unsigned char *A = (unsigned char *)calloc(h->m[i], 1);
+        unsigned char *C = (unsigned char *)calloc(h->m[i], 1);
+        if (!A || !C) {
+            free(A); free(C);
+            for (uint32_t d = 0; d < i; d++) free(Alev[d]);
+            free(F); free(Fnext); free(Alev); oracle_free(h);
+            return ORACLE_ENOMEM;
+        }
+        array_fill(h, i, F, n, A, C);   /* A_i = ArrayFill(F_i, gamma) */
+        uint64_t nn = 0;
+        for (uint64_t k = 0; k < n; k++) {
+            uint64_t p = position(h, i, F[k]);
+            if (A[p] == 0)
+                Fnext[nn++] = F[k];      /* F_{i+1}.add(x) */
+        }
+        Alev[i] = A;
+        h->bitC[i] = C;
+        off += h->m[i];
+        uint64_t *t = F; F = Fnext; Fnext = t;
+        n = nn;
+        i++;
+    }
+    h->L_used = i;
+    h->n[i] = n;
+    h->M = off;
+
+    /* A = A_0 || A_1 || ... || A_last (Sec. 2.1). */
+    h->bitA = (unsigned char *)malloc(h->M ? h->M : 1);
+    if (!h->bitA) {
+        for (uint32_t d = 0; d < i; d++) free(Alev[d]);
+        free(F); free(Fnext); free(Alev); oracle_free(h);
+        return ORACLE_ENOMEM;
+    }
+    for (uint32_t d = 0; d < h->L_used; d++) {
+        memcpy(h->bitA + h->off[d], Alev[d], h->m[d]);
+        free(Alev[d]);
+    }
+    free(Alev);
+
+    /* Rank checkpoints (Sec. 3.1): rank[b] = ones of A in bits [0, 512 b). */
+    uint64_t R = (h->M + ORACLE_RANK_BLOCK - 1) / ORACLE_RANK_BLOCK;
+    h->rank = (uint64_t *)malloc((R ? R : 1) * sizeof(uint64_t));
+    if (!h->rank) {
+        free(F); free(Fnext); oracle_free(h);
+        return ORACLE_ENOMEM;
+    }
+    uint64_t ones = 0;
+    for (uint64_t g = 0; g < h->M; g++) {
+        if (g % ORACLE_RANK_BLOCK == 0)
+            h->rank[g / ORACLE_RANK_BLOCK] = ones;
+        ones += h->bitA[g];
+    }
+
+    /* Fallback H (Sec. 3.5): the keys left in F_{last+1}, sorted. */
+    h->n_fb = n;
+    h->fb = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+    if (!h->fb) {
+        free(F); free(Fnext); oracle_free(h);
+        return ORACLE_ENOMEM;
+    }
+    if (n)
+        memcpy(h->fb, F, n * sizeof(uint64_t));
+    free(F);
+    free(Fnext);
+    qsort(h->fb, n, sizeof(uint64_t), cmp_u64);
+    for (uint64_t k = 1; k < n; k++) {
+        if (h->fb[k] == h->fb[k - 1]) {
+            oracle_free(h);
+            return ORACLE_EDUPLICATE;
+        }
+    }
+    *out = h;
+    return ORACLE_OK;
+}
+
+int oracle_build(const uint64_t *keys, uint64_t N, double gamma, uint32_t L, uint64_t seed,
+                 oracle_mphf **out)
+{
+    return oracle_build_hooked(keys, N, gamma, L, seed, NULL, NULL, out);
+}
+
+/* rank(g): ones of A strictly before global bit g, from checkpoint + the bits in between. */
+static uint64_t rank_at(const oracle_mphf *h, uint64_t g)
+{
+    uint64_t b = g / ORACLE_RANK_BLOCK;
+    uint64_t r = h->rank[b];
+    for (uint64_t t = b * ORACLE_RANK_BLOCK; t < g; t++)
+        r += h->bitA[t];
+    return r;
+}
+
+/* Algorithm 3 (MPHF query), minimal form of Sec. 2.2.3, 0-based. */
+uint64_t oracle_query(const oracle_mphf *h, uint64_t x)
+{
+    for (uint32_t i = 0; i < h->L_used; i++) {
+        uint64_t p = position(h, i, x);
+        if (h->bitA[h->off[i] + p] == 1)
+            return rank_at(h, h->off[i] + p);
+    }
+    /* H[x]: binary search of the sorted fallback. */
+    uint64_t lo = 0, hi = h->n_fb;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (h->fb[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    if (lo < h->n_fb && h->fb[lo] == x)
+        return h->N - h->n_fb + lo;
+    return UINT64_MAX;
+}
+
+void oracle_lookup(const oracle_mphf *h, const uint64_t *keys, uint64_t n, uint64_t *out)
+{
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = oracle_query(h, keys[i]);
+}
+
+/* Level of a key: the d that answers it, L_used for the fallback / a miss. */
+uint32_t oracle_key_level(const oracle_mphf *h, uint64_t x)
+{
+    for (uint32_t i = 0; i < h->L_used; i++) {
+        uint64_t p = position(h, i, x);
+        if (h->bitA[h->off[i] + p] == 1)
+            return i;
+    }
+    return h->L_used;
+}
+
+/* ---- introspection ------------------------------------------------------ */
+
+uint32_t oracle_num_levels(const oracle_mphf *h) { return h->L_used; }
+uint64_t oracle_total_bits(const oracle_mphf *h) { return h->M; }
+uint64_t oracle_num_fallback(const oracle_mphf *h) { return h->n_fb; }
+uint64_t oracle_num_rank(const oracle_mphf *h) { return (h->M + ORACLE_RANK_BLOCK - 1) / ORACLE_RANK_BLOCK; }
+
+int oracle_level_info(const oracle_mphf *h, uint32_t d, uint64_t *n_d, uint64_t *m_d, uint64_t *off_d,
+                      uint64_t *s_d)
+{
+    if (d >= h->L_used)
+        return ORACLE_EINVAL;
+    *n_d = h->n[d];
+    *m_d = h->m[d];
+    *off_d = h->off[d];
+    *s_d = h->s[d];
+    return ORACLE_OK;
+}
+
+/* A packed into 64-bit words: global bit g is bit (g % 64) of word g / 64. */
+void oracle_copy_bits(const oracle_mphf *h, uint64_t *words)
+{
+    uint64_t W = h->M / 64;
+    for (uint64_t w = 0; w < W; w++) {
+        uint64_t v = 0;
+        for (uint64_t b = 0; b < 64; b++)
+            if (h->bitA[w * 64 + b])
+                v |= 1ULL << b;
+        words[w] = v;
+    }
+}
+
+/* C_d packed the same way (m_d / 64 words). */
+int oracle_copy_collision_bits(const oracle_mphf *h, uint32_t d, uint64_t *words)
+{
+    if (d >= h->L_used)
+        return ORACLE_EINVAL;
+    uint64_t W = h->m[d] / 64;
+    for (uint64_t w = 0; w < W; w++) {
+        uint64_t v = 0;
+        for (uint64_t b = 0; b < 64; b++)
+            if (h->bitC[d][w * 64 + b])
+                v |= 1ULL << b;
+        words[w] = v;
+    }
+    return ORACLE_OK;
+}
+
+void oracle_copy_rank(const oracle_mphf *h, uint64_t *out)
+{
+    uint64_t R = oracle_num_rank(h);
+    for (uint64_t b = 0; b < R; b++)
+        out[b] = h->rank[b];
+}
+
+void oracle_copy_fallback(const oracle_mphf *h, uint64_t *out)
+{
+    for (uint64_t i = 0; i < h->n_fb; i++)
+        out[i] = h->fb[i];
+}
+
+/*
+ * Size of the function in bits per key with the rank structure of Sec. 3.1
+ * ((1 + 64/512) per bit of A) and 64 bits per fallback key; level metadata
+ * (a few words per level) is not counted.
+ */
+double oracle_bits_per_key(const oracle_mphf *h)
+{
+    if (h->N == 0)
+        return 0.0;
+    double bits = (double)h->M + 64.0 * (double)oracle_num_rank(h) + 64.0 * (double)h->n_fb;
+    return bits / (double)h->N;
+}

@@ -1,0 +1,333 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+generator outputs, closed forms, the worked example of Fig. 1, brute force on
+tiny inputs, the expectations of Sec. 2.3 / Lemma 1, Table 1, Sec. 3.4 and
+Sec. 3.5, and order independence.  A dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them (see the planted
+mistakes in ``test_oracle_mutants.py``).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_03154_gb300 import inputs
+
+U64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------- hash pieces
+def test_mixer_matches_published_splitmix64(golden_dir):
+    vals = [int(l, 16) for l in open(os.path.join(golden_dir, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    state = 0
+    for v in vals:
+        state = (state + 0x9E3779B97F4A7C15) & U64
+        assert oracle.mix(state) == v
+
+
+def test_mixer_is_a_bijection_on_a_sample():
+    # Distinct inputs give distinct outputs (the finalizer is invertible).
+    xs = inputs.splitmix64_keys(200000, 99)
+    ys = np.array([oracle.mix(int(x)) for x in xs[:20000]], dtype=np.uint64)
+    assert np.unique(ys).size == ys.size
+
+
+def test_level_seeds_differ_per_level():
+    s = [oracle.level_seed(7, d) for d in range(64)]
+    assert len(set(s)) == 64
+    assert oracle.level_seed(7, 0) != oracle.level_seed(8, 0)
+
+
+@pytest.mark.parametrize("h,m,expect", [
+    (0, 64, 0),
+    (U64, 64, 63),
+    (U64, 1 << 40, (1 << 40) - 1),
+    (1 << 63, 1000, 500),
+    (1 << 62, 64, 16),
+    ((1 << 63) - 1, 2, 0),
+    (1 << 63, 2, 1),
+])
+def test_fastrange_closed_forms(h, m, expect):
+    assert oracle.fastrange(h, m) == expect
+
+
+def test_fastrange_against_big_integers():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for _ in range(2000):
+        h = int(rng.integers(0, 1 << 63)) * 2 + int(rng.integers(0, 2))
+        m = int(rng.integers(64, 1 << 40))
+        assert oracle.fastrange(h, m) == (h * m) >> 64
+        assert 0 <= oracle.fastrange(h, m) < m
+
+
+@pytest.mark.parametrize("n,gamma,expect", [
+    (1, 1.0, 64), (64, 1.0, 64), (65, 1.0, 128), (100, 2.0, 256), (1000, 1.5, 1536),
+    (10**6, 2.0, 2000000), (10**6 + 1, 2.0, 2000064), (3, 5.0, 64), (13, 5.0, 128),
+    (10**8, 1.0, 100000000 + 0 if 10**8 % 64 == 0 else 100000000 + 64 - 10**8 % 64),
+])
+def test_level_size_rule(n, gamma, expect):
+    # |A_d| = gamma |F_d| (Sec. 2.2.4), ceil'd and rounded up to 64-bit words.
+    assert oracle.level_bits(n, gamma) == expect
+    assert oracle.level_bits(n, gamma) >= gamma * n
+
+
+# ---------------------------------------------------------- worked example
+def test_fig1_worked_example(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "fig1_worked_example.json")))
+    names = ["k1", "k2", "k3", "k4", "k5", "k6"]
+    key = {nm: 1000 + 17 * i for i, nm in enumerate(names)}
+    name = {v: k for k, v in key.items()}
+    # Positions consistent with the caption: level 0 places k6 < k3 and makes
+    # {k1,k2} and {k4,k5} collide; level 1 places k5 < k1 and makes {k2,k4}
+    # collide; level 2 places k2 < k4.
+    pos = [
+        {"k6": 0, "k3": 1, "k1": 2, "k2": 2, "k4": 4, "k5": 4},
+        {"k5": 0, "k1": 1, "k2": 2, "k4": 2},
+        {"k2": 0, "k4": 1},
+    ]
+
+    def hook(level, k, m):
+        return pos[level][name[k]] if level < len(pos) and name[k] in pos[level] else m - 1
+
+    keys = [key[nm] for nm in names]
+    h = oracle.build(keys, gamma=g["gamma"], levels=25, seed=0, pos_hook=hook)
+    assert h.num_levels == 3
+    assert h.level_sizes() == [6, 4, 2, 0]
+    out = h.lookup(keys)
+    expect = [g["values_1based"][nm] - 1 for nm in names]
+    assert out.tolist() == expect
+    assert h.key_level(key["k2"]) == g["query_k2_level"]
+    assert int(out[1]) + 1 == g["query_k2_value_1based"]
+    # A0 holds exactly k3 and k6, A1 k1 and k5, A2 k2 and k4.
+    placed = {d: sorted(nm for nm in names if h.key_level(key[nm]) == d) for d in range(3)}
+    lv = g["levels_from_caption"]
+    assert placed[0] == sorted(lv["A0_placed"])
+    assert placed[1] == sorted(lv["A1_placed"])
+    assert placed[2] == sorted(lv["A2_placed"])
+
+
+# ------------------------------------------------------------- brute force
+def _is_bijection(out, n):
+    return np.array_equal(np.sort(out), np.arange(n, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("gamma", [1.0, 1.3, 2.0, 5.0])
+@pytest.mark.parametrize("levels", [1, 2, 3, 25])
+def test_bijection_on_tiny_inputs(gamma, levels):
+    for seed in range(60):
+        n = 1 + (seed * 37) % 2000
+        keys = inputs.splitmix64_keys(n, 1000 + seed)
+        h = oracle.build(keys, gamma=gamma, levels=levels, seed=seed)
+        out = h.lookup(keys)
+        assert _is_bijection(out, n), (gamma, levels, seed, n)
+        sizes = h.level_sizes()
+        assert sizes[0] == n and sizes[-1] == h.num_fallback
+        assert h.num_levels <= levels
+
+
+def test_brute_force_index_is_rank_of_level_position():
+    # Independent characterisation: the index of a placed key is the number of
+    # placed keys whose (level offset + position) is smaller; fallback keys come
+    # after all placed keys in increasing key order.
+    for seed in range(20):
+        n = 50 + 31 * seed
+        keys = inputs.splitmix64_keys(n, 77 + seed)
+        h = oracle.build(keys, gamma=1.0, levels=3, seed=seed)
+        lv = h.levels()
+        glob = {}
+        fb = []
+        for x in keys.tolist():
+            d = h.key_level(x)
+            if d == h.num_levels:
+                fb.append(x)
+                continue
+            n_d, m_d, off_d, s_d = lv[d]
+            glob[x] = off_d + oracle.fastrange(oracle.mix(x ^ s_d), m_d)
+        order = sorted(glob, key=lambda x: glob[x])
+        expect = {x: i for i, x in enumerate(order)}
+        for i, x in enumerate(sorted(fb)):
+            expect[x] = len(order) + i
+        out = h.lookup(keys)
+        assert out.tolist() == [expect[x] for x in keys.tolist()]
+
+
+# --------------------------------------------------------------- statistics
+def _build(n, gamma, seed=1, levels=25):
+    return oracle.build(inputs.splitmix64_keys(n, seed), gamma=gamma, levels=levels, seed=seed)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 2.0, 5.0])
+def test_placed_fraction_per_level(gamma):
+    # Sec. 2.3: a fraction ~ e^{-1/gamma} of F_d is placed at level d; exactly,
+    # a key is alone at its position with probability (1 - 1/m_d)^(n_d - 1).
+    h = _build(10**6, gamma)
+    sizes = h.level_sizes()
+    for d in range(4):
+        n_d, m_d, _, _ = h.level_info(d)
+        if n_d < 2000:
+            break
+        p = (1.0 - 1.0 / m_d) ** (n_d - 1)
+        placed = sizes[d] - sizes[d + 1]
+        sigma = math.sqrt(n_d * p * (1 - p))
+        assert abs(placed - n_d * p) < 6 * sigma + 1, (d, placed, n_d * p)
+        assert abs(p - math.exp(-1.0 / gamma)) < 2e-3
+
+
+@pytest.mark.parametrize("gamma,expect", [(1.0, math.e), (2.0, 2 * math.exp(0.5)),
+                                          (5.0, 5 * math.exp(0.2))])
+def test_total_size_matches_gamma_e_1_over_gamma(gamma, expect):
+    # Sec. 2.3 / Appendix: sum |A_d| = gamma e^{1/gamma} N.
+    h = _build(10**6, gamma)
+    assert abs(h.total_bits / 10**6 - expect) / expect < 0.01
+
+
+def test_bits_per_key_matches_table1(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "table1_bits_per_key.json")))
+    for row in g["rows"]:
+        h = _build(10**6, row["gamma"], seed=3)
+        if row["rank_block"] == 512:
+            bpk = h.bits_per_key()
+        else:
+            # minirank: one counter per 1024 bits instead of 512.
+            M = h.total_bits
+            bpk = (M + 64 * math.ceil(M / 1024) + 64 * h.num_fallback) / h.N
+        assert abs(bpk - row["bits_per_key"]) <= g["printed_precision"] + 0.01, (row, bpk)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 2.0, 5.0])
+def test_mean_level_is_e_1_over_gamma(gamma):
+    # Sec. 4.1: the average number of levels a key visits is e^{1/gamma}.
+    h = _build(10**6, gamma)
+    visits = sum(h.level_sizes()[:-1]) / 10**6
+    assert abs(visits - math.exp(1.0 / gamma)) / math.exp(1.0 / gamma) < 0.01
+
+
+def test_temporary_set_sizes_match_sec34(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "sec34_temporary_sets.json")))
+    for row in g["rows"]:
+        h = _build(10**6, row["gamma"], seed=4)
+        s = h.level_sizes()
+        ratio = (s[1] + s[2]) / s[0]
+        assert abs(ratio - row["ratio"]) <= g["printed_precision"] + 0.005, (row, ratio)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 1.2, 2.0, 5.0])
+def test_lemma1_construction_memory(gamma):
+    # Lemma 1: m(d) = sum_{i<d} |A_i| + 2|A_d|; max_d m(d)/S <= 1 for
+    # gamma <= 1/ln 2, in (1, 2) otherwise, with m(0)/S = 2 e^{-1/gamma}.
+    h = _build(10**6, gamma)
+    lv = h.levels()
+    S = h.total_bits
+    m = [sum(x[1] for x in lv[:d]) + 2 * lv[d][1] for d in range(len(lv))]
+    R = max(m) / S
+    assert abs(m[0] / S - 2 * math.exp(-1 / gamma)) < 0.01
+    if gamma <= 1 / math.log(2):
+        assert R <= 1.0 + 0.01
+    else:
+        assert 1.0 < R < 2.0
+        assert abs(R - 2 * math.exp(-1 / gamma)) < 0.01
+
+
+def test_fallback_count_at_gamma1_is_about_1e_5_N():
+    # Sec. 3.5: with D = 25 levels, about 1e-5 N keys reach the hash table at
+    # gamma = 1 (q^25 N with q = 1 - 1/e) and practically none at gamma >= 2.
+    n = 4 * 10**6
+    h = _build(n, 1.0, seed=11)
+    expect = (1 - math.exp(-1)) ** 25 * n
+    assert abs(expect / n - 1e-5) < 0.1e-5
+    assert abs(h.num_fallback - expect) < 6 * math.sqrt(expect)
+    assert _build(10**6, 2.0, seed=11).num_fallback == 0
+
+
+# --------------------------------------------------------------- invariants
+@pytest.mark.parametrize("gamma,levels", [(1.0, 25), (2.0, 25), (1.0, 4)])
+def test_structural_invariants(gamma, levels):
+    n = 200000
+    h = _build(n, gamma, seed=21, levels=levels)
+    sizes = h.level_sizes()
+    A = h.bits()
+    total = 0
+    for d in range(h.num_levels):
+        a = h.level_bits_words(d)
+        c = h.collision_bits(d)
+        assert not np.any(a & c)                             # Alg. 2 footnote
+        w = int(np.unpackbits(a.view(np.uint8)).sum())
+        assert w == sizes[d] - sizes[d + 1]                  # weight(A_d)
+        total += w
+    assert total + h.num_fallback == n
+    bitsA = np.unpackbits(A.view(np.uint8), bitorder="little").astype(np.int64)
+    ones = np.concatenate([[0], np.cumsum(bitsA)])
+    rank = h.rank()
+    assert rank.size == (h.total_bits + 511) // 512
+    assert np.array_equal(rank, ones[np.arange(rank.size) * 512].astype(np.uint64))
+    fb = h.fallback()
+    assert np.all(fb[1:] > fb[:-1])
+
+
+def test_order_independence():
+    keys = inputs.splitmix64_keys(300000, 31)
+    a = oracle.build(keys, gamma=1.0, levels=25, seed=5)
+    b = oracle.build(inputs.shuffled(keys, 9), gamma=1.0, levels=25, seed=5)
+    assert a.levels() == b.levels()
+    assert np.array_equal(a.bits(), b.bits())
+    assert np.array_equal(a.rank(), b.rank())
+    assert np.array_equal(a.fallback(), b.fallback())
+    assert np.array_equal(a.lookup(keys), b.lookup(keys))
+
+
+# --------------------------------------------------------------- edge cases
+def test_empty_and_single_key():
+    h = oracle.build(np.zeros(0, dtype=np.uint64), 2.0, 25, 0)
+    assert h.num_levels == 0 and h.total_bits == 0 and h.num_fallback == 0
+    assert h.lookup([1, 2, 3]).tolist() == [U64] * 3
+    h1 = oracle.build([12345], 2.0, 25, 0)
+    assert h1.lookup([12345]).tolist() == [0]
+    assert h1.num_levels == 1 and h1.total_bits == 64
+
+
+def test_duplicates_are_reported():
+    keys = inputs.splitmix64_keys(1000, 3)
+    keys[500] = keys[17]
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build(keys, 2.0, 25, 0)
+    assert e.value.code == oracle.EDUPLICATE
+    with pytest.raises(oracle.OracleError):
+        oracle.build(np.array([5, 5], dtype=np.uint64), 1.0, 3, 0)
+
+
+@pytest.mark.parametrize("gamma,levels", [(0.5, 25), (float("nan"), 25), (float("inf"), 25),
+                                          (2.0, 0), (2.0, 65)])
+def test_invalid_arguments(gamma, levels):
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build([1, 2, 3], gamma, levels, 0)
+    assert e.value.code == oracle.EINVAL
+
+
+def test_single_level_sends_colliders_to_fallback():
+    keys = inputs.splitmix64_keys(5000, 8)
+    h = oracle.build(keys, gamma=1.0, levels=1, seed=2)
+    n_fb = h.num_fallback
+    assert n_fb > 0
+    out = h.lookup(keys)
+    assert _is_bijection(out, keys.size)
+    fb = h.fallback()
+    pos = {int(x): i for i, x in enumerate(fb)}
+    for x, v in zip(keys.tolist(), out.tolist()):
+        if x in pos:
+            assert v == keys.size - n_fb + pos[x]
+
+
+def test_non_member_keys_follow_algorithm3():
+    keys = inputs.splitmix64_keys(20000, 12)
+    h = oracle.build(keys, gamma=1.0, levels=2, seed=4)
+    others = inputs.splitmix64_keys(20000, 13)
+    out = h.lookup(others)
+    ok = (out < keys.size) | (out == np.uint64(U64))
+    assert np.all(ok)
+    assert np.any(out == np.uint64(U64))       # some fall through every level
+    assert np.array_equal(out, h.lookup(others))
