@@ -1,0 +1,366 @@
+"""Benchmark: build + lookup of a cascading-bit-array MPHF on one GB300.
+
+Workload (one step): build the function over N = 1e8 distinct 64-bit keys
+(SplitMix64 outputs 0..N-1 of seed 2, resident in HBM), gamma = 2, L = 25,
+then look up all N keys in a uniformly shuffled order.  The keys (800 MB) are
+larger than L2, so no L2 flush is needed between steps.
+
+value     = N / (time of one step), Mkeys/s, over all ranks (weak scaling:
+            each rank builds its own function over its own N keys).
+e2e       = the same through the host-buffer C-ABI entry points
+            (mphf_build_host + mphf_lookup_host from pinned memory), so the
+            host<->device copies are inside the timed region.
+roofline  = the dominant kernel's algorithmic bytes / its event-timed duration
+            against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference = the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "build+lookup Mkeys/s (N=1e8, gamma=2, L=25)"
+UNIT = "Mkeys/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=float, default=1e8)
+    p.add_argument("--gamma", type=float, default=2.0)
+    p.add_argument("--levels", type=int, default=25)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--sweep", action="store_true", help="also time gamma = 1 and 5")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------- utils
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- CPU baselines
+def cpu_baseline(n_sample: int, gamma: float, levels: int):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_1702_03154_gb300 import inputs
+    keys = inputs.splitmix64_keys(n_sample, 2)
+    q = inputs.shuffled(keys, 3)
+    t0 = time.perf_counter()
+    h = oracle.build(keys, gamma=gamma, levels=levels, seed=0)
+    t1 = time.perf_counter()
+    h.lookup(q)
+    t2 = time.perf_counter()
+    return {"value": n_sample / (t2 - t0) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"build over the first {n_sample:.0e} keys of the workload + lookup of all of "
+                      f"them in shuffled order (gamma={gamma}, L={levels}); build {t1 - t0:.2f} s, "
+                      f"lookup {t2 - t1:.2f} s, single-threaded C"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n_sample = 2_000_000
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline(n_sample, args.gamma, args.levels)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = cpu_baseline(n_sample, args.gamma, args.levels)
+        per_step.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(per_step))
+    val = n_sample / (ms / 1e3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"oracle on {n_sample:.0e}-key samples of the N=1e8 workload",
+                       "gamma": args.gamma, "levels": args.levels},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def algorithmic_bytes(h, name: str) -> int:
+    """Algorithmic DRAM bytes of all launches of one kernel in one step."""
+    sizes = h.level_sizes()          # n_0 .. n_last, n_fb
+    lv = h.levels()
+    if name == "fill":
+        return 8 * sizes[0]          # read every key of F_0
+    if name == "compact":            # read F_d, write F_{d+1}
+        return sum(8 * sizes[d] + 8 * sizes[d + 1] for d in range(len(sizes) - 1) if sizes[d + 1])
+    if name == "extract":            # read AC (2 m_d bits), write A_d (m_d bits), zero AC
+        return sum(5 * m // 8 for (_, m, _, _) in lv)
+    if name == "lookup":
+        return 16 * sizes[0]         # key in, index out
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_03154_gb300 import mphf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N = int(args.n)
+    gamma, L = args.gamma, args.levels
+    stream = torch.cuda.current_stream()
+    keys = mphf.keygen(N, 2 + rank)                       # resident in HBM
+    perm = torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    q = keys[perm]
+    del perm
+    out = torch.empty(N, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        h = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
+        h.lookup(q, out=out)
+        return h
+
+    for _ in range(args.warmup):
+        step().free()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    mphf.profile_enable(True)
+    launches0 = mphf.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        if last is not None:
+            last.free()
+        last = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = mphf.launch_count() - launches0
+    mphf.profile_enable(False)
+    prof = mphf.profile_report()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+
+    # build / lookup split (separately timed, outside the main region)
+    tb, tl = [], []
+    for _ in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        h = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
+        e1.record(stream)
+        h.lookup(q, out=out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        tl.append(e1.elapsed_time(e2))
+        h.free()
+
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * N / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    kernels = {}
+    total_ms = sum(v[1] for v in prof.values()) or 1.0
+    for name, (cnt, tot) in prof.items():
+        b = algorithmic_bytes(last, name) * args.steps
+        kernels[name] = {"launches": cnt, "total_ms": round(tot, 4),
+                         "share": round(tot / total_ms, 4),
+                         "gbs": round(b / (tot / 1e3) / 1e9, 1) if tot and b else None}
+    if dom:
+        name, (cnt, tot) = dom
+        b = algorithmic_bytes(last, name) * args.steps
+        ach = b / (tot / 1e3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs", "launches_per_step": cnt / args.steps,
+                "avg_launch_ms": tot / cnt}
+    struct = {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
+              "level_sizes": last.level_sizes()[:8], "fallback": last.num_fallback}
+    last.free()
+
+    e2e = None
+    if not args.no_e2e:
+        kh = torch.empty(N, dtype=torch.int64, pin_memory=True)
+        kh.copy_(keys)
+        qh = torch.empty(N, dtype=torch.int64, pin_memory=True)
+        qh.copy_(q)
+        oh = torch.empty(N, dtype=torch.int64, pin_memory=True)
+        del q
+        torch.cuda.empty_cache()
+        for _ in range(1):
+            h = mphf.MPHF.build_host(kh, gamma=gamma, levels=L, seed=0)
+            h.lookup_host(qh, out=oh.numpy().view(np.uint64))
+            h.free()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 5))
+        for _ in range(reps):
+            h = mphf.MPHF.build_host(kh, gamma=gamma, levels=L, seed=0)
+            h.lookup_host(qh, out=oh.numpy().view(np.uint64))
+            h.free()
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = (time.perf_counter() - t0) * 1e3 / reps
+        e_t = torch.tensor([e_ms], device="cuda")
+        if world > 1:
+            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * N / (float(e_t.item()) / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
+               "ms_per_step": float(e_t.item()),
+               "api": "mphf_build_host + mphf_lookup_host, pinned host buffers"}
+
+    sweep = {}
+    if args.sweep:
+        for g2 in (1.0, 5.0):
+            ts = []
+            for i in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                kk = keys
+                e0.record(stream)
+                h = mphf.MPHF.build(kk, gamma=g2, levels=L, seed=0)
+                h.lookup(kk, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i:
+                    ts.append(e0.elapsed_time(e1))
+                h.free()
+            sweep[f"gamma={g2:g}"] = {"mkeys_s": round(N / (np.median(ts) / 1e3) / 1e6, 1),
+                                      "ms": round(float(np.median(ts)), 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(10_000_000, gamma, L)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": "plain single MPHF, N=1e8 SplitMix64 keys (seed 2), "
+                                       "gamma=2, L=25; build + lookup of all N in shuffled order",
+                           "N": N, "gamma": gamma, "levels": L,
+                           "l2": "inputs (800 MB keys + 800 MB queries) larger than L2; no flush"},
+                "build_mkeys_s": round(N / (float(np.median(tb)) / 1e3) / 1e6, 1),
+                "lookup_mkeys_s": round(N / (float(np.median(tl)) / 1e3) / 1e6, 1),
+                "build_ms": round(float(np.median(tb)), 4), "lookup_ms": round(float(np.median(tl)), 4),
+                "structure": struct, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu}
+        if sweep:
+            line["gamma_sweep"] = sweep
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

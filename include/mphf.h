@@ -1,0 +1,150 @@
+/*
+ * mphf.h -- C ABI of the GB300 (sm_103a) cascading-bit-array minimal perfect
+ * hash function library (libmphf.so).
+ *
+ * The method is BBhash (Limasset, Rizk, Chikhi, Peterlongo, "Fast and scalable
+ * minimal perfect hashing for massive key sets", arXiv 1702.03154): keys are
+ * hashed level by level into bit arrays A_d of gamma*|F_d| bits; a key that is
+ * alone at its position sets its bit, colliding keys move on to F_{d+1}
+ * (Sec. 2.1, Algorithms 1-2); the index of a key is the rank of its bit in the
+ * concatenation A = A_0 || A_1 || ... (Sec. 2.2.3, Algorithm 3), with 64-bit
+ * rank checkpoints every 512 bits (Sec. 3.1); keys left after L levels go to a
+ * fallback table (Sec. 3.5).
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - level seed s_d = mix(mix(seed) + d), h_d(x) = mix(x ^ s_d), where mix is
+ *     the SplitMix64 finalizer; position p = floor(h_d(x) * m_d / 2^64);
+ *   - m_d = |A_d| = max(64, ceil(gamma * n_d) rounded up to a multiple of 64);
+ *   - indices are 0-based, in [0, N); rank is exclusive (ones before the bit);
+ *   - bit g of A is bit (g % 64) of 64-bit word g / 64; level d starts at bit
+ *     off_d = m_0 + ... + m_{d-1};
+ *   - rank[b] = number of ones of A in bits [0, 512 b), ceil(M / 512) entries;
+ *   - the fallback is the sorted array of leftover keys; the key at sorted
+ *     position i has index N - n_fb + i;
+ *   - a key that is not in the set gets what Algorithm 3 yields: the rank at
+ *     the first level whose bit is 1, else its fallback index, else
+ *     MPHF_NOT_FOUND.
+ *
+ * Memory and streams.  Pointers named d_* are device pointers (CUDA global
+ * memory of the current device); h_* are host pointers.  A `stream` argument
+ * is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ * device memory a handle owns is allocated by the library and released by
+ * mphf_free.  Functions return MPHF_OK or an error code; none aborts.  Every
+ * function taking a handle is safe to call from one host thread at a time per
+ * handle; lookups on one handle from several streams may overlap.
+ */
+#ifndef MPHF_H
+#define MPHF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mphf mphf_t;
+
+#define MPHF_NOT_FOUND UINT64_MAX
+#define MPHF_MAX_LEVELS 64
+#define MPHF_RANK_BLOCK 512
+
+enum {
+    MPHF_OK = 0,
+    MPHF_EINVAL = 1,      /* bad argument: gamma < 1 or not finite, levels not in [1,64], NULL */
+    MPHF_ENOMEM = 2,      /* a device or host allocation failed */
+    MPHF_EDUPLICATE = 3,  /* the key set holds two equal keys */
+    MPHF_ECUDA = 4,       /* a CUDA runtime call failed (the message is in mphf_last_cuda_error) */
+    MPHF_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    MPHF_EINTERNAL = 6    /* a device-side consistency check failed */
+};
+
+/* Text for an error code (static storage). */
+const char *mphf_strerror(int code);
+/* Last CUDA runtime error text seen by this library (static storage). */
+const char *mphf_last_cuda_error(void);
+/* ABI version of this header. */
+int mphf_abi_version(void);
+
+/*
+ * Build the function over n distinct keys (Algorithm 1 with ArrayFill,
+ * Algorithm 2; rank checkpoints, Sec. 3.1; fallback, Sec. 3.5).
+ *   d_keys  device array of n uint64 keys; read only, owned by the caller, may
+ *           be released as soon as the call returns; any 8-byte alignment.
+ *   n       number of keys (0 gives a valid empty function).
+ *   gamma   |A_d| / |F_d| (Sec. 2.2.4), finite and >= 1.
+ *   levels  level budget L in [1, 64] (D = 25 in the paper).
+ *   seed    selects the hash functions h_d.
+ *   stream  work is issued on this stream; the call returns when it is done.
+ *   out     receives the new handle (NULL on error).
+ * Errors: MPHF_EINVAL, MPHF_ENOMEM, MPHF_EDUPLICATE (nothing is leaked),
+ * MPHF_ECUDA, MPHF_EINTERNAL.
+ */
+int mphf_build(const uint64_t *d_keys, uint64_t n, double gamma, uint32_t levels, uint64_t seed,
+               void *stream, mphf_t **out);
+
+/* As mphf_build, with the keys in host memory (copied to the device inside the call;
+ * page-locked memory makes the copy asynchronous and faster). */
+int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t levels,
+                    uint64_t seed, void *stream, mphf_t **out);
+
+/*
+ * Query n keys (Algorithm 3, minimal index of Sec. 2.2.3).
+ *   d_keys  device array of n keys, any 8-byte alignment.
+ *   d_out   device array of n uint64 results (caller-allocated).
+ * Asynchronous: returns once the kernel is queued on `stream`.  n = 0 is a no-op.
+ */
+int mphf_lookup(const mphf_t *h, const uint64_t *d_keys, uint64_t n, uint64_t *d_out,
+                void *stream);
+
+/* As mphf_lookup with host arrays: copies in, queries, copies out, and waits. */
+int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n, uint64_t *h_out,
+                     void *stream);
+
+/* Size of the function in bits per key: (M + 64 ceil(M/512) + 64 n_fb) / N with M the
+ * total bits of A (Sec. 3.1's (1 + 64/512) gamma e^{1/gamma}); level metadata excluded.
+ * 0 for an empty function or NULL. */
+double mphf_bits_per_key(const mphf_t *h);
+
+/* Release a handle and its device memory; NULL is a no-op. */
+void mphf_free(mphf_t *h);
+
+/* ---- introspection (host copies; for tests and tools) ------------------ */
+uint64_t mphf_num_keys(const mphf_t *h);
+uint32_t mphf_num_levels(const mphf_t *h);      /* levels built, last + 1 */
+uint64_t mphf_total_bits(const mphf_t *h);      /* M */
+uint64_t mphf_num_rank(const mphf_t *h);        /* ceil(M / 512) */
+uint64_t mphf_num_fallback(const mphf_t *h);    /* n_fb */
+/* n_d = |F_d|, m_d = |A_d|, off_d = first bit of A_d in A, s_d = level seed. */
+int mphf_level_info(const mphf_t *h, uint32_t d, uint64_t *n_d, uint64_t *m_d, uint64_t *off_d,
+                    uint64_t *s_d);
+/* Copy A (M/64 words), the rank checkpoints or the sorted fallback to host memory;
+ * `count` must equal the size reported above. */
+int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count);
+int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count);
+int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
+
+/* ---- synthetic keys ------------------------------------------------------ */
+/*
+ * d_out[i] = output (start + i) of the SplitMix64 generator started at state
+ * `seed` (Steele, Lea, Flood, OOPSLA 2014): distinct 64-bit keys, the paper's
+ * workload of unique pseudo-random integers (Sec. 4).  Asynchronous on `stream`.
+ */
+int mphf_keygen(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void *stream);
+
+/* ---- measurement ---------------------------------------------------------- */
+/* Number of kernels this library has launched in this process. */
+uint64_t mphf_launch_count(void);
+/*
+ * Per-kernel timing: while enabled, every kernel the library launches is
+ * bracketed by CUDA events on its own stream.  mphf_profile_report waits for
+ * the recorded work, then writes lines "name launches total_ms\n" into buf
+ * (NUL-terminated, truncated to buflen) and clears the record.
+ */
+int mphf_profile_enable(int on);
+int mphf_profile_report(char *buf, uint64_t buflen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPHF_H */

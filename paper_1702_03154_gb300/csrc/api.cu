@@ -1,0 +1,255 @@
+// api.cu -- handle lifetime, introspection, error text, device memory,
+// launch accounting / per-kernel event timing, and the synthetic key generator.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bbh {
+
+static std::mutex g_err_mu;
+static char g_err_text[512] = "no error";
+
+void set_cuda_error(cudaError_t e, const char *where) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  snprintf(g_err_text, sizeof(g_err_text), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  set_cuda_error(e, where);
+  return MPHF_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Launch accounting and optional per-kernel event timing.
+// ---------------------------------------------------------------------------
+static std::atomic<u64> g_launches{0};
+static std::atomic<int> g_profile_on{0};
+static std::mutex g_prof_mu;
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof;           // recorded launches
+static std::vector<cudaEvent_t> g_event_pool; // reusable events
+static thread_local int t_open = -1;          // index of the open record of this thread
+
+static cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void launch_begin(const char *name, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_profile_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r{name, take_event(), take_event()};
+  cudaEventRecord(r.a, s);
+  g_prof.push_back(r);
+  t_open = (int)g_prof.size() - 1;
+}
+
+void launch_end(cudaStream_t s) {
+  if (t_open < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (t_open < (int)g_prof.size()) cudaEventRecord(g_prof[t_open].b, s);
+  t_open = -1;
+}
+
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
+  b.p = nullptr;
+  b.bytes = bytes;
+  if (bytes == 0) return MPHF_OK;
+  static bool pool_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !pool_set[dev]) {
+    // Keep freed blocks in this process's pool for reuse by the next build
+    // (up to 16 GiB), instead of returning them to the driver at every sync.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      u64 thr = 16ull << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    pool_set[dev] = true;
+  }
+  cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    set_cuda_error(e, "cudaMallocAsync");
+    return MPHF_ENOMEM;
+  }
+  return MPHF_OK;
+}
+
+void dev_free(DevBuf &b, cudaStream_t s) {
+  if (b.p) cudaFreeAsync(b.p, s);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Synthetic keys: output j of SplitMix64 started at `seed` is
+// fin(seed + (j + 1) * 0x9E3779B97F4A7C15), fin = the generator's finalizer.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_keygen(u64 *__restrict__ out, u64 n, u64 seed, u64 start) {
+  const u64 G = 0x9E3779B97F4A7C15ull;
+  u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    out[i] = mix64(seed + (start + i + 1) * G);
+  }
+}
+
+}  // namespace bbh
+
+using namespace bbh;
+
+extern "C" {
+
+const char *mphf_strerror(int code) {
+  switch (code) {
+    case MPHF_OK: return "ok";
+    case MPHF_EINVAL: return "invalid argument";
+    case MPHF_ENOMEM: return "out of memory";
+    case MPHF_EDUPLICATE: return "duplicate keys";
+    case MPHF_ECUDA: return "CUDA error";
+    case MPHF_ETIMEOUT: return "device wait timed out";
+    case MPHF_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+const char *mphf_last_cuda_error(void) { return g_err_text; }
+
+int mphf_abi_version(void) { return 1; }
+
+void mphf_free(mphf_t *h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  dev_free(h->A, 0);
+  dev_free(h->rank, 0);
+  dev_free(h->fb, 0);
+  if (prev != h->device) cudaSetDevice(prev);
+  delete h;
+}
+
+double mphf_bits_per_key(const mphf_t *h) {
+  if (!h || h->N == 0) return 0.0;
+  double bits = (double)h->M + 64.0 * (double)h->n_rank + 64.0 * (double)h->n_fb;
+  return bits / (double)h->N;
+}
+
+uint64_t mphf_num_keys(const mphf_t *h) { return h ? h->N : 0; }
+uint32_t mphf_num_levels(const mphf_t *h) { return h ? h->L_used : 0; }
+uint64_t mphf_total_bits(const mphf_t *h) { return h ? h->M : 0; }
+uint64_t mphf_num_rank(const mphf_t *h) { return h ? h->n_rank : 0; }
+uint64_t mphf_num_fallback(const mphf_t *h) { return h ? h->n_fb : 0; }
+
+int mphf_level_info(const mphf_t *h, uint32_t d, uint64_t *n_d, uint64_t *m_d, uint64_t *off_d,
+                    uint64_t *s_d) {
+  if (!h || d >= h->L_used) return MPHF_EINVAL;
+  if (n_d) *n_d = h->n[d];
+  if (m_d) *m_d = h->m[d];
+  if (off_d) *off_d = h->off[d];
+  if (s_d) *s_d = h->s[d];
+  return MPHF_OK;
+}
+
+static int copy_out(const mphf_t *h, const DevBuf &b, uint64_t *dst, uint64_t count,
+                    uint64_t expect) {
+  if (!h || (count && !dst) || count != expect) return MPHF_EINVAL;
+  if (!count) return MPHF_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  cudaError_t e = cudaMemcpy(dst, b.p, count * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+  if (prev != h->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(D2H)");
+  return MPHF_OK;
+}
+
+int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count) {
+  return copy_out(h, h->A, h_words, count, h ? h->M / 64 : 0);
+}
+int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
+  return copy_out(h, h->rank, h_rank, count, h ? h->n_rank : 0);
+}
+int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count) {
+  return copy_out(h, h->fb, h_keys, count, h ? h->n_fb : 0);
+}
+
+int mphf_keygen(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void *stream) {
+  if (n == 0) return MPHF_OK;
+  if (!d_out) return MPHF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int grid = grid_for(n, 256 * 8, (unsigned)sm_count() * 8);
+  {
+    LaunchScope ls("keygen", s);
+    k_keygen<<<grid, 256, 0, s>>>((u64 *)d_out, n, seed, start);
+  }
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+uint64_t mphf_launch_count(void) { return g_launches.load(); }
+
+int mphf_profile_enable(int on) {
+  g_profile_on.store(on ? 1 : 0);
+  return MPHF_OK;
+}
+
+int mphf_profile_report(char *buf, uint64_t buflen) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::map<std::string, std::pair<u64, double>> agg;
+  std::vector<std::string> order;
+  int rc = MPHF_OK;
+  for (auto &r : g_prof) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      set_cuda_error(e, "cudaEventElapsedTime");
+      rc = MPHF_ECUDA;
+      cudaGetLastError();
+    }
+    std::string k(r.name);
+    if (!agg.count(k)) order.push_back(k);
+    agg[k].first += 1;
+    agg[k].second += ms;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  std::string out;
+  for (auto &k : order) {
+    char line[256];
+    snprintf(line, sizeof(line), "%s %llu %.6f\n", k.c_str(), (unsigned long long)agg[k].first,
+             agg[k].second);
+    out += line;
+  }
+  if (buf && buflen) {
+    size_t n = out.size() < buflen - 1 ? out.size() : (size_t)buflen - 1;
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return rc;
+}
+
+}  // extern "C"

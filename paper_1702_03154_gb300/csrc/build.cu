@@ -1,0 +1,525 @@
+// build.cu -- level-by-level construction (Algorithm 1 with ArrayFill,
+// Algorithm 2) of the cascading-bit-array MPHF on one GPU.
+//
+// Per level d the GPU form of ArrayFill is: every key of F_d sets its
+// position's hit bit with one 64-bit atomicOr; a key that finds the hit bit
+// already set marks the collision bit (a second atomicOr).  The hit and
+// collision bits of 32 consecutive positions share one 64-bit word ("AC"
+// layout: bits 0-31 hit, bits 32-63 collision), so both atomics of a key touch
+// the same L2 sector.  Extraction then computes A_d = hit & ~collision into
+// the concatenated A, counts weight(A_d), and derives |F_{d+1}| = |F_d| -
+// weight(A_d) before any key is moved.  Compaction of level d streams F_d
+// again, keeps the keys whose A_d bit is 0 (Algorithm 1, "if A_i[h] == 0
+// then F_{i+1}.add(x)"), packs them with warp ballots + a block scan, and --
+// since |A_{d+1}| is already known -- runs level d+1's ArrayFill on the
+// survivors in the same pass, so F_{d+1} is read once less.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace bbh {
+
+static constexpr int kFillThreads = 256;
+static constexpr int kFillUnroll = 4;      // uint4 loads (2 keys each) in flight per thread
+static constexpr int kExtractThreads = 256;
+static constexpr int kCompactThreads = 256;
+static constexpr int kCompactKPT = 16;     // keys per thread per tile
+static constexpr int kCompactTile = kCompactThreads * kCompactKPT;
+
+// ArrayFill for one key at position p of an AC array (Alg. 2, read as the
+// three implications of Sec. 2.2.1: first hit sets A; a later hit sees A set
+// and records the collision; the final A is hit & ~collision).
+__device__ __forceinline__ void fill_position(u64 *__restrict__ AC, u64 p) {
+  u64 w = p >> 5;
+  u64 hit = 1ull << (p & 31);
+  u64 old = atomicOr(AC + w, hit);
+  if ((old & hit) && !(old & (hit << 32))) atomicOr(AC + w, hit << 32);
+}
+
+__device__ __forceinline__ uint4 load_stream(const uint4 *p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------------------
+// Level-0 ArrayFill over the caller's keys.  2 keys per 16-byte load, several
+// loads in flight per thread; keys are read with the streaming (evict-first)
+// hint so that the AC array keeps its L2 lines.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFillThreads)
+k_fill_vec(const uint4 *__restrict__ keys2, u64 npairs, u64 s, u64 m, u64 *__restrict__ AC) {
+  const u64 stride = (u64)gridDim.x * kFillThreads * kFillUnroll;
+  for (u64 base = (u64)blockIdx.x * kFillThreads * kFillUnroll + threadIdx.x; base < npairs;
+       base += stride) {
+    uint4 v[kFillUnroll];
+#pragma unroll
+    for (int u = 0; u < kFillUnroll; u++) {
+      u64 i = base + (u64)u * kFillThreads;
+      if (i < npairs) v[u] = load_stream(keys2 + i);
+    }
+#pragma unroll
+    for (int u = 0; u < kFillUnroll; u++) {
+      u64 i = base + (u64)u * kFillThreads;
+      if (i < npairs) {
+        u64 x0 = ((u64)v[u].y << 32) | v[u].x;
+        u64 x1 = ((u64)v[u].w << 32) | v[u].z;
+        fill_position(AC, level_pos(x0, s, m));
+        fill_position(AC, level_pos(x1, s, m));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFillThreads)
+k_fill_scalar(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 *__restrict__ AC) {
+  const u64 stride = (u64)gridDim.x * kFillThreads;
+  for (u64 i = (u64)blockIdx.x * kFillThreads + threadIdx.x; i < n; i += stride)
+    fill_position(AC, level_pos(__ldcs(keys + i), s, m));
+}
+
+// ---------------------------------------------------------------------------
+// Extract A_d = hit & ~collision, count weight(A_d), zero the AC array for
+// reuse two levels later, and (last block) size level d+1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kExtractThreads)
+k_extract(u64 *__restrict__ AC, u64 *__restrict__ A0, u64 *__restrict__ Aarena,
+          BuildMeta *__restrict__ meta, int d, int L, double gamma) {
+  const u64 m = meta->m[d];
+  if (m == 0) return;  // level not built
+  const u64 m0 = meta->m[0];
+  u64 *Alev = (d == 0) ? A0 : Aarena + ((meta->off[d] - m0) >> 6);
+  const u64 W = m >> 6;
+  const u64 stride = (u64)gridDim.x * kExtractThreads;
+  u64 local = 0;
+  uint4 *AC4 = reinterpret_cast<uint4 *>(AC);
+  for (u64 w = (u64)blockIdx.x * kExtractThreads + threadIdx.x; w < W; w += stride) {
+    uint4 v = AC4[w];  // AC words 2w, 2w+1 = positions [64w, 64w + 64)
+    u64 a = (u64)(v.x & ~v.y) | ((u64)(v.z & ~v.w) << 32);
+    Alev[w] = a;
+    local += __popcll(a);
+    AC4[w] = make_uint4(0, 0, 0, 0);
+  }
+  // block reduction of the popcounts
+  __shared__ u64 red[kExtractThreads / 32];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 sum = 0;
+    for (int i = 0; i < kExtractThreads / 32; i++) sum += red[i];
+    if (sum) atomicAdd(&meta->weight[d], sum);
+    __threadfence();
+    unsigned int t = atomicAdd(&meta->done[d], 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    volatile BuildMeta *vm = meta;
+    u64 wgt = vm->weight[d];
+    u64 n = vm->n[d];
+    if (wgt > n) {  // cannot happen: every set bit is one distinct key
+      atomicExch(&meta->status, (unsigned)MPHF_EINTERNAL);
+      wgt = n;
+    }
+    u64 nn = n - wgt;
+    vm->n[d + 1] = nn;
+    vm->off[d + 1] = vm->off[d] + m;
+    vm->m[d + 1] = (nn > 0 && d + 1 < L) ? level_bits(nn, gamma) : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compaction of level d (+ ArrayFill of level d+1 on the survivors).
+// A tile of kCompactTile keys: each warp packs its surviving keys into its own
+// shared-memory segment with ballots, a block scan of the warp counts places
+// the segments, and one atomicAdd per tile reserves the tile's output range.
+// The output order of F_{d+1} is therefore not the input order; nothing
+// downstream depends on it (ArrayFill is a function of the key set).
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restrict__ A0,
+          const u64 *__restrict__ Aarena, u64 *__restrict__ ACnext, BuildMeta *__restrict__ meta,
+          int d, u64 s_d, u64 s_next, int do_fill, u64 cap) {
+  const u64 n = meta->n[d];
+  const u64 m = meta->m[d];
+  if (m == 0 || n == 0 || meta->n[d + 1] == 0) return;
+  const u64 m0 = meta->m[0];
+  const u64 *Alev = (d == 0) ? A0 : Aarena + ((meta->off[d] - m0) >> 6);
+  const u64 m_next = do_fill ? meta->m[d + 1] : 0;
+
+  __shared__ u64 stage[kCompactTile];
+  __shared__ unsigned int wcount[kCompactThreads / 32];
+  __shared__ unsigned int woff[kCompactThreads / 32];
+  __shared__ u64 base_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  u64 *seg = stage + warp * (32 * kCompactKPT);
+
+  const u64 ntiles = (n + kCompactTile - 1) / kCompactTile;
+  for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const u64 t0 = tile * kCompactTile;
+    u64 x[kCompactKPT];
+    bool valid[kCompactKPT];
+    if (VEC) {
+      // thread t of warp w reads pairs (t0/2 + w*32*KPT/2 + k*32 + lane), k < KPT/2
+      const uint4 *F2 = reinterpret_cast<const uint4 *>(F);
+#pragma unroll
+      for (int k = 0; k < kCompactKPT / 2; k++) {
+        u64 i = t0 + (u64)warp * 32 * kCompactKPT + (u64)k * 64 + 2 * lane;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (i + 1 < n) {
+          v = load_stream(F2 + (i >> 1));
+        } else if (i < n) {  // odd tail: never read past the last key
+          u64 t = __ldcs(F + i);
+          v.x = (unsigned)t;
+          v.y = (unsigned)(t >> 32);
+        }
+        x[2 * k] = ((u64)v.y << 32) | v.x;
+        x[2 * k + 1] = ((u64)v.w << 32) | v.z;
+        valid[2 * k] = i < n;
+        valid[2 * k + 1] = i + 1 < n;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kCompactKPT; k++) {
+        u64 i = t0 + (u64)warp * 32 * kCompactKPT + (u64)k * 32 + lane;
+        valid[k] = i < n;
+        x[k] = valid[k] ? __ldcs(F + i) : 0;
+      }
+    }
+    // survival test: the key's bit in A_d is 0
+    bool keep[kCompactKPT];
+#pragma unroll
+    for (int k = 0; k < kCompactKPT; k++) {
+      keep[k] = false;
+      if (valid[k]) {
+        u64 p = level_pos(x[k], s_d, m);
+        keep[k] = !((__ldg(Alev + (p >> 6)) >> (p & 63)) & 1ull);
+      }
+    }
+    unsigned cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kCompactKPT; k++) {
+      unsigned b = __ballot_sync(0xffffffffu, keep[k]);
+      if (keep[k]) seg[cnt + __popc(b & lt_mask)] = x[k];
+      cnt += __popc(b);
+    }
+    if (lane == 0) wcount[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned run = 0;
+      for (int w = 0; w < kCompactThreads / 32; w++) {
+        woff[w] = run;
+        run += wcount[w];
+      }
+      base_s = run ? atomicAdd(&meta->out_count[d], (u64)run) : 0;
+    }
+    __syncthreads();
+    const u64 base = base_s + woff[warp];
+    if (base + cnt > cap && lane == 0) atomicExch(&meta->status, (unsigned)MPHF_EINTERNAL);
+    for (unsigned i = lane; i < cnt; i += 32) {
+      u64 y = seg[i];
+      if (base + i >= cap) break;  // never write past F_{d+1}; status is already set
+      Fout[base + i] = y;
+      if (m_next) fill_position(ACnext, level_pos(y, s_next, m_next));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration.
+// ---------------------------------------------------------------------------
+struct Scratch {
+  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag;
+  void release(cudaStream_t s) {
+    dev_free(meta, s); dev_free(AC0, s); dev_free(AC1, s); dev_free(A0, s);
+    dev_free(arena, s); dev_free(F1, s); dev_free(F2, s); dev_free(dupflag, s);
+  }
+};
+
+static void release_handle(mphf_t *h, cudaStream_t s) {
+  if (!h) return;
+  dev_free(h->A, s);
+  dev_free(h->rank, s);
+  dev_free(h->fb, s);
+  delete h;
+}
+
+static int launch_fill0(const u64 *keys, u64 n, u64 s0, u64 m0, u64 *AC, cudaStream_t st) {
+  unsigned maxb = (unsigned)sm_count() * 8;
+  if (((uintptr_t)keys & 15) == 0) {
+    u64 npairs = n >> 1;
+    if (npairs) {
+      unsigned g = grid_for(npairs, kFillThreads * kFillUnroll, maxb);
+      LaunchScope ls("fill", st);
+      k_fill_vec<<<g, kFillThreads, 0, st>>>(reinterpret_cast<const uint4 *>(keys), npairs, s0,
+                                              m0, AC);
+    }
+    if (n & 1) {
+      LaunchScope ls("fill", st);
+      k_fill_scalar<<<1, kFillThreads, 0, st>>>(keys + (n - 1), 1, s0, m0, AC);
+    }
+  } else {
+    unsigned g = grid_for(n, kFillThreads * 4, maxb);
+    LaunchScope ls("fill", st);
+    k_fill_scalar<<<g, kFillThreads, 0, st>>>(keys, n, s0, m0, AC);
+  }
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+static int launch_extract(u64 *AC, u64 m_bound, u64 *A0, u64 *arena, BuildMeta *meta, int d,
+                          int L, double gamma, cudaStream_t st) {
+  unsigned g = grid_for(m_bound / 64, kExtractThreads * 4, (unsigned)sm_count() * 8);
+  LaunchScope ls("extract", st);
+  k_extract<<<g, kExtractThreads, 0, st>>>(AC, A0, arena, meta, d, L, gamma);
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+static int launch_compact(const u64 *F, u64 n_bound, u64 *Fout, u64 cap, const u64 *A0,
+                          const u64 *arena, u64 *ACnext, BuildMeta *meta, int d, u64 s_d,
+                          u64 s_next, int do_fill, cudaStream_t st) {
+  unsigned g = grid_for(n_bound, kCompactTile, (unsigned)sm_count() * 4);
+  LaunchScope ls("compact", st);
+  if (((uintptr_t)F & 15) == 0)
+    k_compact<true><<<g, kCompactThreads, 0, st>>>(F, Fout, A0, arena, ACnext, meta, d, s_d,
+                                                   s_next, do_fill, cap);
+  else
+    k_compact<false><<<g, kCompactThreads, 0, st>>>(F, Fout, A0, arena, ACnext, meta, d, s_d,
+                                                    s_next, do_fill, cap);
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+static int read_meta(const DevBuf &meta, BuildMeta *hm, cudaStream_t st) {
+  MPHF_CUDA(cudaMemcpyAsync(hm, meta.p, sizeof(BuildMeta), cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  return MPHF_OK;
+}
+
+static int read_u64(const u64 *d_ptr, u64 *out, cudaStream_t st) {
+  MPHF_CUDA(cudaMemcpyAsync(out, d_ptr, sizeof(u64), cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  return MPHF_OK;
+}
+
+static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+                      mphf_t **out) {
+  int rc = MPHF_OK;
+  mphf_t *h = new (std::nothrow) mphf_t();
+  if (!h) return MPHF_ENOMEM;
+  cudaGetDevice(&h->device);
+  h->N = N;
+  h->gamma = gamma;
+  h->L = L;
+  h->seed = seed;
+  for (uint32_t d = 0; d < L; d++) h->s[d] = level_seed(seed, d);
+  if (N == 0) {
+    *out = h;
+    return MPHF_OK;
+  }
+  Scratch sc;
+  BuildMeta hm;
+  memset(&hm, 0, sizeof(hm));
+  const u64 m0 = level_bits(N, gamma);
+  hm.n[0] = N;
+  hm.m[0] = m0;
+  hm.off[0] = 0;
+  u64 n1 = 0, last_level = 0, n_fb = 0;
+  u64 *Ffb = nullptr;
+  BuildMeta *meta = nullptr;
+  unsigned int *dflag = nullptr;
+
+#define TRY(x)                  \
+  do {                          \
+    rc = (x);                   \
+    if (rc != MPHF_OK) goto fail; \
+  } while (0)
+
+  TRY(dev_alloc(sc.meta, sizeof(BuildMeta), st));
+  meta = (BuildMeta *)sc.meta.p;
+  TRY(dev_alloc(sc.AC0, m0 / 32 * 8, st));
+  TRY(dev_alloc(sc.A0, m0 / 64 * 8, st));
+  TRY(dev_alloc(sc.dupflag, 16, st));
+  dflag = (unsigned int *)sc.dupflag.p;
+  if ((rc = cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    rc = cuda_fail((cudaError_t)rc, "cudaMemcpyAsync(meta)");
+    goto fail;
+  }
+  if (cudaMemsetAsync(sc.AC0.p, 0, sc.AC0.bytes, st) != cudaSuccess ||
+      cudaMemsetAsync(dflag, 0, 16, st) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    goto fail;
+  }
+
+  // Level 0: ArrayFill over the caller's keys, then extraction.
+  TRY(launch_fill0(keys, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
+  TRY(launch_extract((u64 *)sc.AC0.p, m0, (u64 *)sc.A0.p, nullptr, meta, 0, (int)L, gamma, st));
+  TRY(read_u64(&meta->n[1], &n1, st));
+
+  if (n1 > 0) {
+    // Every later level holds at most n1 keys, so these bounds are exact worst cases.
+    const u64 m1 = level_bits(n1, gamma);
+    TRY(dev_alloc(sc.F1, n1 * 8, st));
+    if (L > 1) TRY(dev_alloc(sc.F2, n1 * 8, st));
+    if (L > 1) {
+      TRY(dev_alloc(sc.AC1, m1 / 32 * 8, st));
+      TRY(dev_alloc(sc.arena, (u64)(L - 1) * (m1 / 64) * 8, st));
+      if (cudaMemsetAsync(sc.AC1.p, 0, sc.AC1.bytes, st) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+        goto fail;
+      }
+    }
+  }
+
+  {
+    // Level loop: compaction of d (+ fill of d+1), extraction of d+1.
+    u64 n_next = n1;  // |F_{d+1}|
+    const u64 *Fin = keys;
+    int d = 0;
+    for (;;) {
+      if (n_next == 0) {
+        last_level = d;
+        break;
+      }
+      u64 *Fout = ((d + 1) & 1) ? (u64 *)sc.F1.p : (u64 *)sc.F2.p;
+      const bool to_fallback = (uint32_t)(d + 1) == L;
+      u64 *ACnext = ((d + 1) & 1) ? (u64 *)sc.AC1.p : (u64 *)sc.AC0.p;
+      TRY(launch_compact(Fin, d == 0 ? N : n1, Fout, n1, (const u64 *)sc.A0.p,
+                         (const u64 *)sc.arena.p, to_fallback ? nullptr : ACnext, meta, d,
+                         h->s[d], to_fallback ? 0 : h->s[d + 1], to_fallback ? 0 : 1, st));
+      if (to_fallback) {
+        last_level = d;
+        Ffb = Fout;
+        n_fb = n_next;
+        break;
+      }
+      TRY(launch_extract(ACnext, level_bits(n1, gamma), (u64 *)sc.A0.p, (u64 *)sc.arena.p, meta,
+                         d + 1, (int)L, gamma, st));
+      TRY(read_u64(&meta->n[d + 2], &n_next, st));
+      Fin = Fout;
+      d++;
+    }
+  }
+
+  TRY(read_meta(sc.meta, &hm, st));
+  if (hm.status) {
+    rc = (int)hm.status;
+    goto fail;
+  }
+  h->L_used = (uint32_t)last_level + 1;
+  for (uint32_t d = 0; d < h->L_used; d++) {
+    h->n[d] = hm.n[d];
+    h->m[d] = hm.m[d];
+    h->off[d] = hm.off[d];
+    // every compaction must have written exactly |F_{d+1}| keys
+    if (d + 1 < h->L_used || n_fb) {
+      if (hm.out_count[d] != hm.n[d + 1]) {
+        rc = MPHF_EINTERNAL;
+        goto fail;
+      }
+    }
+  }
+  h->n[h->L_used] = n_fb;
+  h->M = hm.off[h->L_used - 1] + hm.m[h->L_used - 1];
+  h->n_rank = (h->M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
+  h->n_fb = n_fb;
+
+  // Final A = A_0 || arena, then the rank checkpoints.
+  TRY(dev_alloc(h->A, h->M / 64 * 8, st));
+  TRY(dev_alloc(h->rank, h->n_rank * 8, st));
+  if (cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 64 * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(A0)");
+    goto fail;
+  }
+  if (h->M > m0 &&
+      cudaMemcpyAsync((u64 *)h->A.p + m0 / 64, sc.arena.p, (h->M - m0) / 64 * 8,
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(arena)");
+    goto fail;
+  }
+  TRY(build_rank_table((const u64 *)h->A.p, h->M / 64, (u64 *)h->rank.p, h->n_rank,
+                       (u64 *)sc.dupflag.p + 1, st));
+
+  // Fallback (Sec. 3.5): sorted leftover keys; equal neighbours mean duplicates.
+  if (n_fb) {
+    TRY(sort_fallback(Ffb, n_fb, dflag, st));
+    TRY(dev_alloc(h->fb, n_fb * 8, st));
+    if (cudaMemcpyAsync(h->fb.p, Ffb, n_fb * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(fb)");
+      goto fail;
+    }
+  }
+  {
+    u64 flags[2] = {0, 0};
+    if (cudaMemcpyAsync(flags, sc.dupflag.p, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "dup flag");
+      goto fail;
+    }
+    if ((unsigned)flags[0]) {
+      rc = MPHF_EDUPLICATE;
+      goto fail;
+    }
+    // rank total must equal the number of placed keys
+    if (flags[1] != N - n_fb) {
+      rc = MPHF_EINTERNAL;
+      goto fail;
+    }
+  }
+  sc.release(st);
+  *out = h;
+  return MPHF_OK;
+
+fail:
+  cudaGetLastError();
+  sc.release(st);
+  release_handle(h, st);
+  cudaStreamSynchronize(st);
+  return rc;
+#undef TRY
+}
+
+}  // namespace bbh
+
+using namespace bbh;
+
+extern "C" int mphf_build(const uint64_t *d_keys, uint64_t n, double gamma, uint32_t levels,
+                          uint64_t seed, void *stream, mphf_t **out) {
+  if (!out) return MPHF_EINVAL;
+  *out = nullptr;
+  if (!(gamma >= 1.0) || isinf(gamma) || levels < 1 || levels > MPHF_MAX_LEVELS ||
+      (n > 0 && !d_keys) || ((uintptr_t)d_keys & 7))
+    return MPHF_EINVAL;
+  return build_impl((const u64 *)d_keys, n, gamma, levels, seed, (cudaStream_t)stream, out);
+}
+
+extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t levels,
+                               uint64_t seed, void *stream, mphf_t **out) {
+  if (!out) return MPHF_EINVAL;
+  *out = nullptr;
+  if (!(gamma >= 1.0) || isinf(gamma) || levels < 1 || levels > MPHF_MAX_LEVELS ||
+      (n > 0 && !h_keys))
+    return MPHF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf kb;
+  int rc = dev_alloc(kb, n * 8, st);
+  if (rc != MPHF_OK) return rc;
+  if (n) {
+    cudaError_t e = cudaMemcpyAsync(kb.p, h_keys, n * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      dev_free(kb, st);
+      return cuda_fail(e, "cudaMemcpyAsync(H2D keys)");
+    }
+  }
+  rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out);
+  dev_free(kb, st);
+  return rc;
+}

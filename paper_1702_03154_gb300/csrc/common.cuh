@@ -1,0 +1,146 @@
+// common.cuh -- shared internals of libmphf (device hash, level sizing, launch
+// accounting, error plumbing).  Internal to the CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mphf.h"
+
+namespace bbh {
+
+typedef unsigned long long u64;
+
+// ---------------------------------------------------------------------------
+// Level hash (Sec. 3.3 asks for a fast "xor-shift based" hash; this library
+// uses the SplitMix64 finalizer, a xor-shift-multiply mixer).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Seed of h_d: a different hash function per level (Sec. 2.1).
+__host__ __device__ __forceinline__ u64 level_seed(u64 seed, uint32_t d) {
+  return mix64(mix64(seed) + (u64)d);
+}
+
+// floor(h * m / 2^64): maps the 64-bit hash onto [0, m) without a division.
+__device__ __forceinline__ u64 reduce_range(u64 h, u64 m) { return __umul64hi(h, m); }
+
+// Position of key x in A_d (m_d bits).
+__device__ __forceinline__ u64 level_pos(u64 x, u64 s_d, u64 m_d) {
+  return reduce_range(mix64(x ^ s_d), m_d);
+}
+
+// |A_d| for n keys (Sec. 2.2.4: gamma * |F_d| bits), in whole 64-bit words, >= 64.
+// ceil(gamma * n) comes from one IEEE double multiply (no fused operation).
+__host__ __device__ __forceinline__ u64 level_bits(u64 n, double gamma) {
+#ifdef __CUDA_ARCH__
+  double t = __dmul_rn(gamma, (double)n);
+#else
+  volatile double t = gamma * (double)n;
+#endif
+  u64 c = (u64)t;
+  if ((double)c < t) c += 1;
+  c = (c + 63) & ~63ull;
+  return c < 64 ? 64 : c;
+}
+
+// ---------------------------------------------------------------------------
+// Per-build device metadata.  The build kernels read level sizes from here and
+// the last block of each extract writes the next level's sizes, so the level
+// loop needs no host round trip to size its launches.
+// ---------------------------------------------------------------------------
+struct BuildMeta {
+  u64 n[MPHF_MAX_LEVELS + 1];   // n[d] = |F_d|
+  u64 m[MPHF_MAX_LEVELS + 1];   // m[d] = |A_d| bits (0 past the last level)
+  u64 off[MPHF_MAX_LEVELS + 1]; // bit offset of A_d in A
+  u64 weight[MPHF_MAX_LEVELS];  // ones in A_d
+  u64 out_count[MPHF_MAX_LEVELS + 1];  // keys written to F_{d+1} by compaction d
+  unsigned int done[MPHF_MAX_LEVELS];  // extract blocks finished
+  unsigned int status;          // 0 or an MPHF_E* code raised on the device
+  unsigned int levels_used;     // set by extract when a level leaves no keys
+};
+
+// ---------------------------------------------------------------------------
+// Host-side plumbing.
+// ---------------------------------------------------------------------------
+void set_cuda_error(cudaError_t e, const char *where);
+int cuda_fail(cudaError_t e, const char *where);  // records and returns MPHF_ECUDA
+
+#define MPHF_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::bbh::cuda_fail(e_, #call); \
+  } while (0)
+
+// Kernel launch accounting + optional event timing.  Every launch in the
+// library goes through LaunchScope so that mphf_launch_count() and the
+// per-kernel profile see it.
+void launch_begin(const char *name, cudaStream_t s);
+void launch_end(cudaStream_t s);
+
+struct LaunchScope {
+  cudaStream_t s;
+  LaunchScope(const char *name, cudaStream_t st) : s(st) { launch_begin(name, st); }
+  ~LaunchScope() { launch_end(s); }
+};
+
+inline int sm_count() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+  }
+  return v;
+}
+
+inline unsigned int grid_for(u64 items, unsigned int per_block, unsigned int max_blocks) {
+  u64 b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (unsigned int)b;
+}
+
+// Device memory owned by a handle or a build.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
+void dev_free(DevBuf &b, cudaStream_t s);
+
+// Rank table over A (rank.cu): rank[b] = ones in bits [0, 512 b).
+int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_total,
+                     cudaStream_t s);
+// Sort n keys ascending in place and flag equal neighbours (sort.cu).
+int sort_fallback(u64 *keys, u64 n, unsigned int *d_dup_flag, cudaStream_t s);
+
+}  // namespace bbh
+
+// The handle.  Host copies of the level metadata plus the device arrays.
+struct mphf {
+  uint64_t N = 0;
+  double gamma = 2.0;
+  uint32_t L = 25;
+  uint64_t seed = 0;
+  uint32_t L_used = 0;
+  uint64_t n[MPHF_MAX_LEVELS + 1] = {0};
+  uint64_t m[MPHF_MAX_LEVELS] = {0};
+  uint64_t off[MPHF_MAX_LEVELS] = {0};
+  uint64_t s[MPHF_MAX_LEVELS] = {0};
+  uint64_t M = 0;        // total bits
+  uint64_t n_rank = 0;   // ceil(M / 512)
+  uint64_t n_fb = 0;
+  bbh::DevBuf A;        // M / 64 words
+  bbh::DevBuf rank;     // n_rank words
+  bbh::DevBuf fb;       // n_fb keys
+  int device = 0;
+};

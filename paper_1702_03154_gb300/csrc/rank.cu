@@ -1,0 +1,128 @@
+// rank.cu -- rank checkpoints over the concatenated bit array A (Sec. 3.1):
+// one 64-bit counter per 512 bits, rank[b] = number of ones in bits [0, 512 b).
+//
+// Three passes: (1) each thread popcounts one 512-bit block (four 16-byte
+// loads) and the CTA turns its 256 counts into exclusive prefixes; (2) one CTA
+// scans the per-CTA totals; (3) each checkpoint adds its CTA's prefix.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bbh {
+
+static constexpr int kRankThreads = 256;
+static constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64 *total) {
+  __shared__ u64 warp_sums[kRankThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64 x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    u64 w = lane < kRankThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kRankThreads / 32) warp_sums[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  u64 before = warp ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[kRankThreads / 32 - 1];
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+k_rank_blocks(const u64 *__restrict__ A, u64 nwords, u64 *__restrict__ rank, u64 nrank,
+              u64 *__restrict__ cta_sums) {
+  u64 b = (u64)blockIdx.x * kRankThreads + threadIdx.x;
+  u64 c = 0;
+  if (b < nrank) {
+    u64 w0 = b * 8;
+    if (w0 + 8 <= nwords) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(A + w0);
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint4 v = __ldg(p + j);
+        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      }
+    } else {
+      for (u64 w = w0; w < nwords; w++) c += __popcll(__ldg(A + w));
+    }
+  }
+  u64 total;
+  u64 ex = block_exclusive_scan(c, &total);
+  if (b < nrank) rank[b] = ex;
+  if (threadIdx.x == 0) cta_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of `count` CTA totals in one CTA; grand total to *d_total.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_sums(u64 *__restrict__ sums, u64 count, u64 *__restrict__ d_total) {
+  __shared__ u64 part[kScanThreads];
+  const u64 per = (count + kScanThreads - 1) / kScanThreads;
+  const u64 lo = threadIdx.x * per;
+  const u64 hi = lo + per < count ? lo + per : count;
+  u64 s = 0;
+  for (u64 i = lo; i < hi; i++) s += sums[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over kScanThreads partials
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    u64 add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  u64 run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (u64 i = lo; i < hi; i++) {
+    u64 v = sums[i];
+    sums[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == kScanThreads - 1 && d_total) *d_total = part[kScanThreads - 1];
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+k_rank_add(u64 *__restrict__ rank, u64 nrank, const u64 *__restrict__ cta_prefix) {
+  u64 b = (u64)blockIdx.x * kRankThreads + threadIdx.x;
+  if (b < nrank) rank[b] += cta_prefix[blockIdx.x];
+}
+
+int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_total,
+                     cudaStream_t s) {
+  if (nrank == 0) {
+    if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
+    return MPHF_OK;
+  }
+  const u64 ctas = (nrank + kRankThreads - 1) / kRankThreads;
+  if (ctas > 0x7fffffffull) return MPHF_EINVAL;
+  DevBuf sums;
+  int rc = dev_alloc(sums, ctas * sizeof(u64), s);
+  if (rc != MPHF_OK) return rc;
+  {
+    LaunchScope ls("rank_blocks", s);
+    k_rank_blocks<<<(unsigned)ctas, kRankThreads, 0, s>>>(A, nwords, rank, nrank, (u64 *)sums.p);
+  }
+  {
+    LaunchScope ls("rank_scan", s);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>((u64 *)sums.p, ctas, d_total);
+  }
+  if (ctas > 1) {
+    LaunchScope ls("rank_add", s);
+    k_rank_add<<<(unsigned)ctas, kRankThreads, 0, s>>>(rank, nrank, (const u64 *)sums.p);
+  }
+  cudaError_t e = cudaGetLastError();
+  dev_free(sums, s);
+  if (e != cudaSuccess) return cuda_fail(e, "rank kernels");
+  return MPHF_OK;
+}
+
+}  // namespace bbh

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of ``libmphf.so`` (C ABI in ``include/mphf.h``).
+
+Argument marshalling only: every step of construction and lookup runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams; keys are
+``torch.int64`` tensors holding the 64-bit key patterns (reinterpreted as
+unsigned by the library).  There is no CPU fallback: if the library cannot be
+built or loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build_ext
+
+OK, EINVAL, ENOMEM, EDUPLICATE, ECUDA, ETIMEOUT, EINTERNAL = range(7)
+NOT_FOUND = (1 << 64) - 1
+RANK_BLOCK = 512
+MAX_LEVELS = 64
+
+_lib = None
+
+
+class MPHFError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        L = lib()
+        msg = L.mphf_strerror(code).decode()
+        if code == ECUDA:
+            msg += ": " + L.mphf_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg}" if what else msg)
+        self.code = code
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MPHFError(rc, what)
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def lib():
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not build_ext.up_to_date():
+        build_ext.build()
+    if not os.path.exists(build_ext.LIB):
+        raise RuntimeError(f"libmphf.so is missing at {build_ext.LIB}; the CUDA path cannot run")
+    L = ctypes.CDLL(build_ext.LIB)
+    vp, u64, u32, dbl, i32 = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                              ctypes.c_int)
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    pu64 = ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "mphf_strerror": ([i32], ctypes.c_char_p),
+        "mphf_last_cuda_error": ([], ctypes.c_char_p),
+        "mphf_abi_version": ([], i32),
+        "mphf_build": ([vp, u64, dbl, u32, u64, vp, pvp], i32),
+        "mphf_build_host": ([vp, u64, dbl, u32, u64, vp, pvp], i32),
+        "mphf_lookup": ([vp, vp, u64, vp, vp], i32),
+        "mphf_lookup_host": ([vp, vp, u64, vp, vp], i32),
+        "mphf_bits_per_key": ([vp], dbl),
+        "mphf_free": ([vp], None),
+        "mphf_num_keys": ([vp], u64),
+        "mphf_num_levels": ([vp], u32),
+        "mphf_total_bits": ([vp], u64),
+        "mphf_num_rank": ([vp], u64),
+        "mphf_num_fallback": ([vp], u64),
+        "mphf_level_info": ([vp, u32, pu64, pu64, pu64, pu64], i32),
+        "mphf_copy_bits": ([vp, vp, u64], i32),
+        "mphf_copy_rank": ([vp, vp, u64], i32),
+        "mphf_copy_fallback": ([vp, vp, u64], i32),
+        "mphf_keygen": ([vp, u64, u64, u64, vp], i32),
+        "mphf_launch_count": ([], u64),
+        "mphf_profile_enable": ([i32], i32),
+        "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def _dev_keys(keys):
+    import torch
+    if not isinstance(keys, torch.Tensor) or not keys.is_cuda:
+        raise TypeError("keys must be a CUDA tensor (use build_host / lookup_host for host arrays)")
+    if keys.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise TypeError("keys must hold 64-bit integers")
+    return keys.contiguous()
+
+
+def _host_u64(a) -> np.ndarray:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            a = a.detach().cpu().numpy()
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.asarray(a)
+    if a.dtype != np.uint64:
+        a = a.astype(np.int64, copy=False).view(np.uint64) if a.dtype == np.int64 else a.astype(np.uint64)
+    return np.ascontiguousarray(a)
+
+
+class MPHF:
+    """A minimal perfect hash function resident in GPU memory."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    # -- construction ---------------------------------------------------
+    @classmethod
+    def build(cls, keys, gamma: float = 2.0, levels: int = 25, seed: int = 0, stream=None) -> "MPHF":
+        keys = _dev_keys(keys)
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build(keys.data_ptr() if keys.numel() else None, keys.numel(), float(gamma),
+                              int(levels), int(seed) & NOT_FOUND, _stream_ptr(stream),
+                              ctypes.byref(h))
+        _check(rc, "mphf_build")
+        return cls(h)
+
+    @classmethod
+    def build_host(cls, keys, gamma: float = 2.0, levels: int = 25, seed: int = 0,
+                   stream=None) -> "MPHF":
+        a = keys if isinstance(keys, np.ndarray) and keys.dtype == np.uint64 else _host_u64(keys)
+        ptr = _host_ptr(keys, a)
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_host(ptr if a.size else None, a.size, float(gamma), int(levels),
+                                   int(seed) & NOT_FOUND, _stream_ptr(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_host")
+        return cls(h)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().mphf_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- queries ----------------------------------------------------------
+    def lookup(self, keys, out=None, stream=None):
+        import torch
+        keys = _dev_keys(keys)
+        if out is None:
+            out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+        rc = lib().mphf_lookup(self._h, keys.data_ptr(), keys.numel(), out.data_ptr(),
+                               _stream_ptr(stream))
+        _check(rc, "mphf_lookup")
+        return out
+
+    def lookup_host(self, keys, out: Optional[np.ndarray] = None, stream=None) -> np.ndarray:
+        a = keys if isinstance(keys, np.ndarray) and keys.dtype == np.uint64 else _host_u64(keys)
+        if out is None:
+            out = np.empty(a.size, dtype=np.uint64)
+        rc = lib().mphf_lookup_host(self._h, _host_ptr(keys, a), a.size, _host_ptr(out, out),
+                                    _stream_ptr(stream))
+        _check(rc, "mphf_lookup_host")
+        return out
+
+    # -- structure ----------------------------------------------------------
+    def bits_per_key(self) -> float:
+        return lib().mphf_bits_per_key(self._h)
+
+    @property
+    def N(self) -> int:
+        return lib().mphf_num_keys(self._h)
+
+    @property
+    def num_levels(self) -> int:
+        return lib().mphf_num_levels(self._h)
+
+    @property
+    def total_bits(self) -> int:
+        return lib().mphf_total_bits(self._h)
+
+    @property
+    def num_rank(self) -> int:
+        return lib().mphf_num_rank(self._h)
+
+    @property
+    def num_fallback(self) -> int:
+        return lib().mphf_num_fallback(self._h)
+
+    def level_info(self, d: int):
+        a, b, c, s = (ctypes.c_uint64() for _ in range(4))
+        _check(lib().mphf_level_info(self._h, d, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                     ctypes.byref(s)), "mphf_level_info")
+        return a.value, b.value, c.value, s.value
+
+    def levels(self):
+        return [self.level_info(d) for d in range(self.num_levels)]
+
+    def level_sizes(self):
+        return [self.level_info(d)[0] for d in range(self.num_levels)] + [self.num_fallback]
+
+    def bits(self) -> np.ndarray:
+        out = np.empty(self.total_bits // 64, dtype=np.uint64)
+        _check(lib().mphf_copy_bits(self._h, out.ctypes.data if out.size else None, out.size),
+               "mphf_copy_bits")
+        return out
+
+    def rank(self) -> np.ndarray:
+        out = np.empty(self.num_rank, dtype=np.uint64)
+        _check(lib().mphf_copy_rank(self._h, out.ctypes.data if out.size else None, out.size),
+               "mphf_copy_rank")
+        return out
+
+    def fallback(self) -> np.ndarray:
+        out = np.empty(self.num_fallback, dtype=np.uint64)
+        _check(lib().mphf_copy_fallback(self._h, out.ctypes.data if out.size else None, out.size),
+               "mphf_copy_fallback")
+        return out
+
+
+def _host_ptr(orig, arr: np.ndarray) -> Optional[int]:
+    """Pointer to host data; a pinned torch CPU tensor is passed through as is."""
+    try:
+        import torch
+        if isinstance(orig, torch.Tensor) and not orig.is_cuda and orig.is_contiguous() \
+                and orig.element_size() == 8:
+            return orig.data_ptr() if orig.numel() else None
+    except ImportError:  # pragma: no cover
+        pass
+    return arr.ctypes.data if arr.size else None
+
+
+def build(keys, gamma: float = 2.0, levels: int = 25, seed: int = 0, stream=None) -> MPHF:
+    return MPHF.build(keys, gamma=gamma, levels=levels, seed=seed, stream=stream)
+
+
+def keygen(n: int, seed: int, start: int = 0, device=None, stream=None):
+    """n distinct keys on the device: outputs start.. of SplitMix64(seed)."""
+    import torch
+    out = torch.empty(int(n), dtype=torch.int64, device=device or "cuda")
+    if n:
+        _check(lib().mphf_keygen(out.data_ptr(), int(n), int(seed) & NOT_FOUND, int(start),
+                                 _stream_ptr(stream)), "mphf_keygen")
+    return out
+
+
+def launch_count() -> int:
+    return lib().mphf_launch_count()
+
+
+def profile_enable(on: bool = True):
+    lib().mphf_profile_enable(1 if on else 0)
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total_ms)} of the launches recorded since the last report."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().mphf_profile_report(buf, len(buf)), "mphf_profile_report")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def to_u64(t) -> np.ndarray:
+    """A torch int64 tensor (any device) as a numpy uint64 array."""
+    return t.detach().cpu().numpy().view(np.uint64)

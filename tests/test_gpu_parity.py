@@ -1,0 +1,188 @@
+"""CUDA path vs the CPU oracle, bit for bit.
+
+The GPU build must give the oracle's level sizes and seeds, the same A bits,
+rank checkpoints and fallback keys, and the same index for every key (members
+and non-members).  All comparisons are exact: the method is integer-only and
+its result does not depend on the order in which keys are processed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_03154_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_03154_gb300 import mphf
+    mphf.lib()
+    return mphf
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def assert_same_structure(g, o):
+    assert g.N == o.N
+    assert g.num_levels == o.num_levels
+    assert g.levels() == o.levels()
+    assert g.total_bits == o.total_bits
+    assert g.num_fallback == o.num_fallback
+    assert np.array_equal(g.bits(), o.bits())
+    assert np.array_equal(g.rank(), o.rank())
+    assert np.array_equal(g.fallback(), o.fallback())
+    assert g.bits_per_key() == pytest.approx(o.bits_per_key(), abs=0, rel=0)
+
+
+def check(M, keys, gamma, levels, seed, queries=None):
+    o = oracle.build(keys, gamma=gamma, levels=levels, seed=seed)
+    g = M.MPHF.build(dev(keys), gamma=gamma, levels=levels, seed=seed)
+    assert_same_structure(g, o)
+    q = keys if queries is None else queries
+    out = M.to_u64(g.lookup(dev(q)))
+    assert np.array_equal(out, o.lookup(q))
+    return g, o
+
+
+def test_config1_full_parity(M):
+    # N = 1e6 keys = SplitMix64 outputs 0..N-1 of seed 1, gamma = 2, L = 25.
+    keys = inputs.splitmix64_keys(10**6, 1)
+    g, o = check(M, keys, 2.0, 25, 0)
+    out = M.to_u64(g.lookup(dev(keys)))
+    assert np.array_equal(np.sort(out), np.arange(keys.size, dtype=np.uint64))
+    others = inputs.splitmix64_keys(200000, 101)
+    assert np.array_equal(M.to_u64(g.lookup(dev(others))), o.lookup(others))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 127, 4095, 4096, 4097, 8191, 12345, 100003])
+@pytest.mark.parametrize("gamma", [1.0, 1.5, 2.0, 5.0])
+def test_ragged_sizes(M, n, gamma):
+    keys = inputs.splitmix64_keys(n, 7 + n)
+    check(M, keys, gamma, 25, n)
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3, 5])
+def test_small_level_budgets_exercise_fallback(M, levels):
+    keys = inputs.splitmix64_keys(50000, 17)
+    g, o = check(M, keys, 1.0, levels, 3)
+    assert g.num_fallback > 0
+
+
+def test_large_fallback_uses_global_sort(M):
+    # L = 1 at gamma = 1 leaves ~63% of the keys in the fallback (> 4096).
+    keys = inputs.splitmix64_keys(100000, 23)
+    g, o = check(M, keys, 1.0, 1, 9)
+    assert g.num_fallback > 4096
+
+
+def test_misaligned_key_pointers(M):
+    keys = inputs.splitmix64_keys(100001, 29)
+    o = oracle.build(keys[1:], gamma=2.0, levels=25, seed=4)
+    buf = dev(keys)
+    g = M.MPHF.build(buf[1:], gamma=2.0, levels=25, seed=4)   # 8-byte aligned only
+    assert_same_structure(g, o)
+    out = torch.empty(keys.size, dtype=torch.int64, device="cuda")
+    g.lookup(buf[1:], out=out[1:])
+    assert np.array_equal(M.to_u64(out[1:]), o.lookup(keys[1:]))
+
+
+def test_order_independence(M):
+    keys = inputs.splitmix64_keys(300000, 31)
+    a = M.MPHF.build(dev(keys), gamma=1.0, levels=25, seed=5)
+    b = M.MPHF.build(dev(inputs.shuffled(keys, 9)), gamma=1.0, levels=25, seed=5)
+    assert a.levels() == b.levels()
+    assert np.array_equal(a.bits(), b.bits())
+    assert np.array_equal(a.rank(), b.rank())
+    assert np.array_equal(a.fallback(), b.fallback())
+
+
+def test_repeated_builds_are_identical(M):
+    keys = inputs.splitmix64_keys(500000, 37)
+    a = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=1)
+    for _ in range(3):
+        b = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=1)
+        assert np.array_equal(a.bits(), b.bits())
+        assert np.array_equal(a.rank(), b.rank())
+
+
+def test_empty_and_single(M):
+    g = M.MPHF.build(torch.empty(0, dtype=torch.int64, device="cuda"), 2.0, 25, 0)
+    assert g.num_levels == 0 and g.total_bits == 0 and g.num_fallback == 0
+    assert g.bits_per_key() == 0.0
+    q = dev(np.array([1, 2, 3], dtype=np.uint64))
+    assert M.to_u64(g.lookup(q)).tolist() == [U64] * 3
+    g1 = M.MPHF.build(dev(np.array([12345], dtype=np.uint64)), 2.0, 25, 0)
+    assert M.to_u64(g1.lookup(dev(np.array([12345], dtype=np.uint64)))).tolist() == [0]
+
+
+@pytest.mark.parametrize("n,levels", [(1000, 25), (100000, 1)])
+def test_duplicates_are_reported(M, n, levels):
+    keys = inputs.splitmix64_keys(n, 41)
+    keys[n // 2] = keys[3]
+    with pytest.raises(M.MPHFError) as e:
+        M.MPHF.build(dev(keys), gamma=1.0, levels=levels, seed=0)
+    assert e.value.code == M.EDUPLICATE
+    # the library is still usable afterwards
+    check(M, inputs.splitmix64_keys(1000, 43), 2.0, 25, 0)
+
+
+def test_invalid_arguments(M):
+    k = dev(inputs.splitmix64_keys(10, 1))
+    for gamma, levels in ((0.9, 25), (float("nan"), 25), (2.0, 0), (2.0, 65)):
+        with pytest.raises(M.MPHFError) as e:
+            M.MPHF.build(k, gamma=gamma, levels=levels)
+        assert e.value.code == M.EINVAL
+
+
+def test_host_buffer_entry_points(M):
+    keys = inputs.splitmix64_keys(200001, 47)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=6)
+    g = M.MPHF.build_host(keys, gamma=2.0, levels=25, seed=6)
+    assert_same_structure(g, o)
+    pinned = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    out = g.lookup_host(pinned)
+    assert np.array_equal(out, o.lookup(keys))
+
+
+def test_device_keygen_matches_generator(M):
+    for n, seed, start in ((1, 0, 0), (1000, 1, 0), (100003, 4, 12345)):
+        got = M.to_u64(M.keygen(n, seed, start))
+        assert np.array_equal(got, inputs.splitmix64_keys(n, seed, start=start))
+
+
+@pytest.mark.parametrize("gamma", [1.0, 2.0, 5.0])
+def test_config2_shape_parity_1e7(M, gamma):
+    # The N = 1e8 workload's shape at 1e7 keys: full structure + every lookup.
+    keys = inputs.splitmix64_keys(10**7, 2)
+    q = inputs.shuffled(keys, 3)
+    check(M, keys, gamma, 25, 0, queries=q)
+
+
+def test_config2_full_size_gamma2(M):
+    # N = 1e8, gamma = 2, L = 25, as the benchmark times it: the full structure
+    # (levels, A, rank, fallback) against the oracle, a bijection check of all
+    # 1e8 lookups in shuffled order on the GPU result, and 2e6 sampled lookups
+    # against the oracle.
+    N = 10**8
+    keys = inputs.splitmix64_keys(N, 2)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=0)
+    kd = dev(keys)
+    g = M.MPHF.build(kd, gamma=2.0, levels=25, seed=0)
+    assert_same_structure(g, o)
+    perm = torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    q = kd[perm]
+    out = g.lookup(q)
+    hits = torch.zeros(N, dtype=torch.int32, device="cuda")
+    assert int(out.min()) >= 0 and int(out.max()) < N
+    hits.index_add_(0, out, torch.ones_like(out, dtype=torch.int32))
+    assert bool((hits == 1).all())
+    idx = inputs.sample_indices(N, 2 * 10**6, 5)
+    assert np.array_equal(M.to_u64(g.lookup(kd[torch.from_numpy(idx).cuda()])), o.lookup(keys[idx]))
