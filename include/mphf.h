@@ -123,6 +123,15 @@ int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count);
 int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count);
 int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
 
+/* Which construction path built h: 1 = bucketed (shared-memory ArrayFill),
+ * 2 = unbucketed (L2 atomics; taken when a bound of the bucketed path is
+ * exceeded, e.g. many duplicate keys).  Both give identical results. */
+int mphf_build_path(const mphf_t *h);
+/* Test hook, process-wide: path 0 = bucketed with automatic fallback (default),
+ * 1 = unbucketed only; cap_scale (default 1) scales the bucket capacities, so a
+ * value < 1 forces the fallback.  Not thread-safe against concurrent builds. */
+int mphf_debug_config(int path, double cap_scale);
+
 /* ---- synthetic keys ------------------------------------------------------ */
 /*
  * d_out[i] = output (start + i) of the SplitMix64 generator started at state

@@ -23,6 +23,10 @@
 
 namespace bbh {
 
+int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+               mphf_t *h, bool *fallback_needed);
+extern double g_cap_scale;
+
 static constexpr int kFillThreads = 256;
 static constexpr int kFillUnroll = 4;      // uint4 loads (2 keys each) in flight per thread
 static constexpr int kExtractThreads = 256;
@@ -310,21 +314,11 @@ static int read_u64(const u64 *d_ptr, u64 *out, cudaStream_t st) {
   return MPHF_OK;
 }
 
-static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
-                      mphf_t **out) {
+// Unbucketed construction: L2 atomics for ArrayFill, one host round trip per
+// level.  Used when a bound of the bucketed path (fastbuild.cu) is exceeded.
+static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed,
+                        cudaStream_t st, mphf_t *h) {
   int rc = MPHF_OK;
-  mphf_t *h = new (std::nothrow) mphf_t();
-  if (!h) return MPHF_ENOMEM;
-  cudaGetDevice(&h->device);
-  h->N = N;
-  h->gamma = gamma;
-  h->L = L;
-  h->seed = seed;
-  for (uint32_t d = 0; d < L; d++) h->s[d] = level_seed(seed, d);
-  if (N == 0) {
-    *out = h;
-    return MPHF_OK;
-  }
   Scratch sc;
   BuildMeta hm;
   memset(&hm, 0, sizeof(hm));
@@ -475,16 +469,57 @@ static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed
     }
   }
   sc.release(st);
-  *out = h;
   return MPHF_OK;
 
 fail:
   cudaGetLastError();
   sc.release(st);
-  release_handle(h, st);
+  dev_free(h->A, st);
+  dev_free(h->rank, st);
+  dev_free(h->fb, st);
   cudaStreamSynchronize(st);
   return rc;
 #undef TRY
+}
+
+int g_build_path = 0;  // 0: bucketed, unbucketed on overflow; 1: unbucketed only
+
+static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+                      mphf_t **out) {
+  mphf_t *h = new (std::nothrow) mphf_t();
+  if (!h) return MPHF_ENOMEM;
+  cudaGetDevice(&h->device);
+  h->N = N;
+  h->gamma = gamma;
+  h->L = L;
+  h->seed = seed;
+  for (uint32_t d = 0; d < L; d++) h->s[d] = level_seed(seed, d);
+  if (N == 0) {
+    *out = h;
+    return MPHF_OK;
+  }
+  int rc = MPHF_OK;
+  bool redo = true;
+  if (g_build_path == 0) {
+    rc = fast_build(keys, N, gamma, L, seed, st, h, &redo);
+    if (rc != MPHF_OK) {
+      release_handle(h, st);
+      cudaStreamSynchronize(st);
+      return rc;
+    }
+    h->path = 1;
+  }
+  if (redo) {
+    rc = robust_build(keys, N, gamma, L, seed, st, h);
+    if (rc != MPHF_OK) {
+      release_handle(h, st);
+      cudaStreamSynchronize(st);
+      return rc;
+    }
+    h->path = 2;
+  }
+  *out = h;
+  return MPHF_OK;
 }
 
 }  // namespace bbh
@@ -523,3 +558,12 @@ extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma,
   dev_free(kb, st);
   return rc;
 }
+
+extern "C" int mphf_debug_config(int path, double cap_scale) {
+  if (path < 0 || path > 1 || !(cap_scale > 0.0) || cap_scale > 16.0) return MPHF_EINVAL;
+  bbh::g_build_path = path;
+  bbh::g_cap_scale = cap_scale;
+  return MPHF_OK;
+}
+
+extern "C" int mphf_build_path(const mphf_t *h) { return h ? h->path : 0; }

@@ -143,4 +143,5 @@ struct mphf {
   bbh::DevBuf rank;     // n_rank words
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;
+  int path = 0;          // 1 bucketed construction, 2 unbucketed
 };

@@ -1,0 +1,882 @@
+// fastbuild.cu -- bucketed construction: ArrayFill in shared memory.
+//
+// The keys of a level are kept grouped by position range ("buckets" of P
+// consecutive positions of A_d, P a power of two).  One CTA then runs the
+// whole of Algorithm 2 for a bucket with its hit / collision bits in shared
+// memory (no L2 atomics), writes the bucket's slice of A_d with plain stores
+// and counts weight(A_d).  Once every bucket is filled, |F_{d+1}| =
+// |F_d| - weight(A_d) and |A_{d+1}| are known, so compaction can place each
+// surviving key straight into its level-(d+1) bucket: the survivors of a tile
+// are counting-sorted by destination bucket in shared memory, one atomicAdd
+// per (tile, bucket) reserves their slots, and they are written out as
+// contiguous runs.  The caller's keys are first partitioned the same way for
+// level 0.  Levels with at most T keys run in a single CTA (k_tail) that keeps
+// keys and bit arrays in shared memory and loops over all remaining levels,
+// sorting the fallback (Sec. 3.5) at the end.
+//
+// Every bound (bucket capacity, bucket count, flat buffer) is checked on the
+// device; when one is exceeded the build is redone by the unbucketed path in
+// build.cu, so results never depend on these choices.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include "fastbuild.cuh"
+
+namespace bbh {
+
+static constexpr int kTT = 1024;           // threads of partition / compaction / fill CTAs
+static constexpr int kKPT = 8;             // keys per thread per tile
+static constexpr int kTile = kTT * kKPT;   // 8192 keys
+static constexpr int kTailThreads = 1024;
+static constexpr u64 kTailMaxKeys = 16384;
+static constexpr u64 kBmax = 4096;
+
+// ---------------------------------------------------------------------------
+// Level sizing (device side, by the last block of a fill).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline unsigned ilog2_u64(u64 v) {
+  unsigned r = 0;
+  while ((v >> r) > 1) r++;
+  return r;
+}
+
+__host__ __device__ inline void size_bucketed(FLevel &lv, u64 n, double gamma, u64 Pmin, u64 Pmax,
+                                              u64 Btarget, double cap_scale) {
+  lv.n = n;
+  lv.m = level_bits(n, gamma);
+  u64 want = ceil_div(lv.m, Btarget);
+  u64 P = Pmin;
+  while (P < want && P < Pmax) P <<= 1;
+  lv.P = P;
+  lv.B = ceil_div(lv.m, P);
+  double mean = (double)n * (double)P / (double)lv.m;
+  u64 cap = (u64)(cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));
+  lv.cap = (cap + 1) & ~1ull;  // even: every bucket starts 16-byte aligned
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers (kTT threads).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ u64 block_sum(u64 v, u64 *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  u64 s = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT / 32; i++) s += red[i];
+    red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Exclusive scan of NT values (one per thread); returns the prefix, *total = sum.
+template <int NT>
+__device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned *red, unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < NT / 32 ? red[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) red[lane] = w;
+  }
+  __syncthreads();
+  unsigned before = warp ? red[warp - 1] : 0u;
+  *total = red[NT / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// Shared memory of the multisplit writer.
+struct SplitSmem {
+  unsigned *cnt;         // [nb] keys per destination in this tile, then their local start
+  unsigned *base;        // [nb] slot reserved in the destination bucket
+  u64 *sorted;           // [kTile]
+  unsigned short *sdst;  // [kTile]
+  unsigned *red;         // [kTT / 32 + 1]
+};
+
+// Write the valid keys of a tile into their destination buckets
+// (arena[b * cap + slot]); slots are reserved with one atomicAdd per
+// non-empty destination; keys of one destination leave as one contiguous run.
+__device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&dst)[kKPT],
+                                 const bool (&ok)[kKPT], unsigned nb, const SplitSmem &sm,
+                                 u64 *__restrict__ arena, u64 cap, u64 *__restrict__ gcnt,
+                                 unsigned *__restrict__ status) {
+  for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;
+  __syncthreads();
+  unsigned rk[kKPT];
+#pragma unroll
+  for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
+  __syncthreads();
+  // reserve, then exclusive scan of the counts (each thread owns a run of entries)
+  const unsigned per = (nb + kTT - 1) / kTT;
+  const unsigned lo = threadIdx.x * per;
+  const unsigned hi = min(lo + per, nb);
+  unsigned s = 0;
+  for (unsigned i = lo; i < hi; i++) {
+    unsigned c = sm.cnt[i];
+    if (c) {
+      u64 b0 = atomicAdd(gcnt + i, (u64)c);
+      sm.base[i] = b0 > 0xffffffffull ? 0xffffffffu : (unsigned)b0;
+    }
+    s += c;
+  }
+  unsigned total;
+  unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+  for (unsigned i = lo; i < hi; i++) {
+    unsigned c = sm.cnt[i];
+    sm.cnt[i] = pre;
+    pre += c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kKPT; k++) {
+    if (ok[k]) {
+      unsigned pos = sm.cnt[dst[k]] + rk[k];
+      sm.sorted[pos] = x[k];
+      sm.sdst[pos] = (unsigned short)dst[k];
+    }
+  }
+  __syncthreads();
+  for (unsigned i = threadIdx.x; i < total; i += kTT) {
+    unsigned b = sm.sdst[i];
+    u64 j = (u64)sm.base[b] + (i - sm.cnt[b]);
+    if (j < cap) arena[(u64)b * cap + j] = sm.sorted[i];
+    else atomicOr(status, ST_OVERFLOW);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
+  SplitSmem s;
+  s.sorted = reinterpret_cast<u64 *>(smem);
+  s.cnt = reinterpret_cast<unsigned *>(smem + kTile * 8);
+  s.base = s.cnt + nb_cap;
+  s.red = s.base + nb_cap;
+  s.sdst = reinterpret_cast<unsigned short *>(s.red + kTT / 32 + 2);
+  return s;
+}
+
+static constexpr size_t split_smem_bytes(unsigned nb_cap) {
+  return (size_t)kTile * 8 + 2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 + (size_t)kTile * 2;
+}
+
+// ---------------------------------------------------------------------------
+// Level 0: partition the caller's keys into position buckets of A_0.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTT, 1)
+k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, FastCfg cfg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const FLevel lv = meta->lv[0];
+  const unsigned nb = (unsigned)lv.B;
+  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  const u64 s0 = level_seed(cfg.seed, 0);
+  const unsigned sh = ilog2_u64(lv.P);
+  const u64 ntiles = ceil_div(n, kTile);
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    u64 x[kKPT];
+    unsigned dst[kKPT];
+    bool ok[kKPT];
+#pragma unroll
+    for (int k = 0; k < kKPT; k++) {
+      u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
+      ok[k] = i < n;
+      x[k] = ok[k] ? __ldcs(keys + i) : 0;
+      dst[k] = ok[k] ? (unsigned)(level_pos(x[k], s0, lv.m) >> sh) : 0u;
+    }
+    multisplit_write(x, dst, ok, nb, sm, cfg.X, lv.cap, cfg.cntX, &meta->status);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fill (Algorithm 2) of level d, one bucket per CTA iteration, bits in shared
+// memory; writes A_d and weight(A_d); the last CTA sizes level d+1.
+// ---------------------------------------------------------------------------
+__device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
+  volatile FLevel *vl = meta->lv;
+  const u64 n = vl[d].n, m = vl[d].m, w = vl[d].weight;
+  if (w > n) atomicOr(&meta->status, ST_INTERNAL);
+  const u64 nn = w > n ? 0 : n - w;
+  FLevel nx;
+  memset(&nx, 0, sizeof(nx));
+  nx.n = nn;
+  nx.off = vl[d].off + m;
+  if (nn == 0) {
+    nx.mode = LM_DONE;
+    meta->levels_used = d + 1;
+  } else if ((uint32_t)(d + 1) == cfg.L) {
+    nx.mode = LM_FLAT;  // fallback
+    if (nn > cfg.flat_cap) atomicOr(&meta->status, ST_OVERFLOW);
+  } else if (nn <= cfg.T) {
+    nx.mode = LM_FLAT;  // tail
+    nx.m = level_bits(nn, cfg.gamma);
+  } else {
+    size_bucketed(nx, nn, cfg.gamma, cfg.Pmin, cfg.Pmax, cfg.Btarget, cfg.cap_scale);
+    nx.off = vl[d].off + m;
+    nx.mode = LM_BUCKETED;
+    const u64 acap = ((d + 1) & 1) ? cfg.capY : cfg.capX;
+    if (nx.B > cfg.Bmax || nx.B * nx.cap > acap) {
+      atomicOr(&meta->status, ST_OVERFLOW);
+      nx.mode = LM_NONE;
+    }
+  }
+  meta->lv[d + 1] = nx;
+  __threadfence();
+}
+
+__global__ void __launch_bounds__(kTT, 1)
+k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ u64 red[kTT / 32];
+  __shared__ bool last;
+  if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
+  const FLevel lv = meta->lv[d];
+  const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
+  const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
+  u64 *Alev = (d == 0) ? cfg.A0 : cfg.arena + ((lv.off - cfg.m0) >> 6);
+  const u64 s_d = level_seed(cfg.seed, d);
+  const unsigned Pw = (unsigned)(lv.P >> 5);  // 32-bit words per bit array
+  unsigned *hit = reinterpret_cast<unsigned *>(smem);
+  unsigned *col = hit + Pw;
+  const u64 mask = lv.P - 1;
+  u64 wsum = 0, got = 0;
+  for (u64 b = blockIdx.x; b < lv.B; b += gridDim.x) {
+    for (unsigned i = threadIdx.x; i < 2 * Pw; i += kTT) hit[i] = 0;
+    __syncthreads();
+    const u64 nk = min(cnt[b], lv.cap);
+    got += (threadIdx.x == 0) ? cnt[b] : 0;
+    const u64 *kb = arena + b * lv.cap;
+    const uint4 *kb2 = reinterpret_cast<const uint4 *>(kb);
+    constexpr int U = 4;  // 16-byte loads in flight per thread
+    for (u64 i0 = threadIdx.x; 2 * i0 < nk; i0 += (u64)U * kTT) {
+      u64 xs[2 * U];
+      int c[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const u64 i = i0 + (u64)u * kTT;
+        c[u] = 0;
+        xs[2 * u] = xs[2 * u + 1] = 0;
+        if (2 * i + 1 < nk) {
+          uint4 v = __ldcs(kb2 + i);
+          xs[2 * u] = ((u64)v.y << 32) | v.x;
+          xs[2 * u + 1] = ((u64)v.w << 32) | v.z;
+          c[u] = 2;
+        } else if (2 * i < nk) {
+          xs[2 * u] = __ldcs(kb + 2 * i);
+          c[u] = 1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          if (j < c[u]) {
+            const unsigned p = (unsigned)(level_pos(xs[2 * u + j], s_d, lv.m) & mask);
+            const unsigned bit = 1u << (p & 31);
+            const unsigned old = atomicOr(hit + (p >> 5), bit);
+            if (old & bit) atomicOr(col + (p >> 5), bit);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // A_d words of this bucket: positions [b P, min((b+1) P, m))
+    const u64 w0 = (b * lv.P) >> 6;
+    const u64 wend = min((b + 1) * lv.P, lv.m) >> 6;
+    for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) {
+      const unsigned j = (unsigned)(w - w0) * 2;
+      const u64 a = (u64)(hit[j] & ~col[j]) | ((u64)(hit[j + 1] & ~col[j + 1]) << 32);
+      Alev[w] = a;
+      wsum += __popcll(a);
+    }
+    __syncthreads();
+  }
+  const u64 tw = block_sum<kTT>(wsum, red);
+  const u64 tg = block_sum<kTT>(got, red);
+  if (threadIdx.x == 0) {
+    if (tw) atomicAdd(&meta->lv[d].weight, tw);
+    if (tg) atomicAdd(&meta->seen[d], tg);
+    __threadfence();
+    unsigned t = atomicAdd(&meta->lv[d].done, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    // the buckets must hold exactly |F_d| keys
+    if (*(volatile u64 *)&meta->seen[d] != meta->lv[d].n) atomicOr(&meta->status, ST_INTERNAL);
+    finish_level(meta, d, cfg);
+  }
+  if (last) {
+    __syncthreads();
+    // zero the counters of the arena that level d+1 is written into
+    const FLevel nx = meta->lv[d + 1];
+    if (nx.mode == LM_BUCKETED) {
+      u64 *c2 = ((d + 1) & 1) ? cfg.cntY : cfg.cntX;
+      for (u64 i = threadIdx.x; i < nx.B; i += kTT) c2[i] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compaction of level d: keys whose A_d bit is 0 go to their level-(d+1)
+// bucket (or, for a small or final level, to the flat buffer).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTT, 1)
+k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
+  const FLevel lv = meta->lv[d];
+  const FLevel nx = meta->lv[d + 1];
+  if (nx.mode == LM_DONE || nx.mode == LM_NONE) return;
+  const bool flat = nx.mode == LM_FLAT;
+  const unsigned nb = flat ? 1u : (unsigned)nx.B;
+  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
+  const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
+  const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
+  u64 *out = flat ? cfg.flat : (((d + 1) & 1) ? cfg.Y : cfg.X);
+  u64 *ocnt = flat ? &meta->n_flat : (((d + 1) & 1) ? cfg.cntY : cfg.cntX);
+  const u64 ocap = flat ? cfg.flat_cap : nx.cap;
+  const u64 *Alev = (d == 0) ? cfg.A0 : cfg.arena + ((lv.off - cfg.m0) >> 6);
+  const u64 s_d = level_seed(cfg.seed, d);
+  const u64 s_n = level_seed(cfg.seed, d + 1);
+  const unsigned shn = flat ? 0u : ilog2_u64(nx.P);
+  const u64 mask = lv.P - 1;
+  for (u64 b = blockIdx.x; b < lv.B; b += gridDim.x) {
+    const u64 w0 = (b * lv.P) >> 6;
+    const u64 wend = min((b + 1) * lv.P, lv.m) >> 6;
+    for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
+    __syncthreads();
+    const u64 nk = min(cnt[b], lv.cap);
+    const u64 *kb = arena + b * lv.cap;
+    for (u64 t0 = 0; t0 < nk; t0 += kTile) {
+      u64 x[kKPT];
+      unsigned dst[kKPT];
+      bool ok[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+        ok[k] = false;
+        dst[k] = 0;
+        x[k] = 0;
+        if (i < nk) {
+          x[k] = __ldcs(kb + i);
+          const unsigned p = (unsigned)(level_pos(x[k], s_d, lv.m) & mask);
+          ok[k] = !((segA[p >> 6] >> (p & 63)) & 1ull);
+          if (ok[k] && !flat) dst[k] = (unsigned)(level_pos(x[k], s_n, nx.m) >> shn);
+        }
+      }
+      multisplit_write(x, dst, ok, nb, sm, out, ocap, ocnt, &meta->status);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-CTA level loop: levels d0.. of a key set of at most kTailMaxKeys keys,
+// keys and bit arrays in shared memory.  Writes A_d words, level metadata and
+// the sorted fallback.
+// ---------------------------------------------------------------------------
+struct TailSmem {
+  u64 *keys;      // [kTailMaxKeys]
+  unsigned *hit;  // [mcap / 32]
+  unsigned *col;
+  unsigned *red;  // [32 + 2]
+  u64 *red64;     // [32]
+};
+
+__device__ void bitonic_sort_smem(u64 *a, unsigned n) {
+  unsigned P = 1;
+  while (P < n) P <<= 1;
+  for (unsigned i = n + threadIdx.x; i < P; i += blockDim.x) a[i] = ~0ull;
+  __syncthreads();
+  for (unsigned k = 2; k <= P; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
+        unsigned l = i ^ j;
+        if (l > i) {
+          u64 x = a[i], y = a[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Returns the number of levels used.  lvs: level records (n/m/off/weight/mode)
+// of this key set; A0 / arena / m0 locate A_d; fb_out receives the sorted
+// fallback (n_fb keys).
+__device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off, FLevel *lvs,
+                               double gamma, uint32_t L, u64 seed, u64 *A0, u64 *arena, u64 m0,
+                               u64 *fb_out, u64 *n_fb_out, unsigned *status) {
+  int d = d0;
+  for (;;) {
+    if (n == 0) {
+      if (threadIdx.x == 0) lvs[d].mode = LM_DONE;
+      return (unsigned)d;
+    }
+    if ((uint32_t)d == L) {
+      bitonic_sort_smem(sm.keys, (unsigned)n);
+      for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        u64 v = sm.keys[i];
+        fb_out[i] = v;
+        if (i + 1 < n && v == sm.keys[i + 1]) atomicOr(status, ST_DUPLICATE);
+      }
+      if (threadIdx.x == 0) {
+        *n_fb_out = n;
+        lvs[d].mode = LM_FLAT;
+        lvs[d].n = n;
+      }
+      __syncthreads();
+      return L;
+    }
+    const u64 m = level_bits(n, gamma);
+    const u64 s = level_seed(seed, (uint32_t)d);
+    const unsigned mw = (unsigned)(m >> 5);
+    for (unsigned i = threadIdx.x; i < mw; i += blockDim.x) {
+      sm.hit[i] = 0;
+      sm.col[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+      const u64 p = level_pos(sm.keys[i], s, m);
+      const unsigned bit = 1u << (p & 31);
+      const unsigned old = atomicOr(sm.hit + (p >> 5), bit);
+      if (old & bit) atomicOr(sm.col + (p >> 5), bit);
+    }
+    __syncthreads();
+    u64 *Alev = (d == 0) ? A0 : arena + ((off - m0) >> 6);
+    u64 wsum = 0;
+    for (unsigned w = threadIdx.x; w < (unsigned)(m >> 6); w += blockDim.x) {
+      const u64 a = (u64)(sm.hit[2 * w] & ~sm.col[2 * w]) |
+                    ((u64)(sm.hit[2 * w + 1] & ~sm.col[2 * w + 1]) << 32);
+      Alev[w] = a;
+      wsum += __popcll(a);
+    }
+    // compaction in place: each thread keeps its contiguous run of keys in registers
+    constexpr unsigned KMAX = (unsigned)(kTailMaxKeys / kTailThreads);
+    const unsigned per = (unsigned)((n + blockDim.x - 1) / blockDim.x);
+    const unsigned lo = threadIdx.x * per;
+    u64 mine[KMAX];
+    unsigned keepmask = 0, c = 0;
+#pragma unroll
+    for (unsigned k = 0; k < KMAX; k++) {
+      mine[k] = 0;
+      const unsigned i = lo + k;
+      if (k < per && i < n) {
+        const u64 x = sm.keys[i];
+        const u64 p = level_pos(x, s, m);
+        const unsigned bit = 1u << (p & 31);
+        const bool placed = (sm.hit[p >> 5] & ~sm.col[p >> 5]) & bit;
+        if (!placed) {
+          mine[k] = x;
+          keepmask |= 1u << k;
+          c++;
+        }
+      }
+    }
+    unsigned total;
+    unsigned pre = block_scan_u32<kTailThreads>(c, sm.red, &total);
+    // every thread has read its keys (block_scan synchronises)
+#pragma unroll
+    for (unsigned k = 0; k < KMAX; k++) {
+      if (keepmask & (1u << k)) sm.keys[pre++] = mine[k];
+    }
+    const u64 wt = block_sum<kTailThreads>(wsum, sm.red64);
+    if (threadIdx.x == 0) {
+      if (wt + total != n) atomicOr(status, ST_INTERNAL);
+      lvs[d].n = n;
+      lvs[d].m = m;
+      lvs[d].off = off;
+      lvs[d].weight = wt;
+      lvs[d].mode = LM_FLAT;
+    }
+    n = total;
+    off += m;
+    d++;
+    if (threadIdx.x == 0) {
+      lvs[d].n = n;
+      lvs[d].off = off;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ TailSmem carve_tail(unsigned char *smem, u64 mcap) {
+  TailSmem t;
+  t.keys = reinterpret_cast<u64 *>(smem);
+  t.hit = reinterpret_cast<unsigned *>(smem + kTailMaxKeys * 8);
+  t.col = t.hit + (mcap >> 5);
+  t.red64 = reinterpret_cast<u64 *>(t.col + (mcap >> 5));
+  t.red = reinterpret_cast<unsigned *>(t.red64 + 32);
+  return t;
+}
+
+static size_t tail_smem_bytes(u64 mcap) {
+  return kTailMaxKeys * 8 + 2 * (mcap >> 5) * 4 + 32 * 8 + 40 * 4;
+}
+
+// Tail of the bucketed build: finds the first level (<= dlim) whose keys were
+// sent to the flat buffer and runs the remaining levels there.
+__global__ void __launch_bounds__(kTailThreads, 1)
+k_tail(FastMeta *__restrict__ meta, int dlim, FastCfg cfg, u64 mcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int t_level;
+  if (meta->status || meta->tail_done) return;
+  if (threadIdx.x == 0) {
+    int t = -1;
+    for (int d = 0; d <= dlim && d <= (int)cfg.L; d++) {
+      const unsigned md = meta->lv[d].mode;
+      if (md == LM_FLAT || md == LM_DONE) {
+        t = d;
+        break;
+      }
+      if (md != LM_BUCKETED) break;
+    }
+    t_level = t;
+  }
+  __syncthreads();
+  const int t = t_level;
+  if (t < 0) return;  // not reached yet: the host enqueues more levels
+  FLevel *lvs = meta->lv;
+  if (lvs[t].mode == LM_DONE) {
+    if (threadIdx.x == 0) meta->tail_done = 1;
+    return;
+  }
+  const u64 n = lvs[t].n;
+  if (threadIdx.x == 0 && meta->n_flat != n) atomicOr(&meta->status, ST_INTERNAL);
+  if ((uint32_t)t == cfg.L && n > kTailMaxKeys) {
+    // large fallback: sorted on the host side of the build (sort.cu)
+    if (threadIdx.x == 0) {
+      meta->n_fb = n;
+      meta->levels_used = cfg.L;
+      meta->tail_done = 2;
+    }
+    return;
+  }
+  TailSmem sm = carve_tail(smem, mcap);
+  for (unsigned i = threadIdx.x; i < n; i += kTailThreads) sm.keys[i] = cfg.flat[i];
+  __syncthreads();
+  unsigned used = cta_levels(sm, n, t, lvs[t].off, lvs, cfg.gamma, cfg.L, cfg.seed, cfg.A0,
+                             cfg.arena, cfg.m0, cfg.flat, &meta->n_fb, &meta->status);
+  if (threadIdx.x == 0) {
+    meta->levels_used = used;
+    meta->tail_done = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static bool g_attr_set = false;
+double g_cap_scale = 1.0;
+static size_t g_split_bytes, g_compact_bytes;
+
+static int set_attrs() {
+  if (g_attr_set) return MPHF_OK;
+  g_split_bytes = split_smem_bytes((unsigned)kBmax);
+  g_compact_bytes = g_split_bytes + (256 * 1024) / 8;  // + A segment for P <= 256K
+  MPHF_CUDA(cudaFuncSetAttribute(k_partition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)g_split_bytes));
+  MPHF_CUDA(cudaFuncSetAttribute(k_compact_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)g_compact_bytes));
+  MPHF_CUDA(cudaFuncSetAttribute(k_fill_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((256 * 1024) / 4)));
+  MPHF_CUDA(cudaFuncSetAttribute(k_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+  g_attr_set = true;
+  return MPHF_OK;
+}
+
+// Expected |F_{d+1}| from |F_d| (a key is alone with probability (1 - 1/m)^(n-1)).
+static double expect_next(double n, double gamma) {
+  const double m = (double)level_bits((u64)n, gamma);
+  return n * (1.0 - pow(1.0 - 1.0 / m, n - 1.0));
+}
+
+struct FastScratch {
+  DevBuf meta, X, Y, cntX, cntY, flat, A0, arena;
+  void release(cudaStream_t s) {
+    dev_free(meta, s); dev_free(X, s); dev_free(Y, s); dev_free(cntX, s); dev_free(cntY, s);
+    dev_free(flat, s); dev_free(A0, s); dev_free(arena, s);
+  }
+};
+
+// Largest level size the tail may take for this gamma (keys + 2 bit arrays in 200 KB).
+static u64 tail_limit(double gamma, u64 *mcap_out) {
+  u64 T = kTailMaxKeys;
+  while (T > 64) {
+    u64 mc = level_bits(T, gamma);
+    if (tail_smem_bytes(mc) <= 200 * 1024) {
+      *mcap_out = mc;
+      return T;
+    }
+    T >>= 1;
+  }
+  *mcap_out = level_bits(64, gamma);
+  return 64;
+}
+
+// Returns MPHF_OK with *fallback_needed = false on success; *fallback_needed =
+// true (and nothing allocated) when a device-side bound was exceeded.
+int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+               mphf_t *h, bool *fallback_needed) {
+  *fallback_needed = false;
+  int rc = set_attrs();
+  if (rc != MPHF_OK) return rc;
+  u64 mcap = 0;
+  const u64 T = tail_limit(gamma, &mcap);
+  if (level_bits(T, gamma) > mcap) mcap = level_bits(T, gamma);
+  FastScratch sc;
+  FastCfg cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gamma = gamma;
+  cfg.L = L;
+  cfg.seed = seed;
+  cfg.Bmax = kBmax;
+  cfg.T = T;
+  cfg.Pmin = 4096;
+  cfg.Pmax = 128 * 1024;
+  cfg.Btarget = (u64)sm_count() * 4;
+  cfg.cap_scale = g_cap_scale;
+  FastMeta hm;
+  memset(&hm, 0, sizeof(hm));
+  const u64 m0 = level_bits(N, gamma);
+  cfg.m0 = m0;
+  FastMeta *meta = nullptr;
+  int dlim = 0;
+
+#define FTRY(x)                    \
+  do {                             \
+    rc = (x);                      \
+    if (rc != MPHF_OK) goto fail;  \
+  } while (0)
+#define FCUDA(x)                                        \
+  do {                                                  \
+    cudaError_t e_ = (x);                               \
+    if (e_ != cudaSuccess) {                            \
+      rc = cuda_fail(e_, #x);                           \
+      goto fail;                                        \
+    }                                                   \
+  } while (0)
+
+  FTRY(dev_alloc(sc.meta, sizeof(FastMeta), st));
+  meta = (FastMeta *)sc.meta.p;
+  FTRY(dev_alloc(sc.A0, m0 / 8, st));
+  cfg.A0 = (u64 *)sc.A0.p;
+  if (N <= T) {
+    // the whole function in one CTA
+    hm.lv[0].n = N;
+    hm.lv[0].m = m0;
+    hm.lv[0].mode = LM_FLAT;
+    hm.n_flat = N;
+    FTRY(dev_alloc(sc.flat, N * 8, st));
+    cfg.flat = (u64 *)sc.flat.p;
+    cfg.flat_cap = N;
+    u64 arena_words = (u64)(L > 1 ? L - 1 : 1) * (level_bits(N, gamma) / 64);
+    FTRY(dev_alloc(sc.arena, arena_words * 8, st));
+    cfg.arena = (u64 *)sc.arena.p;
+    cfg.arena_words = arena_words;
+    FCUDA(cudaMemcpyAsync(cfg.flat, keys, N * 8, cudaMemcpyDeviceToDevice, st));
+    FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
+    {
+      LaunchScope ls("tail", st);
+      k_tail<<<1, kTailThreads, tail_smem_bytes(mcap), st>>>(meta, 0, cfg, mcap);
+    }
+    FCUDA(cudaGetLastError());
+  } else {
+    size_bucketed(hm.lv[0], N, gamma, cfg.Pmin, cfg.Pmax, cfg.Btarget, cfg.cap_scale);
+    hm.lv[0].off = 0;
+    hm.lv[0].mode = LM_BUCKETED;
+    if (hm.lv[0].B > kBmax) {
+      *fallback_needed = true;
+      sc.release(st);
+      return MPHF_OK;
+    }
+    cfg.capX = hm.lv[0].B * hm.lv[0].cap;
+    FTRY(dev_alloc(sc.X, cfg.capX * 8, st));
+    FTRY(dev_alloc(sc.cntX, kBmax * 8, st));
+    FTRY(dev_alloc(sc.cntY, kBmax * 8, st));
+    cfg.X = (u64 *)sc.X.p;
+    cfg.cntX = (u64 *)sc.cntX.p;
+    cfg.cntY = (u64 *)sc.cntY.p;
+    FCUDA(cudaMemsetAsync(sc.cntX.p, 0, kBmax * 8, st));
+    FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
+    const unsigned gridP = grid_for(N, kTile, (unsigned)sm_count());
+    {
+      LaunchScope ls("partition", st);
+      k_partition0<<<gridP, kTT, g_split_bytes, st>>>(keys, N, meta, cfg);
+    }
+    {
+      LaunchScope ls("fill_buckets", st);
+      k_fill_buckets<<<(unsigned)(hm.lv[0].B < (u64)sm_count() * 2 ? hm.lv[0].B
+                                                                    : (u64)sm_count() * 2),
+                       kTT,
+                       (size_t)(hm.lv[0].P / 4), st>>>(meta, 0, cfg);
+    }
+    FCUDA(cudaGetLastError());
+    FCUDA(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    FCUDA(cudaStreamSynchronize(st));
+    if (hm.status & ST_OVERFLOW) {
+      *fallback_needed = true;
+      sc.release(st);
+      return MPHF_OK;
+    }
+    if (hm.status) {
+      rc = MPHF_EINTERNAL;
+      goto fail;
+    }
+    const u64 n1 = hm.lv[1].n;
+    if (n1 > 0) {
+      const u64 m1 = level_bits(n1, gamma);
+      cfg.capY = hm.lv[1].mode == LM_BUCKETED ? hm.lv[1].B * hm.lv[1].cap : 0;
+      if (cfg.capY) {
+        FTRY(dev_alloc(sc.Y, cfg.capY * 8, st));
+        cfg.Y = (u64 *)sc.Y.p;
+      }
+      cfg.flat_cap = n1 < (1ull << 22) ? n1 : (1ull << 22);
+      if (cfg.flat_cap < T) cfg.flat_cap = T;
+      FTRY(dev_alloc(sc.flat, cfg.flat_cap * 8, st));
+      cfg.flat = (u64 *)sc.flat.p;
+      cfg.arena_words = (u64)(L > 1 ? L - 1 : 1) * (m1 / 64);
+      FTRY(dev_alloc(sc.arena, cfg.arena_words * 8, st));
+      cfg.arena = (u64 *)sc.arena.p;
+      // predicted number of bucketed levels after level 0
+      double e = (double)n1;
+      int D = 1;
+      while (e > (double)T && D < (int)L) {
+        e = expect_next(e, gamma);
+        D++;
+      }
+      for (int round = 0; round < 64; round++) {
+        for (; dlim < D && dlim < (int)L; dlim++) {
+          {
+            LaunchScope ls("compact_buckets", st);
+            k_compact_buckets<<<(unsigned)sm_count(), kTT, g_compact_bytes, st>>>(meta, dlim, cfg);
+          }
+          if (dlim + 1 < (int)L) {
+            LaunchScope ls("fill_buckets", st);
+            k_fill_buckets<<<(unsigned)sm_count() * 2, kTT, (size_t)(cfg.Pmax / 4), st>>>(
+                meta, dlim + 1, cfg);
+          }
+        }
+        {
+          LaunchScope ls("tail", st);
+          k_tail<<<1, kTailThreads, tail_smem_bytes(mcap), st>>>(meta, dlim, cfg, mcap);
+        }
+        FCUDA(cudaGetLastError());
+        FCUDA(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, st));
+        FCUDA(cudaStreamSynchronize(st));
+        if (hm.status || hm.tail_done || dlim >= (int)L) break;
+        D = dlim + 2;
+      }
+    } else {
+      hm.tail_done = 1;
+      hm.levels_used = 1;
+    }
+  }
+  if (N <= T) {
+    FCUDA(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    FCUDA(cudaStreamSynchronize(st));
+  }
+  if (hm.status & ST_OVERFLOW) {
+    *fallback_needed = true;
+    sc.release(st);
+    return MPHF_OK;
+  }
+  if (hm.status & ST_DUPLICATE) {
+    rc = MPHF_EDUPLICATE;
+    goto fail;
+  }
+  if (hm.status || !hm.tail_done) {
+    rc = MPHF_EINTERNAL;
+    goto fail;
+  }
+  {
+    // handle: level metadata, A = A_0 || arena, rank, fallback
+    const uint32_t used = hm.levels_used;
+    if (used < 1 || used > L) {
+      rc = MPHF_EINTERNAL;
+      goto fail;
+    }
+    h->L_used = used;
+    for (uint32_t d = 0; d < used; d++) {
+      h->n[d] = hm.lv[d].n;
+      h->m[d] = hm.lv[d].m;
+      h->off[d] = hm.lv[d].off;
+    }
+    const u64 n_fb = (used == L) ? hm.lv[L].n : 0;
+    h->n[used] = n_fb;
+    h->n_fb = n_fb;
+    h->M = h->off[used - 1] + h->m[used - 1];
+    h->n_rank = (h->M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
+    u64 placed = 0;
+    for (uint32_t d = 0; d < used; d++) placed += hm.lv[d].weight;
+    if (placed + n_fb != N) {
+      rc = MPHF_EINTERNAL;
+      goto fail;
+    }
+    FTRY(dev_alloc(h->A, h->M / 8, st));
+    FTRY(dev_alloc(h->rank, h->n_rank * 8, st));
+    FCUDA(cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 8, cudaMemcpyDeviceToDevice, st));
+    if (h->M > m0)
+      FCUDA(cudaMemcpyAsync((u64 *)h->A.p + m0 / 64, sc.arena.p, (h->M - m0) / 8,
+                            cudaMemcpyDeviceToDevice, st));
+    u64 *d_total = &meta->rank_total;
+    FTRY(build_rank_table((const u64 *)h->A.p, h->M / 64, (u64 *)h->rank.p, h->n_rank, d_total,
+                          st));
+    unsigned *dflag = &meta->dup;
+    if (n_fb) {
+      if (hm.tail_done == 2) FTRY(sort_fallback(cfg.flat, n_fb, dflag, st));
+      FTRY(dev_alloc(h->fb, n_fb * 8, st));
+      FCUDA(cudaMemcpyAsync(h->fb.p, cfg.flat, n_fb * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    FCUDA(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    FCUDA(cudaStreamSynchronize(st));
+    if (hm.dup) {
+      rc = MPHF_EDUPLICATE;
+      goto fail;
+    }
+    if (hm.rank_total != N - n_fb) {
+      rc = MPHF_EINTERNAL;
+      goto fail;
+    }
+  }
+  sc.release(st);
+  return MPHF_OK;
+
+fail:
+  cudaGetLastError();
+  sc.release(st);
+  cudaStreamSynchronize(st);
+  return rc;
+#undef FTRY
+#undef FCUDA
+}
+
+}  // namespace bbh

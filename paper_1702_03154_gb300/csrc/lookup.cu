@@ -1,11 +1,17 @@
 // lookup.cu -- batched queries (Algorithm 3 with the minimal index of
 // Sec. 2.2.3 and the rank checkpoints of Sec. 3.1).
 //
-// One thread answers two keys (one 16-byte load, one 16-byte store).  Both
-// keys probe level 0 together, then the still-unanswered ones probe level 1,
-// and so on, so a thread keeps two independent loads in flight.  The index of
-// a key placed at global bit g is rank[g / 512] plus the ones of the words of
-// its 512-bit block before g.
+// A key needs e^{1/gamma} level probes on average but up to L; a warp that
+// kept 32 keys in lock-step would idle most lanes while its slowest key walks
+// down the levels.  Instead every lane owns kSlots independent query slots,
+// each with its own (key, output index, level).  Each round every active slot
+// probes its current level (one 8-byte load of A); a slot whose bit is set
+// computes its rank and retires, the others move to the next level, and
+// retired slots are refilled from the warp's stream of input keys.  So lanes
+// stay busy and each lane keeps kSlots independent loads in flight.
+//
+// Rank of global bit g: rank[g / 512] plus the ones of the words of g's
+// 512-bit block before g (loaded as 16-byte pairs, only those needed).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -13,6 +19,8 @@
 namespace bbh {
 
 static constexpr int kLookupThreads = 256;
+static constexpr int kSlots = 2;
+static constexpr unsigned kChunk = 32 * 64;  // keys a warp takes from the input at a time
 
 struct LevelTable {
   u64 s[MPHF_MAX_LEVELS];
@@ -29,13 +37,27 @@ struct LookupArgs {
   uint32_t L_used;
 };
 
-// Ones of A strictly before global bit g, given the word w = A[g / 64].
-__device__ __forceinline__ u64 rank_before(const LookupArgs &a, u64 g, u64 w) {
+// Ones of A strictly before global bit g; w = A[g / 64] (already loaded).
+__device__ __forceinline__ u64 rank_before(const u64 *__restrict__ A, const u64 *__restrict__ rank,
+                                           u64 g, u64 w) {
   const u64 b = g >> 9;
-  u64 r = __ldg(a.rank + b);
-  const u64 wi = g >> 6;
-  for (u64 j = b << 3; j < wi; j++) r += __popcll(__ldg(a.A + j));
-  return r + __popcll(w & ((1ull << (g & 63)) - 1ull));
+  const unsigned k = (unsigned)(g >> 6) & 7u;  // word of g inside its block
+  const uint4 *blk = reinterpret_cast<const uint4 *>(A + (b << 3));
+  u64 r = __ldg(rank + b);
+  uint4 v[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    v[j] = make_uint4(0, 0, 0, 0);
+    if ((unsigned)(2 * j) < k) v[j] = __ldg(blk + j);
+  }
+  unsigned c = 0;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    unsigned lo = (unsigned)(2 * j) < k ? 0xffffffffu : 0u;
+    unsigned hi = (unsigned)(2 * j + 1) < k ? 0xffffffffu : 0u;
+    c += __popc(v[j].x & lo) + __popc(v[j].y & lo) + __popc(v[j].z & hi) + __popc(v[j].w & hi);
+  }
+  return r + c + __popcll(w & ((1ull << (g & 63)) - 1ull));
 }
 
 __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
@@ -49,68 +71,93 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
-template <int K>
-__device__ __forceinline__ void query_keys(const LookupArgs &a, const LevelTable &t, const u64 (&x)[K],
-                                           u64 (&res)[K]) {
-  bool open[K];
-#pragma unroll
-  for (int k = 0; k < K; k++) {
-    open[k] = true;
-    res[k] = MPHF_NOT_FOUND;
+__global__ void __launch_bounds__(kLookupThreads)
+k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
+  __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
+  for (unsigned i = threadIdx.x; i < a.L_used; i += kLookupThreads) {
+    ts[i] = t.s[i];
+    tm[i] = t.m[i];
+    toff[i] = t.off[i];
   }
-  for (uint32_t d = 0; d < a.L_used; d++) {
-    bool any = false;
-    u64 g[K], w[K];
+  __syncthreads();
+
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const u64 nchunks = (n + kChunk - 1) / kChunk;
+  const u64 warp_id = ((u64)blockIdx.x * kLookupThreads + threadIdx.x) >> 5;
+  const u64 nwarps = ((u64)gridDim.x * kLookupThreads) >> 5;
+  u64 chunk = warp_id;
+  u64 cursor = chunk * kChunk;
+  u64 cend = chunk < nchunks ? min(cursor + kChunk, n) : cursor;
+  bool more = chunk < nchunks;
+
+  u64 x[kSlots], idx[kSlots];
+  unsigned lvl[kSlots];
+  bool act[kSlots];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (open[k]) {
-        g[k] = t.off[d] + level_pos(x[k], t.s[d], t.m[d]);
-        w[k] = __ldg(a.A + (g[k] >> 6));
+  for (int s = 0; s < kSlots; s++) {
+    act[s] = false;
+    lvl[s] = 0;
+    x[s] = 0;
+    idx[s] = 0;
+  }
+
+  for (;;) {
+    // refill retired slots from the warp's input stream (warp-uniform control)
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      unsigned need = __ballot_sync(0xffffffffu, !act[s]);
+      while (need && more) {
+        if (cursor >= cend) {
+          chunk += nwarps;
+          if (chunk >= nchunks) {
+            more = false;
+            break;
+          }
+          cursor = chunk * kChunk;
+          cend = min(cursor + kChunk, n);
+        }
+        const u64 avail = cend - cursor;
+        const unsigned r = __popc(need & lt);
+        const bool mine = ((need >> lane) & 1u) && (u64)r < avail;
+        if (mine) {
+          idx[s] = cursor + r;
+          x[s] = __ldcs(keys + cursor + r);
+          lvl[s] = 0;
+          act[s] = true;
+        }
+        const unsigned taken = __ballot_sync(0xffffffffu, mine);
+        need &= ~taken;
+        cursor += __popc(taken);
+      }
+    }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) any |= act[s];
+    if (!__any_sync(0xffffffffu, any)) break;
+
+    // one probe per active slot: issue all loads, then resolve
+    u64 g[kSlots], w[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      if (act[s]) {
+        const unsigned d = lvl[s];
+        g[s] = toff[d] + level_pos(x[s], ts[d], tm[d]);
+        w[s] = __ldg(a.A + (g[s] >> 6));
       }
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (open[k]) {
-        if ((w[k] >> (g[k] & 63)) & 1ull) {
-          res[k] = rank_before(a, g[k], w[k]);
-          open[k] = false;
-        } else {
-          any = true;
+    for (int s = 0; s < kSlots; s++) {
+      if (act[s]) {
+        if ((w[s] >> (g[s] & 63)) & 1ull) {
+          __stcs(out + idx[s], rank_before(a.A, a.rank, g[s], w[s]));
+          act[s] = false;
+        } else if (++lvl[s] >= a.L_used) {
+          __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
+          act[s] = false;
         }
       }
     }
-    if (!any) break;
-  }
-  if (a.n_fb) {
-#pragma unroll
-    for (int k = 0; k < K; k++)
-      if (open[k]) res[k] = fallback_index(a, x[k]);
-  }
-}
-
-__global__ void __launch_bounds__(kLookupThreads)
-k_lookup_vec(const uint4 *__restrict__ keys2, u64 npairs, uint4 *__restrict__ out2, LookupArgs a,
-             LevelTable t) {
-  const u64 stride = (u64)gridDim.x * kLookupThreads;
-  for (u64 i = (u64)blockIdx.x * kLookupThreads + threadIdx.x; i < npairs; i += stride) {
-    uint4 v = __ldcs(keys2 + i);
-    u64 x[2] = {((u64)v.y << 32) | v.x, ((u64)v.w << 32) | v.z};
-    u64 r[2];
-    query_keys<2>(a, t, x, r);
-    __stcs(out2 + i, make_uint4((unsigned)r[0], (unsigned)(r[0] >> 32), (unsigned)r[1],
-                                (unsigned)(r[1] >> 32)));
-  }
-}
-
-__global__ void __launch_bounds__(kLookupThreads)
-k_lookup_scalar(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a,
-                LevelTable t) {
-  const u64 stride = (u64)gridDim.x * kLookupThreads;
-  for (u64 i = (u64)blockIdx.x * kLookupThreads + threadIdx.x; i < n; i += stride) {
-    u64 x[1] = {keys[i]};
-    u64 r[1];
-    query_keys<1>(a, t, x, r);
-    out[i] = r[0];
   }
 }
 
@@ -132,25 +179,14 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   LookupArgs a;
   LevelTable t;
   fill_tables(h, a, t);
-  const unsigned maxb = (unsigned)sm_count() * 16;
-  const bool aligned = (((uintptr_t)keys | (uintptr_t)out) & 15) == 0;
-  if (aligned) {
-    u64 npairs = n >> 1;
-    if (npairs) {
-      unsigned g = grid_for(npairs, kLookupThreads * 2, maxb);
-      LaunchScope ls("lookup", s);
-      k_lookup_vec<<<g, kLookupThreads, 0, s>>>(reinterpret_cast<const uint4 *>(keys), npairs,
-                                                reinterpret_cast<uint4 *>(out), a, t);
-    }
-    if (n & 1) {
-      LaunchScope ls("lookup", s);
-      k_lookup_scalar<<<1, kLookupThreads, 0, s>>>(keys + (n - 1), 1, out + (n - 1), a, t);
-    }
-  } else {
-    unsigned g = grid_for(n, kLookupThreads * 2, maxb);
-    LaunchScope ls("lookup", s);
-    k_lookup_scalar<<<g, kLookupThreads, 0, s>>>(keys, n, out, a, t);
-  }
+  const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
+  const unsigned per_block = kLookupThreads / 32;
+  unsigned grid = (unsigned)((nwarps_needed + per_block - 1) / per_block);
+  const unsigned maxb = (unsigned)sm_count() * 8;
+  if (grid > maxb) grid = maxb;
+  if (grid < 1) grid = 1;
+  LaunchScope ls("lookup", s);
+  k_lookup<<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }

@@ -77,6 +77,8 @@ def lib():
         "mphf_copy_rank": ([vp, vp, u64], i32),
         "mphf_copy_fallback": ([vp, vp, u64], i32),
         "mphf_keygen": ([vp, u64, u64, u64, vp], i32),
+        "mphf_build_path": ([vp], i32),
+        "mphf_debug_config": ([i32, dbl], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -186,6 +188,11 @@ class MPHF:
         return lib().mphf_bits_per_key(self._h)
 
     @property
+    def build_path(self) -> int:
+        """1 = bucketed (shared-memory) construction, 2 = unbucketed (L2 atomics)."""
+        return lib().mphf_build_path(self._h)
+
+    @property
     def N(self) -> int:
         return lib().mphf_num_keys(self._h)
 
@@ -260,6 +267,12 @@ def keygen(n: int, seed: int, start: int = 0, device=None, stream=None):
         _check(lib().mphf_keygen(out.data_ptr(), int(n), int(seed) & NOT_FOUND, int(start),
                                  _stream_ptr(stream)), "mphf_keygen")
     return out
+
+
+def debug_config(path: int = 0, cap_scale: float = 1.0):
+    """Test hook: path 0 = bucketed with fallback (default), 1 = unbucketed only;
+    cap_scale < 1 shrinks bucket capacities so that the fallback is taken."""
+    _check(lib().mphf_debug_config(int(path), float(cap_scale)), "mphf_debug_config")
 
 
 def launch_count() -> int:

@@ -186,3 +186,47 @@ def test_config2_full_size_gamma2(M):
     assert bool((hits == 1).all())
     idx = inputs.sample_indices(N, 2 * 10**6, 5)
     assert np.array_equal(M.to_u64(g.lookup(kd[torch.from_numpy(idx).cuda()])), o.lookup(keys[idx]))
+
+
+@pytest.mark.parametrize("n,gamma,levels", [(10**6, 2.0, 25), (300001, 1.0, 25), (300001, 5.0, 25),
+                                            (200000, 1.0, 3), (20000, 2.0, 25)])
+def test_unbucketed_path_matches(M, n, gamma, levels):
+    keys = inputs.splitmix64_keys(n, 53)
+    o = oracle.build(keys, gamma=gamma, levels=levels, seed=2)
+    try:
+        M.debug_config(path=1)
+        g = M.MPHF.build(dev(keys), gamma=gamma, levels=levels, seed=2)
+    finally:
+        M.debug_config(path=0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(M.to_u64(g.lookup(dev(keys))), o.lookup(keys))
+
+
+def test_default_path_is_bucketed(M):
+    keys = inputs.splitmix64_keys(10**6, 59)
+    g = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=0)
+    assert g.build_path == 1
+
+
+@pytest.mark.parametrize("n", [10**6, 100000])
+def test_bucket_overflow_falls_back_with_identical_results(M, n):
+    keys = inputs.splitmix64_keys(n, 61)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=3)
+    try:
+        M.debug_config(path=0, cap_scale=0.5)
+        g = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=3)
+    finally:
+        M.debug_config(path=0, cap_scale=1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(M.to_u64(g.lookup(dev(keys))), o.lookup(keys))
+
+
+def test_many_duplicates_are_reported(M):
+    # 5000 copies of one key overflow a bucket: the unbucketed path reports them.
+    keys = inputs.splitmix64_keys(200000, 67)
+    keys[:5000] = keys[5000]
+    with pytest.raises(M.MPHFError) as e:
+        M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=0)
+    assert e.value.code == M.EDUPLICATE
