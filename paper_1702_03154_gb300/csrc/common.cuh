@@ -30,7 +30,19 @@ __host__ __device__ __forceinline__ u64 level_seed(u64 seed, uint32_t d) {
 }
 
 // floor(h * m / 2^64): maps the 64-bit hash onto [0, m) without a division.
-__device__ __forceinline__ u64 reduce_range(u64 h, u64 m) { return __umul64hi(h, m); }
+// For m < 2^32 (every level below ~2^31 keys) the same value comes from two
+// 32x32-bit products: with h = hi 2^32 + lo,
+//   floor(h m / 2^64) = floor((hi m + floor(lo m / 2^32)) / 2^32),
+// since the dropped fraction of lo m / 2^32 is below 1 and hi m + lo m / 2^32
+// stays below 2^64.
+__device__ __forceinline__ u64 reduce_range(u64 h, u64 m) {
+  if ((m >> 32) == 0) {
+    const unsigned m32 = (unsigned)m;
+    const u64 t = ((u64)(unsigned)h * m32) >> 32;
+    return ((u64)(unsigned)(h >> 32) * m32 + t) >> 32;
+  }
+  return __umul64hi(h, m);
+}
 
 // Position of key x in A_d (m_d bits).
 __device__ __forceinline__ u64 level_pos(u64 x, u64 s_d, u64 m_d) {

@@ -25,12 +25,13 @@
 
 namespace bbh {
 
-static constexpr int kTT = 1024;           // threads of partition / compaction / fill CTAs
+static constexpr int kTT = 512;            // threads of partition / compaction / fill CTAs
 static constexpr int kKPT = 8;             // keys per thread per tile
-static constexpr int kTile = kTT * kKPT;   // 8192 keys
+static constexpr int kTile = kTT * kKPT;   // 4096 keys
+static constexpr u64 kPmax = 256 * 1024;   // positions per bucket at most (64 KB of bits)
 static constexpr int kTailThreads = 1024;
 static constexpr u64 kTailMaxKeys = 16384;
-static constexpr u64 kBmax = 4096;
+static constexpr u64 kBmax = 2048;
 
 // ---------------------------------------------------------------------------
 // Level sizing (device side, by the last block of a fill).
@@ -52,7 +53,7 @@ __host__ __device__ inline void size_bucketed(FLevel &lv, u64 n, double gamma, u
   lv.B = ceil_div(lv.m, P);
   double mean = (double)n * (double)P / (double)lv.m;
   u64 cap = (u64)(cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));
-  lv.cap = (cap + 1) & ~1ull;  // even: every bucket starts 16-byte aligned
+  lv.cap = (cap + 3) & ~3ull;  // multiple of 4: every bucket starts 16-byte aligned
 }
 
 // ---------------------------------------------------------------------------
@@ -110,17 +111,21 @@ __device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned *red, un
 struct SplitSmem {
   unsigned *cnt;         // [nb] keys per destination in this tile, then their local start
   unsigned *base;        // [nb] slot reserved in the destination bucket
-  u64 *sorted;           // [kTile]
+  u64 *sorted;           // [kTile] keys in destination order (also the survivor staging area)
+  unsigned *spos;        // [kTile] their in-bucket positions
   unsigned short *sdst;  // [kTile]
-  unsigned *red;         // [kTT / 32 + 1]
+  unsigned *red;         // [kTT / 32 + 2]
 };
 
-// Write the valid keys of a tile into their destination buckets
-// (arena[b * cap + slot]); slots are reserved with one atomicAdd per
-// non-empty destination; keys of one destination leave as one contiguous run.
-__device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&dst)[kKPT],
-                                 const bool (&ok)[kKPT], unsigned nb, const SplitSmem &sm,
-                                 u64 *__restrict__ arena, u64 cap, u64 *__restrict__ gcnt,
+// Write the valid entries of a tile into their destination buckets: key to
+// arena[b * cap + slot] and (WITH_POS) its in-bucket position to
+// parena[b * cap + slot].  Slots are reserved with one atomicAdd per non-empty
+// destination; the entries of one destination leave as one contiguous run.
+template <bool WITH_POS>
+__device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
+                                 const unsigned (&dst)[kKPT], const bool (&ok)[kKPT], unsigned nb,
+                                 const SplitSmem &sm, u64 *__restrict__ arena,
+                                 unsigned *__restrict__ parena, u64 cap, u64 *__restrict__ gcnt,
                                  unsigned *__restrict__ status) {
   for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;
   __syncthreads();
@@ -154,6 +159,7 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&dst)[kKP
     if (ok[k]) {
       unsigned pos = sm.cnt[dst[k]] + rk[k];
       sm.sorted[pos] = x[k];
+      if (WITH_POS) sm.spos[pos] = lp[k];
       sm.sdst[pos] = (unsigned short)dst[k];
     }
   }
@@ -161,8 +167,12 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&dst)[kKP
   for (unsigned i = threadIdx.x; i < total; i += kTT) {
     unsigned b = sm.sdst[i];
     u64 j = (u64)sm.base[b] + (i - sm.cnt[b]);
-    if (j < cap) arena[(u64)b * cap + j] = sm.sorted[i];
-    else atomicOr(status, ST_OVERFLOW);
+    if (j < cap) {
+      arena[(u64)b * cap + j] = sm.sorted[i];
+      if (WITH_POS) parena[(u64)b * cap + j] = sm.spos[i];
+    } else {
+      atomicOr(status, ST_OVERFLOW);
+    }
   }
   __syncthreads();
 }
@@ -170,7 +180,8 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&dst)[kKP
 __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
-  s.cnt = reinterpret_cast<unsigned *>(smem + kTile * 8);
+  s.spos = reinterpret_cast<unsigned *>(smem + kTile * 8);
+  s.cnt = s.spos + kTile;
   s.base = s.cnt + nb_cap;
   s.red = s.base + nb_cap;
   s.sdst = reinterpret_cast<unsigned short *>(s.red + kTT / 32 + 2);
@@ -178,34 +189,69 @@ __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned n
 }
 
 static constexpr size_t split_smem_bytes(unsigned nb_cap) {
-  return (size_t)kTile * 8 + 2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 + (size_t)kTile * 2;
+  return (size_t)kTile * 8 + (size_t)kTile * 4 + 2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 +
+         (size_t)kTile * 2;
 }
 
 // ---------------------------------------------------------------------------
-// Level 0: partition the caller's keys into position buckets of A_0.
+// Level 0: partition the caller's keys into position buckets of A_0; each key
+// is stored with its position inside the bucket, so the fill needs no hash.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTT, 1)
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kTT, 2)
 k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FLevel lv = meta->lv[0];
   const unsigned nb = (unsigned)lv.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  // one tile of input staged by asynchronous copies: each thread takes its
+  // keys of tile t into registers, then starts copying its keys of the next
+  // tile into the same slots while tile t is split
+  u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
   const u64 s0 = level_seed(cfg.seed, 0);
   const unsigned sh = ilog2_u64(lv.P);
+  const unsigned mask = (unsigned)(lv.P - 1);
   const u64 ntiles = ceil_div(n, kTile);
-  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  auto prefetch = [&](u64 t) {
+    if (t < ntiles) {
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
+        if (i < n) cp_async8(inbuf + k * kTT + threadIdx.x, keys + i);
+      }
+    }
+    cp_async_commit();
+  };
+  u64 t = blockIdx.x;
+  prefetch(t);
+  for (; t < ntiles; t += gridDim.x) {
+    cp_async_wait0();  // this thread's copies of tile t have landed
     u64 x[kKPT];
-    unsigned dst[kKPT];
     bool ok[kKPT];
 #pragma unroll
     for (int k = 0; k < kKPT; k++) {
-      u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
+      const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
       ok[k] = i < n;
-      x[k] = ok[k] ? __ldcs(keys + i) : 0;
-      dst[k] = ok[k] ? (unsigned)(level_pos(x[k], s0, lv.m) >> sh) : 0u;
+      x[k] = ok[k] ? inbuf[k * kTT + threadIdx.x] : 0;
     }
-    multisplit_write(x, dst, ok, nb, sm, cfg.X, lv.cap, cfg.cntX, &meta->status);
+    prefetch(t + gridDim.x);
+    unsigned dst[kKPT], lp[kKPT];
+#pragma unroll
+    for (int k = 0; k < kKPT; k++) {
+      const u64 p = ok[k] ? level_pos(x[k], s0, lv.m) : 0;
+      dst[k] = (unsigned)(p >> sh);
+      lp[k] = (unsigned)p & mask;
+    }
+    multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, lv.cap, cfg.cntX,
+                           &meta->status);
   }
+  cp_async_wait0();
 }
 
 // ---------------------------------------------------------------------------
@@ -226,7 +272,7 @@ __device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
     meta->levels_used = d + 1;
   } else if ((uint32_t)(d + 1) == cfg.L) {
     nx.mode = LM_FLAT;  // fallback
-    if (nn > cfg.flat_cap) atomicOr(&meta->status, ST_OVERFLOW);
+    if (d > 0 && nn > cfg.flat_cap) atomicOr(&meta->status, ST_OVERFLOW);
   } else if (nn <= cfg.T) {
     nx.mode = LM_FLAT;  // tail
     nx.m = level_bits(nn, cfg.gamma);
@@ -234,8 +280,9 @@ __device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
     size_bucketed(nx, nn, cfg.gamma, cfg.Pmin, cfg.Pmax, cfg.Btarget, cfg.cap_scale);
     nx.off = vl[d].off + m;
     nx.mode = LM_BUCKETED;
+    // level 1's arena is allocated by the host from these sizes (after level 0)
     const u64 acap = ((d + 1) & 1) ? cfg.capY : cfg.capX;
-    if (nx.B > cfg.Bmax || nx.B * nx.cap > acap) {
+    if (nx.B > cfg.Bmax || (d > 0 && nx.B * nx.cap > acap)) {
       atomicOr(&meta->status, ST_OVERFLOW);
       nx.mode = LM_NONE;
     }
@@ -244,58 +291,52 @@ __device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
   __threadfence();
 }
 
-__global__ void __launch_bounds__(kTT, 1)
+__global__ void __launch_bounds__(kTT, 2)
 k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ u64 red[kTT / 32];
   __shared__ bool last;
   if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
   const FLevel lv = meta->lv[d];
-  const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
+  const unsigned *parena = (d & 1) ? cfg.YP : cfg.XP;
   const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
   u64 *Alev = (d == 0) ? cfg.A0 : cfg.arena + ((lv.off - cfg.m0) >> 6);
-  const u64 s_d = level_seed(cfg.seed, d);
   const unsigned Pw = (unsigned)(lv.P >> 5);  // 32-bit words per bit array
   unsigned *hit = reinterpret_cast<unsigned *>(smem);
   unsigned *col = hit + Pw;
-  const u64 mask = lv.P - 1;
   u64 wsum = 0, got = 0;
   for (u64 b = blockIdx.x; b < lv.B; b += gridDim.x) {
     for (unsigned i = threadIdx.x; i < 2 * Pw; i += kTT) hit[i] = 0;
     __syncthreads();
     const u64 nk = min(cnt[b], lv.cap);
     got += (threadIdx.x == 0) ? cnt[b] : 0;
-    const u64 *kb = arena + b * lv.cap;
-    const uint4 *kb2 = reinterpret_cast<const uint4 *>(kb);
-    constexpr int U = 4;  // 16-byte loads in flight per thread
-    for (u64 i0 = threadIdx.x; 2 * i0 < nk; i0 += (u64)U * kTT) {
-      u64 xs[2 * U];
-      int c[U];
+    const unsigned *pb = parena + b * lv.cap;
+    const uint4 *pb4 = reinterpret_cast<const uint4 *>(pb);  // cap % 4 == 0: 16-byte aligned
+    // 4 positions per 16-byte load, U loads in flight per thread
+    constexpr int U = 4;
+    for (u64 i0 = threadIdx.x; 4 * i0 < nk; i0 += (u64)U * kTT) {
+      unsigned q[4 * U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const u64 i = i0 + (u64)u * kTT;
-        c[u] = 0;
-        xs[2 * u] = xs[2 * u + 1] = 0;
-        if (2 * i + 1 < nk) {
-          uint4 v = __ldcs(kb2 + i);
-          xs[2 * u] = ((u64)v.y << 32) | v.x;
-          xs[2 * u + 1] = ((u64)v.w << 32) | v.z;
-          c[u] = 2;
-        } else if (2 * i < nk) {
-          xs[2 * u] = __ldcs(kb + 2 * i);
-          c[u] = 1;
+        if (4 * i + 3 < nk) {
+          const uint4 v = __ldcs(pb4 + i);
+          q[4 * u] = v.x;
+          q[4 * u + 1] = v.y;
+          q[4 * u + 2] = v.z;
+          q[4 * u + 3] = v.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; j++) q[4 * u + j] = (4 * i + j < nk) ? __ldcs(pb + 4 * i + j) : ~0u;
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-#pragma unroll
-        for (int j = 0; j < 2; j++) {
-          if (j < c[u]) {
-            const unsigned p = (unsigned)(level_pos(xs[2 * u + j], s_d, lv.m) & mask);
-            const unsigned bit = 1u << (p & 31);
-            const unsigned old = atomicOr(hit + (p >> 5), bit);
-            if (old & bit) atomicOr(col + (p >> 5), bit);
-          }
+      for (int j = 0; j < 4 * U; j++) {
+        const unsigned p = q[j];
+        if (p != ~0u) {
+          const unsigned bit = 1u << (p & 31);
+          const unsigned old = atomicOr(hit + (p >> 5), bit);
+          if (old & bit) atomicOr(col + (p >> 5), bit);
         }
       }
     }
@@ -340,11 +381,14 @@ k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
 
 // ---------------------------------------------------------------------------
 // Compaction of level d: keys whose A_d bit is 0 go to their level-(d+1)
-// bucket (or, for a small or final level, to the flat buffer).
+// bucket (or, for a small or final level, to the flat buffer).  The survivors
+// of a tile are first packed densely in shared memory so that their
+// level-(d+1) hashes are computed by full warps.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTT, 1)
+__global__ void __launch_bounds__(kTT, 2)
 k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned tile_cnt;
   if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
   const FLevel lv = meta->lv[d];
   const FLevel nx = meta->lv[d + 1];
@@ -353,16 +397,21 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   const unsigned nb = flat ? 1u : (unsigned)nx.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
   u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
+  u64 *stage = sm.sorted;  // survivors of the tile, before their destinations are known
   const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
+  const unsigned *parena = (d & 1) ? cfg.YP : cfg.XP;
   const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
   u64 *out = flat ? cfg.flat : (((d + 1) & 1) ? cfg.Y : cfg.X);
+  unsigned *pout = flat ? nullptr : (((d + 1) & 1) ? cfg.YP : cfg.XP);
   u64 *ocnt = flat ? &meta->n_flat : (((d + 1) & 1) ? cfg.cntY : cfg.cntX);
   const u64 ocap = flat ? cfg.flat_cap : nx.cap;
   const u64 *Alev = (d == 0) ? cfg.A0 : cfg.arena + ((lv.off - cfg.m0) >> 6);
-  const u64 s_d = level_seed(cfg.seed, d);
   const u64 s_n = level_seed(cfg.seed, d + 1);
   const unsigned shn = flat ? 0u : ilog2_u64(nx.P);
-  const u64 mask = lv.P - 1;
+  const unsigned maskn = flat ? 0u : (unsigned)(nx.P - 1);
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) tile_cnt = 0;
   for (u64 b = blockIdx.x; b < lv.B; b += gridDim.x) {
     const u64 w0 = (b * lv.P) >> 6;
     const u64 wend = min((b + 1) * lv.P, lv.m) >> 6;
@@ -370,24 +419,55 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     __syncthreads();
     const u64 nk = min(cnt[b], lv.cap);
     const u64 *kb = arena + b * lv.cap;
+    const unsigned *pb = parena + b * lv.cap;
     for (u64 t0 = 0; t0 < nk; t0 += kTile) {
-      u64 x[kKPT];
-      unsigned dst[kKPT];
-      bool ok[kKPT];
+      // 1. test every key of the tile; pack the survivors warp by warp.  All
+      // keys are loaded up front: survivors are spread over every sector anyway.
+      unsigned pk[kKPT];
+      u64 xk[kKPT];
 #pragma unroll
       for (int k = 0; k < kKPT; k++) {
         const u64 i = t0 + (u64)k * kTT + threadIdx.x;
-        ok[k] = false;
+        pk[k] = i < nk ? __ldcs(pb + i) : ~0u;
+        xk[k] = i < nk ? __ldcs(kb + i) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const unsigned p = pk[k];
+        const bool keep = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
+        const u64 x = xk[k];
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        unsigned wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&tile_cnt, (unsigned)__popc(bal));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) stage[wbase + __popc(bal & lt)] = x;
+      }
+      __syncthreads();
+      const unsigned ns = tile_cnt;
+      // 2. hash the packed survivors for level d+1 (full warps)
+      u64 x[kKPT];
+      unsigned dst[kKPT], lp[kKPT];
+      bool ok[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const unsigned i = (unsigned)k * kTT + threadIdx.x;
+        ok[k] = i < ns;
+        x[k] = ok[k] ? stage[i] : 0;
         dst[k] = 0;
-        x[k] = 0;
-        if (i < nk) {
-          x[k] = __ldcs(kb + i);
-          const unsigned p = (unsigned)(level_pos(x[k], s_d, lv.m) & mask);
-          ok[k] = !((segA[p >> 6] >> (p & 63)) & 1ull);
-          if (ok[k] && !flat) dst[k] = (unsigned)(level_pos(x[k], s_n, nx.m) >> shn);
+        lp[k] = 0;
+        if (ok[k] && !flat) {
+          const u64 p = level_pos(x[k], s_n, nx.m);
+          dst[k] = (unsigned)(p >> shn);
+          lp[k] = (unsigned)p & maskn;
         }
       }
-      multisplit_write(x, dst, ok, nb, sm, out, ocap, ocnt, &meta->status);
+      __syncthreads();  // the staging area is reused by the writer
+      if (threadIdx.x == 0) tile_cnt = 0;
+      // 3. write them to their destinations
+      if (flat)
+        multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, ocap, ocnt, &meta->status);
+      else
+        multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, ocap, ocnt, &meta->status);
     }
   }
 }
@@ -600,13 +680,13 @@ static size_t g_split_bytes, g_compact_bytes;
 static int set_attrs() {
   if (g_attr_set) return MPHF_OK;
   g_split_bytes = split_smem_bytes((unsigned)kBmax);
-  g_compact_bytes = g_split_bytes + (256 * 1024) / 8;  // + A segment for P <= 256K
+  g_compact_bytes = g_split_bytes + kPmax / 8;  // + the bucket's slice of A_d
   MPHF_CUDA(cudaFuncSetAttribute(k_partition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)g_split_bytes));
+                                 (int)(g_split_bytes + kTile * 8)));
   MPHF_CUDA(cudaFuncSetAttribute(k_compact_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)g_compact_bytes));
   MPHF_CUDA(cudaFuncSetAttribute(k_fill_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((256 * 1024) / 4)));
+                                 (int)(kPmax / 4)));
   MPHF_CUDA(cudaFuncSetAttribute(k_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
   g_attr_set = true;
@@ -620,10 +700,10 @@ static double expect_next(double n, double gamma) {
 }
 
 struct FastScratch {
-  DevBuf meta, X, Y, cntX, cntY, flat, A0, arena;
+  DevBuf meta, X, Y, XP, YP, cntX, cntY, flat, A0, arena;
   void release(cudaStream_t s) {
-    dev_free(meta, s); dev_free(X, s); dev_free(Y, s); dev_free(cntX, s); dev_free(cntY, s);
-    dev_free(flat, s); dev_free(A0, s); dev_free(arena, s);
+    dev_free(meta, s); dev_free(X, s); dev_free(Y, s); dev_free(XP, s); dev_free(YP, s);
+    dev_free(cntX, s); dev_free(cntY, s); dev_free(flat, s); dev_free(A0, s); dev_free(arena, s);
   }
 };
 
@@ -661,7 +741,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
   cfg.Bmax = kBmax;
   cfg.T = T;
   cfg.Pmin = 4096;
-  cfg.Pmax = 128 * 1024;
+  cfg.Pmax = kPmax;
   cfg.Btarget = (u64)sm_count() * 4;
   cfg.cap_scale = g_cap_scale;
   FastMeta hm;
@@ -720,6 +800,8 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     }
     cfg.capX = hm.lv[0].B * hm.lv[0].cap;
     FTRY(dev_alloc(sc.X, cfg.capX * 8, st));
+    FTRY(dev_alloc(sc.XP, cfg.capX * 4, st));
+    cfg.XP = (unsigned *)sc.XP.p;
     FTRY(dev_alloc(sc.cntX, kBmax * 8, st));
     FTRY(dev_alloc(sc.cntY, kBmax * 8, st));
     cfg.X = (u64 *)sc.X.p;
@@ -727,10 +809,10 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     cfg.cntY = (u64 *)sc.cntY.p;
     FCUDA(cudaMemsetAsync(sc.cntX.p, 0, kBmax * 8, st));
     FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
-    const unsigned gridP = grid_for(N, kTile, (unsigned)sm_count());
+    const unsigned gridP = grid_for(N, kTile, (unsigned)sm_count() * 2);
     {
       LaunchScope ls("partition", st);
-      k_partition0<<<gridP, kTT, g_split_bytes, st>>>(keys, N, meta, cfg);
+      k_partition0<<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
     }
     {
       LaunchScope ls("fill_buckets", st);
@@ -757,7 +839,9 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
       cfg.capY = hm.lv[1].mode == LM_BUCKETED ? hm.lv[1].B * hm.lv[1].cap : 0;
       if (cfg.capY) {
         FTRY(dev_alloc(sc.Y, cfg.capY * 8, st));
+        FTRY(dev_alloc(sc.YP, cfg.capY * 4, st));
         cfg.Y = (u64 *)sc.Y.p;
+        cfg.YP = (unsigned *)sc.YP.p;
       }
       cfg.flat_cap = n1 < (1ull << 22) ? n1 : (1ull << 22);
       if (cfg.flat_cap < T) cfg.flat_cap = T;
@@ -777,7 +861,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
         for (; dlim < D && dlim < (int)L; dlim++) {
           {
             LaunchScope ls("compact_buckets", st);
-            k_compact_buckets<<<(unsigned)sm_count(), kTT, g_compact_bytes, st>>>(meta, dlim, cfg);
+            k_compact_buckets<<<(unsigned)sm_count() * 2, kTT, g_compact_bytes, st>>>(meta, dlim, cfg);
           }
           if (dlim + 1 < (int)L) {
             LaunchScope ls("fill_buckets", st);

@@ -48,6 +48,7 @@ struct FastCfg {
   uint32_t L;
   u64 seed;
   u64 *X, *Y;           // bucket arenas: levels with even / odd d
+  unsigned *XP, *YP;    // in-bucket position of each key of X / Y
   u64 capX, capY;       // their capacities in keys
   u64 *cntX, *cntY;     // per-bucket key counts
   u64 Bmax;             // capacity of the count arrays
