@@ -109,16 +109,16 @@ __device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned *red, un
 
 // Shared memory of the multisplit writer.
 struct SplitSmem {
-  unsigned *cnt;         // [nb] keys per destination in this tile, then their local start
-  unsigned *base;        // [nb] slot reserved in the destination bucket
+  unsigned *cnt;         // [nb] entries per destination in this tile, then their local start
+  unsigned *lim;         // [nb] local index past which the destination bucket is full
+  u64 *dbase;            // [nb] arena index of local entry 0 of each destination
   u64 *sorted;           // [kTile] keys in destination order (also the survivor staging area)
-  unsigned *spos;        // [kTile] their in-bucket positions
-  unsigned short *sdst;  // [kTile]
+  unsigned *stag;        // [kTile] (destination << 20) | in-bucket position
   unsigned *red;         // [kTT / 32 + 2]
 };
 
 // Write the valid entries of a tile into their destination buckets: key to
-// arena[b * cap + slot] and (WITH_POS) its in-bucket position to
+// arena[b * cap + slot] and (WITH_POS) its in-bucket position lp (< 2^20) to
 // parena[b * cap + slot].  Slots are reserved with one atomicAdd per non-empty
 // destination; the entries of one destination leave as one contiguous run.
 template <bool WITH_POS>
@@ -133,43 +133,42 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
 #pragma unroll
   for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
   __syncthreads();
-  // reserve, then exclusive scan of the counts (each thread owns a run of entries)
+  // exclusive scan of the counts (each thread owns a run of entries), then
+  // reserve each destination's slots and precompute where its run goes
   const unsigned per = (nb + kTT - 1) / kTT;
   const unsigned lo = threadIdx.x * per;
   const unsigned hi = min(lo + per, nb);
   unsigned s = 0;
-  for (unsigned i = lo; i < hi; i++) {
-    unsigned c = sm.cnt[i];
-    if (c) {
-      u64 b0 = atomicAdd(gcnt + i, (u64)c);
-      sm.base[i] = b0 > 0xffffffffull ? 0xffffffffu : (unsigned)b0;
-    }
-    s += c;
-  }
+  for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
   unsigned total;
   unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
   for (unsigned i = lo; i < hi; i++) {
-    unsigned c = sm.cnt[i];
+    const unsigned c = sm.cnt[i];
+    u64 b0 = 0;
+    if (c) b0 = atomicAdd(gcnt + i, (u64)c);
+    const u64 room = b0 < cap ? cap - b0 : 0;
     sm.cnt[i] = pre;
+    sm.lim[i] = pre + (unsigned)(room < c ? room : c);
+    sm.dbase[i] = (u64)i * cap + b0 - pre;
     pre += c;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kKPT; k++) {
     if (ok[k]) {
-      unsigned pos = sm.cnt[dst[k]] + rk[k];
+      const unsigned pos = sm.cnt[dst[k]] + rk[k];
       sm.sorted[pos] = x[k];
-      if (WITH_POS) sm.spos[pos] = lp[k];
-      sm.sdst[pos] = (unsigned short)dst[k];
+      sm.stag[pos] = (dst[k] << 20) | lp[k];
     }
   }
   __syncthreads();
   for (unsigned i = threadIdx.x; i < total; i += kTT) {
-    unsigned b = sm.sdst[i];
-    u64 j = (u64)sm.base[b] + (i - sm.cnt[b]);
-    if (j < cap) {
-      arena[(u64)b * cap + j] = sm.sorted[i];
-      if (WITH_POS) parena[(u64)b * cap + j] = sm.spos[i];
+    const unsigned tg = sm.stag[i];
+    const unsigned b = tg >> 20;
+    if (i < sm.lim[b]) {
+      const u64 j = sm.dbase[b] + i;
+      arena[j] = sm.sorted[i];
+      if (WITH_POS) parena[j] = tg & 0xfffffu;
     } else {
       atomicOr(status, ST_OVERFLOW);
     }
@@ -180,17 +179,17 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
 __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
-  s.spos = reinterpret_cast<unsigned *>(smem + kTile * 8);
-  s.cnt = s.spos + kTile;
-  s.base = s.cnt + nb_cap;
-  s.red = s.base + nb_cap;
-  s.sdst = reinterpret_cast<unsigned short *>(s.red + kTT / 32 + 2);
+  s.dbase = s.sorted + kTile;
+  s.stag = reinterpret_cast<unsigned *>(s.dbase + nb_cap);
+  s.cnt = s.stag + kTile;
+  s.lim = s.cnt + nb_cap;
+  s.red = s.lim + nb_cap;
   return s;
 }
 
 static constexpr size_t split_smem_bytes(unsigned nb_cap) {
-  return (size_t)kTile * 8 + (size_t)kTile * 4 + 2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 +
-         (size_t)kTile * 2;
+  return (size_t)kTile * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 + 2 * (size_t)nb_cap * 4 +
+         (kTT / 32 + 2) * 4 + 8;
 }
 
 // ---------------------------------------------------------------------------
