@@ -3,27 +3,28 @@
 //
 // A key needs e^{1/gamma} level probes on average but up to L; a warp that
 // kept 32 keys in lock-step would idle most lanes while its slowest key walks
-// down the levels.  Instead each warp copies a chunk of 32 * kPerLane keys
-// into shared memory, and every lane works through its own kPerLane keys
-// with kSlots independent query slots: each round every active slot probes
-// its current level (one 8-byte load of A); a slot whose bit is set computes
-// its rank and writes the result over its key in shared memory; a retired
-// slot takes the lane's next key.  Lanes only meet again at the end of the
-// chunk, which is then written out with coalesced stores.
+// down the levels.  Instead every lane owns kSlots independent query slots,
+// each with its own (key, output index, level).  Each round every active slot
+// probes its current level (one 8-byte load of A); a slot whose bit is set
+// computes its rank and retires, the others move to the next level, and
+// retired slots are refilled from the warp's stream of input keys.  So lanes
+// stay busy and each lane keeps kSlots independent loads in flight.
 //
-// Rank of global bit g: rank[g / 512] plus the ones of the words of g's
-// 512-bit block before g (loaded as 16-byte pairs, only those needed).
+// A slot whose bit is set does not compute its rank on the spot (that would
+// run the rank code with only the lucky lanes active): it queues (g, word,
+// output index) in a per-warp shared-memory list, and once 32 are queued the
+// whole warp computes 32 ranks together.  Rank of global bit g: rank[g / 512]
+// plus the ones of the words of g's 512-bit block before g (loaded as 16-byte
+// pairs, only those needed).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 
 namespace bbh {
 
-static constexpr int kLookupWarps = 8;
-static constexpr int kLookupThreads = kLookupWarps * 32;
+static constexpr int kLookupThreads = 256;
 static constexpr int kSlots = 2;
-static constexpr int kPerLane = 32;
-static constexpr unsigned kChunk = 32 * kPerLane;  // keys per warp chunk
+static constexpr unsigned kChunk = 32 * 64;  // keys a warp takes from the input at a time
 
 struct LevelTable {
   u64 s[MPHF_MAX_LEVELS];
@@ -74,44 +75,80 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
+struct RankJob {
+  u64 g, w, idx;
+};
+
 __global__ void __launch_bounds__(kLookupThreads)
 k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
-  extern __shared__ __align__(16) u64 lbuf[];  // [kLookupWarps][kChunk]
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
+  __shared__ RankJob jobs[kLookupThreads / 32][32 * (kSlots + 1)];
   for (unsigned i = threadIdx.x; i < a.L_used; i += kLookupThreads) {
     ts[i] = t.s[i];
     tm[i] = t.m[i];
     toff[i] = t.off[i];
   }
   __syncthreads();
-  const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  u64 *buf = lbuf + (u64)wib * kChunk;
+
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  RankJob *q = jobs[threadIdx.x >> 5];
+  unsigned nq = 0;  // queued rank jobs of this warp (warp-uniform)
   const u64 nchunks = (n + kChunk - 1) / kChunk;
+  const u64 warp_id = ((u64)blockIdx.x * kLookupThreads + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * kLookupThreads) >> 5;
-  for (u64 chunk = ((u64)blockIdx.x * kLookupThreads + threadIdx.x) >> 5; chunk < nchunks;
-       chunk += nwarps) {
-    const u64 base = chunk * kChunk;
-    const unsigned cnt = (unsigned)min((u64)kChunk, n - base);
-    for (unsigned i = lane; i < cnt; i += 32) buf[i] = __ldcs(keys + base + i);
-    __syncwarp();
-    // this lane's keys: j = lane + 32 k, k < kPerLane, j < cnt
-    unsigned nxt = lane;
-    u64 x[kSlots];
-    unsigned jj[kSlots], lvl[kSlots];
-    bool act[kSlots];
+  u64 chunk = warp_id;
+  u64 cursor = chunk * kChunk;
+  u64 cend = chunk < nchunks ? min(cursor + kChunk, n) : cursor;
+  bool more = chunk < nchunks;
+
+  u64 x[kSlots], idx[kSlots];
+  unsigned lvl[kSlots];
+  bool act[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; s++) {
+    act[s] = false;
+    lvl[s] = 0;
+    x[s] = 0;
+    idx[s] = 0;
+  }
+
+  for (;;) {
+    // refill retired slots from the warp's input stream (warp-uniform control)
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
-      act[s] = nxt < cnt;
-      jj[s] = nxt;
-      lvl[s] = 0;
-      x[s] = act[s] ? buf[nxt] : 0;
-      nxt += 32;
+      unsigned need = __ballot_sync(0xffffffffu, !act[s]);
+      while (need && more) {
+        if (cursor >= cend) {
+          chunk += nwarps;
+          if (chunk >= nchunks) {
+            more = false;
+            break;
+          }
+          cursor = chunk * kChunk;
+          cend = min(cursor + kChunk, n);
+        }
+        const u64 avail = cend - cursor;
+        const unsigned r = __popc(need & lt);
+        const bool mine = ((need >> lane) & 1u) && (u64)r < avail;
+        if (mine) {
+          idx[s] = cursor + r;
+          x[s] = __ldcs(keys + cursor + r);
+          lvl[s] = 0;
+          act[s] = true;
+        }
+        const unsigned taken = __ballot_sync(0xffffffffu, mine);
+        need &= ~taken;
+        cursor += __popc(taken);
+      }
     }
-    for (;;) {
-      bool any = false;
+    bool any = false;
 #pragma unroll
-      for (int s = 0; s < kSlots; s++) any |= act[s];
-      if (!any) break;
+    for (int s = 0; s < kSlots; s++) any |= act[s];
+    const bool warp_any = __any_sync(0xffffffffu, any);
+
+    if (warp_any) {
+      // one probe per active slot: issue all loads, then resolve
       u64 g[kSlots], w[kSlots];
 #pragma unroll
       for (int s = 0; s < kSlots; s++) {
@@ -123,30 +160,33 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
       }
 #pragma unroll
       for (int s = 0; s < kSlots; s++) {
-        if (act[s]) {
-          bool done = false;
-          u64 r = 0;
-          if ((w[s] >> (g[s] & 63)) & 1ull) {
-            r = rank_before(a.A, a.rank, g[s], w[s]);
-            done = true;
-          } else if (++lvl[s] >= a.L_used) {
-            r = a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND;
-            done = true;
-          }
-          if (done) {
-            buf[jj[s]] = r;  // result replaces the key
-            act[s] = nxt < cnt;
-            jj[s] = nxt;
-            lvl[s] = 0;
-            if (act[s]) x[s] = buf[nxt];
-            nxt += 32;
-          }
+        const bool hit = act[s] && ((w[s] >> (g[s] & 63)) & 1ull);
+        const unsigned hb = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          RankJob &j = q[nq + __popc(hb & lt)];
+          j.g = g[s];
+          j.w = w[s];
+          j.idx = idx[s];
+          act[s] = false;
+        } else if (act[s] && ++lvl[s] >= a.L_used) {
+          __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
+          act[s] = false;
         }
+        nq += __popc(hb);
       }
     }
+    // drain queued ranks 32 at a time with every lane busy (all of them at the end)
     __syncwarp();
-    for (unsigned i = lane; i < cnt; i += 32) __stcs(out + base + i, buf[i]);
-    __syncwarp();
+    while (nq >= 32 || (!warp_any && nq > 0)) {
+      const unsigned take = nq < 32 ? nq : 32;
+      nq -= take;
+      if (lane < take) {
+        const RankJob j = q[nq + lane];
+        __stcs(out + j.idx, rank_before(a.A, a.rank, j.g, j.w));
+      }
+      __syncwarp();
+    }
+    if (!warp_any) break;
   }
 }
 
@@ -165,22 +205,17 @@ static void fill_tables(const mphf_t *h, LookupArgs &a, LevelTable &t) {
 }
 
 int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t s) {
-  static bool attr = false;
-  const size_t smem = (size_t)kLookupWarps * kChunk * 8;
-  if (!attr) {
-    MPHF_CUDA(cudaFuncSetAttribute(k_lookup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   LookupArgs a;
   LevelTable t;
   fill_tables(h, a, t);
-  const u64 chunks = (n + kChunk - 1) / kChunk;
-  u64 grid = (chunks + kLookupWarps - 1) / kLookupWarps;
-  const u64 maxb = (u64)sm_count() * 3;
+  const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
+  const unsigned per_block = kLookupThreads / 32;
+  unsigned grid = (unsigned)((nwarps_needed + per_block - 1) / per_block);
+  const unsigned maxb = (unsigned)sm_count() * 8;
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  k_lookup<<<(unsigned)grid, kLookupThreads, smem, s>>>(keys, n, out, a, t);
+  k_lookup<<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
