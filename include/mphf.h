@@ -105,6 +105,12 @@ int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n, uint64
  * 0 for an empty function or NULL. */
 double mphf_bits_per_key(const mphf_t *h);
 
+/* Device memory the handle holds, in bytes: A, the rank table (each 64-bit
+ * checkpoint of Sec. 3.1 is stored beside a 64-bit word of seven 9-bit in-block
+ * prefix counts that speed up queries, so 16 bytes per 512 bits) and the
+ * fallback.  0 for NULL. */
+uint64_t mphf_device_bytes(const mphf_t *h);
+
 /* Release a handle and its device memory; NULL is a no-op. */
 void mphf_free(mphf_t *h);
 

@@ -189,7 +189,20 @@ int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count) {
   return copy_out(h, h->A, h_words, count, h ? h->M / 64 : 0);
 }
 int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
-  return copy_out(h, h->rank, h_rank, count, h ? h->n_rank : 0);
+  // checkpoints are every other word of the device table
+  if (!h || (count && !h_rank) || count != h->n_rank) return MPHF_EINVAL;
+  if (!count) return MPHF_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  cudaError_t e = cudaMemcpy2D(h_rank, 8, h->rank.p, 16, 8, count, cudaMemcpyDeviceToHost);
+  if (prev != h->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2D(rank)");
+  return MPHF_OK;
+}
+
+uint64_t mphf_device_bytes(const mphf_t *h) {
+  return h ? (uint64_t)(h->A.bytes + h->rank.bytes + h->fb.bytes) : 0;
 }
 int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count) {
   return copy_out(h, h->fb, h_keys, count, h ? h->n_fb : 0);

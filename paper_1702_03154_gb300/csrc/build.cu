@@ -428,7 +428,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
 
   // Final A = A_0 || arena, then the rank checkpoints.
   TRY(dev_alloc(h->A, h->M / 64 * 8, st));
-  TRY(dev_alloc(h->rank, h->n_rank * 8, st));
+  TRY(dev_alloc(h->rank, h->n_rank * 16, st));
   if (cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 64 * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(A0)");
     goto fail;

@@ -129,8 +129,9 @@ struct DevBuf {
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
 void dev_free(DevBuf &b, cudaStream_t s);
 
-// Rank table over A (rank.cu): rank[b] = ones in bits [0, 512 b).
-int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_total,
+// Rank table over A (rank.cu): rank2[2b] = ones in bits [0, 512 b) (the
+// paper's checkpoint), rank2[2b+1] = in-block prefix counts of words 1..7.
+int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_total,
                      cudaStream_t s);
 // Sort n keys ascending in place and flag equal neighbours (sort.cu).
 int sort_fallback(u64 *keys, u64 n, unsigned int *d_dup_flag, cudaStream_t s);
@@ -152,7 +153,7 @@ struct mphf {
   uint64_t n_rank = 0;   // ceil(M / 512)
   uint64_t n_fb = 0;
   bbh::DevBuf A;        // M / 64 words
-  bbh::DevBuf rank;     // n_rank words
+  bbh::DevBuf rank;     // 2 n_rank words: checkpoint, in-block prefix counts
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;
   int path = 0;          // 1 bucketed construction, 2 unbucketed

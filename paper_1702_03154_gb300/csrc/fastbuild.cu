@@ -925,7 +925,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
       goto fail;
     }
     FTRY(dev_alloc(h->A, h->M / 8, st));
-    FTRY(dev_alloc(h->rank, h->n_rank * 8, st));
+    FTRY(dev_alloc(h->rank, h->n_rank * 16, st));
     FCUDA(cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 8, cudaMemcpyDeviceToDevice, st));
     if (h->M > m0)
       FCUDA(cudaMemcpyAsync((u64 *)h->A.p + m0 / 64, sc.arena.p, (h->M - m0) / 8,

@@ -10,12 +10,9 @@
 // retired slots are refilled from the warp's stream of input keys.  So lanes
 // stay busy and each lane keeps kSlots independent loads in flight.
 //
-// A slot whose bit is set does not compute its rank on the spot (that would
-// run the rank code with only the lucky lanes active): it queues (g, word,
-// output index) in a per-warp shared-memory list, and once 32 are queued the
-// whole warp computes 32 ranks together.  Rank of global bit g: rank[g / 512]
-// plus the ones of the words of g's 512-bit block before g (loaded as 16-byte
-// pairs, only those needed).
+// Rank of global bit g: the checkpoint of its 512-bit block plus the in-block
+// prefix count of its word (both in one 16-byte entry of the rank table) plus
+// the ones of its own word below g.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -42,26 +39,16 @@ struct LookupArgs {
 };
 
 // Ones of A strictly before global bit g; w = A[g / 64] (already loaded).
-__device__ __forceinline__ u64 rank_before(const u64 *__restrict__ A, const u64 *__restrict__ rank,
-                                           u64 g, u64 w) {
+// rank2[2b] is the checkpoint of block b = g / 512, rank2[2b+1] holds the ones
+// of words 0..k-1 of the block for k = 1..7 in 9-bit fields.
+__device__ __forceinline__ u64 rank_before(const u64 *__restrict__ rank2, u64 g, u64 w) {
   const u64 b = g >> 9;
   const unsigned k = (unsigned)(g >> 6) & 7u;  // word of g inside its block
-  const uint4 *blk = reinterpret_cast<const uint4 *>(A + (b << 3));
-  u64 r = __ldg(rank + b);
-  uint4 v[4];
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    v[j] = make_uint4(0, 0, 0, 0);
-    if ((unsigned)(2 * j) < k) v[j] = __ldg(blk + j);
-  }
-  unsigned c = 0;
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    unsigned lo = (unsigned)(2 * j) < k ? 0xffffffffu : 0u;
-    unsigned hi = (unsigned)(2 * j + 1) < k ? 0xffffffffu : 0u;
-    c += __popc(v[j].x & lo) + __popc(v[j].y & lo) + __popc(v[j].z & hi) + __popc(v[j].w & hi);
-  }
-  return r + c + __popcll(w & ((1ull << (g & 63)) - 1ull));
+  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rank2) + b);
+  const u64 abs = ((u64)v.y << 32) | v.x;
+  const u64 rel = ((u64)v.w << 32) | v.z;
+  const u64 inblk = k ? (rel >> (9 * (k - 1))) & 511ull : 0ull;
+  return abs + inblk + __popcll(w & ((1ull << (g & 63)) - 1ull));
 }
 
 __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
@@ -75,14 +62,9 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
-struct RankJob {
-  u64 g, w, idx;
-};
-
 __global__ void __launch_bounds__(kLookupThreads)
 k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
-  __shared__ RankJob jobs[kLookupThreads / 32][32 * (kSlots + 1)];
   for (unsigned i = threadIdx.x; i < a.L_used; i += kLookupThreads) {
     ts[i] = t.s[i];
     tm[i] = t.m[i];
@@ -92,8 +74,6 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
 
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  RankJob *q = jobs[threadIdx.x >> 5];
-  unsigned nq = 0;  // queued rank jobs of this warp (warp-uniform)
   const u64 nchunks = (n + kChunk - 1) / kChunk;
   const u64 warp_id = ((u64)blockIdx.x * kLookupThreads + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * kLookupThreads) >> 5;
@@ -145,48 +125,30 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
     bool any = false;
 #pragma unroll
     for (int s = 0; s < kSlots; s++) any |= act[s];
-    const bool warp_any = __any_sync(0xffffffffu, any);
+    if (!__any_sync(0xffffffffu, any)) break;
 
-    if (warp_any) {
-      // one probe per active slot: issue all loads, then resolve
-      u64 g[kSlots], w[kSlots];
+    // one probe per active slot: issue all loads, then resolve
+    u64 g[kSlots], w[kSlots];
 #pragma unroll
-      for (int s = 0; s < kSlots; s++) {
-        if (act[s]) {
-          const unsigned d = lvl[s];
-          g[s] = toff[d] + level_pos(x[s], ts[d], tm[d]);
-          w[s] = __ldg(a.A + (g[s] >> 6));
-        }
+    for (int s = 0; s < kSlots; s++) {
+      if (act[s]) {
+        const unsigned d = lvl[s];
+        g[s] = toff[d] + level_pos(x[s], ts[d], tm[d]);
+        w[s] = __ldg(a.A + (g[s] >> 6));
       }
+    }
 #pragma unroll
-      for (int s = 0; s < kSlots; s++) {
-        const bool hit = act[s] && ((w[s] >> (g[s] & 63)) & 1ull);
-        const unsigned hb = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          RankJob &j = q[nq + __popc(hb & lt)];
-          j.g = g[s];
-          j.w = w[s];
-          j.idx = idx[s];
+    for (int s = 0; s < kSlots; s++) {
+      if (act[s]) {
+        if ((w[s] >> (g[s] & 63)) & 1ull) {
+          __stcs(out + idx[s], rank_before(a.rank, g[s], w[s]));
           act[s] = false;
-        } else if (act[s] && ++lvl[s] >= a.L_used) {
+        } else if (++lvl[s] >= a.L_used) {
           __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
           act[s] = false;
         }
-        nq += __popc(hb);
       }
     }
-    // drain queued ranks 32 at a time with every lane busy (all of them at the end)
-    __syncwarp();
-    while (nq >= 32 || (!warp_any && nq > 0)) {
-      const unsigned take = nq < 32 ? nq : 32;
-      nq -= take;
-      if (lane < take) {
-        const RankJob j = q[nq + lane];
-        __stcs(out + j.idx, rank_before(a.A, a.rank, j.g, j.w));
-      }
-      __syncwarp();
-    }
-    if (!warp_any) break;
   }
 }
 

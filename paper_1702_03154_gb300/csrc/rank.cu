@@ -1,9 +1,17 @@
 // rank.cu -- rank checkpoints over the concatenated bit array A (Sec. 3.1):
 // one 64-bit counter per 512 bits, rank[b] = number of ones in bits [0, 512 b).
 //
+// Each checkpoint is stored next to a second 64-bit word holding the seven
+// in-block prefix counts of the block's words 1..7 (9 bits each: the ones of
+// words 0..k-1 for word k), the "rank9" layout of Vigna ("Broadword
+// implementation of rank/select queries", WEA 2008).  A query then needs one
+// 16-byte load and one popcount instead of popcounting up to eight words.  The
+// checkpoints themselves are exactly the paper's.
+//
 // Three passes: (1) each thread popcounts one 512-bit block (four 16-byte
-// loads) and the CTA turns its 256 counts into exclusive prefixes; (2) one CTA
-// scans the per-CTA totals; (3) each checkpoint adds its CTA's prefix.
+// loads), forms its relative counts, and the CTA turns its 256 block counts
+// into exclusive prefixes; (2) one CTA scans the per-CTA totals; (3) each
+// checkpoint adds its CTA's prefix.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -40,26 +48,39 @@ __device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64 *total) {
 }
 
 __global__ void __launch_bounds__(kRankThreads)
-k_rank_blocks(const u64 *__restrict__ A, u64 nwords, u64 *__restrict__ rank, u64 nrank,
+k_rank_blocks(const u64 *__restrict__ A, u64 nwords, u64 *__restrict__ rank2, u64 nrank,
               u64 *__restrict__ cta_sums) {
   u64 b = (u64)blockIdx.x * kRankThreads + threadIdx.x;
-  u64 c = 0;
+  u64 c = 0, rel = 0;
   if (b < nrank) {
     u64 w0 = b * 8;
+    unsigned pc[8];
     if (w0 + 8 <= nwords) {
       const uint4 *p = reinterpret_cast<const uint4 *>(A + w0);
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         uint4 v = __ldg(p + j);
-        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        pc[2 * j] = __popc(v.x) + __popc(v.y);
+        pc[2 * j + 1] = __popc(v.z) + __popc(v.w);
       }
     } else {
-      for (u64 w = w0; w < nwords; w++) c += __popcll(__ldg(A + w));
+#pragma unroll
+      for (int j = 0; j < 8; j++) pc[j] = (w0 + j < nwords) ? __popcll(__ldg(A + w0 + j)) : 0u;
     }
+    unsigned run = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (j) rel |= (u64)run << (9 * (j - 1));
+      run += pc[j];
+    }
+    c = run;
   }
   u64 total;
   u64 ex = block_exclusive_scan(c, &total);
-  if (b < nrank) rank[b] = ex;
+  if (b < nrank) {
+    rank2[2 * b] = ex;
+    rank2[2 * b + 1] = rel;
+  }
   if (threadIdx.x == 0) cta_sums[blockIdx.x] = total;
 }
 
@@ -91,12 +112,12 @@ k_scan_sums(u64 *__restrict__ sums, u64 count, u64 *__restrict__ d_total) {
 }
 
 __global__ void __launch_bounds__(kRankThreads)
-k_rank_add(u64 *__restrict__ rank, u64 nrank, const u64 *__restrict__ cta_prefix) {
+k_rank_add(u64 *__restrict__ rank2, u64 nrank, const u64 *__restrict__ cta_prefix) {
   u64 b = (u64)blockIdx.x * kRankThreads + threadIdx.x;
-  if (b < nrank) rank[b] += cta_prefix[blockIdx.x];
+  if (b < nrank) rank2[2 * b] += cta_prefix[blockIdx.x];
 }
 
-int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_total,
+int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_total,
                      cudaStream_t s) {
   if (nrank == 0) {
     if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
@@ -109,7 +130,7 @@ int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_tota
   if (rc != MPHF_OK) return rc;
   {
     LaunchScope ls("rank_blocks", s);
-    k_rank_blocks<<<(unsigned)ctas, kRankThreads, 0, s>>>(A, nwords, rank, nrank, (u64 *)sums.p);
+    k_rank_blocks<<<(unsigned)ctas, kRankThreads, 0, s>>>(A, nwords, rank2, nrank, (u64 *)sums.p);
   }
   {
     LaunchScope ls("rank_scan", s);
@@ -117,7 +138,7 @@ int build_rank_table(const u64 *A, u64 nwords, u64 *rank, u64 nrank, u64 *d_tota
   }
   if (ctas > 1) {
     LaunchScope ls("rank_add", s);
-    k_rank_add<<<(unsigned)ctas, kRankThreads, 0, s>>>(rank, nrank, (const u64 *)sums.p);
+    k_rank_add<<<(unsigned)ctas, kRankThreads, 0, s>>>(rank2, nrank, (const u64 *)sums.p);
   }
   cudaError_t e = cudaGetLastError();
   dev_free(sums, s);

@@ -66,6 +66,7 @@ def lib():
         "mphf_lookup": ([vp, vp, u64, vp, vp], i32),
         "mphf_lookup_host": ([vp, vp, u64, vp, vp], i32),
         "mphf_bits_per_key": ([vp], dbl),
+        "mphf_device_bytes": ([vp], u64),
         "mphf_free": ([vp], None),
         "mphf_num_keys": ([vp], u64),
         "mphf_num_levels": ([vp], u32),
@@ -186,6 +187,10 @@ class MPHF:
     # -- structure ----------------------------------------------------------
     def bits_per_key(self) -> float:
         return lib().mphf_bits_per_key(self._h)
+
+    def device_bytes(self) -> int:
+        """Device memory held by the function (A, rank table with in-block counts, fallback)."""
+        return lib().mphf_device_bytes(self._h)
 
     @property
     def build_path(self) -> int:
