@@ -165,17 +165,28 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm
 def algorithmic_bytes(h, name: str) -> int:
-    """Algorithmic DRAM bytes of all launches of one kernel in one step."""
+    """Algorithmic DRAM bytes of all launches of one kernel in one build (or lookup).
+
+    Per key of level d the method reads the key once for ArrayFill and once for
+    the compaction, and writes each survivor once (8 B each); A_d is written
+    once (m_d / 8 B).  Moving F_0 into position buckets costs one read and one
+    write of every key.  A lookup reads its key and writes its index.
+    """
     sizes = h.level_sizes()          # n_0 .. n_last, n_fb
     lv = h.levels()
+    nd = sizes[:-1]
+    if name == "partition":
+        return 16 * sizes[0]
+    if name in ("fill_buckets",):
+        return sum(8 * n + m // 8 for (n, m, _, _) in lv)
+    if name in ("compact_buckets", "compact"):
+        return sum(8 * nd[d] + 8 * sizes[d + 1] for d in range(len(nd)))
     if name == "fill":
-        return 8 * sizes[0]          # read every key of F_0
-    if name == "compact":            # read F_d, write F_{d+1}
-        return sum(8 * sizes[d] + 8 * sizes[d + 1] for d in range(len(sizes) - 1) if sizes[d + 1])
-    if name == "extract":            # read AC (2 m_d bits), write A_d (m_d bits), zero AC
-        return sum(5 * m // 8 for (_, m, _, _) in lv)
+        return 8 * sizes[0]
+    if name == "extract":
+        return sum(m // 8 for (_, m, _, _) in lv)
     if name == "lookup":
-        return 16 * sizes[0]         # key in, index out
+        return 16 * sizes[0]
     return 0
 
 

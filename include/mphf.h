@@ -88,6 +88,40 @@ int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t l
                     uint64_t seed, void *stream, mphf_t **out);
 
 /*
+ * Build S independent functions at once, one per key set (the same method
+ * and conventions as mphf_build, applied to each set separately; set s gets
+ * exactly the function mphf_build would give it with the same arguments).
+ *   d_keys     device array holding the sets back to back.
+ *   h_offsets  host array of S + 1 non-decreasing indices into d_keys: set s
+ *              is d_keys[h_offsets[s] .. h_offsets[s+1]).
+ *   out        host array of S handles, each released with mphf_free (their
+ *              device memory is one shared block, returned when the last is
+ *              freed).
+ * All sets advance level by level together (one launch per phase per level
+ * for all sets, recorded once as a CUDA graph and replayed); sets of at most
+ * 16384 keys run every level in one thread block.  Synchronous w.r.t. stream.
+ * Errors as mphf_build; on error no handle is returned.  Builds through this
+ * call are serialised within a process (they share a device workspace, kept
+ * between calls; see mphf_workspace_release).
+ */
+int mphf_build_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S, double gamma,
+                       uint32_t levels, uint64_t seed, void *stream, mphf_t **out);
+
+/* Time the candidate bucket widths of mphf_build_batched on this input and keep
+ * the fastest for inputs of the same size class (process-wide).  The functions
+ * built do not depend on the choice.  *best_ms receives the winning time. */
+int mphf_autotune_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S,
+                          double gamma, uint32_t levels, uint64_t seed, void *stream,
+                          double *best_ms);
+
+/* Test hook: scales the bucket capacities of mphf_build_batched (default 1;
+ * values < 1 make sets overflow and exercise their individual rebuild). */
+int mphf_batched_debug_config(double cap_scale);
+
+/* Free the device workspace kept by mphf_build_batched. */
+void mphf_workspace_release(void);
+
+/*
  * Query n keys (Algorithm 3, minimal index of Sec. 2.2.3).
  *   d_keys  device array of n keys, any 8-byte alignment.
  *   d_out   device array of n uint64 results (caller-allocated).
@@ -131,7 +165,8 @@ int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
 
 /* Which construction path built h: 1 = bucketed (shared-memory ArrayFill),
  * 2 = unbucketed (L2 atomics; taken when a bound of the bucketed path is
- * exceeded, e.g. many duplicate keys).  Both give identical results. */
+ * exceeded, e.g. many duplicate keys), 3 = mphf_build_batched.  All give
+ * identical results. */
 int mphf_build_path(const mphf_t *h);
 /* Test hook, process-wide: path 0 = bucketed with automatic fallback (default),
  * 1 = unbucketed only; cap_scale (default 1) scales the bucket capacities, so a

@@ -63,6 +63,8 @@ void launch_begin(const char *name, cudaStream_t s) {
   t_open = (int)g_prof.size() - 1;
 }
 
+void add_launches(u64 n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void launch_end(cudaStream_t s) {
   if (t_open < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -143,9 +145,13 @@ void mphf_free(mphf_t *h) {
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
-  dev_free(h->A, 0);
-  dev_free(h->rank, 0);
-  dev_free(h->fb, 0);
+  if (h->shared) {
+    release_shared(h->shared);
+  } else {
+    dev_free(h->A, 0);
+    dev_free(h->rank, 0);
+    dev_free(h->fb, 0);
+  }
   if (prev != h->device) cudaSetDevice(prev);
   delete h;
 }

@@ -1,0 +1,1187 @@
+// batched.cu -- many independent key sets built together.
+//
+// Every set gets exactly the function mphf_build would give it (same seed,
+// same conventions); only the scheduling differs.  All sets advance level by
+// level together:
+//   * sets with at most T keys never leave shared memory: one CTA per set runs
+//     all of its levels (k_btail, the same single-CTA loop as the plain build);
+//   * larger sets are kept in position-range buckets (global bucket list:
+//     bucket = (set, index)); one launch per phase and level processes the
+//     buckets of all sets: ArrayFill in shared memory (k_bfill), sizing of the
+//     next level of every set (k_bfinish, one CTA, scans over sets) and the
+//     compaction of the survivors into their next-level buckets (k_bcompact);
+//     a set whose level has at most T keys moves to its flat range and joins
+//     the single-CTA tail.
+// The level loop is recorded once as a CUDA graph and replayed.  Bucket width
+// (and so the number of buckets per set) is a tunable chosen by an autotuner.
+// A set that exceeds any of its reserved bounds is rebuilt on its own with
+// mphf_build, so results never depend on these choices.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "fastbuild.cuh"
+
+namespace bbh {
+
+enum : unsigned { LM_FAILED = 4 };
+
+struct BLvl {     // one set's state at one level of the bucketed loop
+  u64 n, m, off;  // |F_d|, |A_d| bits, first bit of A_d in the set's A
+  u64 P, B;       // bucket width (power of two), buckets
+  u64 bbase;      // first global bucket
+  u64 cap, aoff;  // slots per bucket, arena index of the set's bucket 0
+  u64 weight;     // ones of A_d
+  unsigned mode, sh;
+};
+
+struct BSet {     // per set
+  u64 key_off, n0, m0;
+  u64 a0_off;             // word offset of A_{s,0} in the A0 arena
+  u64 at_off, at_words;   // levels >= 1: word offset / capacity in the tail arena
+  u64 flat_off, flat_cap; // flat range (tail input, then fallback)
+  u64 n_flat;             // keys appended to the flat range
+  u64 n_fb;               // fallback keys
+  u64 rank_total;         // ones of the set's A (rank table check)
+  unsigned levels_used, status, small, tail_level;
+};
+
+struct BCfg {
+  double gamma;
+  uint32_t L;
+  u64 seed;
+  unsigned S;
+  const u64 *keys;
+  BSet *sets;
+  BLvl *lvl[2];                      // level state by d & 1
+  unsigned *bset[2], *bidx[2];       // bucket descriptors by d & 1
+  u64 *cnt[2];                       // bucket counters by d & 1
+  u64 *btotal;                       // [2] buckets of the level held in slot d & 1
+  u64 bcap;                          // descriptor / counter capacity
+  u64 *X[2];                         // key arenas by d & 1
+  unsigned *XP[2];                   // position arenas
+  u64 acap[2];
+  u64 *flat;
+  u64 *A0, *arena;
+  FLevel *hist;                      // [S][L + 1]
+  u64 T, Pmin, Pmax;
+  u64 Bset_max;
+  double cap_scale;
+  unsigned *status;                  // global (any overflow of a shared bound)
+};
+
+__host__ __device__ inline void size_set_level(BLvl &lv, u64 n, const BCfg &c) {
+  lv.n = n;
+  lv.m = level_bits(n, c.gamma);
+  u64 want = ceil_div(lv.m, c.Bset_max);  // keep B <= Bset_max
+  u64 P = c.Pmin;
+  while (P < want && P < c.Pmax) P <<= 1;
+  // spread a set over several buckets where it is cheap to do so
+  while (P > c.Pmin && ceil_div(lv.m, P) < 4 && P > 4096) P >>= 1;
+  lv.P = P;
+  lv.sh = ilog2_u64(P);
+  lv.B = ceil_div(lv.m, P);
+  double mean = (double)n * (double)P / (double)lv.m;
+  u64 cap = (u64)(c.cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));
+  lv.cap = (cap + 3) & ~3ull;
+}
+
+__device__ __forceinline__ u64 *set_level_words(const BCfg &c, const BSet &st, int d, u64 off) {
+  return d == 0 ? c.A0 + st.a0_off : c.arena + st.at_off + ((off - st.m0) >> 6);
+}
+
+__device__ __forceinline__ void fail_set(BSet *st) { atomicOr(&st->status, ST_OVERFLOW); }
+
+// ---------------------------------------------------------------------------
+// Level 0: partition the keys of the large sets into their position buckets.
+// ---------------------------------------------------------------------------
+struct PartDest {
+  const unsigned *bset, *bidx;
+  const BLvl *lvl;
+  u64 *cnt;
+  u64 gb0;
+  __device__ __forceinline__ DestRun operator()(unsigned i) const {
+    const u64 gb = gb0 + i;
+    const BLvl &lv = lvl[bset[gb]];
+    return DestRun{cnt + gb, lv.aoff + (u64)bidx[gb] * lv.cap, lv.cap};
+  }
+};
+
+__global__ void __launch_bounds__(kTT, 2)
+k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned t_sa, t_sb;
+  __shared__ u64 t_gb0;
+  __shared__ unsigned t_nb;
+  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  const u64 s0 = level_seed(c.seed, 0);
+  const u64 ntiles = ceil_div(total, kTile);
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const u64 t0 = t * kTile, t1 = min(t0 + kTile, total);
+    if (threadIdx.x == 0) {
+      // sets overlapping [t0, t1): key_off is non-decreasing with S + 1 entries
+      unsigned lo = 0, hi = c.S;  // first s with key_off[s + 1] > t0
+      while (lo < hi) {
+        unsigned mid = (lo + hi) >> 1;
+        if (key_off[mid + 1] > t0) hi = mid;
+        else lo = mid + 1;
+      }
+      unsigned sb = lo;
+      while (sb + 1 < c.S && key_off[sb + 1] < t1) sb++;
+      t_sa = lo;
+      t_sb = sb;
+      // global buckets of the large sets in [sa, sb] are consecutive
+      u64 g0 = ~0ull, g1 = 0;
+      for (unsigned s = lo; s <= sb; s++) {
+        const BLvl &lv = c.lvl[0][s];
+        if (lv.mode == LM_BUCKETED) {
+          g0 = min(g0, lv.bbase);
+          g1 = max(g1, lv.bbase + lv.B);
+        }
+      }
+      t_gb0 = g0 == ~0ull ? 0 : g0;
+      t_nb = g0 == ~0ull ? 0u : (unsigned)(g1 - g0);
+      if (g0 != ~0ull && g1 - g0 > kBmax) {
+        for (unsigned s = lo; s <= sb; s++)
+          if (c.lvl[0][s].mode == LM_BUCKETED) fail_set(&c.sets[s]);
+        t_nb = 0;
+      }
+    }
+    __syncthreads();
+    const unsigned nb = t_nb;
+    if (nb == 0) {
+      __syncthreads();
+      continue;
+    }
+    u64 x[kKPT];
+    unsigned dst[kKPT], lp[kKPT];
+    bool ok[kKPT];
+    unsigned s = t_sa;
+#pragma unroll
+    for (int k = 0; k < kKPT; k++) {
+      const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+      ok[k] = false;
+      x[k] = 0;
+      dst[k] = 0;
+      lp[k] = 0;
+      if (i < t1) {
+        while (key_off[s + 1] <= i) s++;  // monotone in k
+        const BLvl &lv = c.lvl[0][s];
+        if (lv.mode == LM_BUCKETED) {
+          x[k] = __ldcs(c.keys + i);
+          const u64 p = level_pos(x[k], s0, lv.m);
+          dst[k] = (unsigned)(lv.bbase + (p >> lv.sh) - t_gb0);
+          lp[k] = (unsigned)(p & (lv.P - 1));
+          ok[k] = true;
+        }
+      }
+    }
+    multisplit_write<true>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
+                           PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], t_gb0}, c.status);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ArrayFill of one level for the buckets of every set.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTT, 2) k_bfill(int d, BCfg c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sl = d & 1;
+  const u64 nbk = c.btotal[sl];
+  unsigned *hit = reinterpret_cast<unsigned *>(smem);
+  __shared__ int skip;
+  for (u64 gb = blockIdx.x; gb < nbk; gb += gridDim.x) {
+    const unsigned s = c.bset[sl][gb];
+    const unsigned j = c.bidx[sl][gb];
+    BSet *st = &c.sets[s];
+    const BLvl lv = c.lvl[sl][s];
+    __syncthreads();
+    if (threadIdx.x == 0) skip = (lv.mode != LM_BUCKETED || st->status) ? 1 : 0;
+    __syncthreads();
+    if (skip) continue;  // one decision for the whole CTA
+    const unsigned Pw = (unsigned)(lv.P >> 5);
+    unsigned *col = hit + Pw;
+    for (unsigned i = threadIdx.x; i < 2 * Pw; i += kTT) hit[i] = 0;
+    __syncthreads();
+    const u64 c0 = c.cnt[sl][gb];
+    if (c0 > lv.cap && threadIdx.x == 0) fail_set(st);
+    const u64 nk = min(c0, lv.cap);
+    const unsigned *pb = c.XP[sl] + lv.aoff + (u64)j * lv.cap;
+    const uint4 *pb4 = reinterpret_cast<const uint4 *>(pb);
+    for (u64 i = threadIdx.x; 4 * i < nk; i += kTT) {
+      unsigned q[4];
+      if (4 * i + 3 < nk) {
+        const uint4 v = __ldcs(pb4 + i);
+        q[0] = v.x;
+        q[1] = v.y;
+        q[2] = v.z;
+        q[3] = v.w;
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 4; jj++) q[jj] = (4 * i + jj < nk) ? __ldcs(pb + 4 * i + jj) : ~0u;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; jj++) {
+        const unsigned p = q[jj];
+        if (p != ~0u) {
+          const unsigned bit = 1u << (p & 31);
+          const unsigned old = atomicOr(hit + (p >> 5), bit);
+          if (old & bit) atomicOr(col + (p >> 5), bit);
+        }
+      }
+    }
+    __syncthreads();
+    const bool fits = d == 0 || ((lv.off - st->m0) >> 6) + (lv.m >> 6) <= st->at_words;
+    u64 *Alev = set_level_words(c, *st, d, lv.off);
+    const u64 w0 = ((u64)j * lv.P) >> 6;
+    const u64 wend = min(((u64)j + 1) * lv.P, lv.m) >> 6;
+    u64 wsum = 0;
+    for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) {
+      const unsigned jj = (unsigned)(w - w0) * 2;
+      const u64 a = (u64)(hit[jj] & ~col[jj]) | ((u64)(hit[jj + 1] & ~col[jj + 1]) << 32);
+      if (fits) Alev[w] = a;
+      wsum += __popcll(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o);
+    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&c.lvl[sl][s].weight, wsum);
+    if (!fits && threadIdx.x == 0) fail_set(st);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Next-level sizing for every set (one CTA): records level d, decides where
+// level d+1 lives, lays out its buckets and flat ranges, zeroes counters.
+// ---------------------------------------------------------------------------
+static constexpr int kFinishThreads = 1024;
+
+__global__ void __launch_bounds__(kFinishThreads, 1) k_bfinish(int d, BCfg c) {
+  __shared__ unsigned red32[kFinishThreads / 32 + 2];
+  __shared__ u64 red64[kFinishThreads / 32 + 2];
+  const int sl = d & 1, nl = (d + 1) & 1;
+  const unsigned per = (c.S + kFinishThreads - 1) / kFinishThreads;
+  const unsigned lo = threadIdx.x * per, hi = min(lo + per, c.S);
+  // 1. decide each set's next state; count its buckets and arena slots
+  u64 nbk = 0, nslots = 0;
+  for (unsigned s = lo; s < hi; s++) {
+    BSet *st = &c.sets[s];
+    const BLvl cur = c.lvl[sl][s];
+    BLvl nx = cur;
+    if (cur.mode == LM_BUCKETED && !st->status) {
+      FLevel &h = c.hist[(u64)s * (c.L + 1) + d];
+      h.n = cur.n;
+      h.m = cur.m;
+      h.off = cur.off;
+      h.weight = cur.weight;
+      if (cur.weight > cur.n) atomicOr(&st->status, ST_INTERNAL);
+      const u64 nn = cur.weight > cur.n ? 0 : cur.n - cur.weight;
+      memset(&nx, 0, sizeof(nx));
+      nx.n = nn;
+      nx.off = cur.off + cur.m;
+      if (nn == 0) {
+        nx.mode = LM_DONE;
+        st->levels_used = d + 1;
+      } else if ((uint32_t)(d + 1) == c.L) {
+        nx.mode = LM_FLAT;
+        st->tail_level = d + 1;
+        if (nn > st->flat_cap) fail_set(st);
+      } else if (nn <= c.T) {
+        nx.mode = LM_FLAT;
+        nx.m = level_bits(nn, c.gamma);
+        st->tail_level = d + 1;
+      } else {
+        size_set_level(nx, nn, c);
+        nx.off = cur.off + cur.m;
+        nx.mode = LM_BUCKETED;
+      }
+    } else if (cur.mode == LM_BUCKETED) {
+      nx.mode = LM_FAILED;
+    }
+    if (nx.mode == LM_BUCKETED && !st->status) {
+      nbk += nx.B;
+      nslots += nx.B * nx.cap;
+    } else if (nx.mode == LM_BUCKETED) {
+      nx.mode = LM_FAILED;
+    }
+    nx.weight = 0;
+    c.lvl[nl][s] = nx;
+  }
+  // 2. exclusive scans over sets: bucket bases and arena offsets
+  auto scan64 = [&](u64 v, u64 *total) -> u64 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) red64[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      u64 w = lane < kFinishThreads / 32 ? red64[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < kFinishThreads / 32) red64[lane] = w;
+    }
+    __syncthreads();
+    u64 before = warp ? red64[warp - 1] : 0;
+    *total = red64[kFinishThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+  };
+  u64 tb, ts;
+  u64 gb = scan64(nbk, &tb);
+  u64 ao = scan64(nslots, &ts);
+  (void)red32;
+  const bool fit = tb <= c.bcap && ts <= c.acap[nl];
+  for (unsigned s = lo; s < hi; s++) {
+    BLvl &nx = c.lvl[nl][s];
+    if (nx.mode != LM_BUCKETED) continue;
+    if (!fit) {
+      fail_set(&c.sets[s]);
+      nx.mode = LM_FAILED;
+      continue;
+    }
+    nx.bbase = gb;
+    nx.aoff = ao;
+    for (u64 j = 0; j < nx.B; j++) {
+      c.bset[nl][gb + j] = s;
+      c.bidx[nl][gb + j] = (unsigned)j;
+      c.cnt[nl][gb + j] = 0;
+    }
+    gb += nx.B;
+    ao += nx.B * nx.cap;
+  }
+  if (threadIdx.x == 0) c.btotal[nl] = fit ? tb : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Compaction of level d for the buckets of every set.
+// ---------------------------------------------------------------------------
+struct SetBucketDest {
+  u64 *cnt;
+  u64 bbase, aoff, cap;
+  __device__ __forceinline__ DestRun operator()(unsigned i) const {
+    return DestRun{cnt + bbase + i, aoff + (u64)i * cap, cap};
+  }
+};
+struct SetFlatDest {
+  u64 *counter;
+  u64 base, cap;
+  __device__ __forceinline__ DestRun operator()(unsigned) const {
+    return DestRun{counter, base, cap};
+  }
+};
+
+__global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned tile_cnt;
+  __shared__ int skip;
+  const int sl = d & 1, nl = (d + 1) & 1;
+  const u64 nbk = c.btotal[sl];
+  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
+  u64 *stage = sm.sorted;
+  const u64 s_n = level_seed(c.seed, d + 1);
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned ltm = (1u << lane) - 1u;
+  if (threadIdx.x == 0) tile_cnt = 0;
+  __syncthreads();
+  for (u64 gb = blockIdx.x; gb < nbk; gb += gridDim.x) {
+    const unsigned s = c.bset[sl][gb];
+    const unsigned j = c.bidx[sl][gb];
+    BSet *st = &c.sets[s];
+    const BLvl lv = c.lvl[sl][s];
+    const BLvl nx = c.lvl[nl][s];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      skip = (lv.mode != LM_BUCKETED || st->status ||
+              (nx.mode != LM_BUCKETED && nx.mode != LM_FLAT)) ? 1 : 0;
+    __syncthreads();
+    if (skip) continue;  // one decision for the whole CTA
+    const bool flat = nx.mode == LM_FLAT;
+    const u64 *Alev = set_level_words(c, *st, d, lv.off);
+    const u64 w0 = ((u64)j * lv.P) >> 6;
+    const u64 wend = min(((u64)j + 1) * lv.P, lv.m) >> 6;
+    for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
+    __syncthreads();
+    const u64 nk = min(c.cnt[sl][gb], lv.cap);
+    const u64 *kb = c.X[sl] + lv.aoff + (u64)j * lv.cap;
+    const unsigned *pb = c.XP[sl] + lv.aoff + (u64)j * lv.cap;
+    for (u64 t0 = 0; t0 < nk; t0 += kTile) {
+      unsigned pk[kKPT];
+      u64 xk[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+        pk[k] = i < nk ? __ldcs(pb + i) : ~0u;
+        xk[k] = i < nk ? __ldcs(kb + i) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const unsigned p = pk[k];
+        const bool keep = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        unsigned wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&tile_cnt, (unsigned)__popc(bal));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (keep) stage[wbase + __popc(bal & ltm)] = xk[k];
+      }
+      __syncthreads();
+      const unsigned ns = tile_cnt;
+      u64 x[kKPT];
+      unsigned dst[kKPT], lp[kKPT];
+      bool ok[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const unsigned i = (unsigned)k * kTT + threadIdx.x;
+        ok[k] = i < ns;
+        x[k] = ok[k] ? stage[i] : 0;
+        dst[k] = 0;
+        lp[k] = 0;
+        if (ok[k] && !flat) {
+          const u64 p = level_pos(x[k], s_n, nx.m);
+          dst[k] = (unsigned)(p >> nx.sh);
+          lp[k] = (unsigned)(p & (nx.P - 1));
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) tile_cnt = 0;
+      if (flat)
+        multisplit_write<false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
+                                SetFlatDest{&st->n_flat, st->flat_off, st->flat_cap}, &st->status);
+      else
+        multisplit_write<true>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
+                               SetBucketDest{c.cnt[nl], nx.bbase, nx.aoff, nx.cap}, &st->status);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-CTA tail of every set (sets that never left shared memory start at
+// level 0 from the caller's keys).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTailThreads, 1) k_btail(BCfg c, u64 mcap, int dlim) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned s = blockIdx.x;
+  BSet *st = &c.sets[s];
+  if (st->status || st->levels_used) return;
+  const unsigned t = st->tail_level;
+  if (!st->small && (t == 0 || (int)t > dlim)) return;  // not there yet
+  FLevel *hist = c.hist + (u64)s * (c.L + 1);
+  u64 n, off;
+  if (st->small) {
+    n = st->n0;
+    off = 0;
+  } else {
+    const BLvl &lv = c.lvl[t & 1][s];
+    n = lv.n;
+    off = lv.off;
+    if (st->n_flat != n) {
+      if (threadIdx.x == 0) atomicOr(&st->status, ST_INTERNAL);
+      return;
+    }
+  }
+  if (n > kTailMaxKeys) {  // a fallback too large to sort here
+    if (threadIdx.x == 0) fail_set(st);
+    return;
+  }
+  TailSmem sm = carve_tail(smem, mcap);
+  const u64 *src = st->small ? c.keys + st->key_off : c.flat + st->flat_off;
+  for (unsigned i = threadIdx.x; i < n; i += kTailThreads) sm.keys[i] = src[i];
+  if (threadIdx.x == 0) {
+    hist[st->small ? 0 : t].n = n;
+    hist[st->small ? 0 : t].off = off;
+  }
+  __syncthreads();
+  const unsigned used = cta_levels(sm, n, st->small ? 0 : (int)t, off, hist, c.gamma, c.L, c.seed,
+                                   c.A0 + st->a0_off, c.arena + st->at_off, st->m0, st->at_words,
+                                   c.flat + st->flat_off, &st->n_fb, &st->status);
+  if (threadIdx.x == 0) st->levels_used = used;
+}
+
+// ---------------------------------------------------------------------------
+// Finalisation: each set's A = A_0 || later levels, its rank table and
+// fallback, packed into one arena shared by the handles.
+// ---------------------------------------------------------------------------
+struct BOut {
+  u64 a0_off, at_off, m0, M;       // sources and total bits
+  u64 A_dst, R, rank_dst;          // word offsets in the output arena
+  u64 fb_src, n_fb, fb_dst;
+};
+
+__global__ void k_bassemble(const BOut *__restrict__ outs, unsigned S, const u64 *__restrict__ A0,
+                            const u64 *__restrict__ arena, const u64 *__restrict__ flat,
+                            u64 *__restrict__ dst) {
+  for (unsigned s = blockIdx.x; s < S; s += gridDim.x) {
+    const BOut o = outs[s];
+    const u64 W0 = o.m0 >> 6, W = o.M >> 6;
+    for (u64 w = threadIdx.x; w < W; w += blockDim.x)
+      dst[o.A_dst + w] = w < W0 ? A0[o.a0_off + w] : arena[o.at_off + (w - W0)];
+    for (u64 i = threadIdx.x; i < o.n_fb; i += blockDim.x) dst[o.fb_dst + i] = flat[o.fb_src + i];
+  }
+}
+
+static constexpr int kRankT = 256;
+
+__global__ void __launch_bounds__(kRankT) k_brank(const BOut *__restrict__ outs, unsigned S,
+                                                  u64 *__restrict__ arena, u64 *__restrict__ totals) {
+  __shared__ u64 warp_sums[kRankT / 32];
+  for (unsigned s = blockIdx.x; s < S; s += gridDim.x) {
+    const BOut o = outs[s];
+    const u64 *A = arena + o.A_dst;
+    u64 *rank2 = arena + o.rank_dst;
+    const u64 nwords = o.M >> 6;
+    u64 running = 0;
+    for (u64 b0 = 0; b0 < o.R; b0 += kRankT) {
+      const u64 b = b0 + threadIdx.x;
+      u64 cblk = 0, rel = 0;
+      if (b < o.R) {
+        unsigned run = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const u64 w = b * 8 + j;
+          const unsigned pc = w < nwords ? __popcll(A[w]) : 0u;
+          if (j) rel |= (u64)run << (9 * (j - 1));
+          run += pc;
+        }
+        cblk = run;
+      }
+      // block exclusive scan of cblk
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      u64 x = cblk;
+#pragma unroll
+      for (int of = 1; of < 32; of <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, x, of);
+        if (lane >= of) x += y;
+      }
+      if (lane == 31) warp_sums[warp] = x;
+      __syncthreads();
+      u64 before = 0, tot = 0;
+      for (int i = 0; i < kRankT / 32; i++) {
+        if (i < warp) before += warp_sums[i];
+        tot += warp_sums[i];
+      }
+      __syncthreads();
+      if (b < o.R) {
+        rank2[2 * b] = running + before + x - cblk;
+        rank2[2 * b + 1] = rel;
+      }
+      running += tot;
+    }
+    if (threadIdx.x == 0) totals[s] = running;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: persistent workspace, recorded level loop, autotuned bucket width.
+// ---------------------------------------------------------------------------
+struct BatchTune {
+  u64 Pmax = 128 * 1024;
+  u64 Bset_max = 64;
+};
+
+static std::mutex g_bmu;
+static std::map<u64, BatchTune> g_tuned;  // key: size class
+static double g_bcap_scale = 1.0;
+
+static u64 size_class(unsigned S, u64 total) {
+  unsigned a = 0, b = 0;
+  while ((1ull << a) < S) a++;
+  while ((1ull << b) < total) b++;
+  return ((u64)a << 32) | b;
+}
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  BCfg cfg;
+  int D = -1;
+  u64 total = 0, nbk = 0, mcap = 0;
+  unsigned kernels = 0;
+  cudaStream_t stream = nullptr;
+};
+
+struct Workspace {
+  DevBuf bufs[24];
+  size_t want[24] = {0};
+  GraphCache g;
+};
+static Workspace g_ws;
+
+// Grow workspace slot i to at least `bytes` (kept across calls).
+static int ws_get(int i, size_t bytes, cudaStream_t st, void **p) {
+  DevBuf &b = g_ws.bufs[i];
+  if (b.p && b.bytes >= bytes) {
+    *p = b.p;
+    return MPHF_OK;
+  }
+  if (b.p) {
+    cudaStreamSynchronize(st);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t sz = bytes < 256 ? 256 : bytes;
+  cudaError_t e = cudaMalloc(&b.p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    set_cuda_error(e, "cudaMalloc(workspace)");
+    return MPHF_ENOMEM;
+  }
+  b.bytes = sz;
+  *p = b.p;
+  return MPHF_OK;
+}
+
+}  // namespace bbh
+
+// Shared ownership of a batched arena by many handles.
+struct mphf_shared {
+  bbh::DevBuf arena;
+  std::atomic<int> refs{0};
+};
+
+namespace bbh {
+
+void release_shared(mphf_shared *sh) {
+  if (!sh) return;
+  if (sh->refs.fetch_sub(1) == 1) {
+    if (sh->arena.p) cudaFree(sh->arena.p);
+    delete sh;
+  }
+}
+
+int build_single(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+                 mphf_t **out);  // build.cu
+
+static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double gamma, uint32_t L,
+                        u64 seed, cudaStream_t st, mphf_t **out, const BatchTune &tune,
+                        unsigned *n_rebuilt) {
+  int rc = MPHF_OK;
+  *n_rebuilt = 0;
+  static bool attr = false;
+  const size_t split_b = split_smem_bytes((unsigned)kBmax);
+  const size_t comp_b = split_b + kPmax / 8;
+  u64 mcap = 0;
+  u64 T = kTailMaxKeys;
+  while (T > 64 && tail_smem_bytes(level_bits(T, gamma)) > 200 * 1024) T >>= 1;
+  mcap = level_bits(T, gamma);
+  if (!attr) {
+    MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)split_b));
+    MPHF_CUDA(cudaFuncSetAttribute(k_bcompact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)comp_b));
+    MPHF_CUDA(cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(kPmax / 4)));
+    MPHF_CUDA(cudaFuncSetAttribute(k_btail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+    attr = true;
+  }
+  for (unsigned s = 0; s < S; s++) out[s] = nullptr;
+  const u64 total = h_off[S] - h_off[0];
+  BCfg c;
+  memset(&c, 0, sizeof(c));
+  c.gamma = gamma;
+  c.L = L;
+  c.seed = seed;
+  c.S = S;
+  c.T = T;
+  c.Pmin = 4096;
+  c.Pmax = tune.Pmax;
+  c.Bset_max = tune.Bset_max;
+  c.cap_scale = g_bcap_scale;
+  // ---- host plan: per-set level 0
+  std::vector<BSet> hs(S);
+  std::vector<BLvl> hl0(S);
+  std::vector<u64> koff(S + 1);
+  u64 a0_words = 0, nbk = 0, nslots = 0, flat_total = 0, large_keys = 0;
+  for (unsigned s = 0; s < S; s++) {
+    BSet &b = hs[s];
+    memset(&b, 0, sizeof(b));
+    koff[s] = h_off[s] - h_off[0];
+    b.key_off = koff[s];
+    b.n0 = h_off[s + 1] - h_off[s];
+    b.m0 = b.n0 ? level_bits(b.n0, gamma) : 0;
+    b.a0_off = a0_words;
+    a0_words += b.m0 / 64;
+    BLvl &l = hl0[s];
+    memset(&l, 0, sizeof(l));
+    if (b.n0 == 0) {
+      l.mode = LM_DONE;
+      b.levels_used = 0;
+      b.small = 0;
+      continue;
+    }
+    if (b.n0 <= T) {
+      b.small = 1;
+      l.mode = LM_FLAT;
+      b.flat_off = flat_total;
+      b.flat_cap = b.n0;
+      flat_total += b.n0;
+    } else {
+      size_set_level(l, b.n0, c);
+      l.off = 0;
+      l.mode = LM_BUCKETED;
+      l.bbase = nbk;
+      l.aoff = nslots;
+      nbk += l.B;
+      nslots += l.B * l.cap;
+      large_keys += b.n0;
+      b.flat_off = flat_total;
+      b.flat_cap = T;
+      flat_total += T;
+    }
+  }
+  koff[S] = total;
+  // tail arena (levels >= 1): a generous bound per set, checked on the device
+  const double grow = 1.5 * exp(1.0 / gamma) + 0.5;
+  u64 at_words = 0;
+  for (unsigned s = 0; s < S; s++) {
+    BSet &b = hs[s];
+    if (!b.n0) continue;
+    const u64 n1 = b.small ? b.n0 : (u64)ceil((double)b.n0 * (1.0 - exp(-1.0 / gamma)) * 1.05 + 64);
+    const u64 w = (u64)(grow * (double)(level_bits(n1 < b.n0 ? n1 : b.n0, gamma) / 64)) + 2 * L;
+    b.at_off = at_words;
+    b.at_words = w;
+    at_words += w;
+  }
+  // ---- workspace (persistent across calls so the recorded graph can be replayed)
+  void *p;
+  const u64 bcap = nbk + (u64)S * 2 + 64;
+  c.bcap = bcap;
+  c.acap[0] = nslots;
+  {
+    const double q = 1.0 - exp(-1.0 / gamma);  // expected share of keys left after level 0
+    c.acap[1] = (u64)((double)nslots * std::min(1.0, q + 0.12)) + (u64)S * 4096;
+  }
+#define WS(i, bytes, dst)                                   \
+  do {                                                      \
+    rc = ws_get(i, (size_t)(bytes), st, &p);                \
+    if (rc != MPHF_OK) return rc;                           \
+    *(void **)(dst) = p;                                    \
+  } while (0)
+  WS(0, sizeof(BSet) * S, &c.sets);
+  WS(1, sizeof(BLvl) * S, &c.lvl[0]);
+  WS(2, sizeof(BLvl) * S, &c.lvl[1]);
+  WS(3, 4 * bcap, &c.bset[0]);
+  WS(4, 4 * bcap, &c.bset[1]);
+  WS(5, 4 * bcap, &c.bidx[0]);
+  WS(6, 4 * bcap, &c.bidx[1]);
+  WS(7, 8 * bcap, &c.cnt[0]);
+  WS(8, 8 * bcap, &c.cnt[1]);
+  WS(9, 16, &c.btotal);
+  WS(10, 8 * (c.acap[0] + 4), &c.X[0]);
+  WS(11, 8 * (c.acap[1] + 4), &c.X[1]);
+  WS(12, 4 * (c.acap[0] + 4), &c.XP[0]);
+  WS(13, 4 * (c.acap[1] + 4), &c.XP[1]);
+  WS(14, 8 * (flat_total + 4), &c.flat);
+  WS(15, 8 * (a0_words + 4), &c.A0);
+  WS(16, 8 * (at_words + 4), &c.arena);
+  WS(17, sizeof(FLevel) * (u64)S * (L + 1), &c.hist);
+  WS(18, 16, &c.status);
+  WS(19, sizeof(u64) * (S + 1), &p);
+  u64 *d_koff = (u64 *)p;
+#undef WS
+  c.keys = d_keys;
+  // ---- level-0 bucket descriptors on the host
+  std::vector<unsigned> hb_set(nbk), hb_idx(nbk);
+  for (unsigned s = 0; s < S; s++) {
+    if (hl0[s].mode != LM_BUCKETED) continue;
+    for (u64 j = 0; j < hl0[s].B; j++) {
+      hb_set[hl0[s].bbase + j] = s;
+      hb_idx[hl0[s].bbase + j] = (unsigned)j;
+    }
+  }
+  u64 bt[2] = {nbk, 0};
+  MPHF_CUDA(cudaMemcpyAsync(c.sets, hs.data(), sizeof(BSet) * S, cudaMemcpyHostToDevice, st));
+  MPHF_CUDA(cudaMemcpyAsync(c.lvl[0], hl0.data(), sizeof(BLvl) * S, cudaMemcpyHostToDevice, st));
+  if (nbk) {
+    MPHF_CUDA(cudaMemcpyAsync(c.bset[0], hb_set.data(), 4 * nbk, cudaMemcpyHostToDevice, st));
+    MPHF_CUDA(cudaMemcpyAsync(c.bidx[0], hb_idx.data(), 4 * nbk, cudaMemcpyHostToDevice, st));
+    MPHF_CUDA(cudaMemsetAsync(c.cnt[0], 0, 8 * nbk, st));
+  }
+  MPHF_CUDA(cudaMemcpyAsync(c.btotal, bt, 16, cudaMemcpyHostToDevice, st));
+  MPHF_CUDA(cudaMemcpyAsync(d_koff, koff.data(), 8 * (S + 1), cudaMemcpyHostToDevice, st));
+  MPHF_CUDA(cudaMemsetAsync(c.status, 0, 16, st));
+  MPHF_CUDA(cudaMemsetAsync(c.hist, 0, sizeof(FLevel) * (u64)S * (L + 1), st));
+  // ---- predicted number of bucketed levels (largest set)
+  u64 nmax = 0;
+  for (unsigned s = 0; s < S; s++)
+    if (!hs[s].small) nmax = std::max(nmax, hs[s].n0);
+  int D = 0;
+  {
+    double e = (double)nmax;
+    while (e > (double)T && D < (int)L) {
+      const double m = (double)level_bits((u64)e, gamma);
+      e = e * (1.0 - pow(1.0 - 1.0 / m, e - 1.0));
+      D++;
+    }
+  }
+  // ---- the level loop, recorded as a graph: partition, then per level fill,
+  // finish, compaction; then the single-CTA tails
+  const unsigned grid2 = (unsigned)sm_count() * 2;
+  unsigned nk_rec = 0;
+  auto record = [&](int Dl) -> int {
+    if (nbk) {
+      k_bpartition0<<<grid2, kTT, split_b, st>>>(d_koff, total, c);
+      nk_rec++;
+    }
+    for (int d = 0; d <= Dl && d < (int)L; d++) {
+      if (nbk) {
+        k_bfill<<<grid2, kTT, kPmax / 4, st>>>(d, c);
+        k_bfinish<<<1, kFinishThreads, 0, st>>>(d, c);
+        k_bcompact<<<grid2, kTT, comp_b, st>>>(d, c);
+        nk_rec += 3;
+      }
+    }
+    k_btail<<<S, kTailThreads, tail_smem_bytes(mcap), st>>>(c, mcap, Dl + 1);
+    nk_rec++;
+    return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
+  };
+  // replay the recorded loop when the configuration is unchanged
+  GraphCache &gc = g_ws.g;
+  bool reuse = gc.exec && gc.D == D && gc.stream == st && gc.total == total && gc.nbk == nbk &&
+               gc.mcap == mcap && memcmp(&gc.cfg, &c, sizeof(c)) == 0;
+  if (!reuse) {
+    if (gc.exec) {
+      cudaGraphExecDestroy(gc.exec);
+      gc.exec = nullptr;
+    }
+    // record on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    static cudaStream_t cap = nullptr;
+    if (!cap) MPHF_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaStream_t user = st;
+    st = cap;
+    MPHF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rrc = record(D);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    st = user;
+    if (rrc != MPHF_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown, "graph capture");
+    }
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gc.exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    gc.cfg = c;
+    gc.D = D;
+    gc.total = total;
+    gc.nbk = nbk;
+    gc.mcap = mcap;
+    gc.kernels = nk_rec;
+    gc.stream = st;
+  }
+  {
+    LaunchScope ls("batched_levels", st);
+    MPHF_CUDA(cudaGraphLaunch(gc.exec, st));
+  }
+  add_launches(gc.kernels > 0 ? gc.kernels - 1 : 0);
+  // ---- read back per-set results
+  std::vector<BSet> rs(S);
+  unsigned gstat[4] = {0, 0, 0, 0};
+  MPHF_CUDA(cudaMemcpyAsync(rs.data(), c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaMemcpyAsync(gstat, c.status, 16, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  // sets whose loop did not finish within D levels (prediction short): run the
+  // remaining levels unrecorded
+  for (int extra = 0; extra < 64; extra++) {
+    bool pending = false;
+    for (unsigned s = 0; s < S; s++)
+      if (rs[s].n0 && !rs[s].status && !rs[s].levels_used) pending = true;
+    if (!pending || D + 1 >= (int)L) break;
+    // continue from level D+1: compaction of D was recorded; fill/finish/compact D+1..
+    const int d0 = D + 1;
+    D = std::min((int)L - 1, D + 2);
+    for (int d = d0; d <= D; d++) {
+      {
+        LaunchScope ls("bfill", st);
+        k_bfill<<<grid2, kTT, kPmax / 4, st>>>(d, c);
+      }
+      {
+        LaunchScope ls("bfinish", st);
+        k_bfinish<<<1, kFinishThreads, 0, st>>>(d, c);
+      }
+      {
+        LaunchScope ls("bcompact", st);
+        k_bcompact<<<grid2, kTT, comp_b, st>>>(d, c);
+      }
+    }
+    {
+      LaunchScope ls("btail", st);
+      k_btail<<<S, kTailThreads, tail_smem_bytes(mcap), st>>>(c, mcap, D + 1);
+    }
+    MPHF_CUDA(cudaGetLastError());
+    MPHF_CUDA(cudaMemcpyAsync(rs.data(), c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
+    MPHF_CUDA(cudaStreamSynchronize(st));
+    gc.D = -1;  // the recorded graph no longer matches this build
+  }
+  for (unsigned s = 0; s < S; s++)
+    if (rs[s].status & ST_DUPLICATE) return MPHF_EDUPLICATE;
+  std::vector<FLevel> hist((u64)S * (L + 1));
+  MPHF_CUDA(cudaMemcpyAsync(hist.data(), c.hist, sizeof(FLevel) * hist.size(),
+                            cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  // ---- output layout
+  std::vector<BOut> bo(S);
+  std::vector<char> okset(S, 0);
+  u64 out_words = 0;
+  for (unsigned s = 0; s < S; s++) {
+    const BSet &b = rs[s];
+    BOut &o = bo[s];
+    memset(&o, 0, sizeof(o));
+    if (b.n0 == 0) {
+      okset[s] = 1;
+      continue;
+    }
+    const bool good = !b.status && b.levels_used >= 1 && b.levels_used <= L;
+    if (!good) continue;
+    const FLevel *hl = &hist[(u64)s * (L + 1)];
+    const unsigned U = b.levels_used;
+    u64 placed = 0;
+    for (unsigned d = 0; d < U; d++) placed += hl[d].weight;
+    const u64 n_fb = (U == L) ? b.n_fb : 0;
+    if (placed + n_fb != b.n0) continue;  // rebuild this one on its own
+    o.a0_off = b.a0_off;
+    o.at_off = b.at_off;
+    o.m0 = b.m0;
+    o.M = hl[U - 1].off + hl[U - 1].m;
+    o.R = (o.M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
+    o.fb_src = b.flat_off;
+    o.n_fb = n_fb;
+    o.A_dst = out_words;
+    out_words += ((o.M / 64) + 7) & ~7ull;
+    o.rank_dst = out_words;
+    out_words += 2 * o.R;
+    o.fb_dst = out_words;
+    out_words += (n_fb + 7) & ~7ull;
+    okset[s] = 1;
+  }
+  mphf_shared *sh = new (std::nothrow) mphf_shared();
+  if (!sh) return MPHF_ENOMEM;
+  if (out_words) {
+    cudaError_t e = cudaMalloc(&sh->arena.p, out_words * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete sh;
+      set_cuda_error(e, "cudaMalloc(batched arena)");
+      return MPHF_ENOMEM;
+    }
+    sh->arena.bytes = out_words * 8;
+    DevBuf dbo, dtot;
+    rc = dev_alloc(dbo, sizeof(BOut) * S, st);
+    if (rc == MPHF_OK) rc = dev_alloc(dtot, 8 * S, st);
+    if (rc != MPHF_OK) {
+      dev_free(dbo, st);
+      cudaFree(sh->arena.p);
+      delete sh;
+      return rc;
+    }
+    std::vector<u64> totals(S, 0);
+    cudaMemcpyAsync(dbo.p, bo.data(), sizeof(BOut) * S, cudaMemcpyHostToDevice, st);
+    {
+      LaunchScope ls("bassemble", st);
+      k_bassemble<<<grid2 * 2, 256, 0, st>>>((const BOut *)dbo.p, S, c.A0, c.arena, c.flat,
+                                           (u64 *)sh->arena.p);
+    }
+    {
+      LaunchScope ls("brank", st);
+      k_brank<<<grid2 * 2, kRankT, 0, st>>>((const BOut *)dbo.p, S, (u64 *)sh->arena.p,
+                                           (u64 *)dtot.p);
+    }
+    cudaMemcpyAsync(totals.data(), dtot.p, 8 * S, cudaMemcpyDeviceToHost, st);
+    dev_free(dbo, st);
+    dev_free(dtot, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) {
+      cudaFree(sh->arena.p);
+      delete sh;
+      return cuda_fail(e2, "batched finalise");
+    }
+    for (unsigned s = 0; s < S; s++)
+      if (okset[s] && rs[s].n0 && totals[s] != rs[s].n0 - bo[s].n_fb) okset[s] = 0;
+  }
+  // ---- handles
+  int live = 0;
+  for (unsigned s = 0; s < S; s++) {
+    if (!okset[s]) continue;
+    mphf_t *h = new (std::nothrow) mphf_t();
+    if (!h) {
+      rc = MPHF_ENOMEM;
+      break;
+    }
+    cudaGetDevice(&h->device);
+    const BSet &b = rs[s];
+    h->N = b.n0;
+    h->gamma = gamma;
+    h->L = L;
+    h->seed = seed;
+    for (uint32_t d = 0; d < L; d++) h->s[d] = level_seed(seed, d);
+    h->path = 3;
+    if (b.n0) {
+      const FLevel *hl = &hist[(u64)s * (L + 1)];
+      h->L_used = b.levels_used;
+      for (unsigned d = 0; d < b.levels_used; d++) {
+        h->n[d] = hl[d].n;
+        h->m[d] = hl[d].m;
+        h->off[d] = hl[d].off;
+      }
+      h->n_fb = bo[s].n_fb;
+      h->n[b.levels_used] = h->n_fb;
+      h->M = bo[s].M;
+      h->n_rank = bo[s].R;
+      u64 *base = (u64 *)sh->arena.p;
+      h->A.p = base + bo[s].A_dst;
+      h->A.bytes = h->M / 8;
+      h->rank.p = base + bo[s].rank_dst;
+      h->rank.bytes = h->n_rank * 16;
+      h->fb.p = h->n_fb ? base + bo[s].fb_dst : nullptr;
+      h->fb.bytes = h->n_fb * 8;
+      h->shared = sh;
+      live++;
+    }
+    out[s] = h;
+  }
+  if (live) sh->refs.store(live);
+  else {
+    if (sh->arena.p) cudaFree(sh->arena.p);
+    delete sh;
+  }
+  if (rc != MPHF_OK) return rc;
+  // ---- sets that hit a bound: built on their own
+  for (unsigned s = 0; s < S; s++) {
+    if (out[s]) continue;
+    rc = build_single(d_keys + koff[s], h_off[s + 1] - h_off[s], gamma, L, seed, st, &out[s]);
+    if (rc != MPHF_OK) return rc;
+    (*n_rebuilt)++;
+  }
+  return MPHF_OK;
+}
+
+}  // namespace bbh
+
+using namespace bbh;
+
+extern "C" int mphf_build_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S,
+                                  double gamma, uint32_t levels, uint64_t seed, void *stream,
+                                  mphf_t **out) {
+  if (!out || !h_offsets || S == 0) return MPHF_EINVAL;
+  for (uint32_t s = 0; s < S; s++) out[s] = nullptr;
+  if (!(gamma >= 1.0) || isinf(gamma) || levels < 1 || levels > MPHF_MAX_LEVELS) return MPHF_EINVAL;
+  for (uint32_t s = 0; s < S; s++)
+    if (h_offsets[s + 1] < h_offsets[s]) return MPHF_EINVAL;
+  if (h_offsets[S] > h_offsets[0] && (!d_keys || ((uintptr_t)d_keys & 7))) return MPHF_EINVAL;
+  const u64 total = h_offsets[S] - h_offsets[0];
+  BatchTune tune;
+  {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_tuned.find(size_class(S, total));
+    if (it != g_tuned.end()) tune = it->second;
+  }
+  unsigned rebuilt = 0;
+  std::lock_guard<std::mutex> lk(g_bmu);
+  const u64 *keys = (const u64 *)d_keys + h_offsets[0];
+  int rc = batched_impl(keys, (const u64 *)h_offsets, S, gamma, levels, seed,
+                        (cudaStream_t)stream, out, tune, &rebuilt);
+  if (rc != MPHF_OK) {
+    for (uint32_t s = 0; s < S; s++) {
+      mphf_free(out[s]);
+      out[s] = nullptr;
+    }
+    cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  return rc;
+}
+
+extern "C" int mphf_autotune_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S,
+                                     double gamma, uint32_t levels, uint64_t seed, void *stream,
+                                     double *best_ms) {
+  if (!h_offsets || S == 0) return MPHF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const u64 total = h_offsets[S] - h_offsets[0];
+  std::vector<BatchTune> cands;
+  for (u64 P : {32768ull, 65536ull, 131072ull, 262144ull})
+    for (u64 B : {16ull, 64ull}) {
+      BatchTune t;
+      t.Pmax = P;
+      t.Bset_max = B;
+      cands.push_back(t);
+    }
+  std::vector<mphf_t *> outs(S, nullptr);
+  double best = 1e30;
+  BatchTune bt;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::lock_guard<std::mutex> lk(g_bmu);
+  const u64 *keys = (const u64 *)d_keys + h_offsets[0];
+  for (const BatchTune &t : cands) {
+    double tmin = 1e30;
+    for (int rep = 0; rep < 2; rep++) {
+      unsigned rebuilt = 0;
+      cudaEventRecord(e0, st);
+      int rc = batched_impl(keys, (const u64 *)h_offsets, S, gamma, levels, seed, st, outs.data(),
+                            t, &rebuilt);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      for (auto &h : outs) {
+        mphf_free(h);
+        h = nullptr;
+      }
+      if (rc != MPHF_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rebuilt) ms += 1e6f;  // a configuration that overflows loses
+      tmin = std::min(tmin, (double)ms);
+    }
+    if (tmin < best) {
+      best = tmin;
+      bt = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tuned[size_class(S, total)] = bt;
+  if (best_ms) *best_ms = best;
+  return MPHF_OK;
+}
+
+extern "C" int mphf_batched_debug_config(double cap_scale) {
+  if (!(cap_scale > 0.0) || cap_scale > 16.0) return MPHF_EINVAL;
+  std::lock_guard<std::mutex> lk(g_bmu);
+  g_bcap_scale = cap_scale;
+  return MPHF_OK;
+}
+
+extern "C" void mphf_workspace_release(void) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  if (g_ws.g.exec) cudaGraphExecDestroy(g_ws.g.exec);
+  g_ws.g.exec = nullptr;
+  g_ws.g.D = -1;
+  for (auto &b : g_ws.bufs) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+}

@@ -522,6 +522,11 @@ static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed
   return MPHF_OK;
 }
 
+int build_single(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
+                 mphf_t **out) {
+  return build_impl(keys, N, gamma, L, seed, st, out);
+}
+
 }  // namespace bbh
 
 using namespace bbh;

@@ -96,6 +96,7 @@ int cuda_fail(cudaError_t e, const char *where);  // records and returns MPHF_EC
 // per-kernel profile see it.
 void launch_begin(const char *name, cudaStream_t s);
 void launch_end(cudaStream_t s);
+void add_launches(u64 n);  // kernels replayed inside a recorded graph
 
 struct LaunchScope {
   cudaStream_t s;
@@ -138,6 +139,11 @@ int sort_fallback(u64 *keys, u64 n, unsigned int *d_dup_flag, cudaStream_t s);
 
 }  // namespace bbh
 
+struct mphf_shared;  // one device arena shared by the handles of a batched build
+namespace bbh {
+void release_shared(mphf_shared *sh);
+}
+
 // The handle.  Host copies of the level metadata plus the device arrays.
 struct mphf {
   uint64_t N = 0;
@@ -156,5 +162,6 @@ struct mphf {
   bbh::DevBuf rank;     // 2 n_rank words: checkpoint, in-block prefix counts
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;
-  int path = 0;          // 1 bucketed construction, 2 unbucketed
+  int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched construction
+  mphf_shared *shared = nullptr;  // set: A/rank/fb live in a batched arena
 };

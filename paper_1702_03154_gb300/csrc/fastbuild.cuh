@@ -65,4 +65,358 @@ struct FastCfg {
 
 __host__ __device__ inline u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
 
+static constexpr int kTT = 512;            // threads of partition / compaction / fill CTAs
+static constexpr int kKPT = 8;             // keys per thread per tile
+static constexpr int kTile = kTT * kKPT;   // 4096 keys
+static constexpr u64 kPmax = 256 * 1024;   // positions per bucket at most (64 KB of bits)
+static constexpr int kTailThreads = 1024;
+static constexpr u64 kTailMaxKeys = 16384;
+static constexpr u64 kBmax = 2048;
+
+// ---------------------------------------------------------------------------
+// Level sizing (device side, by the last block of a fill).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline unsigned ilog2_u64(u64 v) {
+  unsigned r = 0;
+  while ((v >> r) > 1) r++;
+  return r;
+}
+
+__host__ __device__ inline void size_bucketed(FLevel &lv, u64 n, double gamma, u64 Pmin, u64 Pmax,
+                                              u64 Btarget, double cap_scale) {
+  lv.n = n;
+  lv.m = level_bits(n, gamma);
+  u64 want = ceil_div(lv.m, Btarget);
+  u64 P = Pmin;
+  while (P < want && P < Pmax) P <<= 1;
+  lv.P = P;
+  lv.B = ceil_div(lv.m, P);
+  double mean = (double)n * (double)P / (double)lv.m;
+  u64 cap = (u64)(cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));
+  lv.cap = (cap + 3) & ~3ull;  // multiple of 4: every bucket starts 16-byte aligned
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers (kTT threads).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ u64 block_sum(u64 v, u64 *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  u64 s = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT / 32; i++) s += red[i];
+    red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Exclusive scan of NT values (one per thread); returns the prefix, *total = sum.
+template <int NT>
+__device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned *red, unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < NT / 32 ? red[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) red[lane] = w;
+  }
+  __syncthreads();
+  unsigned before = warp ? red[warp - 1] : 0u;
+  *total = red[NT / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// Shared memory of the multisplit writer.
+struct SplitSmem {
+  unsigned *cnt;         // [nb] entries per destination in this tile, then their local start
+  unsigned *lim;         // [nb] local index past which the destination bucket is full
+  u64 *dbase;            // [nb] arena index of local entry 0 of each destination
+  u64 *sorted;           // [kTile] keys in destination order (also the survivor staging area)
+  unsigned *stag;        // [kTile] (destination << 20) | in-bucket position
+  unsigned *red;         // [kTT / 32 + 2]
+};
+
+// Destination of a multisplit: where destination bucket i of the tile lives.
+struct DestRun {
+  u64 *counter;  // keys already in the bucket (atomically advanced)
+  u64 base;      // arena index of the bucket's slot 0
+  u64 cap;       // slots in the bucket
+};
+
+// Plain layout: bucket i at arena[i * cap], counters gcnt[i].
+struct UniformDest {
+  u64 *gcnt;
+  u64 cap;
+  __device__ __forceinline__ DestRun operator()(unsigned i) const {
+    return DestRun{gcnt + i, (u64)i * cap, cap};
+  }
+};
+
+// Write the valid entries of a tile into their destination buckets: key to
+// arena[base_b + slot] and (WITH_POS) its in-bucket position lp (< 2^20) to
+// parena[base_b + slot], where dest(b) gives the bucket's counter, base and
+// capacity.  Slots are reserved with one atomicAdd per non-empty destination;
+// the entries of one destination leave as one contiguous run.  Entries past a
+// bucket's capacity are dropped and ST_OVERFLOW is raised.
+template <bool WITH_POS, class Dest>
+__device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
+                                 const unsigned (&dst)[kKPT], const bool (&ok)[kKPT], unsigned nb,
+                                 const SplitSmem &sm, u64 *__restrict__ arena,
+                                 unsigned *__restrict__ parena, const Dest &dest,
+                                 unsigned *__restrict__ status) {
+  for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;
+  __syncthreads();
+  unsigned rk[kKPT];
+#pragma unroll
+  for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
+  __syncthreads();
+  // exclusive scan of the counts (each thread owns a run of entries), then
+  // reserve each destination's slots and precompute where its run goes
+  const unsigned per = (nb + kTT - 1) / kTT;
+  const unsigned lo = threadIdx.x * per;
+  const unsigned hi = min(lo + per, nb);
+  unsigned s = 0;
+  for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
+  unsigned total;
+  unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+  for (unsigned i = lo; i < hi; i++) {
+    const unsigned c = sm.cnt[i];
+    u64 b0 = 0, room = 0, base = 0;
+    if (c) {
+      const DestRun r = dest(i);
+      b0 = atomicAdd(r.counter, (u64)c);
+      room = b0 < r.cap ? r.cap - b0 : 0;
+      base = r.base;
+    }
+    sm.cnt[i] = pre;
+    sm.lim[i] = pre + (unsigned)(room < c ? room : c);
+    sm.dbase[i] = base + b0 - pre;
+    pre += c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kKPT; k++) {
+    if (ok[k]) {
+      const unsigned pos = sm.cnt[dst[k]] + rk[k];
+      sm.sorted[pos] = x[k];
+      sm.stag[pos] = (dst[k] << 20) | lp[k];
+    }
+  }
+  __syncthreads();
+  for (unsigned i = threadIdx.x; i < total; i += kTT) {
+    const unsigned tg = sm.stag[i];
+    const unsigned b = tg >> 20;
+    if (i < sm.lim[b]) {
+      const u64 j = sm.dbase[b] + i;
+      arena[j] = sm.sorted[i];
+      if (WITH_POS) parena[j] = tg & 0xfffffu;
+    } else {
+      atomicOr(status, ST_OVERFLOW);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
+  SplitSmem s;
+  s.sorted = reinterpret_cast<u64 *>(smem);
+  s.dbase = s.sorted + kTile;
+  s.stag = reinterpret_cast<unsigned *>(s.dbase + nb_cap);
+  s.cnt = s.stag + kTile;
+  s.lim = s.cnt + nb_cap;
+  s.red = s.lim + nb_cap;
+  return s;
+}
+
+static constexpr size_t split_smem_bytes(unsigned nb_cap) {
+  return (size_t)kTile * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 + 2 * (size_t)nb_cap * 4 +
+         (kTT / 32 + 2) * 4 + 8;
+}
+
+// ---------------------------------------------------------------------------
+// Level 0: partition the caller's keys into position buckets of A_0; each key
+// is stored with its position inside the bucket, so the fill needs no hash.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+
+// ---------------------------------------------------------------------------
+// Single-CTA level loop: levels d0.. of a key set of at most kTailMaxKeys keys,
+// keys and bit arrays in shared memory.
+// ---------------------------------------------------------------------------
+struct TailSmem {
+  u64 *keys;      // [kTailMaxKeys]
+  unsigned *hit;  // [mcap / 32]
+  unsigned *col;
+  unsigned *red;  // [32 + 2]
+  u64 *red64;     // [32]
+};
+
+static __device__ void bitonic_sort_smem(u64 *a, unsigned n) {
+  unsigned P = 1;
+  while (P < n) P <<= 1;
+  for (unsigned i = n + threadIdx.x; i < P; i += blockDim.x) a[i] = ~0ull;
+  __syncthreads();
+  for (unsigned k = 2; k <= P; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
+        unsigned l = i ^ j;
+        if (l > i) {
+          u64 x = a[i], y = a[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Returns the number of levels used.  lvs: level records (n/m/off/weight/mode)
+// of this key set; A0 / arena / m0 locate A_d; fb_out receives the sorted
+// fallback (n_fb keys).
+static __device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off, FLevel *lvs,
+                                      double gamma, uint32_t L, u64 seed, u64 *A0, u64 *arena,
+                                      u64 m0, u64 arena_words, u64 *fb_out, u64 *n_fb_out,
+                                      unsigned *status) {
+  int d = d0;
+  for (;;) {
+    if (n == 0) {
+      if (threadIdx.x == 0) lvs[d].mode = LM_DONE;
+      return (unsigned)d;
+    }
+    if ((uint32_t)d == L) {
+      bitonic_sort_smem(sm.keys, (unsigned)n);
+      for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        u64 v = sm.keys[i];
+        fb_out[i] = v;
+        if (i + 1 < n && v == sm.keys[i + 1]) atomicOr(status, ST_DUPLICATE);
+      }
+      if (threadIdx.x == 0) {
+        *n_fb_out = n;
+        lvs[d].mode = LM_FLAT;
+        lvs[d].n = n;
+      }
+      __syncthreads();
+      return L;
+    }
+    const u64 m = level_bits(n, gamma);
+    const u64 s = level_seed(seed, (uint32_t)d);
+    const unsigned mw = (unsigned)(m >> 5);
+    for (unsigned i = threadIdx.x; i < mw; i += blockDim.x) {
+      sm.hit[i] = 0;
+      sm.col[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+      const u64 p = level_pos(sm.keys[i], s, m);
+      const unsigned bit = 1u << (p & 31);
+      const unsigned old = atomicOr(sm.hit + (p >> 5), bit);
+      if (old & bit) atomicOr(sm.col + (p >> 5), bit);
+    }
+    __syncthreads();
+    u64 *Alev = (d == 0) ? A0 : arena + ((off - m0) >> 6);
+    // A_d must fit in the space reserved for the levels after the first
+    const bool fits = d == 0 || ((off - m0) >> 6) + (m >> 6) <= arena_words;
+    if (!fits && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
+    u64 wsum = 0;
+    for (unsigned w = threadIdx.x; w < (unsigned)(m >> 6); w += blockDim.x) {
+      const u64 a = (u64)(sm.hit[2 * w] & ~sm.col[2 * w]) |
+                    ((u64)(sm.hit[2 * w + 1] & ~sm.col[2 * w + 1]) << 32);
+      if (fits) Alev[w] = a;
+      wsum += __popcll(a);
+    }
+    // compaction in place: each thread keeps its contiguous run of keys in registers
+    constexpr unsigned KMAX = (unsigned)(kTailMaxKeys / kTailThreads);
+    const unsigned per = (unsigned)((n + blockDim.x - 1) / blockDim.x);
+    const unsigned lo = threadIdx.x * per;
+    u64 mine[KMAX];
+    unsigned keepmask = 0, c = 0;
+#pragma unroll
+    for (unsigned k = 0; k < KMAX; k++) {
+      mine[k] = 0;
+      const unsigned i = lo + k;
+      if (k < per && i < n) {
+        const u64 x = sm.keys[i];
+        const u64 p = level_pos(x, s, m);
+        const unsigned bit = 1u << (p & 31);
+        const bool placed = (sm.hit[p >> 5] & ~sm.col[p >> 5]) & bit;
+        if (!placed) {
+          mine[k] = x;
+          keepmask |= 1u << k;
+          c++;
+        }
+      }
+    }
+    unsigned total;
+    unsigned pre = block_scan_u32<kTailThreads>(c, sm.red, &total);
+    // every thread has read its keys (block_scan synchronises)
+#pragma unroll
+    for (unsigned k = 0; k < KMAX; k++) {
+      if (keepmask & (1u << k)) sm.keys[pre++] = mine[k];
+    }
+    const u64 wt = block_sum<kTailThreads>(wsum, sm.red64);
+    if (threadIdx.x == 0) {
+      if (wt + total != n) atomicOr(status, ST_INTERNAL);
+      lvs[d].n = n;
+      lvs[d].m = m;
+      lvs[d].off = off;
+      lvs[d].weight = wt;
+      lvs[d].mode = LM_FLAT;
+    }
+    n = total;
+    off += m;
+    d++;
+    if (threadIdx.x == 0) {
+      lvs[d].n = n;
+      lvs[d].off = off;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ TailSmem carve_tail(unsigned char *smem, u64 mcap) {
+  TailSmem t;
+  t.keys = reinterpret_cast<u64 *>(smem);
+  t.hit = reinterpret_cast<unsigned *>(smem + kTailMaxKeys * 8);
+  t.col = t.hit + (mcap >> 5);
+  t.red64 = reinterpret_cast<u64 *>(t.col + (mcap >> 5));
+  t.red = reinterpret_cast<unsigned *>(t.red64 + 32);
+  return t;
+}
+
+static size_t tail_smem_bytes(u64 mcap) {
+  return kTailMaxKeys * 8 + 2 * (mcap >> 5) * 4 + 32 * 8 + 40 * 4;
+}
+
+
 }  // namespace bbh

@@ -80,6 +80,10 @@ def lib():
         "mphf_keygen": ([vp, u64, u64, u64, vp], i32),
         "mphf_build_path": ([vp], i32),
         "mphf_debug_config": ([i32, dbl], i32),
+        "mphf_build_batched": ([vp, vp, u32, dbl, u32, u64, vp, vp], i32),
+        "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
+        "mphf_batched_debug_config": ([dbl], i32),
+        "mphf_workspace_release": ([], None),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -258,6 +262,47 @@ def _host_ptr(orig, arr: np.ndarray) -> Optional[int]:
     except ImportError:  # pragma: no cover
         pass
     return arr.ctypes.data if arr.size else None
+
+
+def _offsets(offsets) -> np.ndarray:
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    if off.ndim != 1 or off.size < 2:
+        raise ValueError("offsets must hold S + 1 entries")
+    return off
+
+
+def build_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: int = 0,
+                  stream=None) -> list:
+    """One function per key set: set s is keys[offsets[s]:offsets[s+1]]."""
+    keys = _dev_keys(keys)
+    off = _offsets(offsets)
+    S = off.size - 1
+    arr = (ctypes.c_void_p * S)()
+    rc = lib().mphf_build_batched(keys.data_ptr() if keys.numel() else None, off.ctypes.data, S,
+                                  float(gamma), int(levels), int(seed) & NOT_FOUND,
+                                  _stream_ptr(stream), arr)
+    _check(rc, "mphf_build_batched")
+    return [MPHF(ctypes.c_void_p(arr[i])) for i in range(S)]
+
+
+def autotune_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: int = 0,
+                     stream=None) -> float:
+    keys = _dev_keys(keys)
+    off = _offsets(offsets)
+    best = ctypes.c_double(0.0)
+    rc = lib().mphf_autotune_batched(keys.data_ptr() if keys.numel() else None, off.ctypes.data,
+                                     off.size - 1, float(gamma), int(levels), int(seed) & NOT_FOUND,
+                                     _stream_ptr(stream), ctypes.byref(best))
+    _check(rc, "mphf_autotune_batched")
+    return best.value
+
+
+def batched_debug_config(cap_scale: float = 1.0):
+    _check(lib().mphf_batched_debug_config(float(cap_scale)), "mphf_batched_debug_config")
+
+
+def workspace_release():
+    lib().mphf_workspace_release()
 
 
 def build(keys, gamma: float = 2.0, levels: int = 25, seed: int = 0, stream=None) -> MPHF:
