@@ -173,6 +173,29 @@ int mphf_build_path(const mphf_t *h);
  * value < 1 forces the fallback.  Not thread-safe against concurrent builds. */
 int mphf_debug_config(int path, double cap_scale);
 
+/*
+ * Rank table of a bit array without allocating device memory.  The paper has
+ * no counterpart: this is an allocation-free variant of the rank-table build
+ * that mphf_build runs internally, for callers that must not call cudaMalloc:
+ * code that records work into a CUDA graph (cudaMalloc cannot be captured),
+ * serving loops that run under a fixed device-memory budget, and hosts whose
+ * own allocator owns the device memory (a direct cudaMalloc there fragments
+ * that pool and stalls the device).
+ *   d_words  device array of nwords 64-bit words (16-byte aligned).
+ *   d_rank2  device output of 2 * ceil(nwords / 8) words (16-byte aligned):
+ *            d_rank2[2b] = ones of the array in bits [0, 512 b), d_rank2[2b+1]
+ *            = seven 9-bit in-block prefix counts (the layout handles use).
+ *   d_total  optional device word receiving the total number of ones.
+ * Scratch lives in a fixed array inside the library: at most 2^27 words
+ * (2^33 bits) per call; larger inputs return MPHF_EINVAL.  The first call on
+ * each device looks up that array's device address (make it before any stream
+ * capture that should contain later calls).  All calls share the array:
+ * calls whose work may overlap on the GPU (different streams without ordering)
+ * race and must be avoided.  Asynchronous on `stream`.
+ */
+int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords, uint64_t *d_rank2,
+                            uint64_t *d_total, void *stream);
+
 /* ---- synthetic keys ------------------------------------------------------ */
 /*
  * d_out[i] = output (start + i) of the SplitMix64 generator started at state

@@ -14,6 +14,8 @@
 // checkpoint adds its CTA's prefix.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bbh {
@@ -147,3 +149,70 @@ int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_tot
 }
 
 }  // namespace bbh
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the rank-table build, for callers that cannot
+// allocate device memory.  The per-CTA partial sums that build_rank_table
+// allocates live instead in this file-scope device array.  It is sized for at
+// most kNoAllocMaxCtas CTAs, i.e. 2^24 rank blocks of 512 bits (2^27 words of
+// A, 2^33 bits).  Every process that loads the library holds it on every GPU
+// it uses, until exit.
+// ---------------------------------------------------------------------------
+namespace bbh {
+
+static constexpr u64 kNoAllocMaxCtas = 65536;
+static __device__ __align__(256) u64 g_rank_scratch[kNoAllocMaxCtas];
+
+static std::mutex g_noalloc_mu;
+static u64 *g_noalloc_ptr[64] = {nullptr};  // device address of g_rank_scratch, per device
+
+}  // namespace bbh
+
+extern "C" int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords,
+                                       uint64_t *d_rank2, uint64_t *d_total, void *stream) {
+  using namespace bbh;
+  const u64 nrank = (nwords + 7) / 8;
+  if (nwords > 0 && (!d_words || !d_rank2)) return MPHF_EINVAL;
+  if (((uintptr_t)d_words & 15) || ((uintptr_t)d_rank2 & 15) || ((uintptr_t)d_total & 7))
+    return MPHF_EINVAL;
+  const u64 ctas = (nrank + kRankThreads - 1) / kRankThreads;
+  if (ctas > kNoAllocMaxCtas) return MPHF_EINVAL;  // beyond the fixed scratch
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  MPHF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return MPHF_EINVAL;
+  u64 *scratch;
+  {
+    // First call on a device: look up the array's device address (the host
+    // symbol g_rank_scratch is only a stand-in and must not be passed).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_rank_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(rank scratch)");
+      g_noalloc_ptr[dev] = (u64 *)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (nrank == 0) {
+    if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
+    return MPHF_OK;
+  }
+  // every used entry of the scratch is written by k_rank_blocks before it is
+  // read, so nothing needs clearing between calls
+  {
+    LaunchScope ls("rank_blocks", s);
+    k_rank_blocks<<<(unsigned)ctas, kRankThreads, 0, s>>>((const u64 *)d_words, nwords,
+                                                          (u64 *)d_rank2, nrank, scratch);
+  }
+  {
+    LaunchScope ls("rank_scan", s);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(scratch, ctas, (u64 *)d_total);
+  }
+  if (ctas > 1) {
+    LaunchScope ls("rank_add", s);
+    k_rank_add<<<(unsigned)ctas, kRankThreads, 0, s>>>((u64 *)d_rank2, nrank, scratch);
+  }
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}

@@ -84,6 +84,7 @@ def lib():
         "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
         "mphf_batched_debug_config": ([dbl], i32),
         "mphf_workspace_release": ([], None),
+        "mphf_rank_table_noalloc": ([vp, u64, vp, vp, vp], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
