@@ -43,6 +43,7 @@ extern "C" {
 #endif
 
 typedef struct mphf mphf_t;
+typedef struct mphf_server mphf_server_t;
 
 #define MPHF_NOT_FOUND UINT64_MAX
 #define MPHF_MAX_LEVELS 64
@@ -195,6 +196,59 @@ int mphf_debug_config(int path, double cap_scale);
  */
 int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords, uint64_t *d_rank2,
                             uint64_t *d_total, void *stream);
+
+/* ---- many functions, many requests --------------------------------------- */
+/*
+ * One launch answering nreq lookup requests against different functions:
+ * request i queries counts[i] keys d_keys[i] of function hs[i] into d_out[i]
+ * (Algorithm 3 for each).  Asynchronous on `stream`; the arrays are host
+ * arrays read before return.  Results equal mphf_lookup's for each request.
+ */
+int mphf_lookup_multi(mphf_t *const *hs, const uint64_t *const *d_keys, uint64_t *const *d_out,
+                      const uint64_t *counts, uint32_t nreq, void *stream);
+
+/*
+ * Serving loop for functions resident in HBM (current device).  Lookup
+ * requests are queued and, whenever one of `max_inflight` launch slots is
+ * free, everything pending (up to max_batch_keys keys / max_batch_reqs
+ * requests) is answered by one mphf_lookup_multi-style launch; requests that
+ * arrive meanwhile join the next launch.  Build requests run on
+ * `build_workers` worker threads, each with its own stream, admitted once
+ * their memory footprint fits the free device memory minus
+ * mem_reserve_bytes.  Handles passed to lookups must stay alive until their
+ * requests complete; keys and outputs are device arrays owned by the caller.
+ */
+int mphf_server_create(uint64_t max_batch_keys, uint32_t max_batch_reqs, int max_inflight,
+                       int build_workers, uint64_t mem_reserve_bytes, mphf_server_t **out);
+/* Stops the loop after the launched work has finished; pending requests are dropped. */
+void mphf_server_destroy(mphf_server_t *srv);
+int mphf_server_submit_lookup(mphf_server_t *srv, mphf_t *h, const uint64_t *d_keys, uint64_t n,
+                              uint64_t *d_out, uint64_t *req_id);
+int mphf_server_submit_build(mphf_server_t *srv, const uint64_t *d_keys, uint64_t n, double gamma,
+                             uint32_t levels, uint64_t seed, uint64_t *req_id);
+/* Wait for a request (at most timeout_s, else MPHF_ETIMEOUT); returns its status,
+ * its latency from submission to completion in seconds and, for a build, the
+ * new handle (owned by the caller).  A request can be waited for once. */
+int mphf_server_wait(mphf_server_t *srv, uint64_t req_id, double timeout_s, int *status,
+                     double *latency_s, mphf_t **built);
+int mphf_server_stats(mphf_server_t *srv, uint64_t *batches, uint64_t *requests, uint64_t *keys,
+                      uint64_t *builds);
+/*
+ * Measurement driver: an open-loop Poisson stream of requests at rate_hz for
+ * duration_s against the server.  Each lookup picks one of the nh handles
+ * uniformly and a batch of log-uniform size in [bmin, bmax] of consecutive
+ * member keys at a random offset of keys[h] (count[h] keys), writing into the
+ * device ring d_out (out_cap words >= bmax).  A fraction build_frac of the
+ * arrivals are builds over a prefix of build_keys of log-uniform size in
+ * [nbmin, nbmax].  Latencies of the lookups (seconds) go to lat_out.
+ */
+int mphf_server_loadgen(mphf_server_t *srv, mphf_t *const *hs, const uint64_t *const *keys,
+                        const uint64_t *count, uint32_t nh, double rate_hz, double duration_s,
+                        double bmin, double bmax, uint64_t *d_out, uint64_t out_cap,
+                        double build_frac, const uint64_t *build_keys, uint64_t n_build_keys,
+                        double nbmin, double nbmax, double gamma, uint64_t seed, double *lat_out,
+                        uint64_t lat_cap, uint64_t *n_lookups_out, uint64_t *n_keys_out,
+                        uint64_t *n_builds_out, double *elapsed_out);
 
 /* ---- synthetic keys ------------------------------------------------------ */
 /*

@@ -145,6 +145,7 @@ void mphf_free(mphf_t *h) {
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
+  if (h->ldesc.p) cudaFree(h->ldesc.p);
   if (h->shared) {
     release_shared(h->shared);
   } else {

@@ -164,4 +164,5 @@ struct mphf {
   int device = 0;
   int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched construction
   mphf_shared *shared = nullptr;  // set: A/rank/fb live in a batched arena
+  bbh::DevBuf ldesc;     // device descriptor for multi-function lookups (made on first use)
 };

@@ -85,6 +85,16 @@ def lib():
         "mphf_batched_debug_config": ([dbl], i32),
         "mphf_workspace_release": ([], None),
         "mphf_rank_table_noalloc": ([vp, u64, vp, vp, vp], i32),
+        "mphf_lookup_multi": ([vp, vp, vp, vp, u32, vp], i32),
+        "mphf_server_create": ([u64, u32, i32, i32, u64, pvp], i32),
+        "mphf_server_destroy": ([vp], None),
+        "mphf_server_submit_lookup": ([vp, vp, vp, u64, vp, pu64], i32),
+        "mphf_server_submit_build": ([vp, vp, u64, dbl, u32, u64, pu64], i32),
+        "mphf_server_wait": ([vp, u64, dbl, ctypes.POINTER(i32), ctypes.POINTER(dbl), pvp], i32),
+        "mphf_server_stats": ([vp, pu64, pu64, pu64, pu64], i32),
+        "mphf_server_loadgen": ([vp, vp, vp, vp, u32, dbl, dbl, dbl, dbl, vp, u64, dbl, vp, u64,
+                                 dbl, dbl, dbl, u64, vp, u64, pu64, pu64, pu64,
+                                 ctypes.POINTER(dbl)], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -324,6 +334,96 @@ def debug_config(path: int = 0, cap_scale: float = 1.0):
     """Test hook: path 0 = bucketed with fallback (default), 1 = unbucketed only;
     cap_scale < 1 shrinks bucket capacities so that the fallback is taken."""
     _check(lib().mphf_debug_config(int(path), float(cap_scale)), "mphf_debug_config")
+
+
+def lookup_multi(handles, keys_list, outs_list=None, stream=None):
+    """One launch answering several lookup requests against different functions."""
+    import torch
+    n = len(handles)
+    keys_list = [_dev_keys(k) for k in keys_list]
+    if outs_list is None:
+        outs_list = [torch.empty(k.numel(), dtype=torch.int64, device=k.device) for k in keys_list]
+    H = (ctypes.c_void_p * n)(*[h.handle for h in handles])
+    K = (ctypes.c_void_p * n)(*[k.data_ptr() for k in keys_list])
+    O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs_list])
+    C = (ctypes.c_uint64 * n)(*[k.numel() for k in keys_list])
+    _check(lib().mphf_lookup_multi(H, K, O, C, n, _stream_ptr(stream)), "mphf_lookup_multi")
+    return outs_list
+
+
+class Server:
+    """The C serving loop (continuous batching of lookups, admitted builds)."""
+
+    def __init__(self, max_batch_keys=1 << 22, max_batch_reqs=4096, max_inflight=3,
+                 build_workers=2, mem_reserve=2 << 30):
+        p = ctypes.c_void_p()
+        _check(lib().mphf_server_create(int(max_batch_keys), int(max_batch_reqs),
+                                        int(max_inflight), int(build_workers), int(mem_reserve),
+                                        ctypes.byref(p)), "mphf_server_create")
+        self._p = p
+        self._keep = {}
+
+    def close(self):
+        if self._p is not None and self._p.value:
+            lib().mphf_server_destroy(self._p)
+        self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def submit_lookup(self, h: "MPHF", keys, out) -> int:
+        rid = ctypes.c_uint64()
+        _check(lib().mphf_server_submit_lookup(self._p, h.handle, keys.data_ptr(), keys.numel(),
+                                               out.data_ptr(), ctypes.byref(rid)),
+               "mphf_server_submit_lookup")
+        self._keep[rid.value] = (keys, out)
+        return rid.value
+
+    def submit_build(self, keys, gamma=2.0, levels=25, seed=0) -> int:
+        rid = ctypes.c_uint64()
+        _check(lib().mphf_server_submit_build(self._p, keys.data_ptr(), keys.numel(), float(gamma),
+                                              int(levels), int(seed) & NOT_FOUND,
+                                              ctypes.byref(rid)), "mphf_server_submit_build")
+        self._keep[rid.value] = (keys,)
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 600.0):
+        """(status, latency_s, built MPHF or None)."""
+        st, lat, built = ctypes.c_int(), ctypes.c_double(), ctypes.c_void_p()
+        rc = lib().mphf_server_wait(self._p, rid, float(timeout), ctypes.byref(st),
+                                    ctypes.byref(lat), ctypes.byref(built))
+        if rc != OK:
+            raise MPHFError(rc, "mphf_server_wait")
+        self._keep.pop(rid, None)
+        return st.value, lat.value, (MPHF(built) if built.value else None)
+
+    def stats(self):
+        v = [ctypes.c_uint64() for _ in range(4)]
+        _check(lib().mphf_server_stats(self._p, *[ctypes.byref(x) for x in v]), "mphf_server_stats")
+        return dict(zip(("batches", "requests", "keys", "builds"), (x.value for x in v)))
+
+    def loadgen(self, handles, keys_list, rate_hz, duration_s, bmin, bmax, out, build_frac=0.0,
+                build_keys=None, nbmin=1e5, nbmax=1e7, gamma=2.0, seed=1, lat_cap=1 << 22):
+        n = len(handles)
+        H = (ctypes.c_void_p * n)(*[h.handle for h in handles])
+        K = (ctypes.c_void_p * n)(*[k.data_ptr() for k in keys_list])
+        C = (ctypes.c_uint64 * n)(*[k.numel() for k in keys_list])
+        lat = np.empty(int(lat_cap), dtype=np.float64)
+        nl, nk, nb, el = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+        rc = lib().mphf_server_loadgen(
+            self._p, H, K, C, n, float(rate_hz), float(duration_s), float(bmin), float(bmax),
+            out.data_ptr(), out.numel(), float(build_frac),
+            build_keys.data_ptr() if build_keys is not None else None,
+            build_keys.numel() if build_keys is not None else 0, float(nbmin), float(nbmax),
+            float(gamma), int(seed), lat.ctypes.data, lat.size, ctypes.byref(nl), ctypes.byref(nk),
+            ctypes.byref(nb), ctypes.byref(el))
+        _check(rc, "mphf_server_loadgen")
+        m = int(min(nl.value, lat.size))
+        return {"latencies": lat[:m].copy(), "lookups": nl.value, "keys": nk.value,
+                "builds": nb.value, "elapsed": el.value}
 
 
 def launch_count() -> int:
