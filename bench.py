@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep", action="store_true", help="also time gamma = 1 and 5")
+    p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-seconds", type=float, default=3.0)
     return p.parse_args()
 
 
@@ -188,6 +191,149 @@ def algorithmic_bytes(h, name: str) -> int:
     if name == "lookup":
         return 16 * sizes[0]
     return 0
+
+
+def run_batched(args, stream):
+    """4096 key sets, sizes log-uniform in [1e3, 1e6] (seed 7), gamma = 2, L = 25:
+    one batched build (recorded level loop, autotuned bucket width) vs the
+    same sets built one by one with mphf_build; then all keys looked up in one
+    multi-function launch."""
+    import torch
+
+    from paper_1702_03154_gb300 import inputs, mphf
+    S = 4096
+    sizes = inputs.log_uniform_sizes(S, 1e3, 1e6, 7)
+    off = inputs.set_offsets(sizes)
+    total = int(off[-1])
+    keys = mphf.keygen(total, 7)
+    torch.cuda.synchronize()
+    tune_ms = mphf.autotune_batched(keys, off, gamma=2.0, levels=25, seed=0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = []
+    launches = 0
+    for rep in range(4):
+        l0 = mphf.launch_count()
+        ev[0].record(stream)
+        hs = mphf.build_batched(keys, off, gamma=2.0, levels=25, seed=0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(ev[0].elapsed_time(ev[1]))
+            launches = mphf.launch_count() - l0
+        if rep < 3:
+            del hs
+    t_b = float(np.median(times))
+    # the same sets, one mphf_build each
+    ev[0].record(stream)
+    singles = [mphf.MPHF.build(keys[int(off[i]):int(off[i + 1])], gamma=2.0, levels=25, seed=0)
+               for i in range(S)]
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_p = ev[0].elapsed_time(ev[1])
+    del singles
+    # every key of every set, one multi-function launch
+    out = torch.empty_like(keys)
+    ks = [keys[int(off[i]):int(off[i + 1])] for i in range(S)]
+    os_ = [out[int(off[i]):int(off[i + 1])] for i in range(S)]
+    mphf.lookup_multi(hs, ks, os_)
+    torch.cuda.synchronize()
+    mphf.profile_report()
+    mphf.profile_enable(True)
+    mphf.lookup_multi(hs, ks, os_)       # kernel time from its own events
+    torch.cuda.synchronize()
+    mphf.profile_enable(False)
+    t_l = mphf.profile_report()["lookup_multi"][1]
+    paths = {}
+    for h in hs:
+        paths[h.build_path] = paths.get(h.build_path, 0) + 1
+    res = {"sets": S, "keys": total, "gamma": 2.0, "levels": 25,
+           "batched_build_ms": round(t_b, 3), "batched_build_mkeys_s": round(total / t_b / 1e3, 1),
+           "per_set_build_ms": round(t_p, 3), "per_set_build_mkeys_s": round(total / t_p / 1e3, 1),
+           "speedup_vs_per_set": round(t_p / t_b, 2),
+           "lookup_all_ms": round(t_l, 3), "lookup_mkeys_s": round(total / t_l / 1e3, 1),
+           "autotune_best_ms": round(tune_ms, 3), "kernels_per_batched_build": int(launches),
+           "handles_by_path": {str(k): v for k, v in sorted(paths.items())}}
+    del hs, keys, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_serving(args, stream):
+    """256 resident functions, sizes log-uniform in [1e4, 1e7] (seed 11), gamma = 2;
+    open-loop Poisson lookups (batch sizes log-uniform in [1, 1e6] of member keys)
+    plus 1% build requests of 1e5-1e7 keys, at 50% and 90% of the measured
+    capacity of the multi-function lookup."""
+    import torch
+
+    from paper_1702_03154_gb300 import inputs, mphf
+    H = 256
+    sizes = inputs.log_uniform_sizes(H, 1e4, 1e7, 11)
+    off = inputs.set_offsets(sizes)
+    total = int(off[-1])
+    keys = mphf.keygen(total, 11)
+    hs = mphf.build_batched(keys, off, gamma=2.0, levels=25, seed=0)
+    ks = [keys[int(off[i]):int(off[i + 1])] for i in range(H)]
+    build_keys = mphf.keygen(10_000_000, 12)
+    resident_bytes = sum(h.device_bytes() for h in hs)
+    # capacity: back-to-back launches of requests drawn like the load (mean batch)
+    rng = np.random.default_rng(2)
+    reqs = []
+    while sum(r[2] for r in reqs) < 2e8:
+        i = int(rng.integers(H))
+        b = int(np.exp(rng.uniform(0, np.log(1e6))))
+        b = min(b, int(sizes[i]))
+        o = int(rng.integers(0, int(sizes[i]) - b + 1))
+        reqs.append((i, o, b))
+    out = torch.empty(1 << 23, dtype=torch.int64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    batch, keys_in = [], 0
+    groups = []
+    for r in reqs:
+        batch.append(r)
+        keys_in += r[2]
+        if keys_in >= (1 << 22):
+            groups.append(batch)
+            batch, keys_in = [], 0
+    if batch:
+        groups.append(batch)
+    nk = 0
+    mphf.profile_report()
+    mphf.profile_enable(True)
+    for g in groups:
+        ring = 0
+        ho, ko, oo = [], [], []
+        for (i, o, b) in g:
+            ho.append(hs[i])
+            ko.append(ks[i][o:o + b])
+            oo.append(out[ring:ring + b])
+            ring += b
+            nk += b
+        mphf.lookup_multi(ho, ko, oo)
+    torch.cuda.synchronize()
+    mphf.profile_enable(False)
+    cap_keys_s = nk / (mphf.profile_report()["lookup_multi"][1] / 1e3)
+    mean_batch = float(np.mean([r[2] for r in reqs]))
+    res = {"functions": H, "resident_keys": total, "resident_bytes": int(resident_bytes),
+           "capacity_mkeys_s": round(cap_keys_s / 1e6, 1), "mean_batch_keys": round(mean_batch, 1),
+           "loads": {}}
+    srv = mphf.Server(max_batch_keys=1 << 22, max_batch_reqs=4096, max_inflight=3,
+                      build_workers=2, mem_reserve=8 << 30)
+    ring_out = torch.empty(1 << 24, dtype=torch.int64, device="cuda")
+    for load in (0.5, 0.9):
+        rate = load * cap_keys_s / mean_batch
+        r = srv.loadgen(hs, ks, rate_hz=rate, duration_s=args.serve_seconds, bmin=1, bmax=1e6,
+                        out=ring_out, build_frac=0.01, build_keys=build_keys, nbmin=1e5, nbmax=1e7,
+                        gamma=2.0, seed=int(load * 100))
+        lat = r["latencies"] * 1e3
+        res["loads"][f"{int(load * 100)}%"] = {
+            "offered_req_s": round(rate, 1), "lookups": r["lookups"], "builds": r["builds"],
+            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mkeys_s": round(r["keys"] / r["elapsed"] / 1e6, 1)}
+    srv.close()
+    del hs, keys, build_keys, out, ring_out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -340,6 +486,13 @@ def run_ours(args):
             sweep[f"gamma={g2:g}"] = {"mkeys_s": round(N / (np.median(ts) / 1e3) / 1e6, 1),
                                       "ms": round(float(np.median(ts)), 3)}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, stream)
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(10_000_000, gamma, L)
@@ -360,6 +513,10 @@ def run_ours(args):
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu}
         if sweep:
             line["gamma_sweep"] = sweep
+        if batched:
+            line["batched"] = batched
+        if serving:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
