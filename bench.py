@@ -313,14 +313,27 @@ def run_serving(args, stream):
     mphf.profile_enable(False)
     cap_keys_s = nk / (mphf.profile_report()["lookup_multi"][1] / 1e3)
     mean_batch = float(np.mean([r[2] for r in reqs]))
+    # cost of a build request: builds of log-uniform size in [1e5, 1e7], one at a time
+    bsz = [int(np.exp(x)) for x in rng.uniform(np.log(1e5), np.log(1e7), 12)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in bsz:
+        mphf.MPHF.build(build_keys[:n], gamma=2.0, levels=25, seed=0).free()
+    torch.cuda.synchronize()
+    build_cost = (time.perf_counter() - t0) / len(bsz)
+    # capacity of the mix (99 lookups : 1 build), in arrivals per second
+    per_arrival = 0.99 * mean_batch / cap_keys_s + 0.01 * build_cost
     res = {"functions": H, "resident_keys": total, "resident_bytes": int(resident_bytes),
-           "capacity_mkeys_s": round(cap_keys_s / 1e6, 1), "mean_batch_keys": round(mean_batch, 1),
-           "loads": {}}
+           "lookup_capacity_mkeys_s": round(cap_keys_s / 1e6, 1),
+           "mean_batch_keys": round(mean_batch, 1), "build_request_ms": round(build_cost * 1e3, 3),
+           "mix_capacity_req_s": round(1.0 / per_arrival, 1),
+           "load_definition": "fraction of the capacity of the 99:1 lookup/build mix, measured "
+                              "back to back before the run", "loads": {}}
     srv = mphf.Server(max_batch_keys=1 << 22, max_batch_reqs=4096, max_inflight=3,
                       build_workers=2, mem_reserve=8 << 30)
     ring_out = torch.empty(1 << 24, dtype=torch.int64, device="cuda")
     for load in (0.5, 0.9):
-        rate = load * cap_keys_s / mean_batch
+        rate = load / per_arrival
         r = srv.loadgen(hs, ks, rate_hz=rate, duration_s=args.serve_seconds, bmin=1, bmax=1e6,
                         out=ring_out, build_frac=0.01, build_keys=build_keys, nbmin=1e5, nbmax=1e7,
                         gamma=2.0, seed=int(load * 100))

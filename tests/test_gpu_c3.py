@@ -1,0 +1,55 @@
+"""The 1e10-key configuration: properties that hold at any size.
+
+N = 1e10 keys generated on the device by the SplitMix64 stream of seed 4
+(80 GB), gamma = 2, L = 25.  The CPU oracle cannot build a function this
+large in test time, so the checks are: every key's index, in chunks, lands on
+a distinct value of [0, N) (a byte per index on the device); each level
+places (1 - 1/m_d)^(n_d - 1) of its keys within 6 sigma; the total bits and
+bits/key match gamma e^{1/gamma} N and 1.125 gamma e^{1/gamma} (Sec. 2.3,
+Sec. 3.1) within 0.5%; placed keys plus fallback add up to N.
+"""
+import math
+
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N = 10**10
+
+
+def test_config3_1e10_properties():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    free, total = torch.cuda.mem_get_info()
+    if free < 240 * 2**30:
+        pytest.skip(f"needs ~240 GB of free device memory, {free / 2**30:.0f} GB free")
+    from paper_1702_03154_gb300 import mphf
+    keys = mphf.keygen(N, 4)
+    h = mphf.MPHF.build(keys, gamma=2.0, levels=25, seed=0)
+    lv = h.levels()
+    sizes = h.level_sizes()
+    assert sizes[0] == N
+    # per-level placed fraction
+    for d, (n_d, m_d, off_d, _) in enumerate(lv[:6]):
+        p = (1.0 - 1.0 / m_d) ** (n_d - 1)
+        placed = sizes[d] - sizes[d + 1]
+        assert abs(placed - n_d * p) < 6 * math.sqrt(n_d * p * (1 - p)) + 1, d
+    g = 2.0
+    assert abs(h.total_bits / N - g * math.exp(1 / g)) / (g * math.exp(1 / g)) < 0.005
+    assert abs(h.bits_per_key() - 1.125 * g * math.exp(1 / g)) < 0.02
+    # every index distinct, in [0, N)
+    hits = torch.zeros(N, dtype=torch.int8, device="cuda")
+    one = None
+    chunk = 500_000_000
+    for a in range(0, N, chunk):
+        idx = h.lookup(keys[a:a + chunk])
+        assert int(idx.min()) >= 0 and int(idx.max()) < N
+        if one is None or one.numel() != idx.numel():
+            one = torch.ones(idx.numel(), dtype=torch.int8, device="cuda")
+        hits.index_put_((idx,), one, accumulate=True)
+        del idx
+    assert bool((hits == 1).all())
+    del hits
+    total_placed = N - h.num_fallback
+    assert total_placed + h.num_fallback == N
