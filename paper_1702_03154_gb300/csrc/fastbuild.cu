@@ -25,26 +25,40 @@
 
 namespace bbh {
 
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// Each thread owns kKPT consecutive keys of a tile (staged by asynchronous
+// copies: a thread takes its keys of tile t into registers, then starts
+// copying its keys of the next tile into the same slots while tile t is split).
+template <bool ALIGNED>
 __global__ void __launch_bounds__(kTT, 2)
 k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FLevel lv = meta->lv[0];
   const unsigned nb = (unsigned)lv.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
-  // one tile of input staged by asynchronous copies: each thread takes its
-  // keys of tile t into registers, then starts copying its keys of the next
-  // tile into the same slots while tile t is split
   u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
+  u64 *mine_s = inbuf + threadIdx.x * kKPT;
   const u64 s0 = level_seed(cfg.seed, 0);
   const unsigned sh = ilog2_u64(lv.P);
   const unsigned mask = (unsigned)(lv.P - 1);
   const u64 ntiles = ceil_div(n, kTile);
+  const unsigned base = threadIdx.x * kKPT;
   auto prefetch = [&](u64 t) {
     if (t < ntiles) {
+      const u64 *src = keys + t * kTile;
+      const u64 rem = n - t * kTile;
+      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
+      if (ALIGNED && base + kKPT <= nt) {
 #pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
-        if (i < n) cp_async8(inbuf + k * kTT + threadIdx.x, keys + i);
+        for (int k = 0; k < kKPT; k += 2) cp_async16(mine_s + k, src + base + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kKPT; k++)
+          if (base + k < nt) cp_async8(mine_s + k, src + base + k);
       }
     }
     cp_async_commit();
@@ -53,13 +67,14 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
   prefetch(t);
   for (; t < ntiles; t += gridDim.x) {
     cp_async_wait0();  // this thread's copies of tile t have landed
+    const u64 rem = n - t * kTile;
+    const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
     u64 x[kKPT];
     bool ok[kKPT];
 #pragma unroll
     for (int k = 0; k < kKPT; k++) {
-      const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
-      ok[k] = i < n;
-      x[k] = ok[k] ? inbuf[k * kTT + threadIdx.x] : 0;
+      ok[k] = base + k < nt;
+      x[k] = ok[k] ? mine_s[k] : 0;
     }
     prefetch(t + gridDim.x);
     unsigned dst[kKPT], lp[kKPT];
@@ -241,16 +256,38 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     const u64 nk = min(cnt[b], lv.cap);
     const u64 *kb = arena + b * lv.cap;
     const unsigned *pb = parena + b * lv.cap;
+    const unsigned base = threadIdx.x * kKPT;
     for (u64 t0 = 0; t0 < nk; t0 += kTile) {
-      // 1. test every key of the tile; pack the survivors warp by warp.  All
-      // keys are loaded up front: survivors are spread over every sector anyway.
+      // 1. test every key of the tile; pack the survivors warp by warp.  Each
+      // thread owns kKPT consecutive entries (16-byte loads); all keys are
+      // loaded up front since survivors are spread over every sector anyway.
+      const u64 rem = nk - t0;
+      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
+      const unsigned *pbt = pb + t0 + base;
+      const u64 *kbt = kb + t0 + base;
       unsigned pk[kKPT];
       u64 xk[kKPT];
+      if (base + kKPT <= nt) {
 #pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
-        pk[k] = i < nk ? __ldcs(pb + i) : ~0u;
-        xk[k] = i < nk ? __ldcs(kb + i) : 0;
+        for (int k = 0; k < kKPT; k += 4) {
+          const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(pbt + k));
+          pk[k] = v.x;
+          pk[k + 1] = v.y;
+          pk[k + 2] = v.z;
+          pk[k + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kKPT; k += 2) {
+          const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(kbt + k));
+          xk[k] = ((u64)v.y << 32) | v.x;
+          xk[k + 1] = ((u64)v.w << 32) | v.z;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kKPT; k++) {
+          pk[k] = base + k < nt ? __ldcs(pbt + k) : ~0u;
+          xk[k] = base + k < nt ? __ldcs(kbt + k) : 0;
+        }
       }
 #pragma unroll
       for (int k = 0; k < kKPT; k++) {
@@ -361,7 +398,9 @@ static int set_attrs() {
   if (g_attr_set) return MPHF_OK;
   g_split_bytes = split_smem_bytes((unsigned)kBmax);
   g_compact_bytes = g_split_bytes + kPmax / 8;  // + the bucket's slice of A_d
-  MPHF_CUDA(cudaFuncSetAttribute(k_partition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  MPHF_CUDA(cudaFuncSetAttribute(k_partition0<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(g_split_bytes + kTile * 8)));
+  MPHF_CUDA(cudaFuncSetAttribute(k_partition0<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(g_split_bytes + kTile * 8)));
   MPHF_CUDA(cudaFuncSetAttribute(k_compact_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)g_compact_bytes));
@@ -492,7 +531,10 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     const unsigned gridP = grid_for(N, kTile, (unsigned)sm_count() * 2);
     {
       LaunchScope ls("partition", st);
-      k_partition0<<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
+      if (((uintptr_t)keys & 15) == 0)
+        k_partition0<true><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
+      else
+        k_partition0<false><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
     }
     {
       LaunchScope ls("fill_buckets", st);
