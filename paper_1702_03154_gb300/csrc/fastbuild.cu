@@ -30,9 +30,11 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-// Each thread owns kKPT consecutive keys of a tile (staged by asynchronous
+// Each thread owns kKPT consecutive keys of a tile, staged by asynchronous
 // copies: a thread takes its keys of tile t into registers, then starts
-// copying its keys of the next tile into the same slots while tile t is split).
+// copying its keys of the next tile into the same slots while tile t is
+// split.  Slot layout: pair q (keys 2q, 2q+1) of thread t at 16-byte unit
+// q * kTT + t, so a warp's reads of one pair hit consecutive 16-byte units.
 template <bool ALIGNED>
 __global__ void __launch_bounds__(kTT, 2)
 k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, FastCfg cfg) {
@@ -41,7 +43,7 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
   const unsigned nb = (unsigned)lv.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
   u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
-  u64 *mine_s = inbuf + threadIdx.x * kKPT;
+  auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * kTT + threadIdx.x) + (k & 1); };
   const u64 s0 = level_seed(cfg.seed, 0);
   const unsigned sh = ilog2_u64(lv.P);
   const unsigned mask = (unsigned)(lv.P - 1);
@@ -54,11 +56,11 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
       const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
       if (ALIGNED && base + kKPT <= nt) {
 #pragma unroll
-        for (int k = 0; k < kKPT; k += 2) cp_async16(mine_s + k, src + base + k);
+        for (int k = 0; k < kKPT; k += 2) cp_async16(slot(k), src + base + k);
       } else {
 #pragma unroll
         for (int k = 0; k < kKPT; k++)
-          if (base + k < nt) cp_async8(mine_s + k, src + base + k);
+          if (base + k < nt) cp_async8(slot(k), src + base + k);
       }
     }
     cp_async_commit();
@@ -72,9 +74,15 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
     u64 x[kKPT];
     bool ok[kKPT];
 #pragma unroll
+    for (int k = 0; k < kKPT; k += 2) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(slot(k));
+      x[k] = ((u64)v.y << 32) | v.x;
+      x[k + 1] = ((u64)v.w << 32) | v.z;
+    }
+#pragma unroll
     for (int k = 0; k < kKPT; k++) {
       ok[k] = base + k < nt;
-      x[k] = ok[k] ? mine_s[k] : 0;
+      if (!ok[k]) x[k] = 0;
     }
     prefetch(t + gridDim.x);
     unsigned dst[kKPT], lp[kKPT];

@@ -14,13 +14,13 @@
 // prefix count of its word (both in one 16-byte entry of the rank table) plus
 // the ones of its own word below g.
 #include <cuda_runtime.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 
 namespace bbh {
 
 static constexpr int kLookupThreads = 256;
-static constexpr int kSlots = 2;
 static constexpr unsigned kChunk = 32 * 64;  // keys a warp takes from the input at a time
 
 struct LevelTable {
@@ -62,6 +62,7 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
+template <int kSlots>
 __global__ void __launch_bounds__(kLookupThreads)
 k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
@@ -166,6 +167,18 @@ static void fill_tables(const mphf_t *h, LookupArgs &a, LevelTable &t) {
   }
 }
 
+// Query slots per lane (2 by default; MPHF_LOOKUP_SLOTS = 3 or 4 trades
+// registers for memory-level parallelism).
+static int lookup_slots() {
+  static int v = 0;
+  if (!v) {
+    const char *e = getenv("MPHF_LOOKUP_SLOTS");
+    v = e ? atoi(e) : 2;
+    if (v < 2 || v > 4) v = 2;
+  }
+  return v;
+}
+
 int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t s) {
   LookupArgs a;
   LevelTable t;
@@ -177,7 +190,11 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  k_lookup<<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
+  switch (lookup_slots()) {
+    case 3: k_lookup<3><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+    case 4: k_lookup<4><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+    default: k_lookup<2><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+  }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
