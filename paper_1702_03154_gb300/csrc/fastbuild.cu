@@ -19,11 +19,16 @@
 // build.cu, so results never depend on these choices.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "fastbuild.cuh"
 
 namespace bbh {
+
+// Scatter variant (tuning experiment): 0 = sort runs in shared memory first,
+// 1 = store each entry straight to its slot.  Chosen by MPHF_DIRECT_SPLIT.
+__constant__ int g_direct_split = 0;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -92,8 +97,12 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
       dst[k] = (unsigned)(p >> sh);
       lp[k] = (unsigned)p & mask;
     }
-    multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
-                           &meta->status);
+    if (g_direct_split)
+      multisplit_write_direct<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP,
+                                    UniformDest{cfg.cntX, lv.cap}, &meta->status);
+    else
+      multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
+                             &meta->status);
   }
   cp_async_wait0();
 }
@@ -333,6 +342,9 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
       if (flat)
         multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                                 &meta->status);
+      else if (g_direct_split)
+        multisplit_write_direct<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+                                      &meta->status);
       else
         multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                                &meta->status);
@@ -404,6 +416,11 @@ static size_t g_split_bytes, g_compact_bytes;
 
 static int set_attrs() {
   if (g_attr_set) return MPHF_OK;
+  {
+    const char *e = getenv("MPHF_DIRECT_SPLIT");
+    const int v = (e && atoi(e) == 1) ? 1 : 0;
+    MPHF_CUDA(cudaMemcpyToSymbol(g_direct_split, &v, sizeof(v)));
+  }
   g_split_bytes = split_smem_bytes((unsigned)kBmax);
   g_compact_bytes = g_split_bytes + kPmax / 8;  // + the bucket's slice of A_d
   MPHF_CUDA(cudaFuncSetAttribute(k_partition0<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
