@@ -26,10 +26,6 @@
 
 namespace bbh {
 
-// Scatter variant (tuning experiment): 0 = sort runs in shared memory first,
-// 1 = store each entry straight to its slot.  Chosen by MPHF_DIRECT_SPLIT.
-__constant__ int g_direct_split = 0;
-
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -97,12 +93,8 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
       dst[k] = (unsigned)(p >> sh);
       lp[k] = (unsigned)p & mask;
     }
-    if (g_direct_split)
-      multisplit_write_direct<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP,
-                                    UniformDest{cfg.cntX, lv.cap}, &meta->status);
-    else
-      multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
-                             &meta->status);
+    multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
+                           &meta->status);
   }
   cp_async_wait0();
 }
@@ -342,9 +334,6 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
       if (flat)
         multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                                 &meta->status);
-      else if (g_direct_split)
-        multisplit_write_direct<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
-                                      &meta->status);
       else
         multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                                &meta->status);
@@ -416,11 +405,7 @@ static size_t g_split_bytes, g_compact_bytes;
 
 static int set_attrs() {
   if (g_attr_set) return MPHF_OK;
-  {
-    const char *e = getenv("MPHF_DIRECT_SPLIT");
-    const int v = (e && atoi(e) == 1) ? 1 : 0;
-    MPHF_CUDA(cudaMemcpyToSymbol(g_direct_split, &v, sizeof(v)));
-  }
+
   g_split_bytes = split_smem_bytes((unsigned)kBmax);
   g_compact_bytes = g_split_bytes + kPmax / 8;  // + the bucket's slice of A_d
   MPHF_CUDA(cudaFuncSetAttribute(k_partition0<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

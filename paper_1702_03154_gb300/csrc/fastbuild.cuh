@@ -238,52 +238,6 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   __syncthreads();
 }
 
-// As multisplit_write, without the shared-memory sort: each entry gets its
-// rank among the tile's entries of its destination from a shared-memory
-// atomic, one atomicAdd per non-empty destination reserves the run, and every
-// entry is stored straight to its slot (stores are scattered across the
-// tile's destinations; L2 merges the partial sectors of each run).
-template <bool WITH_POS, class Dest>
-__device__ void multisplit_write_direct(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
-                                        const unsigned (&dst)[kKPT], const bool (&ok)[kKPT],
-                                        unsigned nb, const SplitSmem &sm, u64 *__restrict__ arena,
-                                        unsigned *__restrict__ parena, const Dest &dest,
-                                        unsigned *__restrict__ status) {
-  for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;
-  __syncthreads();
-  unsigned rk[kKPT];
-#pragma unroll
-  for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
-  __syncthreads();
-  for (unsigned i = threadIdx.x; i < nb; i += kTT) {
-    const unsigned c = sm.cnt[i];
-    u64 b0 = 0, room = 0, base = 0;
-    if (c) {
-      const DestRun r = dest(i);
-      b0 = atomicAdd(r.counter, (u64)c);
-      room = b0 < r.cap ? r.cap - b0 : 0;
-      base = r.base;
-    }
-    sm.lim[i] = (unsigned)(room < c ? room : c);
-    sm.dbase[i] = base + b0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kKPT; k++) {
-    if (ok[k]) {
-      const unsigned b = dst[k];
-      if (rk[k] < sm.lim[b]) {
-        const u64 j = sm.dbase[b] + rk[k];
-        arena[j] = x[k];
-        if (WITH_POS) parena[j] = lp[k];
-      } else {
-        atomicOr(status, ST_OVERFLOW);
-      }
-    }
-  }
-  __syncthreads();
-}
-
 __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
