@@ -114,6 +114,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic(kernel: str, n: int):
+    """DRAM bytes per build of `kernel` from the committed ncu summary (a 3e7-key
+    capture scaled by keys), or None if there is none for this workload."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_n3e7_gamma2.md")
+    if not os.path.exists(p) or n != 10**8:
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_build_n1e8:"):
+            return int(line.split(":")[1])
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -441,8 +453,13 @@ def run_ours(args):
         name, (cnt, tot) = dom
         b = algorithmic_bytes(last, name) * args.steps
         ach = b / (tot / 1e3) / 1e9
+        tr = profiled_traffic(f"k_{name}", N) if gamma == 2.0 else None
         roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": round(tr / (cnt / args.steps), 1) if tr else None,
+                "traffic_note": "DRAM read+write per launch (average over the kernel's launches in "
+                                "one build), from profiles/ (3e7-key ncu capture scaled to 1e8)",
+                "per_launch_algorithmic_bytes": round(b / cnt, 1),
                 "peak_source": f"{peak_kind} hbm_gbs", "launches_per_step": cnt / args.steps,
                 "avg_launch_ms": tot / cnt}
     struct = {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
