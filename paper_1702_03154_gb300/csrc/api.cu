@@ -105,6 +105,30 @@ void dev_free(DevBuf &b, cudaStream_t s) {
   b.bytes = 0;
 }
 
+// About 16 chunks of at least 2^20 keys: the first chunk's copy is the
+// pipeline's fill time, so chunks stay small next to the whole copy, but each
+// still carries far more than a launch's worth of work.
+u64 feed_chunk(u64 n) {
+  const u64 kMin = 1ull << 20;
+  if (n < 4 * kMin) return 0;
+  u64 c = (n + 15) / 16;
+  c = (c + 4095) & ~4095ull;
+  return c < kMin ? kMin : c;
+}
+
+int KeyFeed::ensure(u64 upto, cudaStream_t st) {
+  if (upto > n) upto = n;
+  if (issued >= upto) return MPHF_OK;
+  while (issued < upto) {
+    const u64 c = chunk && upto - issued > chunk ? chunk : upto - issued;
+    MPHF_CUDA(cudaMemcpyAsync(d + issued, h + issued, c * 8, cudaMemcpyHostToDevice, cs));
+    issued += c;
+  }
+  MPHF_CUDA(cudaEventRecord(ev, cs));
+  MPHF_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  return MPHF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Synthetic keys: output j of SplitMix64 started at `seed` is
 // fin(seed + (j + 1) * 0x9E3779B97F4A7C15), fin = the generator's finalizer.

@@ -24,7 +24,7 @@
 namespace bbh {
 
 int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
-               mphf_t *h, bool *fallback_needed);
+               mphf_t *h, bool *fallback_needed, KeyFeed *feed);
 extern double g_cap_scale;
 
 static constexpr int kFillThreads = 256;
@@ -484,8 +484,10 @@ fail:
 
 int g_build_path = 0;  // 0: bucketed, unbucketed on overflow; 1: unbucketed only
 
+// feed (optional): the keys are still arriving from the host; fast_build
+// consumes them chunk by chunk, every other step waits for all of them.
 static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
-                      mphf_t **out) {
+                      mphf_t **out, KeyFeed *feed = nullptr) {
   mphf_t *h = new (std::nothrow) mphf_t();
   if (!h) return MPHF_ENOMEM;
   cudaGetDevice(&h->device);
@@ -501,7 +503,8 @@ static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed
   int rc = MPHF_OK;
   bool redo = true;
   if (g_build_path == 0) {
-    rc = fast_build(keys, N, gamma, L, seed, st, h, &redo);
+    rc = fast_build(keys, N, gamma, L, seed, st, h, &redo, feed);
+    if (rc == MPHF_OK && feed) rc = feed->ensure(N, st);
     if (rc != MPHF_OK) {
       release_handle(h, st);
       cudaStreamSynchronize(st);
@@ -510,7 +513,8 @@ static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed
     h->path = 1;
   }
   if (redo) {
-    rc = robust_build(keys, N, gamma, L, seed, st, h);
+    if (feed) rc = feed->ensure(N, st);
+    if (rc == MPHF_OK) rc = robust_build(keys, N, gamma, L, seed, st, h);
     if (rc != MPHF_OK) {
       release_handle(h, st);
       cudaStreamSynchronize(st);
@@ -552,15 +556,44 @@ extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma,
   DevBuf kb;
   int rc = dev_alloc(kb, n * 8, st);
   if (rc != MPHF_OK) return rc;
-  if (n) {
-    cudaError_t e = cudaMemcpyAsync(kb.p, h_keys, n * 8, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-      dev_free(kb, st);
-      return cuda_fail(e, "cudaMemcpyAsync(H2D keys)");
+  const u64 chunk = feed_chunk(n);
+  if (!chunk) {
+    if (n) {
+      cudaError_t e = cudaMemcpyAsync(kb.p, h_keys, n * 8, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        dev_free(kb, st);
+        return cuda_fail(e, "cudaMemcpyAsync(H2D keys)");
+      }
     }
+    rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out);
+    dev_free(kb, st);
+    return rc;
   }
-  rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out);
+  // Large sets: the level-0 partition runs chunk by chunk behind the copy.
+  KeyFeed f;
+  f.h = (const u64 *)h_keys;
+  f.d = (u64 *)kb.p;
+  f.n = n;
+  f.chunk = chunk;
+  cudaError_t e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
+  // the copies must not start before the buffer's allocation in st's order
+  if (e == cudaSuccess) e = cudaEventRecord(f.ev, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(f.cs, f.ev, 0);
+  if (e == cudaSuccess) {
+    rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out, &f);
+    // every copy ever enqueued is ordered before the buffer's release
+    cudaEventRecord(f.ev, f.cs);
+    cudaStreamWaitEvent(st, f.ev, 0);
+  } else {
+    rc = cuda_fail(e, "mphf_build_host (copy stream)");
+  }
   dev_free(kb, st);
+  if (f.ev) cudaEventDestroy(f.ev);
+  if (f.cs) {
+    if (e != cudaSuccess) cudaStreamSynchronize(f.cs);
+    cudaStreamDestroy(f.cs);
+  }
   return rc;
 }
 

@@ -130,6 +130,26 @@ struct DevBuf {
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
 void dev_free(DevBuf &b, cudaStream_t s);
 
+// Host keys copied to a device buffer in chunks on a side stream, so that the
+// consumer's kernels on the main stream can start on chunk c while chunk c+1
+// is still crossing the host link.  ensure(upto, st) enqueues the copies of
+// keys [issued, upto) and makes st wait for them; ensure(n, st) therefore makes
+// the whole buffer visible to st.  The copies of one call share one event
+// record, and cudaStreamWaitEvent binds the record current at the call, so a
+// single event serves every chunk.
+struct KeyFeed {
+  const u64 *h = nullptr;  // host keys (pinned or pageable)
+  u64 *d = nullptr;        // device buffer of n keys, allocated on the main stream
+  u64 n = 0;
+  u64 chunk = 0;           // keys per copy; a multiple of 4096 keeps chunk starts 16-B aligned
+  u64 issued = 0;          // keys whose copy is enqueued (and awaited by the main stream)
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  int ensure(u64 upto, cudaStream_t st);
+};
+// Keys per chunk for n keys (0 = copy in one piece: too few keys to pipeline).
+u64 feed_chunk(u64 n);
+
 // Rank table over A (rank.cu): rank2[2b] = ones in bits [0, 512 b) (the
 // paper's checkpoint), rank2[2b+1] = in-block prefix counts of words 1..7.
 int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_total,

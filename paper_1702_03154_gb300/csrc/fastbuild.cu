@@ -454,7 +454,7 @@ static u64 tail_limit(double gamma, u64 *mcap_out) {
 // Returns MPHF_OK with *fallback_needed = false on success; *fallback_needed =
 // true (and nothing allocated) when a device-side bound was exceeded.
 int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
-               mphf_t *h, bool *fallback_needed) {
+               mphf_t *h, bool *fallback_needed, KeyFeed *feed) {
   *fallback_needed = false;
   int rc = set_attrs();
   if (rc != MPHF_OK) return rc;
@@ -511,6 +511,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     FTRY(dev_alloc(sc.arena, arena_words * 8, st));
     cfg.arena = (u64 *)sc.arena.p;
     cfg.arena_words = arena_words;
+    if (feed) FTRY(feed->ensure(N, st));
     FCUDA(cudaMemcpyAsync(cfg.flat, keys, N * 8, cudaMemcpyDeviceToDevice, st));
     FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
     {
@@ -538,13 +539,20 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     cfg.cntY = (u64 *)sc.cntY.p;
     FCUDA(cudaMemsetAsync(sc.cntX.p, 0, kBmax * 8, st));
     FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
-    const unsigned gridP = grid_for(N, kTile, (unsigned)sm_count() * 2);
-    {
+    // Level-0 partition.  Keys still arriving from the host are partitioned
+    // one chunk per launch as each chunk lands (the buckets' counters only
+    // grow, so the launches compose); chunk starts are multiples of kTile.
+    const u64 pstep = feed && feed->chunk ? feed->chunk : N;
+    for (u64 c0 = 0; c0 < N; c0 += pstep) {
+      const u64 cn = N - c0 < pstep ? N - c0 : pstep;
+      if (feed) FTRY(feed->ensure(c0 + cn, st));
+      const u64 *kc = keys + c0;
+      const unsigned gridP = grid_for(cn, kTile, (unsigned)sm_count() * 2);
       LaunchScope ls("partition", st);
-      if (((uintptr_t)keys & 15) == 0)
-        k_partition0<true><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
+      if (((uintptr_t)kc & 15) == 0)
+        k_partition0<true><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(kc, cn, meta, cfg);
       else
-        k_partition0<false><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(keys, N, meta, cfg);
+        k_partition0<false><<<gridP, kTT, g_split_bytes + kTile * 8, st>>>(kc, cn, meta, cfg);
     }
     {
       LaunchScope ls("fill_buckets", st);

@@ -216,6 +216,13 @@ extern "C" int mphf_lookup(const mphf_t *h, const uint64_t *d_keys, uint64_t n, 
   return lookup_impl(h, (const u64 *)d_keys, n, (u64 *)d_out, s);
 }
 
+// Large batches run as a three-stage pipeline over chunks of the batch: the
+// copy in of chunk c+1 (side stream ci), the lookup of chunk c (the caller's
+// stream) and the copy out of chunk c-1 (side stream co) overlap, so the
+// batch costs about one pass over the host link instead of two plus the
+// kernel.  The D2H copy of chunk c is enqueued after the lookup of chunk c+1,
+// so that a pageable h_out (whose copy blocks the host) still leaves the next
+// lookup queued.
 extern "C" int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n,
                                 uint64_t *h_out, void *stream) {
   if (!h) return MPHF_EINVAL;
@@ -230,14 +237,65 @@ extern "C" int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_
     dev_free(kb, s);
     return rc;
   }
-  cudaError_t e = cudaMemcpyAsync(kb.p, h_keys, n * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    rc = mphf_lookup(h, (const uint64_t *)kb.p, n, (uint64_t *)ob.p, stream);
-    if (rc == MPHF_OK) e = cudaMemcpyAsync(h_out, ob.p, n * 8, cudaMemcpyDeviceToHost, s);
+  const u64 chunk = feed_chunk(n);
+  cudaError_t e = cudaSuccess;
+  if (!chunk) {
+    e = cudaMemcpyAsync(kb.p, h_keys, n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      rc = mphf_lookup(h, (const uint64_t *)kb.p, n, (uint64_t *)ob.p, stream);
+      if (rc == MPHF_OK) e = cudaMemcpyAsync(h_out, ob.p, n * 8, cudaMemcpyDeviceToHost, s);
+    }
+  } else {
+    cudaStream_t ci = nullptr, co = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_k = nullptr;
+    u64 *dk = (u64 *)kb.p, *dout = (u64 *)ob.p;
+    e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k, cudaEventDisableTiming);
+    // both buffers were allocated in s's order: the side streams start after
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev_in, 0);
+    u64 prev0 = 0, prevn = 0;  // chunk whose copy out is still to be enqueued
+    for (u64 c0 = 0; c0 < n && e == cudaSuccess && rc == MPHF_OK; c0 += chunk) {
+      const u64 cn = n - c0 < chunk ? n - c0 : chunk;
+      e = cudaMemcpyAsync(dk + c0, (const u64 *)h_keys + c0, cn * 8, cudaMemcpyHostToDevice, ci);
+      if (e == cudaSuccess) e = cudaEventRecord(ev_in, ci);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in, 0);
+      if (e != cudaSuccess) break;
+      rc = mphf_lookup(h, (const uint64_t *)(dk + c0), cn, (uint64_t *)(dout + c0), stream);
+      if (rc != MPHF_OK) break;
+      e = cudaEventRecord(ev_k, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(co, ev_k, 0);
+      if (e == cudaSuccess && prevn)
+        e = cudaMemcpyAsync((u64 *)h_out + prev0, dout + prev0, prevn * 8, cudaMemcpyDeviceToHost, co);
+      prev0 = c0;
+      prevn = cn;
+    }
+    if (e == cudaSuccess && rc == MPHF_OK && prevn)
+      e = cudaMemcpyAsync((u64 *)h_out + prev0, dout + prev0, prevn * 8, cudaMemcpyDeviceToHost, co);
+    // everything enqueued on the side streams is ordered before the frees
+    if (ci && ev_in) {
+      cudaEventRecord(ev_in, ci);
+      cudaStreamWaitEvent(s, ev_in, 0);
+    }
+    if (co && ev_k) {
+      cudaEventRecord(ev_k, co);
+      cudaStreamWaitEvent(s, ev_k, 0);
+    }
+    if (!ev_in || !ev_k) {  // setup failed part-way: nothing can order the streams
+      if (ci) cudaStreamSynchronize(ci);
+      if (co) cudaStreamSynchronize(co);
+    }
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_k) cudaEventDestroy(ev_k);
+    if (ci) cudaStreamDestroy(ci);
+    if (co) cudaStreamDestroy(co);
   }
   dev_free(kb, s);
   dev_free(ob, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return cuda_fail(e, "mphf_lookup_host");
   return rc;
 }

@@ -152,6 +152,54 @@ def test_host_buffer_entry_points(M):
     assert np.array_equal(out, o.lookup(keys))
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_points_chunked(M, pinned):
+    # Past 4 Mi keys the host entry points stream the batch in chunks (copy of
+    # chunk c+1 beside the work on chunk c); n leaves a ragged last chunk.
+    n = (1 << 22) + 12345
+    keys = inputs.splitmix64_keys(n, 48)
+    q = np.concatenate([inputs.shuffled(keys, 5)[: n - 1000],
+                        inputs.splitmix64_keys(1000, 49)])
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=8)
+    src = torch.from_numpy(keys.view(np.int64)).pin_memory() if pinned else keys
+    g = M.MPHF.build_host(src, gamma=2.0, levels=25, seed=8)
+    assert g.build_path == 1
+    assert_same_structure(g, o)
+    qs = torch.from_numpy(q.view(np.int64)).pin_memory() if pinned else q
+    out = np.empty(n, dtype=np.uint64)
+    if pinned:
+        ot = torch.empty(n, dtype=torch.int64).pin_memory()
+        g.lookup_host(qs, out=ot.numpy().view(np.uint64))
+        out = ot.numpy().view(np.uint64).copy()
+    else:
+        g.lookup_host(qs, out=out)
+    assert np.array_equal(out, o.lookup(q))
+
+
+@pytest.mark.parametrize("path,cap_scale", [(1, 1.0), (0, 0.5)])
+def test_host_build_chunked_unbucketed_path(M, path, cap_scale):
+    # The unbucketed construction reads every key at once: the streamed copy
+    # must be complete before it starts, whether it was chosen up front
+    # (path 1) or after the bucketed partition overflowed (cap_scale 0.5).
+    n = (1 << 22) + 777
+    keys = inputs.splitmix64_keys(n, 50)
+    o = oracle.build(keys, gamma=1.0, levels=25, seed=9)
+    M.debug_config(path, cap_scale)
+    try:
+        g = M.MPHF.build_host(keys, gamma=1.0, levels=25, seed=9)
+    finally:
+        M.debug_config(0, 1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+
+
+def test_host_lookup_chunked_empty_function(M):
+    g = M.MPHF.build_host(np.empty(0, dtype=np.uint64))
+    q = inputs.splitmix64_keys((1 << 22) + 5, 51)
+    out = g.lookup_host(q)
+    assert np.all(out == np.uint64(U64))
+
+
 def test_device_keygen_matches_generator(M):
     for n, seed, start in ((1, 0, 0), (1000, 1, 0), (100003, 4, 12345)):
         got = M.to_u64(M.keygen(n, seed, start))
