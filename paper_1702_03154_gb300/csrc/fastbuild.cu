@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kTT, 2)
 k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ u64 red[kTT / 32];
+  __shared__ unsigned sred[kTT / 32 + 2];
   __shared__ bool last;
   if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
   const FLevel lv = meta->lv[d];
@@ -221,6 +222,25 @@ k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
       u64 *c2 = ((d + 1) & 1) ? cfg.cntY : cfg.cntX;
       for (u64 i = threadIdx.x; i < nx.B; i += kTT) c2[i] = 0;
     }
+    // compaction units (kIn entries) before each bucket of level d, so that
+    // the compaction can hand every CTA the same number of units
+    const unsigned B = (unsigned)lv.B;
+    const unsigned per = (B + kTT - 1) / kTT;
+    const unsigned lo = threadIdx.x * per;
+    const unsigned hi = lo + per < B ? lo + per : B;
+    auto units = [&](unsigned b) -> unsigned {
+      const u64 nk = min(cnt[b], lv.cap);
+      return (unsigned)((nk + kIn - 1) / kIn);
+    };
+    unsigned su = 0;
+    for (unsigned b = lo; b < hi; b++) su += units(b);
+    unsigned total;
+    unsigned pre = block_scan_u32<kTT>(su, sred, &total);
+    for (unsigned b = lo; b < hi; b++) {
+      cfg.upre[b] = pre;
+      pre += units(b);
+    }
+    if (threadIdx.x == 0) cfg.upre[B] = total;
   }
 }
 
@@ -233,16 +253,22 @@ k_fill_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
 __global__ void __launch_bounds__(kTT, 2)
 k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned tile_cnt;
+  __shared__ unsigned scnt[3];  // survivors of the last three units (rotating)
   if (meta->lv[d].mode != LM_BUCKETED || meta->status) return;
   const FLevel lv = meta->lv[d];
   const FLevel nx = meta->lv[d + 1];
   if (nx.mode == LM_DONE || nx.mode == LM_NONE) return;
+  // this CTA's share of the level's units (kIn-entry slices of the buckets)
+  const unsigned *upre = cfg.upre;
+  const unsigned U = upre[lv.B];
+  const unsigned u0 = (unsigned)(((u64)U * blockIdx.x) / gridDim.x);
+  const unsigned u1 = (unsigned)(((u64)U * (blockIdx.x + 1)) / gridDim.x);
+  if (u0 >= u1) return;
   const bool flat = nx.mode == LM_FLAT;
   const unsigned nb = flat ? 1u : (unsigned)nx.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
   u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
-  u64 *stage = sm.sorted;  // survivors of the tile, before their destinations are known
+  u64 *stage = sm.sorted;  // survivors awaiting the multisplit (at most kTile)
   const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
   const unsigned *parena = (d & 1) ? cfg.YP : cfg.XP;
   const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
@@ -256,89 +282,125 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   const unsigned maskn = flat ? 0u : (unsigned)(nx.P - 1);
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  if (threadIdx.x == 0) tile_cnt = 0;
-  for (u64 b = blockIdx.x; b < lv.B; b += gridDim.x) {
-    const u64 w0 = (b * lv.P) >> 6;
-    const u64 wend = min((b + 1) * lv.P, lv.m) >> 6;
+
+  // bucket of unit u0: the last b with upre[b] <= u0 (empty buckets own no unit)
+  unsigned b = 0;
+  {
+    unsigned lo = 0, hi = (unsigned)lv.B;
+    while (hi - lo > 1) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (upre[mid] <= u0) lo = mid;
+      else hi = mid;
+    }
+    b = lo;
+  }
+  unsigned ubase = upre[b], bnext = upre[b + 1];
+  auto load_segA = [&](unsigned bb) {
+    const u64 w0 = ((u64)bb * lv.P) >> 6;
+    const u64 wend = min((u64)(bb + 1) * lv.P, lv.m) >> 6;
     for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
-    __syncthreads();
-    const u64 nk = min(cnt[b], lv.cap);
-    const u64 *kb = arena + b * lv.cap;
-    const unsigned *pb = parena + b * lv.cap;
-    const unsigned base = threadIdx.x * kKPT;
-    for (u64 t0 = 0; t0 < nk; t0 += kTile) {
-      // 1. test every key of the tile; pack the survivors warp by warp.  Each
-      // thread owns kKPT consecutive entries (16-byte loads); all keys are
-      // loaded up front since survivors are spread over every sector anyway.
-      const u64 rem = nk - t0;
-      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
-      const unsigned *pbt = pb + t0 + base;
-      const u64 *kbt = kb + t0 + base;
-      unsigned pk[kKPT];
-      u64 xk[kKPT];
-      if (base + kKPT <= nt) {
+  };
+  if (threadIdx.x < 3) scnt[threadIdx.x] = 0;
+  load_segA(b);
+  __syncthreads();
+
+  // multisplit the ns staged survivors into level d+1's buckets (or the flat list)
+  auto flush = [&](unsigned ns) {
+    u64 x[kKPT];
+    unsigned dst[kKPT], lp[kKPT];
+    bool ok[kKPT];
 #pragma unroll
-        for (int k = 0; k < kKPT; k += 4) {
-          const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(pbt + k));
-          pk[k] = v.x;
-          pk[k + 1] = v.y;
-          pk[k + 2] = v.z;
-          pk[k + 3] = v.w;
-        }
-#pragma unroll
-        for (int k = 0; k < kKPT; k += 2) {
-          const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(kbt + k));
-          xk[k] = ((u64)v.y << 32) | v.x;
-          xk[k + 1] = ((u64)v.w << 32) | v.z;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < kKPT; k++) {
-          pk[k] = base + k < nt ? __ldcs(pbt + k) : ~0u;
-          xk[k] = base + k < nt ? __ldcs(kbt + k) : 0;
-        }
+    for (int k = 0; k < kKPT; k++) {
+      const unsigned i = (unsigned)k * kTT + threadIdx.x;
+      ok[k] = i < ns;
+      x[k] = ok[k] ? stage[i] : 0;
+      dst[k] = 0;
+      lp[k] = 0;
+      if (ok[k] && !flat) {
+        const u64 p = level_pos(x[k], s_n, nx.m);
+        dst[k] = (unsigned)(p >> shn);
+        lp[k] = (unsigned)p & maskn;
       }
-#pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const unsigned p = pk[k];
-        const bool keep = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
-        const u64 x = xk[k];
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        unsigned wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(&tile_cnt, (unsigned)__popc(bal));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (keep) stage[wbase + __popc(bal & lt)] = x;
-      }
+    }
+    __syncthreads();  // the staging area is reused by the writer
+    if (flat)
+      multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+                              &meta->status);
+    else
+      multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+                             &meta->status);
+  };
+
+  unsigned ns = 0;  // staged survivors (the same value in every thread)
+  unsigned it = 0;
+  for (unsigned u = u0; u < u1; u++, it++) {
+    if (u >= bnext) {  // next non-empty bucket: its slice of A_d replaces the old one
+      do {
+        b++;
+        ubase = bnext;
+        bnext = upre[b + 1];
+      } while (u >= bnext);
       __syncthreads();
-      const unsigned ns = tile_cnt;
-      // 2. hash the packed survivors for level d+1 (full warps)
-      u64 x[kKPT];
-      unsigned dst[kKPT], lp[kKPT];
-      bool ok[kKPT];
+      load_segA(b);
+      __syncthreads();
+    }
+    // 1. test kInPT consecutive entries per thread (16-byte loads); a key whose
+    // A_d bit is 0 survives to F_{d+1} (Algorithm 1)
+    const u64 nk = min(cnt[b], lv.cap);
+    const u64 e0 = (u64)(u - ubase) * kIn + (u64)threadIdx.x * kInPT;
+    const unsigned *pe = parena + (u64)b * lv.cap + e0;
+    const u64 *ke = arena + (u64)b * lv.cap + e0;
+    unsigned pk[kInPT];
+    u64 xk[kInPT];
+    if (e0 + kInPT <= nk) {
+      const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(pe));
+      pk[0] = v.x;
+      pk[1] = v.y;
+      pk[2] = v.z;
+      pk[3] = v.w;
 #pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const unsigned i = (unsigned)k * kTT + threadIdx.x;
-        ok[k] = i < ns;
-        x[k] = ok[k] ? stage[i] : 0;
-        dst[k] = 0;
-        lp[k] = 0;
-        if (ok[k] && !flat) {
-          const u64 p = level_pos(x[k], s_n, nx.m);
-          dst[k] = (unsigned)(p >> shn);
-          lp[k] = (unsigned)p & maskn;
-        }
+      for (int k = 0; k < kInPT; k += 2) {
+        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(ke + k));
+        xk[k] = ((u64)w.y << 32) | w.x;
+        xk[k + 1] = ((u64)w.w << 32) | w.z;
       }
-      __syncthreads();  // the staging area is reused by the writer
-      if (threadIdx.x == 0) tile_cnt = 0;
-      // 3. write them to their destinations
-      if (flat)
-        multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
-                                &meta->status);
-      else
-        multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
-                               &meta->status);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kInPT; k++) {
+        pk[k] = e0 + k < nk ? __ldcs(pe + k) : ~0u;
+        xk[k] = e0 + k < nk ? __ldcs(ke + k) : 0;
+      }
+    }
+    unsigned bal[kInPT], tot = 0;
+    bool keep[kInPT];
+#pragma unroll
+    for (int k = 0; k < kInPT; k++) {
+      const unsigned p = pk[k];
+      keep[k] = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
+      bal[k] = __ballot_sync(0xffffffffu, keep[k]);
+      tot += __popc(bal[k]);
+    }
+    // one reservation per warp and unit in the rotating counter of this unit
+    unsigned wbase = 0;
+    if (lane == 0 && tot) wbase = atomicAdd(&scnt[it % 3], tot);
+    wbase = ns + __shfl_sync(0xffffffffu, wbase, 0);
+#pragma unroll
+    for (int k = 0; k < kInPT; k++) {
+      if (keep[k]) stage[wbase + __popc(bal[k] & lt)] = xk[k];
+      wbase += __popc(bal[k]);
+    }
+    // the counter of unit it+1 was last read after the barrier of unit it-2,
+    // which every thread has passed: reset it for the next unit
+    if (threadIdx.x == 0) scnt[(it + 1) % 3] = 0;
+    __syncthreads();
+    ns += scnt[it % 3];
+    // 2.+3. once another unit might not fit, hash and write the staged keys
+    if (ns > (unsigned)(kTile - kIn)) {
+      flush(ns);
+      ns = 0;
     }
   }
+  if (ns) flush(ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -429,8 +491,9 @@ static double expect_next(double n, double gamma) {
 }
 
 struct FastScratch {
-  DevBuf meta, X, Y, XP, YP, cntX, cntY, flat, A0, arena;
+  DevBuf meta, X, Y, XP, YP, cntX, cntY, flat, A0, arena, upre;
   void release(cudaStream_t s) {
+    dev_free(upre, s);
     dev_free(meta, s); dev_free(X, s); dev_free(Y, s); dev_free(XP, s); dev_free(YP, s);
     dev_free(cntX, s); dev_free(cntY, s); dev_free(flat, s); dev_free(A0, s); dev_free(arena, s);
   }
@@ -534,6 +597,8 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     cfg.XP = (unsigned *)sc.XP.p;
     FTRY(dev_alloc(sc.cntX, kBmax * 8, st));
     FTRY(dev_alloc(sc.cntY, kBmax * 8, st));
+    FTRY(dev_alloc(sc.upre, (kBmax + 1) * 4, st));
+    cfg.upre = (unsigned *)sc.upre.p;
     cfg.X = (u64 *)sc.X.p;
     cfg.cntX = (u64 *)sc.cntX.p;
     cfg.cntY = (u64 *)sc.cntY.p;

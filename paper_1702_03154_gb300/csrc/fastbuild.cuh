@@ -61,6 +61,7 @@ struct FastCfg {
   u64 T;                // levels with at most T keys run in the single-CTA tail
   u64 Pmax, Pmin, Btarget;
   double cap_scale;     // bucket capacity multiplier (1 in production; < 1 only in tests)
+  unsigned *upre;       // [Bmax + 1] compaction units (kIn-entry slices) before each bucket
 };
 
 __host__ __device__ inline u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
@@ -68,6 +69,8 @@ __host__ __device__ inline u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; 
 static constexpr int kTT = 512;            // threads of partition / compaction / fill CTAs
 static constexpr int kKPT = 8;             // keys per thread per tile
 static constexpr int kTile = kTT * kKPT;   // 4096 keys
+static constexpr int kInPT = 4;            // compaction: entries per thread per input unit
+static constexpr int kIn = kTT * kInPT;    // 2048 entries per compaction unit
 static constexpr u64 kPmax = 256 * 1024;   // positions per bucket at most (64 KB of bits)
 static constexpr int kTailThreads = 1024;
 static constexpr u64 kTailMaxKeys = 16384;
