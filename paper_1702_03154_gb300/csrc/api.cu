@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -173,8 +174,8 @@ void mphf_free(mphf_t *h) {
   if (h->shared) {
     release_shared(h->shared);
   } else {
-    dev_free(h->A, 0);
-    dev_free(h->rank, 0);
+    dev_free(h->S, 0);
+    dev_free(h->SB, 0);
     dev_free(h->fb, 0);
   }
   if (prev != h->device) cudaSetDevice(prev);
@@ -216,24 +217,53 @@ static int copy_out(const mphf_t *h, const DevBuf &b, uint64_t *dst, uint64_t co
   return MPHF_OK;
 }
 
+// A comes back out of the sectors: words 1..7 of each 32-byte sector are 28
+// consecutive bytes of A, so one strided copy gathers them.
 int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count) {
-  return copy_out(h, h->A, h_words, count, h ? h->M / 64 : 0);
+  if (!h || (count && !h_words) || count != h->M / 64) return MPHF_EINVAL;
+  if (!count) return MPHF_OK;
+  const u64 w32 = h->M / 32;               // A's 32-bit words
+  const u64 full = w32 / kSectWords;       // sectors whose 7 words all belong to A
+  const u64 rest = w32 - full * kSectWords;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  const char *src = (const char *)h->S.p + 4;
+  char *dst = (char *)h_words;
+  cudaError_t e = cudaSuccess;
+  if (full)
+    e = cudaMemcpy2D(dst, 4 * kSectWords, src, 32, 4 * kSectWords, full, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && rest)
+    e = cudaMemcpy(dst + full * 4 * kSectWords, src + full * 32, rest * 4, cudaMemcpyDeviceToHost);
+  if (prev != h->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2D(A from sectors)");
+  return MPHF_OK;
 }
+
+// The paper's checkpoints (ones before bit 512 b), evaluated from the sectors.
 int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
-  // checkpoints are every other word of the device table
   if (!h || (count && !h_rank) || count != h->n_rank) return MPHF_EINVAL;
   if (!count) return MPHF_OK;
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
-  cudaError_t e = cudaMemcpy2D(h_rank, 8, h->rank.p, 16, 8, count, cudaMemcpyDeviceToHost);
+  DevBuf tmp;
+  int rc = dev_alloc(tmp, count * 8, 0);
+  if (rc == MPHF_OK) {
+    rc = sector_checkpoints((const unsigned *)h->S.p, (const u64 *)h->SB.p, count, (u64 *)tmp.p, 0);
+    cudaError_t e = cudaSuccess;
+    if (rc == MPHF_OK) e = cudaMemcpy(h_rank, tmp.p, count * 8, cudaMemcpyDeviceToHost);
+    dev_free(tmp, 0);
+    cudaError_t e2 = cudaStreamSynchronize(0);
+    if (e == cudaSuccess) e = e2;
+    if (rc == MPHF_OK && e != cudaSuccess) rc = cuda_fail(e, "mphf_copy_rank");
+  }
   if (prev != h->device) cudaSetDevice(prev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2D(rank)");
-  return MPHF_OK;
+  return rc;
 }
 
 uint64_t mphf_device_bytes(const mphf_t *h) {
-  return h ? (uint64_t)(h->A.bytes + h->rank.bytes + h->fb.bytes) : 0;
+  return h ? (uint64_t)(h->S.bytes + h->SB.bytes + h->fb.bytes) : 0;
 }
 int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count) {
   return copy_out(h, h->fb, h_keys, count, h ? h->n_fb : 0);

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "fastbuild.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -512,71 +513,86 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_btail(BCfg c, u64 mcap, int
 }
 
 // ---------------------------------------------------------------------------
-// Finalisation: each set's A = A_0 || later levels, its rank table and
-// fallback, packed into one arena shared by the handles.
+// Finalisation: each set's A = A_0 || later levels, stored as sectors with
+// their ranks (sector.cuh), and its fallback, packed into one arena shared by
+// the handles.
 // ---------------------------------------------------------------------------
 struct BOut {
   u64 a0_off, at_off, m0, M;       // sources and total bits
-  u64 A_dst, R, rank_dst;          // word offsets in the output arena
+  u64 S_dst, nsect, SB_dst;        // 64-bit word offsets in the output arena
   u64 fb_src, n_fb, fb_dst;
 };
 
-__global__ void k_bassemble(const BOut *__restrict__ outs, unsigned S, const u64 *__restrict__ A0,
-                            const u64 *__restrict__ arena, const u64 *__restrict__ flat,
+__global__ void k_bassemble(const BOut *__restrict__ outs, unsigned S, const u64 *__restrict__ flat,
                             u64 *__restrict__ dst) {
   for (unsigned s = blockIdx.x; s < S; s += gridDim.x) {
     const BOut o = outs[s];
-    const u64 W0 = o.m0 >> 6, W = o.M >> 6;
-    for (u64 w = threadIdx.x; w < W; w += blockDim.x)
-      dst[o.A_dst + w] = w < W0 ? A0[o.a0_off + w] : arena[o.at_off + (w - W0)];
     for (u64 i = threadIdx.x; i < o.n_fb; i += blockDim.x) dst[o.fb_dst + i] = flat[o.fb_src + i];
   }
 }
 
-static constexpr int kRankT = 256;
+static constexpr int kSectT = 256;
+static_assert(((1u << kSBShift) % kSectT) == 0, "a chunk must not straddle superblocks");
 
-__global__ void __launch_bounds__(kRankT) k_brank(const BOut *__restrict__ outs, unsigned S,
-                                                  u64 *__restrict__ arena, u64 *__restrict__ totals) {
-  __shared__ u64 warp_sums[kRankT / 32];
+// One CTA per set: chunks of kSectT sectors in order, a running count of ones
+// carried from chunk to chunk (and reset into SB at every superblock).
+__global__ void __launch_bounds__(kSectT) k_bsectors(const BOut *__restrict__ outs, unsigned S,
+                                                    const u64 *__restrict__ A0,
+                                                    const u64 *__restrict__ arena,
+                                                    u64 *__restrict__ dst, u64 *__restrict__ totals) {
+  __shared__ unsigned warp_sums[kSectT / 32];
   for (unsigned s = blockIdx.x; s < S; s += gridDim.x) {
     const BOut o = outs[s];
-    const u64 *A = arena + o.A_dst;
-    u64 *rank2 = arena + o.rank_dst;
-    const u64 nwords = o.M >> 6;
-    u64 running = 0;
-    for (u64 b0 = 0; b0 < o.R; b0 += kRankT) {
-      const u64 b = b0 + threadIdx.x;
-      u64 cblk = 0, rel = 0;
-      if (b < o.R) {
-        unsigned run = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const u64 w = b * 8 + j;
-          const unsigned pc = w < nwords ? __popcll(A[w]) : 0u;
-          if (j) rel |= (u64)run << (9 * (j - 1));
-          run += pc;
-        }
-        cblk = run;
+    const u64 W0 = o.m0 >> 6, W = o.M >> 6;
+    unsigned *Sd = reinterpret_cast<unsigned *>(dst + o.S_dst);
+    u64 *SB = dst + o.SB_dst;
+    u64 running = 0, sbase = 0;
+    for (u64 c0 = 0; c0 < o.nsect; c0 += kSectT) {
+      if ((c0 & ((1ull << kSBShift) - 1)) == 0) {
+        sbase = running;
+        if (threadIdx.x == 0) SB[c0 >> kSBShift] = running;
       }
-      // block exclusive scan of cblk
+      const u64 t = c0 + threadIdx.x;
+      unsigned w[kSectWords];
+      unsigned c = 0;
+      if (t < o.nsect) {
+        const u64 q0 = t * kSectWords, k0 = q0 >> 1;
+        unsigned h[8];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const u64 k = k0 + i;
+          const u64 u = k < W0 ? A0[o.a0_off + k] : (k < W ? arena[o.at_off + (k - W0)] : 0ull);
+          h[2 * i] = (unsigned)u;
+          h[2 * i + 1] = (unsigned)(u >> 32);
+        }
+        const bool odd = q0 & 1;
+#pragma unroll
+        for (int i = 0; i < (int)kSectWords; i++) {
+          w[i] = odd ? h[i + 1] : h[i];
+          c += __popc(w[i]);
+        }
+      }
+      // block exclusive scan of c
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      u64 x = cblk;
+      unsigned x = c;
 #pragma unroll
       for (int of = 1; of < 32; of <<= 1) {
-        u64 y = __shfl_up_sync(0xffffffffu, x, of);
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, of);
         if (lane >= of) x += y;
       }
       if (lane == 31) warp_sums[warp] = x;
       __syncthreads();
-      u64 before = 0, tot = 0;
-      for (int i = 0; i < kRankT / 32; i++) {
+      unsigned before = 0, tot = 0;
+      for (int i = 0; i < kSectT / 32; i++) {
         if (i < warp) before += warp_sums[i];
         tot += warp_sums[i];
       }
       __syncthreads();
-      if (b < o.R) {
-        rank2[2 * b] = running + before + x - cblk;
-        rank2[2 * b + 1] = rel;
+      if (t < o.nsect) {
+        const unsigned rel = (unsigned)(running - sbase) + before + x - c;
+        uint4 *p = reinterpret_cast<uint4 *>(Sd + 8 * t);
+        p[0] = make_uint4(rel, w[0], w[1], w[2]);
+        p[1] = make_uint4(w[3], w[4], w[5], w[6]);
       }
       running += tot;
     }
@@ -963,13 +979,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     o.at_off = b.at_off;
     o.m0 = b.m0;
     o.M = hl[U - 1].off + hl[U - 1].m;
-    o.R = (o.M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
+    o.nsect = n_sectors(o.M);
     o.fb_src = b.flat_off;
     o.n_fb = n_fb;
-    o.A_dst = out_words;
-    out_words += ((o.M / 64) + 7) & ~7ull;
-    o.rank_dst = out_words;
-    out_words += 2 * o.R;
+    o.S_dst = out_words;  // 8-word (64-byte) steps keep every sector 32-byte aligned
+    out_words += (o.nsect * 4 + 7) & ~7ull;
+    o.SB_dst = out_words;
+    out_words += (n_superblocks(o.nsect) + 7) & ~7ull;
     o.fb_dst = out_words;
     out_words += (n_fb + 7) & ~7ull;
     okset[s] = 1;
@@ -998,13 +1014,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     cudaMemcpyAsync(dbo.p, bo.data(), sizeof(BOut) * S, cudaMemcpyHostToDevice, st);
     {
       LaunchScope ls("bassemble", st);
-      k_bassemble<<<grid2 * 2, 256, 0, st>>>((const BOut *)dbo.p, S, c.A0, c.arena, c.flat,
+      k_bassemble<<<grid2 * 2, 256, 0, st>>>((const BOut *)dbo.p, S, c.flat,
                                            (u64 *)sh->arena.p);
     }
     {
-      LaunchScope ls("brank", st);
-      k_brank<<<grid2 * 2, kRankT, 0, st>>>((const BOut *)dbo.p, S, (u64 *)sh->arena.p,
-                                           (u64 *)dtot.p);
+      LaunchScope ls("bsectors", st);
+      k_bsectors<<<grid2 * 2, kSectT, 0, st>>>((const BOut *)dbo.p, S, c.A0, c.arena,
+                                              (u64 *)sh->arena.p, (u64 *)dtot.p);
     }
     cudaMemcpyAsync(totals.data(), dtot.p, 8 * S, cudaMemcpyDeviceToHost, st);
     dev_free(dbo, st);
@@ -1046,12 +1062,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       h->n_fb = bo[s].n_fb;
       h->n[b.levels_used] = h->n_fb;
       h->M = bo[s].M;
-      h->n_rank = bo[s].R;
+      h->n_rank = (h->M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
+      h->n_sect = bo[s].nsect;
       u64 *base = (u64 *)sh->arena.p;
-      h->A.p = base + bo[s].A_dst;
-      h->A.bytes = h->M / 8;
-      h->rank.p = base + bo[s].rank_dst;
-      h->rank.bytes = h->n_rank * 16;
+      h->S.p = base + bo[s].S_dst;
+      h->S.bytes = h->n_sect * 32;
+      h->SB.p = base + bo[s].SB_dst;
+      h->SB.bytes = n_superblocks(h->n_sect) * 8;
       h->fb.p = h->n_fb ? base + bo[s].fb_dst : nullptr;
       h->fb.bytes = h->n_fb * 8;
       h->shared = sh;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -249,8 +250,8 @@ struct Scratch {
 
 static void release_handle(mphf_t *h, cudaStream_t s) {
   if (!h) return;
-  dev_free(h->A, s);
-  dev_free(h->rank, s);
+  dev_free(h->S, s);
+  dev_free(h->SB, s);
   dev_free(h->fb, s);
   delete h;
 }
@@ -426,21 +427,9 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   h->n_rank = (h->M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
   h->n_fb = n_fb;
 
-  // Final A = A_0 || arena, then the rank checkpoints.
-  TRY(dev_alloc(h->A, h->M / 64 * 8, st));
-  TRY(dev_alloc(h->rank, h->n_rank * 16, st));
-  if (cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 64 * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-    rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(A0)");
-    goto fail;
-  }
-  if (h->M > m0 &&
-      cudaMemcpyAsync((u64 *)h->A.p + m0 / 64, sc.arena.p, (h->M - m0) / 64 * 8,
-                      cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-    rc = cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(arena)");
-    goto fail;
-  }
-  TRY(build_rank_table((const u64 *)h->A.p, h->M / 64, (u64 *)h->rank.p, h->n_rank,
-                       (u64 *)sc.dupflag.p + 1, st));
+  // Final A = A_0 || arena, stored as sectors with their ranks.
+  TRY(make_sectors(h, ASrc{(const u64 *)sc.A0.p, m0 / 64, (const u64 *)sc.arena.p, h->M / 64},
+                   (u64 *)sc.dupflag.p + 1, st));
 
   // Fallback (Sec. 3.5): sorted leftover keys; equal neighbours mean duplicates.
   if (n_fb) {
@@ -474,8 +463,8 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
 fail:
   cudaGetLastError();
   sc.release(st);
-  dev_free(h->A, st);
-  dev_free(h->rank, st);
+  dev_free(h->S, st);
+  dev_free(h->SB, st);
   dev_free(h->fb, st);
   cudaStreamSynchronize(st);
   return rc;

@@ -115,6 +115,19 @@ inline int sm_count() {
   return v;
 }
 
+// CTAs of `kernel` (block threads, dynamic smem bytes) that fit on the whole
+// GPU at once: a grid of this size runs in a single wave.
+template <class K>
+inline unsigned int resident_grid(K kernel, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (unsigned int)(per_sm * sm_count());
+}
+
 inline unsigned int grid_for(u64 items, unsigned int per_block, unsigned int max_blocks) {
   u64 b = (items + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -150,10 +163,6 @@ struct KeyFeed {
 // Keys per chunk for n keys (0 = copy in one piece: too few keys to pipeline).
 u64 feed_chunk(u64 n);
 
-// Rank table over A (rank.cu): rank2[2b] = ones in bits [0, 512 b) (the
-// paper's checkpoint), rank2[2b+1] = in-block prefix counts of words 1..7.
-int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_total,
-                     cudaStream_t s);
 // Sort n keys ascending in place and flag equal neighbours (sort.cu).
 int sort_fallback(u64 *keys, u64 n, unsigned int *d_dup_flag, cudaStream_t s);
 
@@ -178,11 +187,12 @@ struct mphf {
   uint64_t M = 0;        // total bits
   uint64_t n_rank = 0;   // ceil(M / 512)
   uint64_t n_fb = 0;
-  bbh::DevBuf A;        // M / 64 words
-  bbh::DevBuf rank;     // 2 n_rank words: checkpoint, in-block prefix counts
+  uint64_t n_sect = 0;   // 32-byte sectors holding A and its ranks (sector.cuh)
+  bbh::DevBuf S;        // n_sect * 8 32-bit words
+  bbh::DevBuf SB;       // ones before each superblock of 2^24 sectors
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;
   int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched construction
-  mphf_shared *shared = nullptr;  // set: A/rank/fb live in a batched arena
+  mphf_shared *shared = nullptr;  // set: S/SB/fb live in a batched arena
   bbh::DevBuf ldesc;     // device descriptor for multi-function lookups (made on first use)
 };

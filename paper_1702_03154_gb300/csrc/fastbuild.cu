@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include "fastbuild.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -730,15 +731,9 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
       rc = MPHF_EINTERNAL;
       goto fail;
     }
-    FTRY(dev_alloc(h->A, h->M / 8, st));
-    FTRY(dev_alloc(h->rank, h->n_rank * 16, st));
-    FCUDA(cudaMemcpyAsync(h->A.p, sc.A0.p, m0 / 8, cudaMemcpyDeviceToDevice, st));
-    if (h->M > m0)
-      FCUDA(cudaMemcpyAsync((u64 *)h->A.p + m0 / 64, sc.arena.p, (h->M - m0) / 8,
-                            cudaMemcpyDeviceToDevice, st));
-    u64 *d_total = &meta->rank_total;
-    FTRY(build_rank_table((const u64 *)h->A.p, h->M / 64, (u64 *)h->rank.p, h->n_rank, d_total,
-                          st));
+    // A = A_0 || (A_1 A_2 ... in the arena), stored as sectors with their ranks
+    FTRY(make_sectors(h, ASrc{(const u64 *)sc.A0.p, m0 / 64, (const u64 *)sc.arena.p, h->M / 64},
+                      &meta->rank_total, st));
     unsigned *dflag = &meta->dup;
     if (n_fb) {
       if (hm.tail_done == 2) FTRY(sort_fallback(cfg.flat, n_fb, dflag, st));

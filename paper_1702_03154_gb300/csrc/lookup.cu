@@ -1,22 +1,22 @@
 // lookup.cu -- batched queries (Algorithm 3 with the minimal index of
-// Sec. 2.2.3 and the rank checkpoints of Sec. 3.1).
+// Sec. 2.2.3 and the ranks of Sec. 3.1).
 //
 // A key needs e^{1/gamma} level probes on average but up to L; a warp that
 // kept 32 keys in lock-step would idle most lanes while its slowest key walks
 // down the levels.  Instead every lane owns kSlots independent query slots,
 // each with its own (key, output index, level).  Each round every active slot
-// probes its current level (one 8-byte load of A); a slot whose bit is set
-// computes its rank and retires, the others move to the next level, and
-// retired slots are refilled from the warp's stream of input keys.  So lanes
-// stay busy and each lane keeps kSlots independent loads in flight.
-//
-// Rank of global bit g: the checkpoint of its 512-bit block plus the in-block
-// prefix count of its word (both in one 16-byte entry of the rank table) plus
-// the ones of its own word below g.
+// probes its current level with one 256-bit load of the sector holding its
+// bit (sector.cuh: the A word and the count of ones before the sector come
+// together); a slot whose bit is set finishes its rank from those registers
+// and retires, the others move to the next level, and retired slots are
+// refilled from the warp's stream of input keys.  So lanes stay busy, each
+// lane keeps kSlots independent loads in flight, and a placed key costs one
+// memory request per level probed.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 
 #include "common.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -30,26 +30,13 @@ struct LevelTable {
 };
 
 struct LookupArgs {
-  const u64 *A;
-  const u64 *rank;
+  const unsigned *S;  // sectors: A with its ranks
+  const u64 *SB;      // ones before each superblock
   const u64 *fb;
   u64 n_fb;
   u64 N;
   uint32_t L_used;
 };
-
-// Ones of A strictly before global bit g; w = A[g / 64] (already loaded).
-// rank2[2b] is the checkpoint of block b = g / 512, rank2[2b+1] holds the ones
-// of words 0..k-1 of the block for k = 1..7 in 9-bit fields.
-__device__ __forceinline__ u64 rank_before(const u64 *__restrict__ rank2, u64 g, u64 w) {
-  const u64 b = g >> 9;
-  const unsigned k = (unsigned)(g >> 6) & 7u;  // word of g inside its block
-  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rank2) + b);
-  const u64 abs = ((u64)v.y << 32) | v.x;
-  const u64 rel = ((u64)v.w << 32) | v.z;
-  const u64 inblk = k ? (rel >> (9 * (k - 1))) & 511ull : 0ull;
-  return abs + inblk + __popcll(w & ((1ull << (g & 63)) - 1ull));
-}
 
 __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   u64 lo = 0, hi = a.n_fb;
@@ -129,20 +116,22 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
     if (!__any_sync(0xffffffffu, any)) break;
 
     // one probe per active slot: issue all loads, then resolve
-    u64 g[kSlots], w[kSlots];
+    SectPos p[kSlots];
+    Sect v[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
-        g[s] = toff[d] + level_pos(x[s], ts[d], tm[d]);
-        w[s] = __ldg(a.A + (g[s] >> 6));
+        p[s] = sect_pos(toff[d] + level_pos(x[s], ts[d], tm[d]));
+        v[s] = sect_load(a.S, p[s].t);
       }
     }
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
-        if ((w[s] >> (g[s] & 63)) & 1ull) {
-          __stcs(out + idx[s], rank_before(a.rank, g[s], w[s]));
+        const unsigned w = sect_word(v[s], p[s].j);
+        if ((w >> p[s].b) & 1u) {
+          __stcs(out + idx[s], sect_rank(v[s], p[s], w, a.SB));
           act[s] = false;
         } else if (++lvl[s] >= a.L_used) {
           __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
@@ -154,8 +143,8 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
 }
 
 static void fill_tables(const mphf_t *h, LookupArgs &a, LevelTable &t) {
-  a.A = (const u64 *)h->A.p;
-  a.rank = (const u64 *)h->rank.p;
+  a.S = (const unsigned *)h->S.p;
+  a.SB = (const u64 *)h->SB.p;
   a.fb = (const u64 *)h->fb.p;
   a.n_fb = h->n_fb;
   a.N = h->N;
@@ -186,11 +175,19 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
   const unsigned per_block = kLookupThreads / 32;
   unsigned grid = (unsigned)((nwarps_needed + per_block - 1) / per_block);
-  const unsigned maxb = (unsigned)sm_count() * 8;
-  if (grid > maxb) grid = maxb;
+  // one wave of resident CTAs: warps take chunks in a fixed order, so a
+  // second wave would only start after the first has drained
+  static unsigned maxb[5] = {0, 0, 0, 0, 0};
+  const int slots = lookup_slots();
+  if (!maxb[slots]) {
+    maxb[slots] = slots == 3   ? resident_grid(k_lookup<3>, kLookupThreads, 0)
+                  : slots == 4 ? resident_grid(k_lookup<4>, kLookupThreads, 0)
+                               : resident_grid(k_lookup<2>, kLookupThreads, 0);
+  }
+  if (grid > maxb[slots]) grid = maxb[slots];
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  switch (lookup_slots()) {
+  switch (slots) {
     case 3: k_lookup<3><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
     case 4: k_lookup<4><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
     default: k_lookup<2><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;

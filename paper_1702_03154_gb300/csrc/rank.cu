@@ -1,22 +1,24 @@
-// rank.cu -- rank checkpoints over the concatenated bit array A (Sec. 3.1):
-// one 64-bit counter per 512 bits, rank[b] = number of ones in bits [0, 512 b).
+// rank.cu -- the ranks of Sec. 3.1 over the concatenated bit array A.
 //
-// Each checkpoint is stored next to a second 64-bit word holding the seven
-// in-block prefix counts of the block's words 1..7 (9 bits each: the ones of
-// words 0..k-1 for word k), the "rank9" layout of Vigna ("Broadword
-// implementation of rank/select queries", WEA 2008).  A query then needs one
-// 16-byte load and one popcount instead of popcounting up to eight words.  The
-// checkpoints themselves are exactly the paper's.
+// Every function's A is stored in the sector layout of sector.cuh (A's words
+// interleaved with counts of the ones before them); build_sectors writes it
+// in three passes: (1) each thread popcounts one 224-bit sector and each CTA
+// sums its sectors, (2) one CTA scans the per-CTA sums, (3) each sector is
+// written with its count relative to its superblock.  sector_checkpoints
+// evaluates the paper's checkpoints (ones before bit 512 b) from the sectors.
 //
-// Three passes: (1) each thread popcounts one 512-bit block (four 16-byte
-// loads), forms its relative counts, and the CTA turns its 256 block counts
-// into exclusive prefixes; (2) one CTA scans the per-CTA totals; (3) each
-// checkpoint adds its CTA's prefix.
+// The file also holds a standalone rank-table builder over caller-supplied
+// words (mphf_rank_table_noalloc): one 64-bit checkpoint per 512 bits, stored
+// next to a word of seven 9-bit in-block prefix counts -- the "rank9" layout of
+// Vigna ("Broadword implementation of rank/select queries", WEA 2008) -- in
+// three passes: per-block counts with a CTA scan, a scan of the CTA totals,
+// and the addition of each CTA's prefix.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "common.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
@@ -119,32 +121,133 @@ k_rank_add(u64 *__restrict__ rank2, u64 nrank, const u64 *__restrict__ cta_prefi
   if (b < nrank) rank2[2 * b] += cta_prefix[blockIdx.x];
 }
 
-int build_rank_table(const u64 *A, u64 nwords, u64 *rank2, u64 nrank, u64 *d_total,
-                     cudaStream_t s) {
-  if (nrank == 0) {
+// ---------------------------------------------------------------------------
+// Sector layout (sector.cuh): one thread per 224-bit sector, 256 sectors per
+// CTA, so a superblock (2^24 sectors) is exactly 2^16 CTAs.  Pass 1 sums the
+// ones of each CTA's sectors, k_scan_sums turns the sums into exclusive
+// prefixes, pass 2 reads A again and writes every sector with its count
+// relative to the start of its superblock.
+// ---------------------------------------------------------------------------
+static constexpr int kSectThreads = kRankThreads;
+static_assert(((1u << kSBShift) % kSectThreads) == 0, "a CTA must not straddle superblocks");
+
+__device__ __forceinline__ u64 a_word(const ASrc &a, u64 k) {
+  if (k < a.w0) return __ldg(a.a0 + k);
+  return k < a.W ? __ldg(a.a1 + (k - a.w0)) : 0ull;
+}
+
+// A's 32-bit words 7t .. 7t+6 (zero past the end of A).
+__device__ __forceinline__ void sect_words(const ASrc &a, u64 t, unsigned (&w)[kSectWords]) {
+  const u64 q0 = t * kSectWords;
+  const u64 k0 = q0 >> 1;
+  unsigned h[8];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const u64 u = a_word(a, k0 + i);
+    h[2 * i] = (unsigned)u;
+    h[2 * i + 1] = (unsigned)(u >> 32);
+  }
+  const bool odd = q0 & 1;
+#pragma unroll
+  for (int i = 0; i < (int)kSectWords; i++) w[i] = odd ? h[i + 1] : h[i];
+}
+
+__global__ void __launch_bounds__(kSectThreads)
+k_sect_sums(ASrc a, u64 nsect, u64 *__restrict__ cta_sums) {
+  const u64 t = (u64)blockIdx.x * kSectThreads + threadIdx.x;
+  unsigned c = 0;
+  if (t < nsect) {
+    unsigned w[kSectWords];
+    sect_words(a, t, w);
+#pragma unroll
+    for (int i = 0; i < (int)kSectWords; i++) c += __popc(w[i]);
+  }
+  u64 total;
+  block_exclusive_scan(c, &total);
+  if (threadIdx.x == 0) cta_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kSectThreads)
+k_sect_write(ASrc a, u64 nsect, unsigned *__restrict__ S, const u64 *__restrict__ cta_prefix,
+             u64 *__restrict__ SB) {
+  const u64 t = (u64)blockIdx.x * kSectThreads + threadIdx.x;
+  unsigned w[kSectWords];
+  unsigned c = 0;
+  if (t < nsect) {
+    sect_words(a, t, w);
+#pragma unroll
+    for (int i = 0; i < (int)kSectWords; i++) c += __popc(w[i]);
+  }
+  u64 total;
+  const u64 ex = block_exclusive_scan(c, &total);
+  constexpr unsigned kCtaPerSB = (1u << kSBShift) / kSectThreads;
+  const u64 sb_cta = (u64)blockIdx.x / kCtaPerSB * kCtaPerSB;  // first CTA of the superblock
+  if (t < nsect) {
+    const unsigned rel = (unsigned)(cta_prefix[blockIdx.x] - cta_prefix[sb_cta] + ex);
+    uint4 *dst = reinterpret_cast<uint4 *>(S + 8 * t);
+    dst[0] = make_uint4(rel, w[0], w[1], w[2]);
+    dst[1] = make_uint4(w[3], w[4], w[5], w[6]);
+  }
+  if (threadIdx.x == 0 && (u64)blockIdx.x == sb_cta)
+    SB[blockIdx.x / kCtaPerSB] = cta_prefix[blockIdx.x];
+}
+
+int build_sectors(const ASrc &src, u64 M, unsigned *S, u64 *SB, u64 *d_total, cudaStream_t s) {
+  const u64 nsect = n_sectors(M);
+  if (nsect == 0) {
     if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
     return MPHF_OK;
   }
-  const u64 ctas = (nrank + kRankThreads - 1) / kRankThreads;
+  const u64 ctas = (nsect + kSectThreads - 1) / kSectThreads;
   if (ctas > 0x7fffffffull) return MPHF_EINVAL;
   DevBuf sums;
   int rc = dev_alloc(sums, ctas * sizeof(u64), s);
   if (rc != MPHF_OK) return rc;
   {
-    LaunchScope ls("rank_blocks", s);
-    k_rank_blocks<<<(unsigned)ctas, kRankThreads, 0, s>>>(A, nwords, rank2, nrank, (u64 *)sums.p);
+    LaunchScope ls("sect_sums", s);
+    k_sect_sums<<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, (u64 *)sums.p);
   }
   {
-    LaunchScope ls("rank_scan", s);
+    LaunchScope ls("sect_scan", s);
     k_scan_sums<<<1, kScanThreads, 0, s>>>((u64 *)sums.p, ctas, d_total);
   }
-  if (ctas > 1) {
-    LaunchScope ls("rank_add", s);
-    k_rank_add<<<(unsigned)ctas, kRankThreads, 0, s>>>(rank2, nrank, (const u64 *)sums.p);
+  {
+    LaunchScope ls("sect_write", s);
+    k_sect_write<<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, S, (const u64 *)sums.p, SB);
   }
   cudaError_t e = cudaGetLastError();
   dev_free(sums, s);
-  if (e != cudaSuccess) return cuda_fail(e, "rank kernels");
+  if (e != cudaSuccess) return cuda_fail(e, "sector kernels");
+  return MPHF_OK;
+}
+
+int make_sectors(mphf_t *h, const ASrc &src, u64 *d_total, cudaStream_t s) {
+  h->n_sect = n_sectors(h->M);
+  int rc = dev_alloc(h->S, h->n_sect * 32, s);
+  if (rc == MPHF_OK) rc = dev_alloc(h->SB, n_superblocks(h->n_sect) * 8, s);
+  if (rc == MPHF_OK) rc = build_sectors(src, h->M, (unsigned *)h->S.p, (u64 *)h->SB.p, d_total, s);
+  return rc;
+}
+
+__global__ void __launch_bounds__(256)
+k_checkpoints(const unsigned *__restrict__ S, const u64 *__restrict__ SB, u64 n_rank,
+              u64 *__restrict__ out) {
+  const u64 b = (u64)blockIdx.x * 256 + threadIdx.x;
+  if (b >= n_rank) return;
+  const SectPos p = sect_pos(b * MPHF_RANK_BLOCK);
+  const Sect v = sect_load(S, p.t);
+  out[b] = sect_rank(v, p, sect_word(v, p.j), SB);
+}
+
+int sector_checkpoints(const unsigned *S, const u64 *SB, u64 n_rank, u64 *d_out, cudaStream_t s) {
+  if (n_rank == 0) return MPHF_OK;
+  const u64 ctas = (n_rank + 255) / 256;
+  if (ctas > 0x7fffffffull) return MPHF_EINVAL;
+  {
+    LaunchScope ls("checkpoints", s);
+    k_checkpoints<<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
+  }
+  MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
 

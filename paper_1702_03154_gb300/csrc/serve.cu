@@ -26,12 +26,14 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sector.cuh"
 
 namespace bbh {
 
 // Device descriptor of a handle for the multi-function lookup.
 struct LookupDev {
-  const u64 *A, *rank, *fb;
+  const unsigned *S;  // sectors (sector.cuh)
+  const u64 *SB, *fb;
   u64 n_fb, N;
   uint32_t L_used, pad;
   u64 s[MPHF_MAX_LEVELS], m[MPHF_MAX_LEVELS], off[MPHF_MAX_LEVELS];
@@ -51,8 +53,8 @@ int ensure_lookup_desc(mphf_t *h) {
   if (h->ldesc.p) return MPHF_OK;
   LookupDev d;
   memset(&d, 0, sizeof(d));
-  d.A = (const u64 *)h->A.p;
-  d.rank = (const u64 *)h->rank.p;
+  d.S = (const unsigned *)h->S.p;
+  d.SB = (const u64 *)h->SB.p;
   d.fb = (const u64 *)h->fb.p;
   d.n_fb = h->n_fb;
   d.N = h->N;
@@ -76,16 +78,6 @@ int ensure_lookup_desc(mphf_t *h) {
   h->ldesc.p = p;
   h->ldesc.bytes = sizeof(d);
   return MPHF_OK;
-}
-
-__device__ __forceinline__ u64 rank_before_m(const u64 *__restrict__ rank2, u64 g, u64 w) {
-  const u64 b = g >> 9;
-  const unsigned k = (unsigned)(g >> 6) & 7u;
-  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rank2) + b);
-  const u64 abs = ((u64)v.y << 32) | v.x;
-  const u64 rel = ((u64)v.w << 32) | v.z;
-  const u64 inblk = k ? (rel >> (9 * (k - 1))) & 511ull : 0ull;
-  return abs + inblk + __popcll(w & ((1ull << (g & 63)) - 1ull));
 }
 
 __device__ __forceinline__ u64 fallback_index_m(const LookupDev *h, u64 x) {
@@ -189,22 +181,24 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) any |= act[s];
     if (!__any_sync(0xffffffffu, any)) break;
-    u64 g[kMultiSlots], w[kMultiSlots];
+    SectPos p[kMultiSlots];
+    Sect v[kMultiSlots];
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
         const LookupDev *h = hd[s];
-        g[s] = __ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d));
-        w[s] = __ldg(h->A + (g[s] >> 6));
+        p[s] = sect_pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        v[s] = sect_load(h->S, p[s].t);
       }
     }
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const LookupDev *h = hd[s];
-        if ((w[s] >> (g[s] & 63)) & 1ull) {
-          *optr[s] = rank_before_m(h->rank, g[s], w[s]);
+        const unsigned w = sect_word(v[s], p[s].j);
+        if ((w >> p[s].b) & 1u) {
+          *optr[s] = sect_rank(v[s], p[s], w, h->SB);
           act[s] = false;
         } else if (++lvl[s] >= h->L_used) {
           *optr[s] = h->n_fb ? fallback_index_m(h, x[s]) : MPHF_NOT_FOUND;
@@ -219,7 +213,8 @@ int launch_lookup_multi(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStre
   if (total == 0 || nreq == 0) return MPHF_OK;
   const u64 chunks = (total + kMultiChunk - 1) / kMultiChunk;
   u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
-  const u64 maxb = (u64)sm_count() * 5;
+  static u64 maxb = 0;  // one wave of resident CTAs
+  if (!maxb) maxb = resident_grid(k_lookup_multi, kMultiThreads, 0);
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup_multi", s);
