@@ -33,6 +33,7 @@ _LIB = os.path.join(_BUILD, "libmphf_oracle.so")
 OK, EINVAL, ENOMEM, EDUPLICATE = 0, 1, 2, 3
 RANK_BLOCK = 512
 MAX_LEVELS = 64
+MASK64 = (1 << 64) - 1
 
 POS_HOOK = ctypes.CFUNCTYPE(ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32,
                             ctypes.c_uint64, ctypes.c_uint64)
@@ -89,6 +90,8 @@ def lib():
         L.oracle_copy_rank.argtypes, L.oracle_copy_rank.restype = [vp, vp], None
         L.oracle_copy_fallback.argtypes, L.oracle_copy_fallback.restype = [vp, vp], None
         L.oracle_bits_per_key.argtypes, L.oracle_bits_per_key.restype = [vp], dbl
+        L.oracle_string_key.argtypes, L.oracle_string_key.restype = [vp, u64, u64], u64
+        L.oracle_string_keys.argtypes, L.oracle_string_keys.restype = [vp, vp, u64, u64, vp], None
         _lib = L
     return _lib
 
@@ -225,6 +228,24 @@ class OracleMPHF:
 
     def bits_per_key(self) -> float:
         return lib().oracle_bits_per_key(self._h)
+
+
+def string_key(s: bytes, seed: int = 0) -> int:
+    """64-bit key of one byte string (the library's string convention)."""
+    buf = ctypes.create_string_buffer(bytes(s), max(1, len(s)))
+    return lib().oracle_string_key(buf, len(s), seed & MASK64)
+
+
+def string_keys(data: np.ndarray, offsets: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Keys of the strings data[offsets[i]:offsets[i+1]] (uint8 data, n+1 offsets)."""
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = off.size - 1
+    out = np.empty(n, dtype=np.uint64)
+    if n:
+        lib().oracle_string_keys(_ptr(data) if data.size else None, _ptr(off), n, seed & MASK64,
+                                 _ptr(out))
+    return out
 
 
 def build(keys, gamma: float = 2.0, levels: int = 25, seed: int = 0, pos_hook=None) -> OracleMPHF:

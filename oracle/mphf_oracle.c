@@ -34,6 +34,8 @@
  *               fallback; two equal neighbours there -> ORACLE_EDUPLICATE.
  *   non-members Algorithm 3 run as is: the first level whose bit is 1 gives
  *               the rank, else a fallback hit, else UINT64_MAX.
+ *   strings     byte-string keys (Sec. 4.3) become 64-bit keys by the rule of
+ *               oracle_string_key below, then take the same path.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -399,4 +401,44 @@ double oracle_bits_per_key(const oracle_mphf *h)
         return 0.0;
     double bits = (double)h->M + 64.0 * (double)oracle_num_rank(h) + 64.0 * (double)h->n_fb;
     return bits / (double)h->N;
+}
+
+/*
+ * String keys (Sec. 4.3, Table 2: the method run on n-grams and random words
+ * of 18 characters).  The method itself takes 64-bit keys; a string is first
+ * turned into one by this library's convention (the paper does not give its
+ * string hash):
+ *
+ *   h = mix(seed + (len + 1) * 0x9E3779B97F4A7C15)
+ *   for each group of 8 bytes of the string, in order (the last group padded
+ *   with zero bytes): w = the 8 bytes read as a little-endian integer,
+ *   h = mix(h XOR w)
+ *   key = h
+ *
+ * The length enters the first state, so a string and the same string with
+ * zero bytes appended give different keys (len + 1 keeps the empty string
+ * away from mix's fixed point mix(0) = 0).  For a fixed length and fixed
+ * leading groups the last step is a bijection of the last group (mix is one),
+ * so strings that differ only in their last 8-byte group never collide.
+ */
+uint64_t oracle_string_key(const uint8_t *s, uint64_t len, uint64_t seed)
+{
+    uint64_t h = oracle_mix(seed + (len + 1) * 0x9E3779B97F4A7C15ULL);
+    for (uint64_t k = 0; k < len; k += 8) {
+        uint64_t w = 0;
+        for (uint64_t i = 0; i < 8; i++) {
+            uint64_t byte = (k + i < len) ? (uint64_t)s[k + i] : 0;
+            w |= byte << (8 * i);
+        }
+        h = oracle_mix(h ^ w);
+    }
+    return h;
+}
+
+/* Keys of n strings: string i is bytes[off[i] .. off[i+1]). */
+void oracle_string_keys(const uint8_t *bytes, const uint64_t *off, uint64_t n, uint64_t seed,
+                        uint64_t *out)
+{
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = oracle_string_key(bytes + off[i], off[i + 1] - off[i], seed);
 }

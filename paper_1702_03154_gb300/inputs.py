@@ -76,3 +76,21 @@ def set_offsets(sizes: np.ndarray) -> np.ndarray:
     off = np.zeros(sizes.size + 1, dtype=np.uint64)
     np.cumsum(sizes.astype(np.uint64), out=off[1:])
     return off
+
+
+def random_words(n: int, seed: int, length: int = 18, max_length: int = 0):
+    """n random lower-case ASCII words as (uint8 bytes, n + 1 uint64 offsets).
+
+    Every word has `length` characters, or (max_length > length) a length drawn
+    uniformly from [length, max_length].  Words are drawn from PCG64(seed)
+    and may repeat only by chance (26^18 choices at the default length).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if max_length > length:
+        lens = rng.integers(length, max_length + 1, size=n, dtype=np.int64)
+    else:
+        lens = np.full(n, length, dtype=np.int64)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(lens.astype(np.uint64), out=off[1:])
+    data = rng.integers(ord("a"), ord("z") + 1, size=int(off[-1]), dtype=np.uint8)
+    return data, off

@@ -43,6 +43,13 @@ MUTANTS = {
     "fastrange_shift": ("(unsigned __int128)m) >> 64);", "(unsigned __int128)m) >> 63);"),
     # Offsets: each level starts at bit 0.
     "offset_not_accumulated": ("off += h->m[i];", "off += 0 * h->m[i];"),
+    # String keys (Sec. 4.3): the length left out of the first state.
+    "string_length_dropped": ("oracle_mix(seed + (len + 1) * 0x9E3779B97F4A7C15ULL)",
+                              "oracle_mix(seed + 1 * 0x9E3779B97F4A7C15ULL)"),
+    # String keys: groups read big-endian.
+    "string_big_endian": ("w |= byte << (8 * i);", "w |= byte << (8 * (7 - i));"),
+    # String keys: a group OR-ed into the state instead of XOR-ed.
+    "string_group_or": ("h = oracle_mix(h ^ w);", "h = oracle_mix(h | w);"),
 }
 
 

@@ -331,3 +331,76 @@ def test_non_member_keys_follow_algorithm3():
     assert np.all(ok)
     assert np.any(out == np.uint64(U64))       # some fall through every level
     assert np.array_equal(out, h.lookup(others))
+
+
+# ---------------------------------------------------------------- string keys
+# Strings become 64-bit keys before the method runs (Sec. 4.3).  The pins tie
+# the conversion to the published SplitMix64 outputs: the first state of a
+# string of length len is output len of the generator, and a group equal to
+# that state cancels it (mix(0) = 0), so chosen strings have keys that are
+# themselves generator outputs.
+def test_empty_string_key_is_generator_output_0(golden_dir):
+    first = int([l for l in open(os.path.join(golden_dir, "splitmix64_seed0.txt"))
+                 if l.strip() and not l.startswith("#")][0], 16)
+    assert oracle.string_key(b"", 0) == first
+    for seed in (1, 77, 2**63 + 5):
+        assert oracle.string_key(b"", seed) == int(inputs.splitmix64_keys(1, seed)[0])
+
+
+def test_string_key_group_cancels_the_length_state():
+    # A string of 8 bytes whose value (little-endian) is the first state
+    # mix(seed + 9 G) = generator output 8 has key mix(0) = 0.
+    for seed in (0, 3, 991):
+        state = int(inputs.splitmix64_keys(9, seed)[8])
+        assert oracle.string_key(state.to_bytes(8, "little"), seed) == 0
+        assert oracle.string_key(state.to_bytes(8, "big"), seed) != 0
+
+
+def test_string_key_groups_chain_in_order():
+    # 16 bytes: group 0 cancels the first state (output 16 of the generator),
+    # so the key is mix(group 1); with group 1 = t + (j + 1) G that is output j
+    # of a generator started at t.
+    G = 0x9E3779B97F4A7C15
+    for seed, t, j in ((0, 5, 0), (12, 99, 7), (2**40, 1, 3)):
+        first = int(inputs.splitmix64_keys(17, seed)[16])
+        g1 = (t + (j + 1) * G) & U64
+        s = first.to_bytes(8, "little") + g1.to_bytes(8, "little")
+        assert oracle.string_key(s, seed) == int(inputs.splitmix64_keys(j + 1, t)[j])
+        # swapping the two groups breaks it
+        assert oracle.string_key(s[8:] + s[:8], seed) != int(inputs.splitmix64_keys(j + 1, t)[j])
+
+
+def test_string_keys_distinct_in_the_last_group():
+    # For fixed length and leading groups the key is a bijection of the last
+    # group: distinct last groups can never collide.
+    prefix = b"0123456789abcdef"
+    tails = inputs.splitmix64_keys(20000, 5)
+    data = np.frombuffer(b"".join(prefix + int(t).to_bytes(8, "little") for t in tails),
+                         dtype=np.uint8)
+    off = np.arange(0, 24 * (tails.size + 1), 24, dtype=np.uint64)
+    k = oracle.string_keys(data, off, 9)
+    assert np.unique(k).size == tails.size
+
+
+def test_string_key_depends_on_length_and_seed():
+    data, off = inputs.random_words(2000, 3, length=0, max_length=30)
+    for i in range(0, 2000, 7):
+        s = data[int(off[i]):int(off[i + 1])].tobytes()
+        assert oracle.string_key(s, 1) != oracle.string_key(s + b"\0", 1)
+        assert oracle.string_key(s, 1) != oracle.string_key(s, 2)
+
+
+def test_string_key_batch_matches_single():
+    data, off = inputs.random_words(3000, 4, length=1, max_length=40)
+    k = oracle.string_keys(data, off, 123)
+    for i in range(0, 3000, 11):
+        assert int(k[i]) == oracle.string_key(data[int(off[i]):int(off[i + 1])].tobytes(), 123)
+
+
+def test_string_keys_bits_per_key_matches_table2(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "table2_string_keys.json")))
+    data, off = inputs.random_words(200000, 6, length=18)
+    keys = oracle.string_keys(data, off, 0)
+    assert np.unique(keys).size == keys.size
+    o = oracle.build(keys, gamma=g["gamma"], levels=25, seed=0)
+    assert abs(o.bits_per_key() - g["bits_per_key"]) <= g["printed_precision"]
