@@ -140,10 +140,13 @@ int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n, uint64
  * 0 for an empty function or NULL. */
 double mphf_bits_per_key(const mphf_t *h);
 
-/* Device memory the handle holds, in bytes: A, the rank table (each 64-bit
- * checkpoint of Sec. 3.1 is stored beside a 64-bit word of seven 9-bit in-block
- * prefix counts that speed up queries, so 16 bytes per 512 bits) and the
- * fallback.  0 for NULL. */
+/* Device memory the handle holds, in bytes.  A and its ranks are stored
+ * together in 32-byte sectors (224 bits of A and a 32-bit count of the ones
+ * before the sector within its superblock of 2^24 sectors), plus one 64-bit
+ * count per superblock and the fallback keys.  A query then reads one sector
+ * per level it probes.  The counts cost 1/7 of A, where Sec. 3.1's 64-bit
+ * checkpoint per 512 bits costs 1/8 (mphf_bits_per_key counts the paper's).
+ * 0 for NULL. */
 uint64_t mphf_device_bytes(const mphf_t *h);
 
 /* Release a handle and its device memory; NULL is a no-op. */
@@ -166,8 +169,8 @@ int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
 
 /* Which construction path built h: 1 = bucketed (shared-memory ArrayFill),
  * 2 = unbucketed (L2 atomics; taken when a bound of the bucketed path is
- * exceeded, e.g. many duplicate keys), 3 = mphf_build_batched.  All give
- * identical results. */
+ * exceeded, e.g. many duplicate keys), 3 = mphf_build_batched, 4 = loaded by
+ * mphf_deserialize.  All give identical results. */
 int mphf_build_path(const mphf_t *h);
 /* Test hook, process-wide: path 0 = bucketed with automatic fallback (default),
  * 1 = unbucketed only; cap_scale (default 1) scales the bucket capacities, so a
@@ -176,8 +179,9 @@ int mphf_debug_config(int path, double cap_scale);
 
 /*
  * Rank table of a bit array without allocating device memory.  The paper has
- * no counterpart: this is an allocation-free variant of the rank-table build
- * that mphf_build runs internally, for callers that must not call cudaMalloc:
+ * no counterpart: this is an allocation-free rank-table build over a caller's
+ * bit array (Sec. 3.1's 512-bit checkpoints, each beside seven 9-bit in-block
+ * counts), for callers that must not call cudaMalloc:
  * code that records work into a CUDA graph (cudaMalloc cannot be captured),
  * serving loops that run under a fixed device-memory budget, and hosts whose
  * own allocator owns the device memory (a direct cudaMalloc there fragments
@@ -185,7 +189,8 @@ int mphf_debug_config(int path, double cap_scale);
  *   d_words  device array of nwords 64-bit words (16-byte aligned).
  *   d_rank2  device output of 2 * ceil(nwords / 8) words (16-byte aligned):
  *            d_rank2[2b] = ones of the array in bits [0, 512 b), d_rank2[2b+1]
- *            = seven 9-bit in-block prefix counts (the layout handles use).
+ *            = seven 9-bit in-block prefix counts (ones of words 0..k-1 of the
+ *            block in bits 9(k-1) .. 9k-1, k = 1..7).
  *   d_total  optional device word receiving the total number of ones.
  * Scratch lives in a fixed array inside the library: at most 2^27 words
  * (2^33 bits) per call; larger inputs return MPHF_EINVAL.  The first call on
@@ -196,6 +201,46 @@ int mphf_debug_config(int path, double cap_scale);
  */
 int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords, uint64_t *d_rank2,
                             uint64_t *d_total, void *stream);
+
+/* ---- string keys ------------------------------------------------------------ */
+/*
+ * 64-bit keys of n byte strings (Sec. 4.3 / Table 2 run the method on n-grams
+ * and random words; the paper does not fix how a string becomes a key).
+ * String i is d_bytes[d_offsets[i] .. d_offsets[i+1]); its key is
+ *   h = mix(seed + (len + 1) * 0x9E3779B97F4A7C15), then for each group of 8
+ *   bytes in order (the last padded with zero bytes) h = mix(h ^ w), w the
+ *   group read as a little-endian integer; key = h  (mix = SplitMix64's
+ *   finalizer).
+ * The keys then go to mphf_build / mphf_lookup like any others.
+ *   d_bytes     device array of total_bytes bytes, any alignment.
+ *   d_offsets   device array of n + 1 offsets (8-byte aligned), non-decreasing,
+ *               at most total_bytes.
+ *   d_out       device array of n keys (8-byte aligned).
+ * A string whose offsets fall outside [0, total_bytes] or decrease is not read;
+ * the call then returns MPHF_EINVAL.  Waits for the device before returning.
+ */
+int mphf_string_keys(const uint8_t *d_bytes, uint64_t total_bytes, const uint64_t *d_offsets,
+                     uint64_t n, uint64_t seed, uint64_t *d_out, void *stream);
+
+/* ---- serialization -------------------------------------------------------- */
+/*
+ * A handle as a self-contained byte image (host memory), so that a function
+ * built once can be stored and loaded again, on this or another GPU.  Format
+ * (little-endian): a 128-byte header -- magic "BBHGB300", format version,
+ * N, gamma, L, levels used, seed, M, fallback size, sector and superblock
+ * counts, and a 64-bit checksum of everything after the header -- then the
+ * per-level (n_d, m_d, off_d) triples and n_L, then the sectors, the
+ * superblock counts and the sorted fallback keys.
+ *   mphf_serialized_size  bytes the image of h takes.
+ *   mphf_serialize        writes the image to h_buf (bytes >= that size);
+ *                         waits for the device.
+ *   mphf_deserialize      builds a new handle on the current device from an
+ *                         image; a wrong magic, version, size, checksum or an
+ *                         inconsistent header returns MPHF_EINVAL and no handle.
+ */
+int mphf_serialized_size(const mphf_t *h, uint64_t *bytes);
+int mphf_serialize(const mphf_t *h, void *h_buf, uint64_t bytes);
+int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream, mphf_t **out);
 
 /* ---- many functions, many requests --------------------------------------- */
 /*

@@ -95,6 +95,10 @@ def lib():
         "mphf_server_loadgen": ([vp, vp, vp, vp, u32, dbl, dbl, dbl, dbl, vp, u64, dbl, vp, u64,
                                  dbl, dbl, dbl, u64, vp, u64, pu64, pu64, pu64,
                                  ctypes.POINTER(dbl)], i32),
+        "mphf_string_keys": ([vp, u64, vp, u64, u64, vp, vp], i32),
+        "mphf_serialized_size": ([vp, pu64], i32),
+        "mphf_serialize": ([vp, vp, u64], i32),
+        "mphf_deserialize": ([vp, u64, vp, pvp], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -164,6 +168,33 @@ class MPHF:
         _check(rc, "mphf_build_host")
         return cls(h)
 
+    # -- serialization -------------------------------------------------------
+    def to_bytes(self) -> bytes:
+        """The function as a self-contained byte image (mphf_serialize)."""
+        n = ctypes.c_uint64()
+        _check(lib().mphf_serialized_size(self._h, ctypes.byref(n)), "mphf_serialized_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().mphf_serialize(self._h, buf.ctypes.data, n.value), "mphf_serialize")
+        return buf.tobytes()
+
+    @classmethod
+    def from_bytes(cls, image, stream=None) -> "MPHF":
+        """A new function on the current device from an image made by to_bytes."""
+        a = np.frombuffer(image, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        _check(lib().mphf_deserialize(a.ctypes.data if a.size else None, a.size,
+                                      _stream_ptr(stream), ctypes.byref(h)), "mphf_deserialize")
+        return cls(h)
+
+    def save(self, path: str) -> None:
+        with open(path, "wb") as f:
+            f.write(self.to_bytes())
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "MPHF":
+        with open(path, "rb") as f:
+            return cls.from_bytes(f.read(), stream)
+
     def free(self):
         if self._h is not None and self._h.value:
             lib().mphf_free(self._h)
@@ -209,7 +240,8 @@ class MPHF:
 
     @property
     def build_path(self) -> int:
-        """1 = bucketed (shared-memory) construction, 2 = unbucketed (L2 atomics)."""
+        """1 = bucketed (shared-memory) construction, 2 = unbucketed (L2 atomics),
+        3 = batched construction, 4 = loaded from a serialized image."""
         return lib().mphf_build_path(self._h)
 
     @property
@@ -327,6 +359,31 @@ def keygen(n: int, seed: int, start: int = 0, device=None, stream=None):
     if n:
         _check(lib().mphf_keygen(out.data_ptr(), int(n), int(seed) & NOT_FOUND, int(start),
                                  _stream_ptr(stream)), "mphf_keygen")
+    return out
+
+
+def string_keys(data, offsets, seed: int = 0, stream=None):
+    """64-bit keys (int64 CUDA tensor) of the byte strings data[offsets[i]:offsets[i+1]].
+
+    data: uint8 bytes (numpy array, bytes, or a CUDA uint8 tensor); offsets:
+    n + 1 non-decreasing offsets (numpy or CUDA int64/uint64 tensor).
+    """
+    import torch
+    if isinstance(data, (bytes, bytearray)):
+        data = np.frombuffer(bytes(data), dtype=np.uint8)
+    if isinstance(data, np.ndarray):
+        data = torch.from_numpy(np.ascontiguousarray(data, dtype=np.uint8)).cuda()
+    if isinstance(offsets, np.ndarray):
+        offsets = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.uint64).view(np.int64)).cuda()
+    data = data.contiguous()
+    offsets = offsets.contiguous()
+    n = offsets.numel() - 1
+    out = torch.empty(max(n, 0), dtype=torch.int64, device=offsets.device)
+    if n > 0:
+        rc = lib().mphf_string_keys(data.data_ptr() if data.numel() else None, data.numel(),
+                                    offsets.data_ptr(), n, int(seed) & NOT_FOUND, out.data_ptr(),
+                                    _stream_ptr(stream))
+        _check(rc, "mphf_string_keys")
     return out
 
 
