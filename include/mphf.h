@@ -170,7 +170,8 @@ int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
 /* Which construction path built h: 1 = bucketed (shared-memory ArrayFill),
  * 2 = unbucketed (L2 atomics; taken when a bound of the bucketed path is
  * exceeded, e.g. many duplicate keys), 3 = mphf_build_batched, 4 = loaded by
- * mphf_deserialize.  All give identical results. */
+ * mphf_deserialize, 5 = mphf_build_nodisk / mphf_build_generated.  All give
+ * identical results. */
 int mphf_build_path(const mphf_t *h);
 /* Test hook, process-wide: path 0 = bucketed with automatic fallback (default),
  * 1 = unbucketed only; cap_scale (default 1) scales the bucket capacities, so a
@@ -201,6 +202,31 @@ int mphf_debug_config(int path, double cap_scale);
  */
 int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords, uint64_t *d_rank2,
                             uint64_t *d_total, void *stream);
+
+/* ---- construction without stored key sets ---------------------------------- */
+/*
+ * Build without storing F_d (Sec. 3.4, the second strategy; Sec. 4.4): level d
+ * re-reads every input key, asks levels 0..d-1 whether it was placed there
+ * (the query of Algorithm 3), and fills A_d with the keys that were not.  The
+ * device holds the bit arrays only, until |F_d| <= keep_fraction * n; then F_d
+ * is collected once and the remaining levels run on that list (Sec. 4.4
+ * keeps keys in memory below 2%: keep_fraction = 0.02).  The function equals
+ * mphf_build's on the same keys, bit for bit.
+ *   mphf_build_nodisk     keys in a caller-owned device array (8-byte aligned),
+ *                         read again at every streamed level, never copied.
+ *   mphf_build_generated  keys are key(j) = mix(key_seed + (key_start + j + 1)
+ *                         * 0x9E3779B97F4A7C15), j in [0, n) -- the stream of
+ *                         mphf_keygen -- computed on the fly and never stored,
+ *                         so n is bounded by the bit arrays (about 2 gamma bits
+ *                         per key at level 0) instead of 8 bytes per key.
+ * keep_fraction must lie in [0, 1]; other arguments as mphf_build.  Waits for
+ * the device before returning.
+ */
+int mphf_build_nodisk(const uint64_t *d_keys, uint64_t n, double gamma, uint32_t levels,
+                      uint64_t seed, double keep_fraction, void *stream, mphf_t **out);
+int mphf_build_generated(uint64_t n, uint64_t key_seed, uint64_t key_start, double gamma,
+                         uint32_t levels, uint64_t seed, double keep_fraction, void *stream,
+                         mphf_t **out);
 
 /* ---- string keys ------------------------------------------------------------ */
 /*

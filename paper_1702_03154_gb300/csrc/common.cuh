@@ -192,7 +192,7 @@ struct mphf {
   bbh::DevBuf SB;       // ones before each superblock of 2^24 sectors
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;
-  int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched construction, 4 loaded
+  int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched, 4 loaded, 5 without stored F_d
   mphf_shared *shared = nullptr;  // set: S/SB/fb live in a batched arena
   bbh::DevBuf ldesc;     // device descriptor for multi-function lookups (made on first use)
 };

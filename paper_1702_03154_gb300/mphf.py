@@ -96,6 +96,8 @@ def lib():
                                  dbl, dbl, dbl, u64, vp, u64, pu64, pu64, pu64,
                                  ctypes.POINTER(dbl)], i32),
         "mphf_string_keys": ([vp, u64, vp, u64, u64, vp, vp], i32),
+        "mphf_build_nodisk": ([vp, u64, dbl, u32, u64, dbl, vp, pvp], i32),
+        "mphf_build_generated": ([u64, u64, u64, dbl, u32, u64, dbl, vp, pvp], i32),
         "mphf_serialized_size": ([vp, pu64], i32),
         "mphf_serialize": ([vp, vp, u64], i32),
         "mphf_deserialize": ([vp, u64, vp, pvp], i32),
@@ -166,6 +168,31 @@ class MPHF:
         rc = lib().mphf_build_host(ptr if a.size else None, a.size, float(gamma), int(levels),
                                    int(seed) & NOT_FOUND, _stream_ptr(stream), ctypes.byref(h))
         _check(rc, "mphf_build_host")
+        return cls(h)
+
+    @classmethod
+    def build_nodisk(cls, keys, gamma: float = 2.0, levels: int = 25, seed: int = 0,
+                     keep_fraction: float = 0.02, stream=None) -> "MPHF":
+        """Build without storing F_d: every level re-reads the caller's keys (Sec. 3.4)."""
+        keys = _dev_keys(keys)
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_nodisk(keys.data_ptr() if keys.numel() else None, keys.numel(),
+                                     float(gamma), int(levels), int(seed) & NOT_FOUND,
+                                     float(keep_fraction), _stream_ptr(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_nodisk")
+        return cls(h)
+
+    @classmethod
+    def build_generated(cls, n: int, key_seed: int, key_start: int = 0, gamma: float = 2.0,
+                        levels: int = 25, seed: int = 0, keep_fraction: float = 0.02,
+                        stream=None) -> "MPHF":
+        """Build over the SplitMix64 keys key(j), j < n, generated on the fly (Sec. 4.4)."""
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_generated(int(n), int(key_seed) & NOT_FOUND,
+                                        int(key_start) & NOT_FOUND, float(gamma), int(levels),
+                                        int(seed) & NOT_FOUND, float(keep_fraction),
+                                        _stream_ptr(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_generated")
         return cls(h)
 
     # -- serialization -------------------------------------------------------

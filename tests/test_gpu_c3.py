@@ -53,3 +53,17 @@ def test_config3_1e10_properties():
     del hits
     total_placed = N - h.num_fallback
     assert total_placed + h.num_fallback == N
+    # The same function built without storing any key (Sec. 3.4, second
+    # strategy; Sec. 4.4 streams generated keys the same way): equal, bit for bit.
+    import time
+    import numpy as np
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g2 = mphf.MPHF.build_generated(N, 4, 0, gamma=2.0, levels=25, seed=0)
+    t1 = time.perf_counter()
+    print(f"generated-key build of 1e10 keys: {t1 - t0:.2f} s")
+    assert g2.levels() == lv and g2.total_bits == h.total_bits
+    assert g2.num_fallback == h.num_fallback
+    assert np.array_equal(g2.rank(), h.rank())
+    q = keys[::997]
+    assert torch.equal(g2.lookup(q), h.lookup(q))
