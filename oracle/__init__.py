@@ -90,6 +90,8 @@ def lib():
         L.oracle_copy_rank.argtypes, L.oracle_copy_rank.restype = [vp, vp], None
         L.oracle_copy_fallback.argtypes, L.oracle_copy_fallback.restype = [vp, vp], None
         L.oracle_bits_per_key.argtypes, L.oracle_bits_per_key.restype = [vp], dbl
+        L.oracle_bits_per_key_sampled.argtypes = [vp, u64]
+        L.oracle_bits_per_key_sampled.restype = dbl
         L.oracle_string_key.argtypes, L.oracle_string_key.restype = [vp, u64, u64], u64
         L.oracle_string_keys.argtypes, L.oracle_string_keys.restype = [vp, vp, u64, u64, vp], None
         _lib = L
@@ -228,6 +230,10 @@ class OracleMPHF:
 
     def bits_per_key(self) -> float:
         return lib().oracle_bits_per_key(self._h)
+
+    def bits_per_key_sampled(self, rank_block: int) -> float:
+        """Size with one 64-bit rank counter every rank_block bits (1024: minirank)."""
+        return lib().oracle_bits_per_key_sampled(self._h, rank_block)
 
 
 def string_key(s: bytes, seed: int = 0) -> int:

@@ -395,12 +395,22 @@ void oracle_copy_fallback(const oracle_mphf *h, uint64_t *out)
  * ((1 + 64/512) per bit of A) and 64 bits per fallback key; level metadata
  * (a few words per level) is not counted.
  */
+/*
+ * The same with one 64-bit counter every rank_block bits: Sec. 3.1's default
+ * is 512; the "minirank" setting of Sec. 4.3 (Table 1) samples every 1024.
+ */
+double oracle_bits_per_key_sampled(const oracle_mphf *h, uint64_t rank_block)
+{
+    if (h->N == 0 || rank_block == 0)
+        return 0.0;
+    uint64_t counters = (h->M + rank_block - 1) / rank_block;
+    double bits = (double)h->M + 64.0 * (double)counters + 64.0 * (double)h->n_fb;
+    return bits / (double)h->N;
+}
+
 double oracle_bits_per_key(const oracle_mphf *h)
 {
-    if (h->N == 0)
-        return 0.0;
-    double bits = (double)h->M + 64.0 * (double)oracle_num_rank(h) + 64.0 * (double)h->n_fb;
-    return bits / (double)h->N;
+    return oracle_bits_per_key_sampled(h, ORACLE_RANK_BLOCK);
 }
 
 /*

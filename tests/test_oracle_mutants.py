@@ -43,6 +43,9 @@ MUTANTS = {
     "fastrange_shift": ("(unsigned __int128)m) >> 64);", "(unsigned __int128)m) >> 63);"),
     # Offsets: each level starts at bit 0.
     "offset_not_accumulated": ("off += h->m[i];", "off += 0 * h->m[i];"),
+    # Sec. 4.3 minirank: the counter interval ignored (always 512).
+    "rank_sampling_ignored": ("uint64_t counters = (h->M + rank_block - 1) / rank_block;",
+                              "uint64_t counters = (h->M + 511) / 512;"),
     # String keys (Sec. 4.3): the length left out of the first state.
     "string_length_dropped": ("oracle_mix(seed + (len + 1) * 0x9E3779B97F4A7C15ULL)",
                               "oracle_mix(seed + 1 * 0x9E3779B97F4A7C15ULL)"),

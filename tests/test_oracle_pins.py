@@ -190,13 +190,15 @@ def test_bits_per_key_matches_table1(golden_dir):
     g = json.load(open(os.path.join(golden_dir, "table1_bits_per_key.json")))
     for row in g["rows"]:
         h = _build(10**6, row["gamma"], seed=3)
+        # minirank (rank_block 1024): one counter per 1024 bits instead of 512
+        bpk = h.bits_per_key_sampled(row["rank_block"])
         if row["rank_block"] == 512:
-            bpk = h.bits_per_key()
-        else:
-            # minirank: one counter per 1024 bits instead of 512.
-            M = h.total_bits
-            bpk = (M + 64 * math.ceil(M / 1024) + 64 * h.num_fallback) / h.N
+            assert bpk == h.bits_per_key()
         assert abs(bpk - row["bits_per_key"]) <= g["printed_precision"] + 0.01, (row, bpk)
+        # the counters of a block size cost exactly 64 / rank_block bits per bit of A
+        M = h.total_bits
+        want = (M + 64 * math.ceil(M / row["rank_block"]) + 64 * h.num_fallback) / h.N
+        assert bpk == pytest.approx(want, rel=1e-12)
 
 
 @pytest.mark.parametrize("gamma", [1.0, 2.0, 5.0])
