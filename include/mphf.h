@@ -136,7 +136,8 @@ int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n, uint64
                      void *stream);
 
 /* Size of the function in bits per key: (M + 64 ceil(M/512) + 64 n_fb) / N with M the
- * total bits of A (Sec. 3.1's (1 + 64/512) gamma e^{1/gamma}); level metadata excluded.
+ * total bits of A (Sec. 3.1's (1 + 64/512) gamma e^{1/gamma}); 1024 in place of 512
+ * for the minirank layout (mphf_set_layout); level metadata excluded.
  * 0 for an empty function or NULL. */
 double mphf_bits_per_key(const mphf_t *h);
 
@@ -148,6 +149,22 @@ double mphf_bits_per_key(const mphf_t *h);
  * checkpoint per 512 bits costs 1/8 (mphf_bits_per_key counts the paper's).
  * 0 for NULL. */
 uint64_t mphf_device_bytes(const mphf_t *h);
+
+/*
+ * Rank sampling (Sec. 3.1; the "minirank" setting of Sec. 4.3).  A and its
+ * ranks live in sectors of 32 bytes (224 bits of A + one 32-bit count: the
+ * default, every probe one 256-bit load) or 64 bytes (480 bits of A + one
+ * count: "minirank", counts cost 1/15 of A instead of 1/7, at gamma = 1 the
+ * size drops from 3.1 to 2.9 bits/key as in the paper, and a probe loads both
+ * halves of its sector).  Builds make 32-byte sectors; mphf_set_layout
+ * re-stores a function in the other size (sector_bytes 32 or 64), keeping
+ * every index unchanged; a handle of a batched build then gets arrays of its
+ * own.  mphf_bits_per_key counts one 64-bit counter per 512 bits of A for
+ * 32-byte sectors and per 1024 bits for 64-byte ones (the paper's two
+ * settings).  Waits for the device before returning.
+ */
+int mphf_set_layout(mphf_t *h, uint32_t sector_bytes, void *stream);
+uint32_t mphf_sector_bytes(const mphf_t *h);   /* 32 or 64; 0 for NULL */
 
 /* Release a handle and its device memory; NULL is a no-op. */
 void mphf_free(mphf_t *h);
@@ -254,7 +271,8 @@ int mphf_string_keys(const uint8_t *d_bytes, uint64_t total_bytes, const uint64_
  * built once can be stored and loaded again, on this or another GPU.  Format
  * (little-endian): a 128-byte header -- magic "BBHGB300", format version,
  * N, gamma, L, levels used, seed, M, fallback size, sector and superblock
- * counts, and a 64-bit checksum of everything after the header -- then the
+ * counts, a 64-bit checksum of everything after the header, and the sector
+ * size (A words per sector: 7 or 15) -- then the
  * per-level (n_d, m_d, off_d) triples and n_L, then the sectors, the
  * superblock counts and the sorted fallback keys.
  *   mphf_serialized_size  bytes the image of h takes.

@@ -182,9 +182,13 @@ void mphf_free(mphf_t *h) {
   delete h;
 }
 
+// Sec. 3.1's size with one 64-bit counter per 512 bits of A, or per 1024
+// bits for the minirank layout (Sec. 4.3).
 double mphf_bits_per_key(const mphf_t *h) {
   if (!h || h->N == 0) return 0.0;
-  double bits = (double)h->M + 64.0 * (double)h->n_rank + 64.0 * (double)h->n_fb;
+  const u64 block = h->sw == kSectWordsMini ? 2 * MPHF_RANK_BLOCK : MPHF_RANK_BLOCK;
+  const u64 counters = (h->M + block - 1) / block;
+  double bits = (double)h->M + 64.0 * (double)counters + 64.0 * (double)h->n_fb;
   return bits / (double)h->N;
 }
 
@@ -217,24 +221,24 @@ static int copy_out(const mphf_t *h, const DevBuf &b, uint64_t *dst, uint64_t co
   return MPHF_OK;
 }
 
-// A comes back out of the sectors: words 1..7 of each 32-byte sector are 28
+// A comes back out of the sectors: words 1..W of each sector are 4 W
 // consecutive bytes of A, so one strided copy gathers them.
 int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count) {
   if (!h || (count && !h_words) || count != h->M / 64) return MPHF_EINVAL;
   if (!count) return MPHF_OK;
-  const u64 w32 = h->M / 32;               // A's 32-bit words
-  const u64 full = w32 / kSectWords;       // sectors whose 7 words all belong to A
-  const u64 rest = w32 - full * kSectWords;
+  const u64 W = h->sw, pitch = sector_bytes(h->sw);
+  const u64 w32 = h->M / 32;  // A's 32-bit words
+  const u64 full = w32 / W;   // sectors whose W words all belong to A
+  const u64 rest = w32 - full * W;
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
   const char *src = (const char *)h->S.p + 4;
   char *dst = (char *)h_words;
   cudaError_t e = cudaSuccess;
-  if (full)
-    e = cudaMemcpy2D(dst, 4 * kSectWords, src, 32, 4 * kSectWords, full, cudaMemcpyDeviceToHost);
+  if (full) e = cudaMemcpy2D(dst, 4 * W, src, pitch, 4 * W, full, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && rest)
-    e = cudaMemcpy(dst + full * 4 * kSectWords, src + full * 32, rest * 4, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(dst + full * 4 * W, src + full * pitch, rest * 4, cudaMemcpyDeviceToHost);
   if (prev != h->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2D(A from sectors)");
   return MPHF_OK;
@@ -250,7 +254,8 @@ int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
   DevBuf tmp;
   int rc = dev_alloc(tmp, count * 8, 0);
   if (rc == MPHF_OK) {
-    rc = sector_checkpoints((const unsigned *)h->S.p, (const u64 *)h->SB.p, count, (u64 *)tmp.p, 0);
+    rc = sector_checkpoints((const unsigned *)h->S.p, (const u64 *)h->SB.p, h->sw, count,
+                            (u64 *)tmp.p, 0);
     cudaError_t e = cudaSuccess;
     if (rc == MPHF_OK) e = cudaMemcpy(h_rank, tmp.p, count * 8, cudaMemcpyDeviceToHost);
     dev_free(tmp, 0);
@@ -261,6 +266,77 @@ int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
   if (prev != h->device) cudaSetDevice(prev);
   return rc;
 }
+
+// Re-store A and its ranks in the other sector size (the rank-sampling choice
+// of Sec. 4.3): A is gathered out of the old sectors with one strided copy on
+// the device and the new sectors are built from it.
+int mphf_set_layout(mphf_t *h, uint32_t sector_bytes_, void *stream) {
+  if (!h || (sector_bytes_ != 32 && sector_bytes_ != 64)) return MPHF_EINVAL;
+  const unsigned W = sector_bytes_ == 32 ? kSectWords : kSectWordsMini;
+  if (W == h->sw) return MPHF_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mphf_t nh;  // the new arrays, built beside the old ones
+  nh.M = h->M;
+  nh.sw = W;
+  DevBuf A, fb;
+  const u64 w32 = h->M / 32, Wo = h->sw, pitch = sector_bytes(h->sw);
+  const u64 full = w32 / Wo, rest = w32 - full * Wo;
+  int rc = dev_alloc(A, h->M / 8, s);
+  cudaError_t e = cudaSuccess;
+  if (rc == MPHF_OK && full)
+    e = cudaMemcpy2DAsync(A.p, 4 * Wo, (const char *)h->S.p + 4, pitch, 4 * Wo, full,
+                          cudaMemcpyDeviceToDevice, s);
+  if (rc == MPHF_OK && e == cudaSuccess && rest)
+    e = cudaMemcpyAsync((char *)A.p + full * 4 * Wo, (const char *)h->S.p + 4 + full * pitch,
+                        rest * 4, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) rc = cuda_fail(e, "mphf_set_layout (gather A)");
+  if (rc == MPHF_OK && h->M)
+    rc = make_sectors(&nh, ASrc{(const u64 *)A.p, h->M / 64, nullptr, h->M / 64}, nullptr, s);
+  // a handle of a batched build gets arrays of its own
+  if (rc == MPHF_OK && h->shared && h->n_fb) {
+    rc = dev_alloc(fb, h->n_fb * 8, s);
+    if (rc == MPHF_OK &&
+        (e = cudaMemcpyAsync(fb.p, h->fb.p, h->n_fb * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      rc = cuda_fail(e, "mphf_set_layout (fallback)");
+  }
+  dev_free(A, s);
+  e = cudaStreamSynchronize(s);
+  if (rc == MPHF_OK && e != cudaSuccess) rc = cuda_fail(e, "mphf_set_layout");
+  if (rc != MPHF_OK) {
+    dev_free(nh.S, s);
+    dev_free(nh.SB, s);
+    dev_free(fb, s);
+    cudaStreamSynchronize(s);
+    if (prev != h->device) cudaSetDevice(prev);
+    return rc;
+  }
+  if (h->ldesc.p) {  // multi-lookup descriptor of the old arrays
+    cudaFree(h->ldesc.p);
+    h->ldesc = DevBuf();
+  }
+  if (h->shared) {
+    if (h->n_fb) h->fb = fb;
+    else h->fb = DevBuf();
+    release_shared(h->shared);
+    h->shared = nullptr;
+  } else {
+    dev_free(h->S, s);
+    dev_free(h->SB, s);
+  }
+  h->S = nh.S;
+  h->SB = nh.SB;
+  h->sw = W;
+  h->n_sect = nh.n_sect;
+  nh.S = DevBuf();
+  nh.SB = DevBuf();
+  if (prev != h->device) cudaSetDevice(prev);
+  return MPHF_OK;
+}
+
+uint32_t mphf_sector_bytes(const mphf_t *h) { return h ? (uint32_t)sector_bytes(h->sw) : 0; }
 
 uint64_t mphf_device_bytes(const mphf_t *h) {
   return h ? (uint64_t)(h->S.bytes + h->SB.bytes + h->fb.bytes) : 0;

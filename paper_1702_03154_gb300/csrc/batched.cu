@@ -979,7 +979,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     o.at_off = b.at_off;
     o.m0 = b.m0;
     o.M = hl[U - 1].off + hl[U - 1].m;
-    o.nsect = n_sectors(o.M);
+    o.nsect = n_sectors(o.M, kSectWords);
     o.fb_src = b.flat_off;
     o.n_fb = n_fb;
     o.S_dst = out_words;  // 8-word (64-byte) steps keep every sector 32-byte aligned
@@ -1066,7 +1066,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       h->n_sect = bo[s].nsect;
       u64 *base = (u64 *)sh->arena.p;
       h->S.p = base + bo[s].S_dst;
-      h->S.bytes = h->n_sect * 32;
+      h->S.bytes = h->n_sect * sector_bytes(kSectWords);
       h->SB.p = base + bo[s].SB_dst;
       h->SB.bytes = n_superblocks(h->n_sect) * 8;
       h->fb.p = h->n_fb ? base + bo[s].fb_dst : nullptr;

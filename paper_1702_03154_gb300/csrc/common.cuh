@@ -187,8 +187,9 @@ struct mphf {
   uint64_t M = 0;        // total bits
   uint64_t n_rank = 0;   // ceil(M / 512)
   uint64_t n_fb = 0;
-  uint64_t n_sect = 0;   // 32-byte sectors holding A and its ranks (sector.cuh)
-  bbh::DevBuf S;        // n_sect * 8 32-bit words
+  uint32_t sw = 7;       // A words per sector: 7 (32-byte sectors) or 15 (minirank)
+  uint64_t n_sect = 0;   // sectors holding A and its ranks (sector.cuh)
+  bbh::DevBuf S;        // n_sect * (sw + 1) 32-bit words
   bbh::DevBuf SB;       // ones before each superblock of 2^24 sectors
   bbh::DevBuf fb;       // n_fb keys
   int device = 0;

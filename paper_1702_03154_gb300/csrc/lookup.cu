@@ -49,7 +49,7 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
-template <int kSlots>
+template <int kSlots, int W>
 __global__ void __launch_bounds__(kLookupThreads)
 k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
@@ -117,21 +117,21 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
 
     // one probe per active slot: issue all loads, then resolve
     SectPos p[kSlots];
-    Sect v[kSlots];
+    Sect<W> v[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
-        p[s] = sect_pos(toff[d] + level_pos(x[s], ts[d], tm[d]));
-        v[s] = sect_load(a.S, p[s].t);
+        p[s] = sect_pos<W>(toff[d] + level_pos(x[s], ts[d], tm[d]));
+        v[s] = sect_load<W>(a.S, p[s].t);
       }
     }
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
-        const unsigned w = sect_word(v[s], p[s].j);
+        const unsigned w = sect_word<W>(v[s], p[s].j);
         if ((w >> p[s].b) & 1u) {
-          __stcs(out + idx[s], sect_rank(v[s], p[s], w, a.SB));
+          __stcs(out + idx[s], sect_rank<W>(v[s], p[s], w, a.SB));
           act[s] = false;
         } else if (++lvl[s] >= a.L_used) {
           __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
@@ -177,20 +177,27 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   unsigned grid = (unsigned)((nwarps_needed + per_block - 1) / per_block);
   // one wave of resident CTAs: warps take chunks in a fixed order, so a
   // second wave would only start after the first has drained
-  static unsigned maxb[5] = {0, 0, 0, 0, 0};
   const int slots = lookup_slots();
-  if (!maxb[slots]) {
-    maxb[slots] = slots == 3   ? resident_grid(k_lookup<3>, kLookupThreads, 0)
-                  : slots == 4 ? resident_grid(k_lookup<4>, kLookupThreads, 0)
-                               : resident_grid(k_lookup<2>, kLookupThreads, 0);
+  const bool mini = h->sw == kSectWordsMini;
+  static unsigned maxb[5][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  unsigned &mb = maxb[slots][mini];
+  if (!mb) {
+    if (mini) mb = resident_grid(k_lookup<2, kSectWordsMini>, kLookupThreads, 0);
+    else if (slots == 3) mb = resident_grid(k_lookup<3, kSectWords>, kLookupThreads, 0);
+    else if (slots == 4) mb = resident_grid(k_lookup<4, kSectWords>, kLookupThreads, 0);
+    else mb = resident_grid(k_lookup<2, kSectWords>, kLookupThreads, 0);
   }
-  if (grid > maxb[slots]) grid = maxb[slots];
+  if (grid > mb) grid = mb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  switch (slots) {
-    case 3: k_lookup<3><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
-    case 4: k_lookup<4><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
-    default: k_lookup<2><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+  if (mini) {  // a 64-byte sector already takes 16 registers per slot
+    k_lookup<2, kSectWordsMini><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
+  } else {
+    switch (slots) {
+      case 3: k_lookup<3, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+      case 4: k_lookup<4, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+      default: k_lookup<2, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
+    }
   }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;

@@ -122,9 +122,9 @@ k_rank_add(u64 *__restrict__ rank2, u64 nrank, const u64 *__restrict__ cta_prefi
 }
 
 // ---------------------------------------------------------------------------
-// Sector layout (sector.cuh): one thread per 224-bit sector, 256 sectors per
-// CTA, so a superblock (2^24 sectors) is exactly 2^16 CTAs.  Pass 1 sums the
-// ones of each CTA's sectors, k_scan_sums turns the sums into exclusive
+// Sector layout (sector.cuh): one thread per sector of W A-words, 256 sectors
+// per CTA, so a superblock (2^24 sectors) is exactly 2^16 CTAs.  Pass 1 sums
+// the ones of each CTA's sectors, k_scan_sums turns the sums into exclusive
 // prefixes, pass 2 reads A again and writes every sector with its count
 // relative to the start of its superblock.
 // ---------------------------------------------------------------------------
@@ -136,47 +136,51 @@ __device__ __forceinline__ u64 a_word(const ASrc &a, u64 k) {
   return k < a.W ? __ldg(a.a1 + (k - a.w0)) : 0ull;
 }
 
-// A's 32-bit words 7t .. 7t+6 (zero past the end of A).
-__device__ __forceinline__ void sect_words(const ASrc &a, u64 t, unsigned (&w)[kSectWords]) {
-  const u64 q0 = t * kSectWords;
+// A's 32-bit words W t .. W t + W - 1 (zero past the end of A).
+template <int W>
+__device__ __forceinline__ void sect_words(const ASrc &a, u64 t, unsigned (&w)[W]) {
+  constexpr int K = W / 2 + 1;  // 64-bit words covering W + 1 32-bit words
+  const u64 q0 = t * W;
   const u64 k0 = q0 >> 1;
-  unsigned h[8];
+  unsigned h[2 * K];
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < K; i++) {
     const u64 u = a_word(a, k0 + i);
     h[2 * i] = (unsigned)u;
     h[2 * i + 1] = (unsigned)(u >> 32);
   }
   const bool odd = q0 & 1;
 #pragma unroll
-  for (int i = 0; i < (int)kSectWords; i++) w[i] = odd ? h[i + 1] : h[i];
+  for (int i = 0; i < W; i++) w[i] = odd ? h[i + 1] : h[i];
 }
 
+template <int W>
 __global__ void __launch_bounds__(kSectThreads)
 k_sect_sums(ASrc a, u64 nsect, u64 *__restrict__ cta_sums) {
   const u64 t = (u64)blockIdx.x * kSectThreads + threadIdx.x;
   unsigned c = 0;
   if (t < nsect) {
-    unsigned w[kSectWords];
-    sect_words(a, t, w);
+    unsigned w[W];
+    sect_words<W>(a, t, w);
 #pragma unroll
-    for (int i = 0; i < (int)kSectWords; i++) c += __popc(w[i]);
+    for (int i = 0; i < W; i++) c += __popc(w[i]);
   }
   u64 total;
   block_exclusive_scan(c, &total);
   if (threadIdx.x == 0) cta_sums[blockIdx.x] = total;
 }
 
+template <int W>
 __global__ void __launch_bounds__(kSectThreads)
 k_sect_write(ASrc a, u64 nsect, unsigned *__restrict__ S, const u64 *__restrict__ cta_prefix,
              u64 *__restrict__ SB) {
   const u64 t = (u64)blockIdx.x * kSectThreads + threadIdx.x;
-  unsigned w[kSectWords];
+  unsigned w[W];
   unsigned c = 0;
   if (t < nsect) {
-    sect_words(a, t, w);
+    sect_words<W>(a, t, w);
 #pragma unroll
-    for (int i = 0; i < (int)kSectWords; i++) c += __popc(w[i]);
+    for (int i = 0; i < W; i++) c += __popc(w[i]);
   }
   u64 total;
   const u64 ex = block_exclusive_scan(c, &total);
@@ -184,16 +188,20 @@ k_sect_write(ASrc a, u64 nsect, unsigned *__restrict__ S, const u64 *__restrict_
   const u64 sb_cta = (u64)blockIdx.x / kCtaPerSB * kCtaPerSB;  // first CTA of the superblock
   if (t < nsect) {
     const unsigned rel = (unsigned)(cta_prefix[blockIdx.x] - cta_prefix[sb_cta] + ex);
-    uint4 *dst = reinterpret_cast<uint4 *>(S + 8 * t);
+    uint4 *dst = reinterpret_cast<uint4 *>(S + (u64)(W + 1) * t);
     dst[0] = make_uint4(rel, w[0], w[1], w[2]);
-    dst[1] = make_uint4(w[3], w[4], w[5], w[6]);
+#pragma unroll
+    for (int k = 1; k < (W + 1) / 4; k++)
+      dst[k] = make_uint4(w[4 * k - 1], w[4 * k], w[4 * k + 1], w[4 * k + 2]);
   }
   if (threadIdx.x == 0 && (u64)blockIdx.x == sb_cta)
     SB[blockIdx.x / kCtaPerSB] = cta_prefix[blockIdx.x];
 }
 
-int build_sectors(const ASrc &src, u64 M, unsigned *S, u64 *SB, u64 *d_total, cudaStream_t s) {
-  const u64 nsect = n_sectors(M);
+int build_sectors(const ASrc &src, u64 M, unsigned W, unsigned *S, u64 *SB, u64 *d_total,
+                  cudaStream_t s) {
+  if (W != kSectWords && W != kSectWordsMini) return MPHF_EINVAL;
+  const u64 nsect = n_sectors(M, W);
   if (nsect == 0) {
     if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
     return MPHF_OK;
@@ -205,7 +213,11 @@ int build_sectors(const ASrc &src, u64 M, unsigned *S, u64 *SB, u64 *d_total, cu
   if (rc != MPHF_OK) return rc;
   {
     LaunchScope ls("sect_sums", s);
-    k_sect_sums<<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, (u64 *)sums.p);
+    if (W == kSectWords)
+      k_sect_sums<kSectWords><<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, (u64 *)sums.p);
+    else
+      k_sect_sums<kSectWordsMini><<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect,
+                                                                          (u64 *)sums.p);
   }
   {
     LaunchScope ls("sect_scan", s);
@@ -213,7 +225,12 @@ int build_sectors(const ASrc &src, u64 M, unsigned *S, u64 *SB, u64 *d_total, cu
   }
   {
     LaunchScope ls("sect_write", s);
-    k_sect_write<<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, S, (const u64 *)sums.p, SB);
+    if (W == kSectWords)
+      k_sect_write<kSectWords><<<(unsigned)ctas, kSectThreads, 0, s>>>(src, nsect, S,
+                                                                       (const u64 *)sums.p, SB);
+    else
+      k_sect_write<kSectWordsMini><<<(unsigned)ctas, kSectThreads, 0, s>>>(
+          src, nsect, S, (const u64 *)sums.p, SB);
   }
   cudaError_t e = cudaGetLastError();
   dev_free(sums, s);
@@ -222,30 +239,36 @@ int build_sectors(const ASrc &src, u64 M, unsigned *S, u64 *SB, u64 *d_total, cu
 }
 
 int make_sectors(mphf_t *h, const ASrc &src, u64 *d_total, cudaStream_t s) {
-  h->n_sect = n_sectors(h->M);
-  int rc = dev_alloc(h->S, h->n_sect * 32, s);
+  h->n_sect = n_sectors(h->M, h->sw);
+  int rc = dev_alloc(h->S, h->n_sect * sector_bytes(h->sw), s);
   if (rc == MPHF_OK) rc = dev_alloc(h->SB, n_superblocks(h->n_sect) * 8, s);
-  if (rc == MPHF_OK) rc = build_sectors(src, h->M, (unsigned *)h->S.p, (u64 *)h->SB.p, d_total, s);
+  if (rc == MPHF_OK)
+    rc = build_sectors(src, h->M, h->sw, (unsigned *)h->S.p, (u64 *)h->SB.p, d_total, s);
   return rc;
 }
 
+template <int W>
 __global__ void __launch_bounds__(256)
 k_checkpoints(const unsigned *__restrict__ S, const u64 *__restrict__ SB, u64 n_rank,
               u64 *__restrict__ out) {
   const u64 b = (u64)blockIdx.x * 256 + threadIdx.x;
   if (b >= n_rank) return;
-  const SectPos p = sect_pos(b * MPHF_RANK_BLOCK);
-  const Sect v = sect_load(S, p.t);
-  out[b] = sect_rank(v, p, sect_word(v, p.j), SB);
+  const SectPos p = sect_pos<W>(b * MPHF_RANK_BLOCK);
+  const Sect<W> v = sect_load<W>(S, p.t);
+  out[b] = sect_rank<W>(v, p, sect_word<W>(v, p.j), SB);
 }
 
-int sector_checkpoints(const unsigned *S, const u64 *SB, u64 n_rank, u64 *d_out, cudaStream_t s) {
+int sector_checkpoints(const unsigned *S, const u64 *SB, unsigned W, u64 n_rank, u64 *d_out,
+                       cudaStream_t s) {
   if (n_rank == 0) return MPHF_OK;
   const u64 ctas = (n_rank + 255) / 256;
-  if (ctas > 0x7fffffffull) return MPHF_EINVAL;
+  if (ctas > 0x7fffffffull || (W != kSectWords && W != kSectWordsMini)) return MPHF_EINVAL;
   {
     LaunchScope ls("checkpoints", s);
-    k_checkpoints<<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
+    if (W == kSectWords)
+      k_checkpoints<kSectWords><<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
+    else
+      k_checkpoints<kSectWordsMini><<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
   }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;

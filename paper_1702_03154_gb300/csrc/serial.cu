@@ -30,7 +30,8 @@ struct Header {
   double gamma;
   uint32_t L, L_used;
   uint64_t seed, M, n_fb, n_sect, n_sb, total_bytes, checksum;
-  uint64_t reserved[4];
+  uint32_t sector_words, pad;  // A words per sector (7 or 15)
+  uint64_t reserved[3];
 };
 static_assert(sizeof(Header) == kHeader, "header layout");
 
@@ -48,8 +49,9 @@ static uint64_t checksum(const unsigned char *p, uint64_t nwords) {
 
 static uint64_t level_table_bytes(uint32_t L_used) { return (3ull * L_used + 1) * 8; }
 
-static uint64_t image_bytes(uint32_t L_used, uint64_t n_sect, uint64_t n_sb, uint64_t n_fb) {
-  return kHeader + level_table_bytes(L_used) + n_sect * 32 + n_sb * 8 + n_fb * 8;
+static uint64_t image_bytes(uint32_t L_used, uint64_t n_sect, unsigned W, uint64_t n_sb,
+                            uint64_t n_fb) {
+  return kHeader + level_table_bytes(L_used) + n_sect * sector_bytes(W) + n_sb * 8 + n_fb * 8;
 }
 
 }  // namespace bbh
@@ -58,14 +60,15 @@ using namespace bbh;
 
 extern "C" int mphf_serialized_size(const mphf_t *h, uint64_t *bytes) {
   if (!h || !bytes) return MPHF_EINVAL;
-  *bytes = image_bytes(h->L_used, h->n_sect, n_superblocks(h->n_sect), h->n_fb);
+  *bytes = image_bytes(h->L_used, h->n_sect, h->sw, n_superblocks(h->n_sect), h->n_fb);
   return MPHF_OK;
 }
 
 extern "C" int mphf_serialize(const mphf_t *h, void *h_buf, uint64_t bytes) {
   if (!h || !h_buf) return MPHF_EINVAL;
   const uint64_t n_sb = n_superblocks(h->n_sect);
-  const uint64_t total = image_bytes(h->L_used, h->n_sect, n_sb, h->n_fb);
+  const uint64_t total = image_bytes(h->L_used, h->n_sect, h->sw, n_sb, h->n_fb);
+  const uint64_t sbytes = h->n_sect * sector_bytes(h->sw);
   if (bytes < total) return MPHF_EINVAL;
   unsigned char *b = (unsigned char *)h_buf;
   uint64_t *lv = (uint64_t *)malloc(level_table_bytes(h->L_used));
@@ -84,8 +87,8 @@ extern "C" int mphf_serialize(const mphf_t *h, void *h_buf, uint64_t bytes) {
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
   cudaError_t e = cudaSuccess;
-  if (h->n_sect) e = cudaMemcpy(b + at, h->S.p, h->n_sect * 32, cudaMemcpyDeviceToHost);
-  at += h->n_sect * 32;
+  if (h->n_sect) e = cudaMemcpy(b + at, h->S.p, sbytes, cudaMemcpyDeviceToHost);
+  at += sbytes;
   if (e == cudaSuccess && n_sb) e = cudaMemcpy(b + at, h->SB.p, n_sb * 8, cudaMemcpyDeviceToHost);
   at += n_sb * 8;
   if (e == cudaSuccess && h->n_fb)
@@ -106,6 +109,7 @@ extern "C" int mphf_serialize(const mphf_t *h, void *h_buf, uint64_t bytes) {
   hd.n_fb = h->n_fb;
   hd.n_sect = h->n_sect;
   hd.n_sb = n_sb;
+  hd.sector_words = h->sw;
   hd.total_bytes = total;
   hd.checksum = checksum(b + kHeader, (total - kHeader) / 8);
   memcpy(b, &hd, sizeof(hd));
@@ -125,9 +129,11 @@ extern "C" int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream,
       hd.L_used > hd.L)
     return MPHF_EINVAL;
   // sizes, before reading anything they locate
-  if (hd.n_sect != n_sectors(hd.M) || hd.n_sb != n_superblocks(hd.n_sect)) return MPHF_EINVAL;
-  if (hd.n_fb > hd.N || hd.M > (1ull << 56)) return MPHF_EINVAL;
-  if (hd.total_bytes != image_bytes(hd.L_used, hd.n_sect, hd.n_sb, hd.n_fb) ||
+  const unsigned W = hd.sector_words;
+  if (W != kSectWords && W != kSectWordsMini) return MPHF_EINVAL;
+  if (hd.M > (1ull << 56) || hd.n_fb > hd.N) return MPHF_EINVAL;
+  if (hd.n_sect != n_sectors(hd.M, W) || hd.n_sb != n_superblocks(hd.n_sect)) return MPHF_EINVAL;
+  if (hd.total_bytes != image_bytes(hd.L_used, hd.n_sect, W, hd.n_sb, hd.n_fb) ||
       hd.total_bytes > bytes)
     return MPHF_EINVAL;
   if (checksum(b + kHeader, (hd.total_bytes - kHeader) / 8) != hd.checksum) return MPHF_EINVAL;
@@ -169,16 +175,18 @@ extern "C" int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream,
   h->n_rank = (hd.M + MPHF_RANK_BLOCK - 1) / MPHF_RANK_BLOCK;
   h->n_fb = hd.n_fb;
   h->n_sect = hd.n_sect;
+  h->sw = W;
   h->path = 4;  // loaded from an image
   cudaStream_t st = (cudaStream_t)stream;
   uint64_t at = kHeader + level_table_bytes(hd.L_used);
-  int rc = dev_alloc(h->S, hd.n_sect * 32, st);
+  const uint64_t sbytes = hd.n_sect * sector_bytes(W);
+  int rc = dev_alloc(h->S, sbytes, st);
   if (rc == MPHF_OK) rc = dev_alloc(h->SB, hd.n_sb * 8, st);
   if (rc == MPHF_OK) rc = dev_alloc(h->fb, hd.n_fb * 8, st);
   cudaError_t e = cudaSuccess;
   if (rc == MPHF_OK && hd.n_sect)
-    e = cudaMemcpyAsync(h->S.p, b + at, hd.n_sect * 32, cudaMemcpyHostToDevice, st);
-  at += hd.n_sect * 32;
+    e = cudaMemcpyAsync(h->S.p, b + at, sbytes, cudaMemcpyHostToDevice, st);
+  at += sbytes;
   if (rc == MPHF_OK && e == cudaSuccess && hd.n_sb)
     e = cudaMemcpyAsync(h->SB.p, b + at, hd.n_sb * 8, cudaMemcpyHostToDevice, st);
   at += hd.n_sb * 8;

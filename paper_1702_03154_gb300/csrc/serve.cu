@@ -35,7 +35,7 @@ struct LookupDev {
   const unsigned *S;  // sectors (sector.cuh)
   const u64 *SB, *fb;
   u64 n_fb, N;
-  uint32_t L_used, pad;
+  uint32_t L_used, sw;  // levels, A words per sector
   u64 s[MPHF_MAX_LEVELS], m[MPHF_MAX_LEVELS], off[MPHF_MAX_LEVELS];
 };
 
@@ -59,6 +59,7 @@ int ensure_lookup_desc(mphf_t *h) {
   d.n_fb = h->n_fb;
   d.N = h->N;
   d.L_used = h->L_used;
+  d.sw = h->sw;
   for (uint32_t i = 0; i < h->L_used; i++) {
     d.s[i] = h->s[i];
     d.m[i] = h->m[i];
@@ -98,6 +99,7 @@ static constexpr unsigned kMultiChunk = 32 * 64;
 // Lookups of a batch of requests against different functions: the keys of all
 // requests form one index space [0, total); warps take chunks of it and keep
 // kMultiSlots query slots per lane, each slot carrying its request's function.
+template <int W>
 __global__ void __launch_bounds__(kMultiThreads)
 k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
   const unsigned lane = threadIdx.x & 31;
@@ -182,23 +184,23 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
     for (int s = 0; s < kMultiSlots; s++) any |= act[s];
     if (!__any_sync(0xffffffffu, any)) break;
     SectPos p[kMultiSlots];
-    Sect v[kMultiSlots];
+    Sect<W> v[kMultiSlots];
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
         const LookupDev *h = hd[s];
-        p[s] = sect_pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
-        v[s] = sect_load(h->S, p[s].t);
+        p[s] = sect_pos<W>(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        v[s] = sect_load<W>(h->S, p[s].t);
       }
     }
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const LookupDev *h = hd[s];
-        const unsigned w = sect_word(v[s], p[s].j);
+        const unsigned w = sect_word<W>(v[s], p[s].j);
         if ((w >> p[s].b) & 1u) {
-          *optr[s] = sect_rank(v[s], p[s], w, h->SB);
+          *optr[s] = sect_rank<W>(v[s], p[s], w, h->SB);
           act[s] = false;
         } else if (++lvl[s] >= h->L_used) {
           *optr[s] = h->n_fb ? fallback_index_m(h, x[s]) : MPHF_NOT_FOUND;
@@ -209,18 +211,53 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
   }
 }
 
-int launch_lookup_multi(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
+template <int W>
+static int launch_multi_w(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
   if (total == 0 || nreq == 0) return MPHF_OK;
   const u64 chunks = (total + kMultiChunk - 1) / kMultiChunk;
   u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
   static u64 maxb = 0;  // one wave of resident CTAs
-  if (!maxb) maxb = resident_grid(k_lookup_multi, kMultiThreads, 0);
+  if (!maxb) maxb = resident_grid(k_lookup_multi<W>, kMultiThreads, 0);
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup_multi", s);
-  k_lookup_multi<<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total);
+  k_lookup_multi<W><<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
+}
+
+// Request table of a batch, grouped by sector size: the default-layout
+// requests first (index space [0, g.total[0])), then the minirank ones (their
+// own index space from 0), so that each group runs in the kernel compiled for
+// its layout.
+struct TableGroups {
+  unsigned n[2] = {0, 0};
+  u64 total[2] = {0, 0};
+};
+template <class GetH, class GetKeys, class GetOut, class GetN>
+static TableGroups fill_table(ReqDev *t, size_t nreq, GetH geth, GetKeys getk, GetOut geto,
+                              GetN getn) {
+  TableGroups g;
+  for (int grp = 0; grp < 2; grp++) {
+    for (size_t i = 0; i < nreq; i++) {
+      const mphf_t *h = geth(i);
+      if ((h->sw == kSectWordsMini) != (grp == 1)) continue;
+      ReqDev &r = t[g.n[0] + g.n[1]];
+      r.h = (const LookupDev *)h->ldesc.p;
+      r.keys = getk(i);
+      r.out = geto(i);
+      r.start = g.total[grp];
+      g.total[grp] += getn(i);
+      g.n[grp]++;
+    }
+  }
+  return g;
+}
+
+static int launch_lookup_multi(const ReqDev *d_reqs, const TableGroups &g, cudaStream_t s) {
+  int rc = launch_multi_w<kSectWords>(d_reqs, g.n[0], g.total[0], s);
+  if (rc == MPHF_OK) rc = launch_multi_w<kSectWordsMini>(d_reqs + g.n[0], g.n[1], g.total[1], s);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -340,18 +377,14 @@ static void scheduler(mphf_server *sv) {
       }
       if (!take.empty()) {
         ReqDev *ht = sv->htab[slot];
-        u64 start = 0;
-        for (size_t i = 0; i < take.size(); i++) {
-          ht[i].h = (const LookupDev *)take[i]->h->ldesc.p;
-          ht[i].keys = take[i]->keys;
-          ht[i].out = take[i]->out;
-          ht[i].start = start;
-          start += take[i]->n;
-        }
+        const TableGroups g = fill_table(
+            ht, take.size(), [&](size_t i) { return (const mphf_t *)take[i]->h; },
+            [&](size_t i) { return take[i]->keys; }, [&](size_t i) { return take[i]->out; },
+            [&](size_t i) { return take[i]->n; });
         cudaStream_t s = sv->lstream[rr++ & 1];
         cudaMemcpyAsync(sv->dtab[slot].p, ht, sizeof(ReqDev) * take.size(),
                         cudaMemcpyHostToDevice, s);
-        launch_lookup_multi((const ReqDev *)sv->dtab[slot].p, (unsigned)take.size(), start, s);
+        launch_lookup_multi((const ReqDev *)sv->dtab[slot].p, g, s);
         Batch b;
         b.reqs = take;
         b.slot = slot;
@@ -361,7 +394,7 @@ static void scheduler(mphf_server *sv) {
         sv->inflight.push_back(b);
         sv->batches++;
         sv->batched_reqs += take.size();
-        sv->batched_keys += start;
+        sv->batched_keys += g.total[0] + g.total[1];
         worked = true;
       }
     }
@@ -650,23 +683,21 @@ int mphf_lookup_multi(mphf_t *const *hs, const uint64_t *const *d_keys, uint64_t
   if (!hs || !d_keys || !d_out || !counts) return MPHF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<ReqDev> t(nreq);
-  u64 start = 0;
   for (uint32_t i = 0; i < nreq; i++) {
     if (!hs[i] || (counts[i] && (!d_keys[i] || !d_out[i]))) return MPHF_EINVAL;
     if (hs[i]->L_used == 0 && counts[i]) return MPHF_EINVAL;
     int rc = ensure_lookup_desc(hs[i]);
     if (rc != MPHF_OK) return rc;
-    t[i].h = (const LookupDev *)hs[i]->ldesc.p;
-    t[i].keys = (const u64 *)d_keys[i];
-    t[i].out = (u64 *)d_out[i];
-    t[i].start = start;
-    start += counts[i];
   }
+  const TableGroups g = fill_table(
+      t.data(), nreq, [&](size_t i) { return (const mphf_t *)hs[i]; },
+      [&](size_t i) { return (const u64 *)d_keys[i]; }, [&](size_t i) { return (u64 *)d_out[i]; },
+      [&](size_t i) { return (u64)counts[i]; });
   DevBuf d;
   int rc = dev_alloc(d, sizeof(ReqDev) * nreq, s);
   if (rc != MPHF_OK) return rc;
   cudaError_t e = cudaMemcpyAsync(d.p, t.data(), sizeof(ReqDev) * nreq, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) rc = launch_lookup_multi((const ReqDev *)d.p, nreq, start, s);
+  if (e == cudaSuccess) rc = launch_lookup_multi((const ReqDev *)d.p, g, s);
   else rc = cuda_fail(e, "cudaMemcpyAsync(requests)");
   dev_free(d, s);  // stream-ordered: released after the kernel
   return rc;        // (a pageable copy has taken the table before returning)

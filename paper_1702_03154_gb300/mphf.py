@@ -96,6 +96,8 @@ def lib():
                                  dbl, dbl, dbl, u64, vp, u64, pu64, pu64, pu64,
                                  ctypes.POINTER(dbl)], i32),
         "mphf_string_keys": ([vp, u64, vp, u64, u64, vp, vp], i32),
+        "mphf_set_layout": ([vp, u32, vp], i32),
+        "mphf_sector_bytes": ([vp], u32),
         "mphf_build_nodisk": ([vp, u64, dbl, u32, u64, dbl, vp, pvp], i32),
         "mphf_build_generated": ([u64, u64, u64, dbl, u32, u64, dbl, vp, pvp], i32),
         "mphf_serialized_size": ([vp, pu64], i32),
@@ -194,6 +196,16 @@ class MPHF:
                                         _stream_ptr(stream), ctypes.byref(h))
         _check(rc, "mphf_build_generated")
         return cls(h)
+
+    # -- rank sampling -------------------------------------------------------
+    def set_layout(self, sector_bytes: int, stream=None) -> None:
+        """Re-store A and its ranks in 32-byte (default) or 64-byte ("minirank") sectors."""
+        _check(lib().mphf_set_layout(self._h, int(sector_bytes), _stream_ptr(stream)),
+               "mphf_set_layout")
+
+    @property
+    def sector_bytes(self) -> int:
+        return lib().mphf_sector_bytes(self._h)
 
     # -- serialization -------------------------------------------------------
     def to_bytes(self) -> bytes:
