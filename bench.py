@@ -52,6 +52,23 @@ def parse():
 
 
 # ----------------------------------------------------------------------- utils
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (every rank's step time counts: the slowest
+    rank sets the job's time).  One all-reduce; no collective for world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput in Mkeys/s: all ranks' keys over the slowest rank's time."""
+    return world * n_per_rank / (ms_max / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -432,11 +449,8 @@ def run_ours(args):
         tl.append(e1.elapsed_time(e2))
         h.free()
 
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * N / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, world)
+    value = job_value(N, world, ms_max)
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -490,12 +504,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         e_ms = (time.perf_counter() - t0) * 1e3 / reps
-        e_t = torch.tensor([e_ms], device="cuda")
-        if world > 1:
-            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * N / (float(e_t.item()) / 1e3) / 1e6, "unit": UNIT,
+        e_max = max_over_ranks(e_ms, world)
+        e2e = {"value": job_value(N, world, e_max), "unit": UNIT,
                "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
-               "ms_per_step": float(e_t.item()),
+               "ms_per_step": e_max,
                "api": "mphf_build_host + mphf_lookup_host, pinned host buffers"}
 
     sweep = {}

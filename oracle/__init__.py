@@ -93,6 +93,8 @@ def lib():
         L.oracle_bits_per_key_sampled.argtypes = [vp, u64]
         L.oracle_bits_per_key_sampled.restype = dbl
         L.oracle_string_key.argtypes, L.oracle_string_key.restype = [vp, u64, u64], u64
+        L.oracle_fill_level.argtypes, L.oracle_fill_level.restype = [vp, u64, u64, u64, vp, vp], None
+        L.oracle_merge_fill.argtypes, L.oracle_merge_fill.restype = [vp, vp, vp, vp, u64], None
         L.oracle_string_keys.argtypes, L.oracle_string_keys.restype = [vp, vp, u64, u64, vp], None
         _lib = L
     return _lib
@@ -234,6 +236,25 @@ class OracleMPHF:
     def bits_per_key_sampled(self, rank_block: int) -> float:
         """Size with one 64-bit rank counter every rank_block bits (1024: minirank)."""
         return lib().oracle_bits_per_key_sampled(self._h, rank_block)
+
+
+def fill_level(keys, s_d: int, m: int):
+    """ArrayFill of one level over `keys`: byte arrays (A, C) of m positions."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    A = np.zeros(m, dtype=np.uint8)
+    C = np.zeros(m, dtype=np.uint8)
+    lib().oracle_fill_level(_ptr(k) if k.size else None, k.size, s_d & MASK64, m, _ptr(A), _ptr(C))
+    return A, C
+
+
+def merge_fill(A1, C1, A2, C2):
+    """Fill of the union of two disjoint key sets from their two fills (new arrays)."""
+    A = np.array(A1, dtype=np.uint8, copy=True)
+    C = np.array(C1, dtype=np.uint8, copy=True)
+    a2 = np.ascontiguousarray(A2, dtype=np.uint8)
+    c2 = np.ascontiguousarray(C2, dtype=np.uint8)
+    lib().oracle_merge_fill(_ptr(A), _ptr(C), _ptr(a2), _ptr(c2), A.size)
+    return A, C
 
 
 def string_key(s: bytes, seed: int = 0) -> int:

@@ -452,3 +452,42 @@ void oracle_string_keys(const uint8_t *bytes, const uint64_t *off, uint64_t n, u
     for (uint64_t i = 0; i < n; i++)
         out[i] = oracle_string_key(bytes + off[i], off[i + 1] - off[i], seed);
 }
+
+/*
+ * One level's ArrayFill over an arbitrary key set, outside a build: keys are
+ * hashed with h_d (seed s_d) onto m positions and Algorithm 2 runs on the
+ * byte arrays A, C (m entries, zeroed by the caller).  A rank of a
+ * multi-GPU build holding a shard of F_d would compute exactly this.
+ */
+void oracle_fill_level(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t m,
+                       unsigned char *A, unsigned char *C)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = oracle_fastrange(oracle_hash(keys[i], s_d), m);
+        if (A[p] == 0 && C[p] == 0) {
+            A[p] = 1;
+        } else if (A[p] == 1 && C[p] == 0) {
+            A[p] = 0;
+            C[p] = 1;
+        }
+    }
+}
+
+/*
+ * Combine the fills of two disjoint key sets into the fill of their union
+ * (the exchange step of a monolithic multi-GPU level).  Per position, A says
+ * "exactly one key" and C says "two or more", so the union has two or more
+ * if either side has, or if both sides have exactly one; it has exactly one
+ * if one side has one and the union has no collision:
+ *   C = C1 | C2 | (A1 & A2),   A = (A1 | A2) & ~C.
+ * The result is written to (A1, C1).
+ */
+void oracle_merge_fill(unsigned char *A1, unsigned char *C1, const unsigned char *A2,
+                       const unsigned char *C2, uint64_t m)
+{
+    for (uint64_t p = 0; p < m; p++) {
+        unsigned char c = (unsigned char)(C1[p] | C2[p] | (A1[p] & A2[p]));
+        A1[p] = (unsigned char)((A1[p] | A2[p]) & !c);
+        C1[p] = c;
+    }
+}

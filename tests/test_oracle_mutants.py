@@ -46,6 +46,12 @@ MUTANTS = {
     # Sec. 4.3 minirank: the counter interval ignored (always 512).
     "rank_sampling_ignored": ("uint64_t counters = (h->M + rank_block - 1) / rank_block;",
                               "uint64_t counters = (h->M + 511) / 512;"),
+    # Multi-rank merge: two single hits on different ranks not seen as a collision.
+    "merge_drops_cross_collision": ("(unsigned char)(C1[p] | C2[p] | (A1[p] & A2[p]))",
+                                    "(unsigned char)(C1[p] | C2[p])"),
+    # Multi-rank merge: a collided position keeps its A bit.
+    "merge_keeps_collided_A": ("A1[p] = (unsigned char)((A1[p] | A2[p]) & !c);",
+                               "A1[p] = (unsigned char)(A1[p] | A2[p]);"),
     # String keys (Sec. 4.3): the length left out of the first state.
     "string_length_dropped": ("oracle_mix(seed + (len + 1) * 0x9E3779B97F4A7C15ULL)",
                               "oracle_mix(seed + 1 * 0x9E3779B97F4A7C15ULL)"),

@@ -406,3 +406,59 @@ def test_string_keys_bits_per_key_matches_table2(golden_dir):
     assert np.unique(keys).size == keys.size
     o = oracle.build(keys, gamma=g["gamma"], levels=25, seed=0)
     assert abs(o.bits_per_key() - g["bits_per_key"]) <= g["printed_precision"]
+
+
+# ------------------------------------------------- multi-rank level exchange
+# A monolithic multi-GPU level (keys of F_d sharded over ranks) needs each
+# rank's ArrayFill of its shard and one exchange that merges them.  The merge
+# is pinned to brute force (count the keys per position) and to the level
+# arrays of a whole build.
+def _brute_fill(keys, s_d, m):
+    pos = np.array([oracle.fastrange(oracle.mix(int(k) ^ s_d), m) for k in keys], dtype=np.int64)
+    cnt = np.bincount(pos, minlength=m)
+    return (cnt == 1).astype(np.uint8), (cnt >= 2).astype(np.uint8)
+
+
+def test_level_fill_is_brute_force_counting():
+    keys = inputs.splitmix64_keys(3000, 140)
+    for m in (64, 2048, 6000):
+        s = oracle.level_seed(5, 2)
+        A, C = oracle.fill_level(keys, s, m)
+        bA, bC = _brute_fill(keys, s, m)
+        assert np.array_equal(A, bA) and np.array_equal(C, bC)
+
+
+@pytest.mark.parametrize("K", [2, 3, 4, 7])
+def test_sharded_fills_merge_to_the_whole_fill(K):
+    keys = inputs.splitmix64_keys(5000, 141)
+    s, m = oracle.level_seed(1, 0), 4096  # crowded: many collisions of every kind
+    A, C = oracle.fill_level(keys, s, m)
+    rng = np.random.default_rng(K)
+    owner = rng.integers(0, K, size=keys.size)
+    parts = [oracle.fill_level(keys[owner == r], s, m) for r in range(K)]
+    mA, mC = parts[0]
+    for a, c in parts[1:]:
+        mA, mC = oracle.merge_fill(mA, mC, a, c)
+    assert np.array_equal(mA, A) and np.array_equal(mC, C)
+    # any merge order gives the same result (commutative, associative)
+    rA, rC = parts[-1]
+    for a, c in reversed(parts[:-1]):
+        rA, rC = oracle.merge_fill(a, c, rA, rC)
+    assert np.array_equal(rA, A) and np.array_equal(rC, C)
+    # the empty fill is the identity
+    z = np.zeros(m, dtype=np.uint8)
+    eA, eC = oracle.merge_fill(A, C, z, z)
+    assert np.array_equal(eA, A) and np.array_equal(eC, C)
+
+
+def test_sharded_level0_equals_the_builds_A0():
+    keys = inputs.splitmix64_keys(20000, 142)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=9)
+    n0, m0, off0, s0 = o.level_info(0)
+    half = keys.size // 2
+    A, C = oracle.merge_fill(*oracle.fill_level(keys[:half], s0, m0),
+                             *oracle.fill_level(keys[half:], s0, m0))
+    words = o.level_bits_words(0)
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little")[:m0]
+    assert np.array_equal(A, bits)
+    assert int(A.sum()) == n0 - o.level_info(1)[0]
