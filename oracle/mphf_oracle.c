@@ -145,20 +145,23 @@ void oracle_free(oracle_mphf *h)
  * fires per key, which is what the three implications of Sec. 2.2.1 state:
  *   (0,0) -> A=1;   (1,0) -> A=0, C=1;   (0,1) -> skip.
  */
+static void fill_one(unsigned char *A, unsigned char *C, uint64_t p)
+{
+    if (A[p] == 0 && C[p] == 0) {
+        A[p] = 1;
+    } else if (A[p] == 1 && C[p] == 0) {
+        A[p] = 0;
+        C[p] = 1;
+    } else {
+        /* A[p] == 0 and C[p] == 1: skip.  (1,1) never happens. */
+    }
+}
+
 static void array_fill(const oracle_mphf *h, uint32_t d, const uint64_t *F, uint64_t n,
                        unsigned char *A, unsigned char *C)
 {
-    for (uint64_t i = 0; i < n; i++) {
-        uint64_t p = position(h, d, F[i]);
-        if (A[p] == 0 && C[p] == 0) {
-            A[p] = 1;
-        } else if (A[p] == 1 && C[p] == 0) {
-            A[p] = 0;
-            C[p] = 1;
-        } else {
-            /* A[p] == 0 and C[p] == 1: skip.  (1,1) never happens. */
-        }
-    }
+    for (uint64_t i = 0; i < n; i++)
+        fill_one(A, C, position(h, d, F[i]));
 }
 
 /*
@@ -462,15 +465,8 @@ void oracle_string_keys(const uint8_t *bytes, const uint64_t *off, uint64_t n, u
 void oracle_fill_level(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t m,
                        unsigned char *A, unsigned char *C)
 {
-    for (uint64_t i = 0; i < n; i++) {
-        uint64_t p = oracle_fastrange(oracle_hash(keys[i], s_d), m);
-        if (A[p] == 0 && C[p] == 0) {
-            A[p] = 1;
-        } else if (A[p] == 1 && C[p] == 0) {
-            A[p] = 0;
-            C[p] = 1;
-        }
-    }
+    for (uint64_t i = 0; i < n; i++)
+        fill_one(A, C, oracle_fastrange(oracle_hash(keys[i], s_d), m));
 }
 
 /*

@@ -20,7 +20,7 @@ MUTANTS = {
     # ArrayFill: a third key at a collided position sets A again.
     "fill_ignores_C": ("if (A[p] == 0 && C[p] == 0) {", "if (A[p] == 0) {"),
     # ArrayFill: a collision leaves A set.
-    "collision_keeps_A": ("A[p] = 0;\n            C[p] = 1;", "C[p] = 1;"),
+    "collision_keeps_A": ("A[p] = 0;\n        C[p] = 1;", "C[p] = 1;"),
     # Alg. 1: the colliding keys are dropped and the placed ones kept.
     "compaction_inverted": ("if (A[p] == 0)\n                Fnext[nn++] = F[k];",
                             "if (A[p] == 1)\n                Fnext[nn++] = F[k];"),
