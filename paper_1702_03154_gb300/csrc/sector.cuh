@@ -76,9 +76,27 @@ struct SectPos {
   u64 t;
   unsigned j, b;
 };
+// q / W for q < 2^32 by a multiply-high (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): for 7 the 33-bit
+// magic 2^35/7 is applied as m' = 0x24924925 plus one add-and-shift fixup; for
+// 15, 0x88888889 = ceil(2^35 / 15) is exact for every 32-bit q.
+template <int W>
+__device__ __forceinline__ unsigned div_sector(unsigned q) {
+  if (W == 7) {
+    const unsigned t = __umulhi(q, 0x24924925u);
+    return (t + ((q - t) >> 1)) >> 2;
+  }
+  return __umulhi(q, 0x88888889u) >> 3;
+}
+
 template <int W>
 __device__ __forceinline__ SectPos sect_pos(u64 g) {
   const u64 q = g >> 5;
+  if ((q >> 32) == 0) {  // A below 2^37 bits: 32-bit arithmetic
+    const unsigned q32 = (unsigned)q;
+    const unsigned t = div_sector<W>(q32);
+    return SectPos{t, q32 - t * (unsigned)W, (unsigned)g & 31u};
+  }
   const u64 t = q / W;
   return SectPos{t, (unsigned)(q - t * W), (unsigned)g & 31u};
 }
