@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "build+lookup Mkeys/s (N=1e8, gamma=2, L=25)"
+L2_RANDOM_256B_GLOADS = 270.0  # measured ceiling of random 32-byte loads into L2 (G/s)
 UNIT = "Mkeys/s"
 
 
@@ -471,13 +472,26 @@ def run_ours(args):
         roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4),
                 "traffic": round(tr / (cnt / args.steps), 1) if tr else None,
-                "traffic_note": "DRAM read+write per launch (average over the kernel's launches in "
-                                "one build), from profiles/ (3e7-key ncu capture scaled to 1e8)",
+                "traffic_note": "DRAM read+write per launch (averaged over the kernel's launches "
+                                "in one step), from profiles/ (3e7-key ncu capture scaled to 1e8)",
                 "per_launch_algorithmic_bytes": round(b / cnt, 1),
                 "peak_source": f"{peak_kind} hbm_gbs", "launches_per_step": cnt / args.steps,
                 "avg_launch_ms": tot / cnt}
     struct = {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
               "level_sizes": last.level_sizes()[:8], "fallback": last.num_fallback}
+    # The lookup's own bound: its level probes are random 256-bit loads of an
+    # L2-resident sector array (sum of n_d of them for N member queries).
+    l2_probe = None
+    if "lookup" in prof:
+        cnt, tot = prof["lookup"]
+        probes = float(sum(last.level_sizes()[:last.num_levels])) * args.steps
+        ach = probes / (tot / 1e3) / 1e9
+        l2_probe = {"kernel": "lookup", "bound": "l2_random_sector_loads",
+                    "achieved": round(ach, 1), "peak": L2_RANDOM_256B_GLOADS, "unit": "G loads/s",
+                    "frac": round(ach / L2_RANDOM_256B_GLOADS, 4),
+                    "probes_per_query": round(probes / args.steps / N, 4),
+                    "peak_source": "random 256-bit loads over a 53 MB L2-resident array on this "
+                                   "GB300 (microbenchmark; 8-byte loads reach ~600 G/s)"}
     last.free()
 
     e2e = None
@@ -544,15 +558,19 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
-                "config": {"workload": "plain single MPHF, N=1e8 SplitMix64 keys (seed 2), "
-                                       "gamma=2, L=25; build + lookup of all N in shuffled order",
+                "config": {"workload": f"plain single MPHF, N={N:.0e} SplitMix64 keys (seed "
+                                       f"{2 + rank}), gamma={gamma:g}, L={L}; build + lookup of "
+                                       "all N in shuffled order",
                            "N": N, "gamma": gamma, "levels": L,
-                           "l2": "inputs (800 MB keys + 800 MB queries) larger than L2; no flush"},
+                           "l2": (f"inputs ({8 * N / 1e6:.0f} MB keys + {8 * N / 1e6:.0f} MB "
+                                  "queries) larger than L2; no flush" if 8 * N > 129e6 else
+                                  "inputs smaller than L2 (a reduced test size, not the bench "
+                                  "workload)")},
                 "build_mkeys_s": round(N / (float(np.median(tb)) / 1e3) / 1e6, 1),
                 "lookup_mkeys_s": round(N / (float(np.median(tl)) / 1e3) / 1e6, 1),
                 "build_ms": round(float(np.median(tb)), 4), "lookup_ms": round(float(np.median(tl)), 4),
                 "structure": struct, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu}
+                "roofline": roof, "l2_probe": l2_probe, "kernels": kernels, "cpu_baseline": cpu}
         if sweep:
             line["gamma_sweep"] = sweep
         if batched:
