@@ -75,6 +75,7 @@ struct BCfg {
   u64 Bset_max;
   double cap_scale;
   unsigned *status;                  // global (any overflow of a shared bound)
+  unsigned *upre;                    // [bcap + 1] compaction units before each bucket of level d
 };
 
 __host__ __device__ inline void size_set_level(BLvl &lv, u64 n, const BCfg &c) {
@@ -344,7 +345,6 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_bfinish(int d, BCfg c) {
   u64 tb, ts;
   u64 gb = scan64(nbk, &tb);
   u64 ao = scan64(nslots, &ts);
-  (void)red32;
   const bool fit = tb <= c.bcap && ts <= c.acap[nl];
   for (unsigned s = lo; s < hi; s++) {
     BLvl &nx = c.lvl[nl][s];
@@ -365,6 +365,27 @@ __global__ void __launch_bounds__(kFinishThreads, 1) k_bfinish(int d, BCfg c) {
     ao += nx.B * nx.cap;
   }
   if (threadIdx.x == 0) c.btotal[nl] = fit ? tb : 0;
+  // 3. compaction units (kIn entries) before each bucket of level d, so that
+  //    the compaction hands every CTA the same number of units
+  {
+    const u64 nbk_d = c.btotal[sl];
+    const u64 bper = (nbk_d + kFinishThreads - 1) / kFinishThreads;
+    const u64 b0 = threadIdx.x * bper, b1 = b0 + bper < nbk_d ? b0 + bper : nbk_d;
+    auto units = [&](u64 g) -> unsigned {
+      const u64 cap = c.lvl[sl][c.bset[sl][g]].cap;
+      const u64 nk = c.cnt[sl][g] < cap ? c.cnt[sl][g] : cap;
+      return (unsigned)((nk + kIn - 1) / kIn);
+    };
+    unsigned su = 0;
+    for (u64 g = b0; g < b1; g++) su += units(g);
+    unsigned total;
+    unsigned pre = block_scan_u32<kFinishThreads>(su, red32, &total);
+    for (u64 g = b0; g < b1; g++) {
+      c.upre[g] = pre;
+      pre += units(g);
+    }
+    if (threadIdx.x == 0) c.upre[nbk_d] = total;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -387,86 +408,176 @@ struct SetFlatDest {
 
 __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned tile_cnt;
-  __shared__ int skip;
+  __shared__ unsigned scnt[3];  // survivors of the last three units (rotating)
+  __shared__ int b_skip;
+  __shared__ unsigned b_set;
+  __shared__ u64 b_kbase, b_nk, b_w0, b_wend;
+  __shared__ const u64 *b_A;
   const int sl = d & 1, nl = (d + 1) & 1;
   const u64 nbk = c.btotal[sl];
+  if (nbk == 0) return;
+  // this CTA's share of the level's units (kIn-entry slices of the buckets)
+  const unsigned *upre = c.upre;
+  const unsigned U = upre[nbk];
+  const unsigned u0 = (unsigned)(((u64)U * blockIdx.x) / gridDim.x);
+  const unsigned u1 = (unsigned)(((u64)U * (blockIdx.x + 1)) / gridDim.x);
+  if (u0 >= u1) return;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
   u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
-  u64 *stage = sm.sorted;
+  u64 *stage = sm.sorted;  // survivors awaiting the multisplit (at most kTile, one set)
   const u64 s_n = level_seed(c.seed, d + 1);
   const unsigned lane = threadIdx.x & 31;
   const unsigned ltm = (1u << lane) - 1u;
-  if (threadIdx.x == 0) tile_cnt = 0;
-  __syncthreads();
-  for (u64 gb = blockIdx.x; gb < nbk; gb += gridDim.x) {
-    const unsigned s = c.bset[sl][gb];
-    const unsigned j = c.bidx[sl][gb];
-    BSet *st = &c.sets[s];
-    const BLvl lv = c.lvl[sl][s];
+
+  // multisplit the ns staged survivors of set s into its level d+1 buckets (or flat range)
+  auto flush = [&](unsigned ns, unsigned s) {
     const BLvl nx = c.lvl[nl][s];
-    __syncthreads();
-    if (threadIdx.x == 0)
-      skip = (lv.mode != LM_BUCKETED || st->status ||
-              (nx.mode != LM_BUCKETED && nx.mode != LM_FLAT)) ? 1 : 0;
-    __syncthreads();
-    if (skip) continue;  // one decision for the whole CTA
+    BSet *st = &c.sets[s];
     const bool flat = nx.mode == LM_FLAT;
-    const u64 *Alev = set_level_words(c, *st, d, lv.off);
-    const u64 w0 = ((u64)j * lv.P) >> 6;
-    const u64 wend = min(((u64)j + 1) * lv.P, lv.m) >> 6;
-    for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
+    u64 x[kKPT];
+    unsigned dst[kKPT], lp[kKPT];
+    bool ok[kKPT];
+#pragma unroll
+    for (int k = 0; k < kKPT; k++) {
+      const unsigned i = (unsigned)k * kTT + threadIdx.x;
+      ok[k] = i < ns;
+      x[k] = ok[k] ? stage[i] : 0;
+      dst[k] = 0;
+      lp[k] = 0;
+      if (ok[k] && !flat) {
+        const u64 p = level_pos(x[k], s_n, nx.m);
+        dst[k] = (unsigned)(p >> nx.sh);
+        lp[k] = (unsigned)(p & (nx.P - 1));
+      }
+    }
+    __syncthreads();  // the staging area is reused by the writer
+    if (flat)
+      multisplit_write<false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
+                              SetFlatDest{&st->n_flat, st->flat_off, st->flat_cap}, &st->status);
+    else
+      multisplit_write<true>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
+                             SetBucketDest{c.cnt[nl], nx.bbase, nx.aoff, nx.cap}, &st->status);
+  };
+
+  // bucket holding unit u0: the last g with upre[g] <= u0 (empty buckets own no unit)
+  u64 gb = 0;
+  {
+    u64 lo = 0, hi = nbk;
+    while (hi - lo > 1) {
+      const u64 mid = (lo + hi) >> 1;
+      if (upre[mid] <= u0) lo = mid;
+      else hi = mid;
+    }
+    gb = lo;
+  }
+  unsigned ubase = upre[gb], bnext = upre[gb + 1];
+  bool fresh = true;        // the bucket of the current unit is not loaded yet
+  unsigned cur_set = ~0u;   // set whose survivors are staged
+  bool skip = true;
+  unsigned ns = 0, it = 0;
+  if (threadIdx.x < 3) scnt[threadIdx.x] = 0;
+  for (unsigned u = u0; u < u1; u++) {
+    if (u >= bnext) {
+      do {
+        gb++;
+        ubase = bnext;
+        bnext = upre[gb + 1];
+      } while (u >= bnext);
+      fresh = true;
+    }
+    if (fresh) {
+      // one thread reads the bucket's set state (another CTA may be raising
+      // that set's status right now); every thread takes the same decision
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned s = c.bset[sl][gb];
+        const unsigned j = c.bidx[sl][gb];
+        const BSet *st = &c.sets[s];
+        const BLvl lv = c.lvl[sl][s];
+        const BLvl nx = c.lvl[nl][s];
+        b_skip = (lv.mode != LM_BUCKETED || *(volatile const unsigned *)&st->status ||
+                  (nx.mode != LM_BUCKETED && nx.mode != LM_FLAT)) ? 1 : 0;
+        b_set = s;
+        b_kbase = lv.aoff + (u64)j * lv.cap;
+        b_nk = c.cnt[sl][gb] < lv.cap ? c.cnt[sl][gb] : lv.cap;
+        b_w0 = ((u64)j * lv.P) >> 6;
+        b_wend = min(((u64)j + 1) * lv.P, lv.m) >> 6;
+        b_A = set_level_words(c, *st, d, lv.off);
+      }
+      __syncthreads();
+      const unsigned s = b_set;
+      skip = b_skip != 0;
+      if (s != cur_set) {
+        if (ns) flush(ns, cur_set);  // survivors of another set leave first
+        ns = 0;
+        cur_set = s;
+      }
+      if (!skip) {
+        const u64 w0 = b_w0, wend = b_wend;
+        const u64 *Alev = b_A;
+        for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
+        __syncthreads();
+      }
+      fresh = false;
+    }
+    if (skip) continue;
+    // 1. test kInPT consecutive entries per thread (16-byte loads); a key whose
+    // A_d bit is 0 survives to F_{d+1} (Algorithm 1)
+    const u64 nk = b_nk;
+    const u64 e0 = (u64)(u - ubase) * kIn + (u64)threadIdx.x * kInPT;
+    const unsigned *pe = c.XP[sl] + b_kbase + e0;
+    const u64 *ke = c.X[sl] + b_kbase + e0;
+    unsigned pk[kInPT];
+    u64 xk[kInPT];
+    if (e0 + kInPT <= nk) {
+      const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(pe));
+      pk[0] = v.x;
+      pk[1] = v.y;
+      pk[2] = v.z;
+      pk[3] = v.w;
+#pragma unroll
+      for (int k = 0; k < kInPT; k += 2) {
+        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(ke + k));
+        xk[k] = ((u64)w.y << 32) | w.x;
+        xk[k + 1] = ((u64)w.w << 32) | w.z;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kInPT; k++) {
+        pk[k] = e0 + k < nk ? __ldcs(pe + k) : ~0u;
+        xk[k] = e0 + k < nk ? __ldcs(ke + k) : 0;
+      }
+    }
+    unsigned bal[kInPT], tot = 0;
+    bool keep[kInPT];
+#pragma unroll
+    for (int k = 0; k < kInPT; k++) {
+      const unsigned p = pk[k];
+      keep[k] = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
+      bal[k] = __ballot_sync(0xffffffffu, keep[k]);
+      tot += __popc(bal[k]);
+    }
+    unsigned wbase = 0;
+    if (lane == 0 && tot) wbase = atomicAdd(&scnt[it % 3], tot);
+    wbase = ns + __shfl_sync(0xffffffffu, wbase, 0);
+#pragma unroll
+    for (int k = 0; k < kInPT; k++) {
+      if (keep[k]) stage[wbase + __popc(bal[k] & ltm)] = xk[k];
+      wbase += __popc(bal[k]);
+    }
+    // the counter of unit it+1 was last read after the barrier of unit it-2,
+    // which every thread has passed: reset it for the next unit
+    if (threadIdx.x == 0) scnt[(it + 1) % 3] = 0;
     __syncthreads();
-    const u64 nk = min(c.cnt[sl][gb], lv.cap);
-    const u64 *kb = c.X[sl] + lv.aoff + (u64)j * lv.cap;
-    const unsigned *pb = c.XP[sl] + lv.aoff + (u64)j * lv.cap;
-    for (u64 t0 = 0; t0 < nk; t0 += kTile) {
-      unsigned pk[kKPT];
-      u64 xk[kKPT];
-#pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
-        pk[k] = i < nk ? __ldcs(pb + i) : ~0u;
-        xk[k] = i < nk ? __ldcs(kb + i) : 0;
-      }
-#pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const unsigned p = pk[k];
-        const bool keep = p != ~0u && !((segA[p >> 6] >> (p & 63)) & 1ull);
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        unsigned wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(&tile_cnt, (unsigned)__popc(bal));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (keep) stage[wbase + __popc(bal & ltm)] = xk[k];
-      }
-      __syncthreads();
-      const unsigned ns = tile_cnt;
-      u64 x[kKPT];
-      unsigned dst[kKPT], lp[kKPT];
-      bool ok[kKPT];
-#pragma unroll
-      for (int k = 0; k < kKPT; k++) {
-        const unsigned i = (unsigned)k * kTT + threadIdx.x;
-        ok[k] = i < ns;
-        x[k] = ok[k] ? stage[i] : 0;
-        dst[k] = 0;
-        lp[k] = 0;
-        if (ok[k] && !flat) {
-          const u64 p = level_pos(x[k], s_n, nx.m);
-          dst[k] = (unsigned)(p >> nx.sh);
-          lp[k] = (unsigned)(p & (nx.P - 1));
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) tile_cnt = 0;
-      if (flat)
-        multisplit_write<false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
-                                SetFlatDest{&st->n_flat, st->flat_off, st->flat_cap}, &st->status);
-      else
-        multisplit_write<true>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
-                               SetBucketDest{c.cnt[nl], nx.bbase, nx.aoff, nx.cap}, &st->status);
+    ns += scnt[it % 3];
+    it++;
+    // 2.+3. once another unit might not fit, hash and write the staged keys
+    if (ns > (unsigned)(kTile - kIn)) {
+      flush(ns, cur_set);
+      ns = 0;
     }
   }
+  if (ns) flush(ns, cur_set);
 }
 
 // ---------------------------------------------------------------------------
@@ -809,6 +920,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   WS(18, 16, &c.status);
   WS(19, sizeof(u64) * (S + 1), &p);
   u64 *d_koff = (u64 *)p;
+  WS(20, 4 * (bcap + 1), &c.upre);
 #undef WS
   c.keys = d_keys;
   // ---- level-0 bucket descriptors on the host
