@@ -121,6 +121,8 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
   __shared__ unsigned t_sa, t_sb;
   __shared__ u64 t_gb0;
   __shared__ unsigned t_nb;
+  __shared__ u64 t_m, t_base;  // one bucketed set in the tile: its m and first bucket - gb0
+  __shared__ unsigned t_sh, t_one;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
   const u64 s0 = level_seed(c.seed, 0);
   const u64 ntiles = ceil_div(total, kTile);
@@ -154,6 +156,13 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
           if (c.lvl[0][s].mode == LM_BUCKETED) fail_set(&c.sets[s]);
         t_nb = 0;
       }
+      // the common case: the whole tile lies in one bucketed set
+      t_one = (lo == sb && c.lvl[0][lo].mode == LM_BUCKETED) ? 1u : 0u;
+      if (t_one) {
+        t_m = c.lvl[0][lo].m;
+        t_sh = c.lvl[0][lo].sh;
+        t_base = c.lvl[0][lo].bbase - t_gb0;
+      }
     }
     __syncthreads();
     const unsigned nb = t_nb;
@@ -164,23 +173,37 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
     u64 x[kKPT];
     unsigned dst[kKPT], lp[kKPT];
     bool ok[kKPT];
-    unsigned s = t_sa;
+    if (t_one) {  // one set: its parameters for every key, no per-key set search
+      const u64 m = t_m, base = t_base;
+      const unsigned sh = t_sh, mask = (1u << sh) - 1u;
 #pragma unroll
-    for (int k = 0; k < kKPT; k++) {
-      const u64 i = t0 + (u64)k * kTT + threadIdx.x;
-      ok[k] = false;
-      x[k] = 0;
-      dst[k] = 0;
-      lp[k] = 0;
-      if (i < t1) {
-        while (key_off[s + 1] <= i) s++;  // monotone in k
-        const BLvl &lv = c.lvl[0][s];
-        if (lv.mode == LM_BUCKETED) {
-          x[k] = __ldcs(c.keys + i);
-          const u64 p = level_pos(x[k], s0, lv.m);
-          dst[k] = (unsigned)(lv.bbase + (p >> lv.sh) - t_gb0);
-          lp[k] = (unsigned)(p & (lv.P - 1));
-          ok[k] = true;
+      for (int k = 0; k < kKPT; k++) {
+        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+        ok[k] = i < t1;
+        x[k] = ok[k] ? __ldcs(c.keys + i) : 0;
+        const u64 p = level_pos(x[k], s0, m);
+        dst[k] = (unsigned)(base + (p >> sh));
+        lp[k] = (unsigned)p & mask;
+      }
+    } else {
+      unsigned s = t_sa;
+#pragma unroll
+      for (int k = 0; k < kKPT; k++) {
+        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+        ok[k] = false;
+        x[k] = 0;
+        dst[k] = 0;
+        lp[k] = 0;
+        if (i < t1) {
+          while (key_off[s + 1] <= i) s++;  // monotone in k
+          const BLvl &lv = c.lvl[0][s];
+          if (lv.mode == LM_BUCKETED) {
+            x[k] = __ldcs(c.keys + i);
+            const u64 p = level_pos(x[k], s0, lv.m);
+            dst[k] = (unsigned)(lv.bbase + (p >> lv.sh) - t_gb0);
+            lp[k] = (unsigned)(p & (lv.P - 1));
+            ok[k] = true;
+          }
         }
       }
     }
@@ -743,8 +766,32 @@ struct Workspace {
   DevBuf bufs[24];
   size_t want[24] = {0};
   GraphCache g;
+  void *pin = nullptr;  // pinned host staging for the per-set results
+  size_t pin_bytes = 0;
 };
 static Workspace g_ws;
+
+// Pinned host staging of at least `bytes` (kept across calls; the read-back
+// of per-set state and level history is a few MB for thousands of sets).
+static int pin_get(size_t bytes, void **p) {
+  if (g_ws.pin && g_ws.pin_bytes >= bytes) {
+    *p = g_ws.pin;
+    return MPHF_OK;
+  }
+  if (g_ws.pin) cudaFreeHost(g_ws.pin);
+  g_ws.pin = nullptr;
+  g_ws.pin_bytes = 0;
+  cudaError_t e = cudaMallocHost(&g_ws.pin, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_ws.pin = nullptr;
+    set_cuda_error(e, "cudaMallocHost(batched staging)");
+    return MPHF_ENOMEM;
+  }
+  g_ws.pin_bytes = bytes;
+  *p = g_ws.pin;
+  return MPHF_OK;
+}
 
 // Grow workspace slot i to at least `bytes` (kept across calls).
 static int ws_get(int i, size_t bytes, cudaStream_t st, void **p) {
@@ -785,7 +832,7 @@ namespace bbh {
 void release_shared(mphf_shared *sh) {
   if (!sh) return;
   if (sh->refs.fetch_sub(1) == 1) {
-    if (sh->arena.p) cudaFree(sh->arena.p);
+    dev_free(sh->arena, 0);  // stream-ordered on the legacy stream, like a handle's own arrays
     delete sh;
   }
 }
@@ -1022,10 +1069,16 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     MPHF_CUDA(cudaGraphLaunch(gc.exec, st));
   }
   add_launches(gc.kernels > 0 ? gc.kernels - 1 : 0);
-  // ---- read back per-set results
-  std::vector<BSet> rs(S);
+  // ---- read back per-set results (pinned staging)
+  const size_t rs_bytes = (sizeof(BSet) * S + 255) & ~(size_t)255;
+  const u64 n_hist = (u64)S * (L + 1);
+  void *pin = nullptr;
+  rc = pin_get(rs_bytes + sizeof(FLevel) * n_hist, &pin);
+  if (rc != MPHF_OK) return rc;
+  BSet *rs = (BSet *)pin;
+  FLevel *hist = (FLevel *)((char *)pin + rs_bytes);
   unsigned gstat[4] = {0, 0, 0, 0};
-  MPHF_CUDA(cudaMemcpyAsync(rs.data(), c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaMemcpyAsync(gstat, c.status, 16, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaStreamSynchronize(st));
   // sets whose loop did not finish within D levels (prediction short): run the
@@ -1057,15 +1110,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       k_btail<<<S, kTailThreads, tail_smem_bytes(mcap), st>>>(c, mcap, D + 1);
     }
     MPHF_CUDA(cudaGetLastError());
-    MPHF_CUDA(cudaMemcpyAsync(rs.data(), c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
+    MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
     MPHF_CUDA(cudaStreamSynchronize(st));
     gc.D = -1;  // the recorded graph no longer matches this build
   }
   for (unsigned s = 0; s < S; s++)
     if (rs[s].status & ST_DUPLICATE) return MPHF_EDUPLICATE;
-  std::vector<FLevel> hist((u64)S * (L + 1));
-  MPHF_CUDA(cudaMemcpyAsync(hist.data(), c.hist, sizeof(FLevel) * hist.size(),
-                            cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaMemcpyAsync(hist, c.hist, sizeof(FLevel) * n_hist, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaStreamSynchronize(st));
   // ---- output layout
   std::vector<BOut> bo(S);
@@ -1105,20 +1156,17 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   mphf_shared *sh = new (std::nothrow) mphf_shared();
   if (!sh) return MPHF_ENOMEM;
   if (out_words) {
-    cudaError_t e = cudaMalloc(&sh->arena.p, out_words * 8);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
+    rc = dev_alloc(sh->arena, out_words * 8, st);  // stream-ordered pool: fast to reuse
+    if (rc != MPHF_OK) {
       delete sh;
-      set_cuda_error(e, "cudaMalloc(batched arena)");
-      return MPHF_ENOMEM;
+      return rc;
     }
-    sh->arena.bytes = out_words * 8;
     DevBuf dbo, dtot;
     rc = dev_alloc(dbo, sizeof(BOut) * S, st);
     if (rc == MPHF_OK) rc = dev_alloc(dtot, 8 * S, st);
     if (rc != MPHF_OK) {
       dev_free(dbo, st);
-      cudaFree(sh->arena.p);
+      dev_free(sh->arena, st);
       delete sh;
       return rc;
     }
@@ -1139,7 +1187,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     dev_free(dtot, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (e2 != cudaSuccess) {
-      cudaFree(sh->arena.p);
+      dev_free(sh->arena, st);
       delete sh;
       return cuda_fail(e2, "batched finalise");
     }
@@ -1190,7 +1238,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   }
   if (live) sh->refs.store(live);
   else {
-    if (sh->arena.p) cudaFree(sh->arena.p);
+    dev_free(sh->arena, st);
     delete sh;
   }
   if (rc != MPHF_OK) return rc;
@@ -1313,4 +1361,7 @@ extern "C" void mphf_workspace_release(void) {
     b.p = nullptr;
     b.bytes = 0;
   }
+  if (g_ws.pin) cudaFreeHost(g_ws.pin);
+  g_ws.pin = nullptr;
+  g_ws.pin_bytes = 0;
 }
