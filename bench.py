@@ -479,6 +479,20 @@ def run_ours(args):
                 "avg_launch_ms": tot / cnt}
     struct = {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
               "level_sizes": last.level_sizes()[:8], "fallback": last.num_fallback}
+    # the same function's lookup in each storage layout (mphf_set_layout)
+    by_layout = {}
+    for nbytes in (64, 8, 32):
+        last.set_layout(nbytes)
+        tt = []
+        for _ in range(3):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            last.lookup(q, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        by_layout[f"{nbytes}B"] = {"lookup_ms": round(float(np.median(tt)), 4),
+                                   "device_bytes_per_key": round(last.device_bytes() / N, 4)}
     # The lookup's own bound: its level probes are random 256-bit loads of an
     # L2-resident sector array (sum of n_d of them for N member queries).
     l2_probe = None
@@ -570,7 +584,8 @@ def run_ours(args):
                 "lookup_mkeys_s": round(N / (float(np.median(tl)) / 1e3) / 1e6, 1),
                 "build_ms": round(float(np.median(tb)), 4), "lookup_ms": round(float(np.median(tl)), 4),
                 "structure": struct, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roof, "l2_probe": l2_probe, "kernels": kernels, "cpu_baseline": cpu}
+                "roofline": roof, "l2_probe": l2_probe, "lookup_by_layout": by_layout,
+                "kernels": kernels, "cpu_baseline": cpu}
         if sweep:
             line["gamma_sweep"] = sweep
         if batched:

@@ -152,19 +152,24 @@ uint64_t mphf_device_bytes(const mphf_t *h);
 
 /*
  * Rank sampling (Sec. 3.1; the "minirank" setting of Sec. 4.3).  A and its
- * ranks live in sectors of 32 bytes (224 bits of A + one 32-bit count: the
- * default, every probe one 256-bit load) or 64 bytes (480 bits of A + one
- * count: "minirank", counts cost 1/15 of A instead of 1/7, at gamma = 1 the
- * size drops from 3.1 to 2.9 bits/key as in the paper, and a probe loads both
- * halves of its sector).  Builds make 32-byte sectors; mphf_set_layout
- * re-stores a function in the other size (sector_bytes 32 or 64), keeping
- * every index unchanged; a handle of a batched build then gets arrays of its
- * own.  mphf_bits_per_key counts one 64-bit counter per 512 bits of A for
- * 32-byte sectors and per 1024 bits for 64-byte ones (the paper's two
- * settings).  Waits for the device before returning.
+ * ranks live in one of three layouts, chosen by sector_bytes:
+ *   32  sectors of 224 bits of A + one 32-bit count (the default): every probe
+ *       is one 256-bit load; the counts cost 1/7 of A;
+ *   64  sectors of 480 bits of A + one count ("minirank"): counts cost 1/15 of
+ *       A, at gamma = 1 the size drops from 3.1 to 2.9 bits/key as in the
+ *       paper, and a probe loads both halves of its sector;
+ *   8   units of 48 bits of A + a 16-bit count within blocks of 1024 units (a
+ *       64-bit count per block): every probe is one 8-byte load, the fastest
+ *       lookups, at the price of counts costing 1/3 of A.
+ * Builds make 32-byte sectors; mphf_set_layout re-stores a function in
+ * another layout, keeping every index unchanged; a handle of a batched build
+ * then gets arrays of its own.  mphf_bits_per_key counts one 64-bit counter
+ * per 512 bits of A (per 1024 bits for the 64-byte layout: the paper's two
+ * settings); mphf_device_bytes gives the memory actually held.  Waits for the
+ * device before returning.
  */
 int mphf_set_layout(mphf_t *h, uint32_t sector_bytes, void *stream);
-uint32_t mphf_sector_bytes(const mphf_t *h);   /* 32 or 64; 0 for NULL */
+uint32_t mphf_sector_bytes(const mphf_t *h);   /* 32, 64 or 8; 0 for NULL */
 
 /* Release a handle and its device memory; NULL is a no-op. */
 void mphf_free(mphf_t *h);
@@ -271,8 +276,8 @@ int mphf_string_keys(const uint8_t *d_bytes, uint64_t total_bytes, const uint64_
  * built once can be stored and loaded again, on this or another GPU.  Format
  * (little-endian): a 128-byte header -- magic "BBHGB300", format version,
  * N, gamma, L, levels used, seed, M, fallback size, sector and superblock
- * counts, a 64-bit checksum of everything after the header, and the sector
- * size (A words per sector: 7 or 15) -- then the
+ * counts, a 64-bit checksum of everything after the header, and the layout
+ * (A words per sector: 7 or 15; 48 for 8-byte units) -- then the
  * per-level (n_d, m_d, off_d) triples and n_L, then the sectors, the
  * superblock counts and the sorted fallback keys.
  *   mphf_serialized_size  bytes the image of h takes.

@@ -221,24 +221,21 @@ static int copy_out(const mphf_t *h, const DevBuf &b, uint64_t *dst, uint64_t co
   return MPHF_OK;
 }
 
-// A comes back out of the sectors: words 1..W of each sector are 4 W
-// consecutive bytes of A, so one strided copy gathers them.
+// A comes back out of the sectors: each sector (unit) holds a run of whole
+// bytes of A at a fixed offset, so one strided copy gathers them.
 int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count) {
   if (!h || (count && !h_words) || count != h->M / 64) return MPHF_EINVAL;
   if (!count) return MPHF_OK;
-  const u64 W = h->sw, pitch = sector_bytes(h->sw);
-  const u64 w32 = h->M / 32;  // A's 32-bit words
-  const u64 full = w32 / W;   // sectors whose W words all belong to A
-  const u64 rest = w32 - full * W;
+  const AGather g = a_gather(h->M, h->sw);
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
-  const char *src = (const char *)h->S.p + 4;
+  const char *src = (const char *)h->S.p + g.offset;
   char *dst = (char *)h_words;
   cudaError_t e = cudaSuccess;
-  if (full) e = cudaMemcpy2D(dst, 4 * W, src, pitch, 4 * W, full, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && rest)
-    e = cudaMemcpy(dst + full * 4 * W, src + full * pitch, rest * 4, cudaMemcpyDeviceToHost);
+  if (g.full) e = cudaMemcpy2D(dst, g.width, src, g.pitch, g.width, g.full, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && g.rest)
+    e = cudaMemcpy(dst + g.full * g.width, src + g.full * g.pitch, g.rest, cudaMemcpyDeviceToHost);
   if (prev != h->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2D(A from sectors)");
   return MPHF_OK;
@@ -271,8 +268,9 @@ int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count) {
 // of Sec. 4.3): A is gathered out of the old sectors with one strided copy on
 // the device and the new sectors are built from it.
 int mphf_set_layout(mphf_t *h, uint32_t sector_bytes_, void *stream) {
-  if (!h || (sector_bytes_ != 32 && sector_bytes_ != 64)) return MPHF_EINVAL;
-  const unsigned W = sector_bytes_ == 32 ? kSectWords : kSectWordsMini;
+  if (!h || (sector_bytes_ != 8 && sector_bytes_ != 32 && sector_bytes_ != 64)) return MPHF_EINVAL;
+  const unsigned W = sector_bytes_ == 32 ? kSectWords
+                     : sector_bytes_ == 64 ? kSectWordsMini : kUnitBits;
   if (W == h->sw) return MPHF_OK;
   int prev = 0;
   cudaGetDevice(&prev);
@@ -282,16 +280,15 @@ int mphf_set_layout(mphf_t *h, uint32_t sector_bytes_, void *stream) {
   nh.M = h->M;
   nh.sw = W;
   DevBuf A, fb;
-  const u64 w32 = h->M / 32, Wo = h->sw, pitch = sector_bytes(h->sw);
-  const u64 full = w32 / Wo, rest = w32 - full * Wo;
+  const AGather g = a_gather(h->M, h->sw);
+  const char *src = (const char *)h->S.p + g.offset;
   int rc = dev_alloc(A, h->M / 8, s);
   cudaError_t e = cudaSuccess;
-  if (rc == MPHF_OK && full)
-    e = cudaMemcpy2DAsync(A.p, 4 * Wo, (const char *)h->S.p + 4, pitch, 4 * Wo, full,
-                          cudaMemcpyDeviceToDevice, s);
-  if (rc == MPHF_OK && e == cudaSuccess && rest)
-    e = cudaMemcpyAsync((char *)A.p + full * 4 * Wo, (const char *)h->S.p + 4 + full * pitch,
-                        rest * 4, cudaMemcpyDeviceToDevice, s);
+  if (rc == MPHF_OK && g.full)
+    e = cudaMemcpy2DAsync(A.p, g.width, src, g.pitch, g.width, g.full, cudaMemcpyDeviceToDevice, s);
+  if (rc == MPHF_OK && e == cudaSuccess && g.rest)
+    e = cudaMemcpyAsync((char *)A.p + g.full * g.width, src + g.full * g.pitch, g.rest,
+                        cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) rc = cuda_fail(e, "mphf_set_layout (gather A)");
   if (rc == MPHF_OK && h->M)
     rc = make_sectors(&nh, ASrc{(const u64 *)A.p, h->M / 64, nullptr, h->M / 64}, nullptr, s);

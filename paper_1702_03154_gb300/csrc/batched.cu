@@ -1228,7 +1228,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       h->S.p = base + bo[s].S_dst;
       h->S.bytes = h->n_sect * sector_bytes(kSectWords);
       h->SB.p = base + bo[s].SB_dst;
-      h->SB.bytes = n_superblocks(h->n_sect) * 8;
+      h->SB.bytes = n_sb_entries(h->n_sect, kSectWords) * 8;
       h->fb.p = h->n_fb ? base + bo[s].fb_dst : nullptr;
       h->fb.bytes = h->n_fb * 8;
       h->shared = sh;

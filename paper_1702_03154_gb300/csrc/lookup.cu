@@ -116,22 +116,23 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
     if (!__any_sync(0xffffffffu, any)) break;
 
     // one probe per active slot: issue all loads, then resolve
-    SectPos p[kSlots];
-    Sect<W> v[kSlots];
+    using LW = Lay<W>;
+    typename LW::Pos p[kSlots];
+    typename LW::Data v[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
-        p[s] = sect_pos<W>(toff[d] + level_pos(x[s], ts[d], tm[d]));
-        v[s] = sect_load<W>(a.S, p[s].t);
+        p[s] = LW::pos(toff[d] + level_pos(x[s], ts[d], tm[d]));
+        v[s] = LW::load(a.S, p[s]);
       }
     }
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
-        const unsigned w = sect_word<W>(v[s], p[s].j);
-        if ((w >> p[s].b) & 1u) {
-          __stcs(out + idx[s], sect_rank<W>(v[s], p[s], w, a.SB));
+        unsigned w = 0;
+        if (LW::hit(v[s], p[s], w)) {
+          __stcs(out + idx[s], LW::rank(v[s], p[s], w, a.SB));
           act[s] = false;
         } else if (++lvl[s] >= a.L_used) {
           __stcs(out + idx[s], a.n_fb ? fallback_index(a, x[s]) : MPHF_NOT_FOUND);
@@ -156,51 +157,35 @@ static void fill_tables(const mphf_t *h, LookupArgs &a, LevelTable &t) {
   }
 }
 
-// Query slots per lane (2 by default; MPHF_LOOKUP_SLOTS = 3 or 4 trades
-// registers for memory-level parallelism).
-static int lookup_slots() {
-  static int v = 0;
-  if (!v) {
-    const char *e = getenv("MPHF_LOOKUP_SLOTS");
-    v = e ? atoi(e) : 2;
-    if (v < 2 || v > 4) v = 2;
-  }
-  return v;
+// Query slots per lane: 2 for every layout.  (8-byte units would leave room
+// for more, but measured on a GB300 3, 4 or 6 slots run slower than 2.)
+static constexpr int kUnitSlots = 2;
+
+template <int SLOTS, int W>
+static int launch_lookup(const u64 *keys, u64 n, u64 *out, const LookupArgs &a,
+                         const LevelTable &t, cudaStream_t s) {
+  // one wave of resident CTAs: warps take chunks in a fixed order, so a
+  // second wave would only start after the first has drained
+  static unsigned mb = 0;
+  if (!mb) mb = resident_grid(k_lookup<SLOTS, W>, kLookupThreads, 0);
+  const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
+  const unsigned per_block = kLookupThreads / 32;
+  u64 grid = (nwarps_needed + per_block - 1) / per_block;
+  if (grid > mb) grid = mb;
+  if (grid < 1) grid = 1;
+  LaunchScope ls("lookup", s);
+  k_lookup<SLOTS, W><<<(unsigned)grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
 }
 
 int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t s) {
   LookupArgs a;
   LevelTable t;
   fill_tables(h, a, t);
-  const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
-  const unsigned per_block = kLookupThreads / 32;
-  unsigned grid = (unsigned)((nwarps_needed + per_block - 1) / per_block);
-  // one wave of resident CTAs: warps take chunks in a fixed order, so a
-  // second wave would only start after the first has drained
-  const int slots = lookup_slots();
-  const bool mini = h->sw == kSectWordsMini;
-  static unsigned maxb[5][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  unsigned &mb = maxb[slots][mini];
-  if (!mb) {
-    if (mini) mb = resident_grid(k_lookup<2, kSectWordsMini>, kLookupThreads, 0);
-    else if (slots == 3) mb = resident_grid(k_lookup<3, kSectWords>, kLookupThreads, 0);
-    else if (slots == 4) mb = resident_grid(k_lookup<4, kSectWords>, kLookupThreads, 0);
-    else mb = resident_grid(k_lookup<2, kSectWords>, kLookupThreads, 0);
-  }
-  if (grid > mb) grid = mb;
-  if (grid < 1) grid = 1;
-  LaunchScope ls("lookup", s);
-  if (mini) {  // a 64-byte sector already takes 16 registers per slot
-    k_lookup<2, kSectWordsMini><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
-  } else {
-    switch (slots) {
-      case 3: k_lookup<3, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
-      case 4: k_lookup<4, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
-      default: k_lookup<2, kSectWords><<<grid, kLookupThreads, 0, s>>>(keys, n, out, a, t); break;
-    }
-  }
-  MPHF_CUDA(cudaGetLastError());
-  return MPHF_OK;
+  if (h->sw == kSectWordsMini) return launch_lookup<2, kSectWordsMini>(keys, n, out, a, t, s);
+  if (h->sw == kUnitBits) return launch_lookup<kUnitSlots, kUnitBits>(keys, n, out, a, t, s);
+  return launch_lookup<2, kSectWords>(keys, n, out, a, t, s);
 }
 
 }  // namespace bbh

@@ -198,9 +198,61 @@ k_sect_write(ASrc a, u64 nsect, unsigned *__restrict__ S, const u64 *__restrict_
     SB[blockIdx.x / kCtaPerSB] = cta_prefix[blockIdx.x];
 }
 
+// 8-byte units: one CTA per block of 1024 units, 4 units per thread.  The
+// counts restart at every block, so each CTA writes its block alone; the
+// per-block sums then become SB by one exclusive scan.
+static constexpr int kUnitThreads = 256;
+static constexpr int kUnitsPerThread = (1 << kUnitBlockShift) / kUnitThreads;
+
+__device__ __forceinline__ u64 a_bits48(const ASrc &a, u64 u) {
+  const u64 bit = u * kUnitBits, k = bit >> 6;
+  const unsigned sh = (unsigned)(bit & 63);
+  u64 v = a_word(a, k) >> sh;
+  if (sh > 64 - kUnitBits) v |= a_word(a, k + 1) << (64 - sh);
+  return v & ((1ull << kUnitBits) - 1ull);
+}
+
+__global__ void __launch_bounds__(kUnitThreads)
+k_unit_write(ASrc a, u64 nunits, u64 *__restrict__ S8, u64 *__restrict__ block_sums) {
+  const u64 u0 = ((u64)blockIdx.x << kUnitBlockShift) + (u64)threadIdx.x * kUnitsPerThread;
+  u64 v[kUnitsPerThread];
+  unsigned c[kUnitsPerThread], run = 0;
+#pragma unroll
+  for (int i = 0; i < kUnitsPerThread; i++) {
+    v[i] = u0 + i < nunits ? a_bits48(a, u0 + i) : 0;
+    c[i] = run;
+    run += __popcll(v[i]);
+  }
+  u64 total;
+  const u64 ex = block_exclusive_scan(run, &total);
+#pragma unroll
+  for (int i = 0; i < kUnitsPerThread; i++)
+    if (u0 + i < nunits) S8[u0 + i] = v[i] | ((ex + c[i]) << kUnitBits);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
 int build_sectors(const ASrc &src, u64 M, unsigned W, unsigned *S, u64 *SB, u64 *d_total,
                   cudaStream_t s) {
-  if (W != kSectWords && W != kSectWordsMini) return MPHF_EINVAL;
+  if (!layout_ok(W)) return MPHF_EINVAL;
+  if (W == kUnitBits) {
+    const u64 nunits = n_sectors(M, W);
+    if (nunits == 0) {
+      if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
+      return MPHF_OK;
+    }
+    const u64 blocks = n_sb_entries(nunits, W);
+    if (blocks > 0x7fffffffull) return MPHF_EINVAL;
+    {
+      LaunchScope ls("unit_write", s);
+      k_unit_write<<<(unsigned)blocks, kUnitThreads, 0, s>>>(src, nunits, (u64 *)S, SB);
+    }
+    {
+      LaunchScope ls("sect_scan", s);
+      k_scan_sums<<<1, kScanThreads, 0, s>>>(SB, blocks, d_total);
+    }
+    MPHF_CUDA(cudaGetLastError());
+    return MPHF_OK;
+  }
   const u64 nsect = n_sectors(M, W);
   if (nsect == 0) {
     if (d_total) MPHF_CUDA(cudaMemsetAsync(d_total, 0, sizeof(u64), s));
@@ -241,7 +293,7 @@ int build_sectors(const ASrc &src, u64 M, unsigned W, unsigned *S, u64 *SB, u64 
 int make_sectors(mphf_t *h, const ASrc &src, u64 *d_total, cudaStream_t s) {
   h->n_sect = n_sectors(h->M, h->sw);
   int rc = dev_alloc(h->S, h->n_sect * sector_bytes(h->sw), s);
-  if (rc == MPHF_OK) rc = dev_alloc(h->SB, n_superblocks(h->n_sect) * 8, s);
+  if (rc == MPHF_OK) rc = dev_alloc(h->SB, n_sb_entries(h->n_sect, h->sw) * 8, s);
   if (rc == MPHF_OK)
     rc = build_sectors(src, h->M, h->sw, (unsigned *)h->S.p, (u64 *)h->SB.p, d_total, s);
   return rc;
@@ -253,22 +305,27 @@ k_checkpoints(const unsigned *__restrict__ S, const u64 *__restrict__ SB, u64 n_
               u64 *__restrict__ out) {
   const u64 b = (u64)blockIdx.x * 256 + threadIdx.x;
   if (b >= n_rank) return;
-  const SectPos p = sect_pos<W>(b * MPHF_RANK_BLOCK);
-  const Sect<W> v = sect_load<W>(S, p.t);
-  out[b] = sect_rank<W>(v, p, sect_word<W>(v, p.j), SB);
+  using LW = Lay<W>;
+  const typename LW::Pos p = LW::pos(b * MPHF_RANK_BLOCK);
+  const typename LW::Data v = LW::load(S, p);
+  unsigned w = 0;
+  LW::hit(v, p, w);
+  out[b] = LW::rank(v, p, w, SB);
 }
 
 int sector_checkpoints(const unsigned *S, const u64 *SB, unsigned W, u64 n_rank, u64 *d_out,
                        cudaStream_t s) {
   if (n_rank == 0) return MPHF_OK;
   const u64 ctas = (n_rank + 255) / 256;
-  if (ctas > 0x7fffffffull || (W != kSectWords && W != kSectWordsMini)) return MPHF_EINVAL;
+  if (ctas > 0x7fffffffull || !layout_ok(W)) return MPHF_EINVAL;
   {
     LaunchScope ls("checkpoints", s);
     if (W == kSectWords)
       k_checkpoints<kSectWords><<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
-    else
+    else if (W == kSectWordsMini)
       k_checkpoints<kSectWordsMini><<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
+    else
+      k_checkpoints<kUnitBits><<<(unsigned)ctas, 256, 0, s>>>(S, SB, n_rank, d_out);
   }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;

@@ -31,12 +31,54 @@ namespace bbh {
 static constexpr unsigned kSectWords = 7;       // default A words per sector
 static constexpr unsigned kSectWordsMini = 15;  // minirank
 static constexpr unsigned kSBShift = 24;        // 2^24 sectors per superblock
+// Third layout: 8-byte units of 48 bits of A (bits 0-47) and a 16-bit count
+// (bits 48-63) of the ones in the unit's block of 1024 units before the unit;
+// SB[k] holds the ones before block k.  A probe is one 8-byte load (fewer
+// registers in flight, cheaper requests) at the price of counts costing 1/3 of
+// A.  The layout id stored in a handle is the 48.
+static constexpr unsigned kUnitBits = 48;
+static constexpr unsigned kUnitBlockShift = 10;
 
-__host__ __device__ inline u64 n_sectors(u64 M, unsigned W) { return (M / 32 + W - 1) / W; }
+__host__ __device__ inline bool layout_ok(unsigned W) {
+  return W == kSectWords || W == kSectWordsMini || W == kUnitBits;
+}
+// sectors (or units) holding M bits of A
+__host__ __device__ inline u64 n_sectors(u64 M, unsigned W) {
+  if (W == kUnitBits) return (M + kUnitBits - 1) / kUnitBits;
+  return (M / 32 + W - 1) / W;
+}
 __host__ __device__ inline u64 n_superblocks(u64 nsect) {
   return (nsect + (1ull << kSBShift) - 1) >> kSBShift;
 }
-__host__ __device__ inline u64 sector_bytes(unsigned W) { return 4ull * (W + 1); }
+// entries of SB for nsect sectors (units) of layout W
+__host__ __device__ inline u64 n_sb_entries(u64 nsect, unsigned W) {
+  if (W == kUnitBits) return (nsect + (1ull << kUnitBlockShift) - 1) >> kUnitBlockShift;
+  return n_superblocks(nsect);
+}
+__host__ __device__ inline u64 sector_bytes(unsigned W) { return W == kUnitBits ? 8 : 4ull * (W + 1); }
+
+// Where A's bytes sit in the stored array: `full` records of `width` bytes of A
+// at `pitch`-byte steps starting `offset` bytes in, then `rest` bytes of A in
+// the next record -- so one strided copy gathers the plain A back.
+struct AGather {
+  u64 pitch, width, offset, full, rest;
+};
+__host__ inline AGather a_gather(u64 M, unsigned W) {
+  const u64 bytes = M / 8;  // A is whole 64-bit words
+  AGather g;
+  if (W == kUnitBits) {
+    g.pitch = 8;
+    g.width = 6;
+    g.offset = 0;
+  } else {
+    g.pitch = 4ull * (W + 1);
+    g.width = 4ull * W;
+    g.offset = 4;
+  }
+  g.full = bytes / g.width;
+  g.rest = bytes - g.full * g.width;
+  return g;
+}
 
 // One sector in registers: r = word 0, w[i] = word i + 1.
 template <int W>
@@ -45,14 +87,14 @@ struct Sect {
 };
 
 __device__ __forceinline__ void ld256(const unsigned *p, unsigned (&v)[8]) {
-  asm("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7])
       : "l"(p));
 }
 
-// Sector t of S (sectors are 32-byte aligned): 256-bit loads that skip L1 (a
-// probe's sector is rarely touched again by the same SM).
+// Sector t of S (sectors are 32-byte aligned): 256-bit non-coherent loads (the
+// sectors are read-only while a lookup runs).
 template <int W>
 __device__ __forceinline__ Sect<W> sect_load(const unsigned *__restrict__ S, u64 t) {
   static_assert(W == 7 || W == 15, "sector sizes: 32 or 64 bytes");
@@ -121,6 +163,60 @@ __device__ __forceinline__ u64 sect_rank(const Sect<W> &v, const SectPos &p, uns
   return (k ? __ldg(SB + k) : 0ull) + c;
 }
 
+// ---------------------------------------------------------------------------
+// The probe of a lookup through one interface for every layout:
+//   Pos p = Lay<W>::pos(g);          where bit g lives
+//   Data v = Lay<W>::load(S, p);     the one memory request of the probe
+//   Lay<W>::hit(v, p, w)             bit g of A (w: the A word, for rank)
+//   Lay<W>::rank(v, p, w, SB)        ones of A before bit g
+// ---------------------------------------------------------------------------
+template <int W>
+struct Lay {
+  using Pos = SectPos;
+  using Data = Sect<W>;
+  static __device__ __forceinline__ Pos pos(u64 g) { return sect_pos<W>(g); }
+  static __device__ __forceinline__ Data load(const unsigned *__restrict__ S, const Pos &p) {
+    return sect_load<W>(S, p.t);
+  }
+  static __device__ __forceinline__ bool hit(const Data &v, const Pos &p, unsigned &w) {
+    w = sect_word<W>(v, p.j);
+    return (w >> p.b) & 1u;
+  }
+  static __device__ __forceinline__ u64 rank(const Data &v, const Pos &p, unsigned w,
+                                             const u64 *__restrict__ SB) {
+    return sect_rank<W>(v, p, w, SB);
+  }
+};
+
+struct UnitPos {
+  u64 u;       // unit
+  unsigned b;  // bit within the unit's 48 bits of A
+};
+template <>
+struct Lay<(int)kUnitBits> {
+  using Pos = UnitPos;
+  using Data = u64;
+  // g / 48 = (g / 16) / 3; for g / 16 < 2^32, q / 3 = umulhi(q, 0xAAAAAAAB) >> 1
+  // exactly (Granlund and Montgomery, as for the sector widths above)
+  static __device__ __forceinline__ Pos pos(u64 g) {
+    const u64 q = g >> 4;
+    const u64 u = (q >> 32) == 0 ? (u64)(__umulhi((unsigned)q, 0xAAAAAAABu) >> 1) : q / 3;
+    return UnitPos{u, (unsigned)(g - u * kUnitBits)};
+  }
+  // an ordinary cached load: measured on a GB300, the same 8-byte probes with
+  // an L1 no-allocate hint ran 1.6x slower
+  static __device__ __forceinline__ Data load(const unsigned *__restrict__ S, const Pos &p) {
+    return __ldg(reinterpret_cast<const u64 *>(S) + p.u);
+  }
+  static __device__ __forceinline__ bool hit(const Data &v, const Pos &p, unsigned &) {
+    return (v >> p.b) & 1ull;
+  }
+  static __device__ __forceinline__ u64 rank(const Data &v, const Pos &p, unsigned,
+                                             const u64 *__restrict__ SB) {
+    return __ldg(SB + (p.u >> kUnitBlockShift)) + (v >> 48) + __popcll(v & ((1ull << p.b) - 1ull));
+  }
+};
+
 // A as 64-bit words in two pieces: words [0, w0) at a0, [w0, W) at a1.
 struct ASrc {
   const u64 *a0;
@@ -129,7 +225,7 @@ struct ASrc {
   u64 W;
 };
 
-// Build the sectors S (n_sectors(M, W) of them) and SB (n_superblocks words)
+// Build the sectors S (n_sectors(M, W) of them) and SB (n_sb_entries words)
 // of the M-bit array src; *d_total receives the number of ones.
 int build_sectors(const ASrc &src, u64 M, unsigned W, unsigned *S, u64 *SB, u64 *d_total,
                   cudaStream_t s);

@@ -30,7 +30,7 @@ struct Header {
   double gamma;
   uint32_t L, L_used;
   uint64_t seed, M, n_fb, n_sect, n_sb, total_bytes, checksum;
-  uint32_t sector_words, pad;  // A words per sector (7 or 15)
+  uint32_t sector_words, pad;  // layout: A words per sector (7 or 15), or 48 (8-byte units)
   uint64_t reserved[3];
 };
 static_assert(sizeof(Header) == kHeader, "header layout");
@@ -60,13 +60,13 @@ using namespace bbh;
 
 extern "C" int mphf_serialized_size(const mphf_t *h, uint64_t *bytes) {
   if (!h || !bytes) return MPHF_EINVAL;
-  *bytes = image_bytes(h->L_used, h->n_sect, h->sw, n_superblocks(h->n_sect), h->n_fb);
+  *bytes = image_bytes(h->L_used, h->n_sect, h->sw, n_sb_entries(h->n_sect, h->sw), h->n_fb);
   return MPHF_OK;
 }
 
 extern "C" int mphf_serialize(const mphf_t *h, void *h_buf, uint64_t bytes) {
   if (!h || !h_buf) return MPHF_EINVAL;
-  const uint64_t n_sb = n_superblocks(h->n_sect);
+  const uint64_t n_sb = n_sb_entries(h->n_sect, h->sw);
   const uint64_t total = image_bytes(h->L_used, h->n_sect, h->sw, n_sb, h->n_fb);
   const uint64_t sbytes = h->n_sect * sector_bytes(h->sw);
   if (bytes < total) return MPHF_EINVAL;
@@ -130,9 +130,9 @@ extern "C" int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream,
     return MPHF_EINVAL;
   // sizes, before reading anything they locate
   const unsigned W = hd.sector_words;
-  if (W != kSectWords && W != kSectWordsMini) return MPHF_EINVAL;
+  if (!layout_ok(W)) return MPHF_EINVAL;
   if (hd.M > (1ull << 56) || hd.n_fb > hd.N) return MPHF_EINVAL;
-  if (hd.n_sect != n_sectors(hd.M, W) || hd.n_sb != n_superblocks(hd.n_sect)) return MPHF_EINVAL;
+  if (hd.n_sect != n_sectors(hd.M, W) || hd.n_sb != n_sb_entries(hd.n_sect, W)) return MPHF_EINVAL;
   if (hd.total_bytes != image_bytes(hd.L_used, hd.n_sect, W, hd.n_sb, hd.n_fb) ||
       hd.total_bytes > bytes)
     return MPHF_EINVAL;

@@ -183,24 +183,25 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) any |= act[s];
     if (!__any_sync(0xffffffffu, any)) break;
-    SectPos p[kMultiSlots];
-    Sect<W> v[kMultiSlots];
+    using LW = Lay<W>;
+    typename LW::Pos p[kMultiSlots];
+    typename LW::Data v[kMultiSlots];
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
         const LookupDev *h = hd[s];
-        p[s] = sect_pos<W>(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
-        v[s] = sect_load<W>(h->S, p[s].t);
+        p[s] = LW::pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        v[s] = LW::load(h->S, p[s]);
       }
     }
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       if (act[s]) {
         const LookupDev *h = hd[s];
-        const unsigned w = sect_word<W>(v[s], p[s].j);
-        if ((w >> p[s].b) & 1u) {
-          *optr[s] = sect_rank<W>(v[s], p[s], w, h->SB);
+        unsigned w = 0;
+        if (LW::hit(v[s], p[s], w)) {
+          *optr[s] = LW::rank(v[s], p[s], w, h->SB);
           act[s] = false;
         } else if (++lvl[s] >= h->L_used) {
           *optr[s] = h->n_fb ? fallback_index_m(h, x[s]) : MPHF_NOT_FOUND;
@@ -226,23 +227,28 @@ static int launch_multi_w(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaSt
   return MPHF_OK;
 }
 
-// Request table of a batch, grouped by sector size: the default-layout
-// requests first (index space [0, g.total[0])), then the minirank ones (their
-// own index space from 0), so that each group runs in the kernel compiled for
-// its layout.
+// Request table of a batch, grouped by layout: the default-layout requests
+// first (index space [0, g.total[0])), then the minirank ones, then those in
+// 8-byte units (each group with its own index space from 0), so that each
+// group runs in the kernel compiled for its layout.
+static constexpr int kLayouts = 3;  // 32-byte sectors, 64-byte sectors, 8-byte units
+__host__ inline int layout_group(unsigned sw) {
+  return sw == kSectWords ? 0 : sw == kSectWordsMini ? 1 : 2;
+}
 struct TableGroups {
-  unsigned n[2] = {0, 0};
-  u64 total[2] = {0, 0};
+  unsigned n[kLayouts] = {0, 0, 0};
+  u64 total[kLayouts] = {0, 0, 0};
 };
 template <class GetH, class GetKeys, class GetOut, class GetN>
 static TableGroups fill_table(ReqDev *t, size_t nreq, GetH geth, GetKeys getk, GetOut geto,
                               GetN getn) {
   TableGroups g;
-  for (int grp = 0; grp < 2; grp++) {
+  unsigned placed = 0;
+  for (int grp = 0; grp < kLayouts; grp++) {
     for (size_t i = 0; i < nreq; i++) {
       const mphf_t *h = geth(i);
-      if ((h->sw == kSectWordsMini) != (grp == 1)) continue;
-      ReqDev &r = t[g.n[0] + g.n[1]];
+      if (layout_group(h->sw) != grp) continue;
+      ReqDev &r = t[placed++];
       r.h = (const LookupDev *)h->ldesc.p;
       r.keys = getk(i);
       r.out = geto(i);
@@ -257,6 +263,8 @@ static TableGroups fill_table(ReqDev *t, size_t nreq, GetH geth, GetKeys getk, G
 static int launch_lookup_multi(const ReqDev *d_reqs, const TableGroups &g, cudaStream_t s) {
   int rc = launch_multi_w<kSectWords>(d_reqs, g.n[0], g.total[0], s);
   if (rc == MPHF_OK) rc = launch_multi_w<kSectWordsMini>(d_reqs + g.n[0], g.n[1], g.total[1], s);
+  if (rc == MPHF_OK)
+    rc = launch_multi_w<kUnitBits>(d_reqs + g.n[0] + g.n[1], g.n[2], g.total[2], s);
   return rc;
 }
 

@@ -199,7 +199,8 @@ class MPHF:
 
     # -- rank sampling -------------------------------------------------------
     def set_layout(self, sector_bytes: int, stream=None) -> None:
-        """Re-store A and its ranks in 32-byte (default) or 64-byte ("minirank") sectors."""
+        """Re-store A and its ranks in 32-byte sectors (default), 64-byte sectors
+        ("minirank", smaller) or 8-byte units (faster lookups, larger)."""
         _check(lib().mphf_set_layout(self._h, int(sector_bytes), _stream_ptr(stream)),
                "mphf_set_layout")
 

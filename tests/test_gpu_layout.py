@@ -1,4 +1,4 @@
-"""Rank sampling: 32-byte (default) and 64-byte ("minirank") sectors.
+"""Rank sampling: 32-byte (default), 64-byte ("minirank") sectors, 8-byte units.
 
 Re-storing a function in the other sector size must leave every index, the
 plain A and the paper's checkpoints unchanged; only the size moves, and it
@@ -33,7 +33,8 @@ def dev(a):
 
 
 @pytest.mark.parametrize("gamma,levels", [(1.0, 25), (2.0, 25), (5.0, 25), (1.0, 3)])
-def test_minirank_keeps_every_index(M, gamma, levels):
+@pytest.mark.parametrize("nbytes", [64, 8])
+def test_relayout_keeps_every_index(M, gamma, levels, nbytes):
     keys = inputs.splitmix64_keys(400009, 111)
     o = oracle.build(keys, gamma=gamma, levels=levels, seed=7)
     g = M.MPHF.build(dev(keys), gamma=gamma, levels=levels, seed=7)
@@ -41,17 +42,28 @@ def test_minirank_keeps_every_index(M, gamma, levels):
     q = np.concatenate([keys, inputs.splitmix64_keys(20000, 112)])
     want = o.lookup(q)
     small_before = g.device_bytes()
-    g.set_layout(64)
-    assert g.sector_bytes == 64
+    g.set_layout(nbytes)
+    assert g.sector_bytes == nbytes
     assert np.array_equal(g.bits(), o.bits())
     assert np.array_equal(g.rank(), o.rank())
     assert np.array_equal(g.fallback(), o.fallback())
     assert np.array_equal(M.to_u64(g.lookup(dev(q))), want)
-    assert g.bits_per_key() == pytest.approx(o.bits_per_key_sampled(1024), rel=1e-12)
-    # counts: 1/15 of A instead of 1/7
-    a_bytes = o.total_bits / 8
-    assert g.device_bytes() < small_before
-    assert abs(g.device_bytes() - 8 * g.num_fallback - a_bytes * 16 / 15) < 64 + a_bytes * 0.001
+    M_bits = o.total_bits
+    if nbytes == 64:
+        # minirank: the paper's accounting with 1024-bit counters; one 32-bit
+        # count per 15 A words, one 64-bit count per 2^24 sectors
+        assert g.bits_per_key() == pytest.approx(o.bits_per_key_sampled(1024), rel=1e-12)
+        assert g.device_bytes() < small_before
+        nsect = -(-(M_bits // 32) // 15)
+        want_bytes = 64 * nsect + 8 * -(-nsect // 2**24)
+    else:
+        # 8-byte units of 48 bits of A; one 64-bit count per 1024 units; the
+        # paper's default accounting
+        assert g.bits_per_key() == pytest.approx(o.bits_per_key(), rel=1e-12)
+        assert g.device_bytes() > small_before
+        nunits = -(-M_bits // 48)
+        want_bytes = 8 * nunits + 8 * -(-nunits // 1024)
+    assert g.device_bytes() == want_bytes + 8 * g.num_fallback
     g.set_layout(32)
     assert g.sector_bytes == 32 and g.device_bytes() == small_before
     assert np.array_equal(M.to_u64(g.lookup(dev(q))), want)
@@ -69,12 +81,13 @@ def test_minirank_sizes_match_the_paper(M, golden_dir):
     assert abs(g.bits_per_key() - rows[(1.0, 1024)]) <= tol
 
 
-def test_minirank_image_round_trip(M):
+@pytest.mark.parametrize("nbytes", [64, 8])
+def test_relayout_image_round_trip(M, nbytes):
     keys = inputs.splitmix64_keys(123457, 114)
     g = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=1)
-    g.set_layout(64)
+    g.set_layout(nbytes)
     h = M.MPHF.from_bytes(g.to_bytes())
-    assert h.sector_bytes == 64
+    assert h.sector_bytes == nbytes
     assert np.array_equal(h.bits(), g.bits()) and np.array_equal(h.rank(), g.rank())
     assert torch.equal(h.lookup(dev(keys)), g.lookup(dev(keys)))
 
@@ -83,6 +96,7 @@ def test_multi_lookup_mixes_layouts(M):
     sets = [inputs.splitmix64_keys(n, 115 + i) for i, n in enumerate((5000, 70000, 300, 123456))]
     hs = [M.MPHF.build(dev(k), gamma=2.0, levels=25, seed=3) for k in sets]
     hs[1].set_layout(64)
+    hs[2].set_layout(8)
     hs[3].set_layout(64)
     qs = [dev(np.concatenate([k, inputs.splitmix64_keys(777, 130 + i)])) for i, k in enumerate(sets)]
     outs = M.lookup_multi(hs, qs)
@@ -107,7 +121,7 @@ def test_batched_handle_takes_its_own_arrays(M):
 
 def test_bad_sector_size_is_refused(M):
     g = M.MPHF.build(dev(inputs.splitmix64_keys(100, 117)))
-    for b in (0, 16, 48, 128):
+    for b in (0, 16, 48, 128, 4):
         with pytest.raises(M.MPHFError) as e:
             g.set_layout(b)
         assert e.value.code == M.EINVAL
