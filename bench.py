@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--profile-batched", action="store_true",
+                   help="only the 4096-set batched build: autotune, then two builds (for ncu)")
     return p.parse_args()
 
 
@@ -597,10 +599,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_batched():
+    """The batched workload alone, for a profiler: the 4096 sets of the batched
+    bench line, autotuned, then built twice."""
+    import torch
+
+    from paper_1702_03154_gb300 import inputs, mphf
+    off = inputs.set_offsets(inputs.log_uniform_sizes(4096, 1e3, 1e6, 7))
+    keys = mphf.keygen(int(off[-1]), 7)
+    mphf.autotune_batched(keys, off, gamma=2.0, levels=25, seed=0)
+    for _ in range(2):
+        hs = mphf.build_batched(keys, off, gamma=2.0, levels=25, seed=0)
+        torch.cuda.synchronize()
+        del hs
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_batched:
+        profile_batched()
     else:
         run_ours(args)
 
