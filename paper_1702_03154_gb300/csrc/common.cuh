@@ -187,7 +187,7 @@ struct mphf {
   uint64_t M = 0;        // total bits
   uint64_t n_rank = 0;   // ceil(M / 512)
   uint64_t n_fb = 0;
-  uint32_t sw = 7;       // A words per sector: 7 (32-byte sectors) or 15 (minirank)
+  uint32_t sw = 7;       // layout: A words per sector, 7 (32 B) or 15 (64 B); 48 = 8-byte units
   uint64_t n_sect = 0;   // sectors holding A and its ranks (sector.cuh)
   bbh::DevBuf S;        // n_sect * (sw + 1) 32-bit words
   bbh::DevBuf SB;       // ones before each superblock of 2^24 sectors

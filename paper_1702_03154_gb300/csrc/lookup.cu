@@ -5,13 +5,13 @@
 // kept 32 keys in lock-step would idle most lanes while its slowest key walks
 // down the levels.  Instead every lane owns kSlots independent query slots,
 // each with its own (key, output index, level).  Each round every active slot
-// probes its current level with one 256-bit load of the sector holding its
-// bit (sector.cuh: the A word and the count of ones before the sector come
-// together); a slot whose bit is set finishes its rank from those registers
-// and retires, the others move to the next level, and retired slots are
-// refilled from the warp's stream of input keys.  So lanes stay busy, each
-// lane keeps kSlots independent loads in flight, and a placed key costs one
-// memory request per level probed.
+// probes its current level with one load of the record holding its bit (a
+// 256-bit sector or an 8-byte unit, sector.cuh: the A word and a count of the
+// ones before it come together); a slot whose bit is set finishes its rank
+// from those registers and retires, the others move to the next level, and
+// retired slots are refilled from the warp's stream of input keys.  So lanes
+// stay busy, each lane keeps kSlots independent loads in flight, and a placed
+// key costs one memory request per level probed.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 

@@ -1,11 +1,14 @@
 // rank.cu -- the ranks of Sec. 3.1 over the concatenated bit array A.
 //
-// Every function's A is stored in the sector layout of sector.cuh (A's words
-// interleaved with counts of the ones before them); build_sectors writes it
-// in three passes: (1) each thread popcounts one 224-bit sector and each CTA
+// Every function's A is stored in one of the layouts of sector.cuh (A's words
+// interleaved with counts of the ones before them); build_sectors writes
+// sectors in three passes: (1) each thread popcounts one sector and each CTA
 // sums its sectors, (2) one CTA scans the per-CTA sums, (3) each sector is
-// written with its count relative to its superblock.  sector_checkpoints
-// evaluates the paper's checkpoints (ones before bit 512 b) from the sectors.
+// written with its count relative to its superblock; 8-byte units in two:
+// one CTA per 1024-unit block writes the units with their in-block counts,
+// then one CTA scans the block sums into the block table.
+// sector_checkpoints evaluates the paper's checkpoints (ones before bit
+// 512 b) in any layout.
 //
 // The file also holds a standalone rank-table builder over caller-supplied
 // words (mphf_rank_table_noalloc): one 64-bit checkpoint per 512 bits, stored
