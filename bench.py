@@ -172,6 +172,16 @@ def cpu_baseline(n_sample: int, gamma: float, levels: int):
                       f"lookup {t2 - t1:.2f} s, single-threaded C"}
 
 
+def workload_config(N: int, gamma: float, L: int, rank: int = 0) -> dict:
+    """The `config` of the bench line (the same for both arms)."""
+    return {"workload": f"plain single MPHF, N={N:.0e} SplitMix64 keys (seed {2 + rank}), "
+                        f"gamma={gamma:g}, L={L}; build + lookup of all N in shuffled order",
+            "N": N, "gamma": gamma, "levels": L,
+            "l2": (f"inputs ({8 * N / 1e6:.0f} MB keys + {8 * N / 1e6:.0f} MB queries) larger "
+                   "than L2; no flush" if 8 * N > 129e6 else
+                   "inputs smaller than L2 (a reduced test size, not the bench workload)")}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -190,8 +200,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": f"oracle on {n_sample:.0e}-key samples of the N=1e8 workload",
-                       "gamma": args.gamma, "levels": args.levels},
+            "config": workload_config(int(args.n), args.gamma, args.levels),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -574,14 +583,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
-                "config": {"workload": f"plain single MPHF, N={N:.0e} SplitMix64 keys (seed "
-                                       f"{2 + rank}), gamma={gamma:g}, L={L}; build + lookup of "
-                                       "all N in shuffled order",
-                           "N": N, "gamma": gamma, "levels": L,
-                           "l2": (f"inputs ({8 * N / 1e6:.0f} MB keys + {8 * N / 1e6:.0f} MB "
-                                  "queries) larger than L2; no flush" if 8 * N > 129e6 else
-                                  "inputs smaller than L2 (a reduced test size, not the bench "
-                                  "workload)")},
+                "config": workload_config(N, gamma, L, rank),
                 "build_mkeys_s": round(N / (float(np.median(tb)) / 1e3) / 1e6, 1),
                 "lookup_mkeys_s": round(N / (float(np.median(tl)) / 1e3) / 1e6, 1),
                 "build_ms": round(float(np.median(tb)), 4), "lookup_ms": round(float(np.median(tl)), 4),
