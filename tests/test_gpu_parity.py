@@ -278,3 +278,37 @@ def test_many_duplicates_are_reported(M):
     with pytest.raises(M.MPHFError) as e:
         M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=0)
     assert e.value.code == M.EDUPLICATE
+
+
+@pytest.mark.parametrize("kind", ["sequential", "stride_2_40", "high_bit", "extremes"])
+def test_structured_keys(M, kind):
+    # the method hashes every key, so structured (non-random) keys must give
+    # exactly the oracle's function too
+    n = 200003
+    j = np.arange(n, dtype=np.uint64)
+    if kind == "sequential":
+        keys = j
+    elif kind == "stride_2_40":
+        keys = j << np.uint64(40)
+    elif kind == "high_bit":
+        keys = j | np.uint64(1 << 63)
+    else:
+        keys = np.concatenate([np.array([0, (1 << 64) - 1, 1 << 63, (1 << 63) - 1], dtype=np.uint64),
+                               inputs.splitmix64_keys(n - 4, 120)])
+    check(M, keys, 2.0, 25, 11)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 7.5, 100.0])
+def test_extreme_gamma(M, gamma):
+    keys = inputs.splitmix64_keys(50021, 121)
+    g, o = check(M, keys, gamma, 25, 12)
+    # at large gamma almost every key is placed at level 0
+    if gamma == 100.0:
+        assert g.level_sizes()[1] < keys.size * 0.02
+
+
+def test_large_fallback_at_scale(M):
+    # L = 1 at gamma = 1: ~63% of 2e6 keys go to the sorted fallback
+    keys = inputs.splitmix64_keys(2 * 10**6, 122)
+    g, o = check(M, keys, 1.0, 1, 13)
+    assert g.num_fallback > 10**6
