@@ -267,9 +267,15 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
   if (u0 >= u1) return;
   const bool flat = nx.mode == LM_FLAT;
   const unsigned nb = flat ? 1u : (unsigned)nx.B;
-  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
-  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
-  u64 *stage = sm.sorted;  // survivors awaiting the multisplit (at most kTile)
+  if (nb > cfg.nbcap) {  // more destinations than the arrays were sized for
+    if (threadIdx.x == 0) atomicOr(&meta->status, ST_OVERFLOW);
+    return;
+  }
+  // the stage holds up to kTile + kIn survivors: a full tile goes to the
+  // multisplit, the rest waits for the next one
+  SplitSmem sm = carve_split(smem, (unsigned)cfg.nbcap, kTile + kIn);
+  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)cfg.nbcap, kTile + kIn));
+  u64 *stage = sm.sorted;
   const u64 *arena = (d & 1) ? cfg.Y : cfg.X;
   const unsigned *parena = (d & 1) ? cfg.YP : cfg.XP;
   const u64 *cnt = (d & 1) ? cfg.cntY : cfg.cntX;
@@ -395,10 +401,15 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     if (threadIdx.x == 0) scnt[(it + 1) % 3] = 0;
     __syncthreads();
     ns += scnt[it % 3];
-    // 2.+3. once another unit might not fit, hash and write the staged keys
-    if (ns > (unsigned)(kTile - kIn)) {
-      flush(ns);
-      ns = 0;
+    // 2.+3. a full tile of survivors: hash and write it; the survivors past it
+    // (fewer than kIn, beyond the multisplit's part of the stage) move to the
+    // front for the next tile
+    if (ns >= (unsigned)kTile) {
+      flush(kTile);
+      const unsigned left = ns - kTile;
+      for (unsigned i = threadIdx.x; i < left; i += kTT) stage[i] = stage[kTile + i];
+      __syncthreads();
+      ns = left;
     }
   }
   if (ns) flush(ns);
@@ -470,7 +481,8 @@ static int set_attrs() {
   if (g_attr_set) return MPHF_OK;
 
   g_split_bytes = split_smem_bytes((unsigned)kBmax);
-  g_compact_bytes = g_split_bytes + kPmax / 8;  // + the bucket's slice of A_d
+  // compaction: its largest layout (kBmax destinations) + the bucket's slice of A_d
+  g_compact_bytes = split_smem_bytes((unsigned)kBmax, kTile + kIn) + kPmax / 8;
   MPHF_CUDA(cudaFuncSetAttribute(k_partition0<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(g_split_bytes + kTile * 8)));
   MPHF_CUDA(cudaFuncSetAttribute(k_partition0<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -543,6 +555,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
   cfg.m0 = m0;
   FastMeta *meta = nullptr;
   int dlim = 0;
+  size_t comp_bytes = g_compact_bytes;  // compaction's shared memory for this build
 
 #define FTRY(x)                    \
   do {                             \
@@ -656,6 +669,17 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
       cfg.arena_words = (u64)(L > 1 ? L - 1 : 1) * (m1 / 64);
       FTRY(dev_alloc(sc.arena, cfg.arena_words * 8, st));
       cfg.arena = (u64 *)sc.arena.p;
+      // Destination buckets of any compaction: level 1 has the most keys of the
+      // levels >= 1, and a smaller level never takes more than Btarget buckets
+      // (its width shrinks first), so max(B_1, Btarget) bounds them all; the
+      // compaction checks it and falls back if ever exceeded.
+      {
+        u64 nbc = hm.lv[1].mode == LM_BUCKETED ? hm.lv[1].B : 1;
+        if (nbc < cfg.Btarget) nbc = cfg.Btarget;
+        if (nbc > kBmax) nbc = kBmax;
+        cfg.nbcap = nbc;
+        comp_bytes = split_smem_bytes((unsigned)nbc, kTile + kIn) + kPmax / 8;
+      }
       // predicted number of bucketed levels after level 0
       double e = (double)n1;
       int D = 1;
@@ -667,7 +691,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
         for (; dlim < D && dlim < (int)L; dlim++) {
           {
             LaunchScope ls("compact_buckets", st);
-            k_compact_buckets<<<(unsigned)sm_count() * 2, kTT, g_compact_bytes, st>>>(meta, dlim, cfg);
+            k_compact_buckets<<<(unsigned)sm_count() * 2, kTT, comp_bytes, st>>>(meta, dlim, cfg);
           }
           if (dlim + 1 < (int)L) {
             LaunchScope ls("fill_buckets", st);

@@ -62,6 +62,7 @@ struct FastCfg {
   u64 Pmax, Pmin, Btarget;
   double cap_scale;     // bucket capacity multiplier (1 in production; < 1 only in tests)
   unsigned *upre;       // [Bmax + 1] compaction units (kIn-entry slices) before each bucket
+  u64 nbcap;            // compaction: capacity of its per-destination-bucket arrays
 };
 
 __host__ __device__ inline u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
@@ -241,10 +242,13 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   __syncthreads();
 }
 
-__device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap) {
+// sorted_cap >= kTile entries of `sorted` (a caller may stage more keys there
+// than one multisplit takes; the multisplit itself uses the first kTile).
+__device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap,
+                                                 unsigned sorted_cap = kTile) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
-  s.dbase = s.sorted + kTile;
+  s.dbase = s.sorted + sorted_cap;
   s.stag = reinterpret_cast<unsigned *>(s.dbase + nb_cap);
   s.cnt = s.stag + kTile;
   s.lim = s.cnt + nb_cap;
@@ -252,9 +256,9 @@ __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned n
   return s;
 }
 
-static constexpr size_t split_smem_bytes(unsigned nb_cap) {
-  return (size_t)kTile * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 + 2 * (size_t)nb_cap * 4 +
-         (kTT / 32 + 2) * 4 + 8;
+static constexpr size_t split_smem_bytes(unsigned nb_cap, unsigned sorted_cap = kTile) {
+  return (size_t)sorted_cap * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 +
+         2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 + 8;
 }
 
 // ---------------------------------------------------------------------------
