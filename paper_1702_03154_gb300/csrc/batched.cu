@@ -445,9 +445,11 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
   const unsigned u0 = (unsigned)(((u64)U * blockIdx.x) / gridDim.x);
   const unsigned u1 = (unsigned)(((u64)U * (blockIdx.x + 1)) / gridDim.x);
   if (u0 >= u1) return;
-  SplitSmem sm = carve_split(smem, (unsigned)kBmax);
-  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
-  u64 *stage = sm.sorted;  // survivors awaiting the multisplit (at most kTile, one set)
+  // destinations of one flush: the next-level buckets of one set (at most
+  // Bset_max); the stage holds kTile + kIn survivors of that set
+  SplitSmem sm = carve_split(smem, (unsigned)c.Bset_max, kTile + kIn);
+  u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)c.Bset_max, kTile + kIn));
+  u64 *stage = sm.sorted;
   const u64 s_n = level_seed(c.seed, d + 1);
   const unsigned lane = threadIdx.x & 31;
   const unsigned ltm = (1u << lane) - 1u;
@@ -457,6 +459,10 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
     const BLvl nx = c.lvl[nl][s];
     BSet *st = &c.sets[s];
     const bool flat = nx.mode == LM_FLAT;
+    if (!flat && nx.B > c.Bset_max) {  // more buckets than the arrays hold: the set is rebuilt alone
+      if (threadIdx.x == 0) fail_set(st);
+      return;
+    }
     u64 x[kKPT];
     unsigned dst[kKPT], lp[kKPT];
     bool ok[kKPT];
@@ -594,10 +600,14 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
     __syncthreads();
     ns += scnt[it % 3];
     it++;
-    // 2.+3. once another unit might not fit, hash and write the staged keys
-    if (ns > (unsigned)(kTile - kIn)) {
-      flush(ns, cur_set);
-      ns = 0;
+    // 2.+3. a full tile of this set's survivors: hash and write it; the rest
+    // (fewer than kIn) move to the front of the stage for the next tile
+    if (ns >= (unsigned)kTile) {
+      flush(kTile, cur_set);
+      const unsigned left = ns - kTile;
+      for (unsigned i = threadIdx.x; i < left; i += kTT) stage[i] = stage[kTile + i];
+      __syncthreads();
+      ns = left;
     }
   }
   if (ns) flush(ns, cur_set);
@@ -847,7 +857,10 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   *n_rebuilt = 0;
   static bool attr = false;
   const size_t split_b = split_smem_bytes((unsigned)kBmax);
-  const size_t comp_b = split_b + kPmax / 8;
+  // compaction: per-set destination arrays (Bset_max) + a stage of kTile + kIn
+  // + the bucket's slice of A_d; the attribute admits the largest Bset_max
+  const size_t comp_b = split_smem_bytes((unsigned)tune.Bset_max, kTile + kIn) + kPmax / 8;
+  const size_t comp_max = split_smem_bytes((unsigned)kBmax, kTile + kIn) + kPmax / 8;
   u64 mcap = 0;
   u64 T = kTailMaxKeys;
   while (T > 64 && tail_smem_bytes(level_bits(T, gamma)) > 200 * 1024) T >>= 1;
@@ -856,7 +869,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)split_b));
     MPHF_CUDA(cudaFuncSetAttribute(k_bcompact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)comp_b));
+                                   (int)comp_max));
     MPHF_CUDA(cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(kPmax / 4)));
     MPHF_CUDA(cudaFuncSetAttribute(k_btail, cudaFuncAttributeMaxDynamicSharedMemorySize,
