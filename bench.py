@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--no-layouts", action="store_true",
+                   help="skip timing the lookup in the other storage layouts")
     p.add_argument("--profile-batched", action="store_true",
                    help="only the 4096-set batched build: autotune, then two builds (for ncu)")
     return p.parse_args()
@@ -492,7 +494,7 @@ def run_ours(args):
               "level_sizes": last.level_sizes()[:8], "fallback": last.num_fallback}
     # the same function's lookup in each storage layout (mphf_set_layout)
     by_layout = {}
-    for nbytes in (64, 8, 32):
+    for nbytes in (() if args.no_layouts else (64, 8, 32)):
         last.set_layout(nbytes)
         tt = []
         for _ in range(3):
