@@ -617,7 +617,13 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
 // Single-CTA tail of every set (sets that never left shared memory start at
 // level 0 from the caller's keys).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTailThreads, 1) k_btail(BCfg c, u64 mcap, int dlim) {
+// Batched tails are small: sets join the tail at kBTailKeys keys and run on
+// kBTailThreads threads with ~kBTailKeys * 8 bytes of shared memory, so that
+// several tails share an SM (the tail is a chain of short, barrier-bound levels).
+static constexpr int kBTailThreads = 512;
+static constexpr int kBTailKeys = 8192;
+
+__global__ void __launch_bounds__(kBTailThreads) k_btail(BCfg c, u64 mcap, int dlim) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned s = blockIdx.x;
   BSet *st = &c.sets[s];
@@ -638,19 +644,20 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_btail(BCfg c, u64 mcap, int
       return;
     }
   }
-  if (n > kTailMaxKeys) {  // a fallback too large to sort here
+  if (n > (u64)kBTailKeys) {  // a fallback too large to sort here
     if (threadIdx.x == 0) fail_set(st);
     return;
   }
-  TailSmem sm = carve_tail(smem, mcap);
+  TailSmem sm = carve_tail(smem, mcap, kBTailKeys);
   const u64 *src = st->small ? c.keys + st->key_off : c.flat + st->flat_off;
-  for (unsigned i = threadIdx.x; i < n; i += kTailThreads) sm.keys[i] = src[i];
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) sm.keys[i] = src[i];
   if (threadIdx.x == 0) {
     hist[st->small ? 0 : t].n = n;
     hist[st->small ? 0 : t].off = off;
   }
   __syncthreads();
-  const unsigned used = cta_levels(sm, n, st->small ? 0 : (int)t, off, hist, c.gamma, c.L, c.seed,
+  const unsigned used = cta_levels<kBTailThreads, kBTailKeys>(
+      sm, n, st->small ? 0 : (int)t, off, hist, c.gamma, c.L, c.seed,
                                    c.A0 + st->a0_off, c.arena + st->at_off, st->m0, st->at_words,
                                    c.flat + st->flat_off, &st->n_fb, &st->status);
   if (threadIdx.x == 0) st->levels_used = used;
@@ -862,9 +869,10 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   const size_t comp_b = split_smem_bytes((unsigned)tune.Bset_max, kTile + kIn) + kPmax / 8;
   const size_t comp_max = split_smem_bytes((unsigned)kBmax, kTile + kIn) + kPmax / 8;
   u64 mcap = 0;
-  u64 T = kTailMaxKeys;
-  while (T > 64 && tail_smem_bytes(level_bits(T, gamma)) > 200 * 1024) T >>= 1;
+  u64 T = kBTailKeys;  // keep a tail's shared memory small enough for several CTAs per SM
+  while (T > 64 && tail_smem_bytes(level_bits(T, gamma), kBTailKeys) > 96 * 1024) T >>= 1;
   mcap = level_bits(T, gamma);
+  const size_t tail_b = tail_smem_bytes(mcap, kBTailKeys);
   if (!attr) {
     MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)split_b));
@@ -873,7 +881,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     MPHF_CUDA(cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(kPmax / 4)));
     MPHF_CUDA(cudaFuncSetAttribute(k_btail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
+                                   100 * 1024));  // tail_b <= 96 KB by the choice of T above
     attr = true;
   }
   for (unsigned s = 0; s < S; s++) out[s] = nullptr;
@@ -1034,7 +1042,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
         nk_rec += 3;
       }
     }
-    k_btail<<<S, kTailThreads, tail_smem_bytes(mcap), st>>>(c, mcap, Dl + 1);
+    k_btail<<<S, kBTailThreads, tail_b, st>>>(c, mcap, Dl + 1);
     nk_rec++;
     return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
   };
@@ -1120,7 +1128,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     }
     {
       LaunchScope ls("btail", st);
-      k_btail<<<S, kTailThreads, tail_smem_bytes(mcap), st>>>(c, mcap, D + 1);
+      k_btail<<<S, kBTailThreads, tail_b, st>>>(c, mcap, D + 1);
     }
     MPHF_CUDA(cudaGetLastError());
     MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));

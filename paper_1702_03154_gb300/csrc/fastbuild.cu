@@ -461,7 +461,8 @@ k_tail(FastMeta *__restrict__ meta, int dlim, FastCfg cfg, u64 mcap) {
   TailSmem sm = carve_tail(smem, mcap);
   for (unsigned i = threadIdx.x; i < n; i += kTailThreads) sm.keys[i] = cfg.flat[i];
   __syncthreads();
-  unsigned used = cta_levels(sm, n, t, lvs[t].off, lvs, cfg.gamma, cfg.L, cfg.seed, cfg.A0,
+  unsigned used = cta_levels<kTailThreads, (int)kTailMaxKeys>(
+      sm, n, t, lvs[t].off, lvs, cfg.gamma, cfg.L, cfg.seed, cfg.A0,
                              cfg.arena, cfg.m0, cfg.arena_words, cfg.flat, &meta->n_fb,
                              &meta->status);
   if (threadIdx.x == 0) {

@@ -310,11 +310,13 @@ static __device__ void bitonic_sort_smem(u64 *a, unsigned n) {
 
 // Returns the number of levels used.  lvs: level records (n/m/off/weight/mode)
 // of this key set; A0 / arena / m0 locate A_d; fb_out receives the sorted
-// fallback (n_fb keys).
+// fallback (n_fb keys).  NT threads, at most MAXK keys (MAXK / NT <= 32).
+template <int NT, int MAXK>
 static __device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off, FLevel *lvs,
                                       double gamma, uint32_t L, u64 seed, u64 *A0, u64 *arena,
                                       u64 m0, u64 arena_words, u64 *fb_out, u64 *n_fb_out,
                                       unsigned *status) {
+  static_assert(MAXK % NT == 0 && MAXK / NT <= 32, "keys per thread must fit a 32-bit mask");
   int d = d0;
   for (;;) {
     if (n == 0) {
@@ -363,7 +365,7 @@ static __device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off
       wsum += __popcll(a);
     }
     // compaction in place: each thread keeps its contiguous run of keys in registers
-    constexpr unsigned KMAX = (unsigned)(kTailMaxKeys / kTailThreads);
+    constexpr unsigned KMAX = (unsigned)(MAXK / NT);
     const unsigned per = (unsigned)((n + blockDim.x - 1) / blockDim.x);
     const unsigned lo = threadIdx.x * per;
     u64 mine[KMAX];
@@ -385,13 +387,13 @@ static __device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off
       }
     }
     unsigned total;
-    unsigned pre = block_scan_u32<kTailThreads>(c, sm.red, &total);
+    unsigned pre = block_scan_u32<NT>(c, sm.red, &total);
     // every thread has read its keys (block_scan synchronises)
 #pragma unroll
     for (unsigned k = 0; k < KMAX; k++) {
       if (keepmask & (1u << k)) sm.keys[pre++] = mine[k];
     }
-    const u64 wt = block_sum<kTailThreads>(wsum, sm.red64);
+    const u64 wt = block_sum<NT>(wsum, sm.red64);
     if (threadIdx.x == 0) {
       if (wt + total != n) atomicOr(status, ST_INTERNAL);
       lvs[d].n = n;
@@ -411,18 +413,19 @@ static __device__ unsigned cta_levels(const TailSmem &sm, u64 n, int d0, u64 off
   }
 }
 
-__device__ __forceinline__ TailSmem carve_tail(unsigned char *smem, u64 mcap) {
+__device__ __forceinline__ TailSmem carve_tail(unsigned char *smem, u64 mcap,
+                                               u64 maxk = kTailMaxKeys) {
   TailSmem t;
   t.keys = reinterpret_cast<u64 *>(smem);
-  t.hit = reinterpret_cast<unsigned *>(smem + kTailMaxKeys * 8);
+  t.hit = reinterpret_cast<unsigned *>(smem + maxk * 8);
   t.col = t.hit + (mcap >> 5);
   t.red64 = reinterpret_cast<u64 *>(t.col + (mcap >> 5));
   t.red = reinterpret_cast<unsigned *>(t.red64 + 32);
   return t;
 }
 
-static size_t tail_smem_bytes(u64 mcap) {
-  return kTailMaxKeys * 8 + 2 * (mcap >> 5) * 4 + 32 * 8 + 40 * 4;
+static size_t tail_smem_bytes(u64 mcap, u64 maxk = kTailMaxKeys) {
+  return maxk * 8 + 2 * (mcap >> 5) * 4 + 32 * 8 + 40 * 4;
 }
 
 
