@@ -322,7 +322,9 @@ int mphf_server_submit_build(mphf_server_t *srv, const uint64_t *d_keys, uint64_
                              uint32_t levels, uint64_t seed, uint64_t *req_id);
 /* Wait for a request (at most timeout_s, else MPHF_ETIMEOUT); returns its status,
  * its latency from submission to completion in seconds and, for a build, the
- * new handle (owned by the caller).  A request can be waited for once. */
+ * new handle (owned by the caller; with built == NULL it is released here).
+ * A request can be waited for once; mphf_server_destroy releases the builds
+ * of requests never waited for. */
 int mphf_server_wait(mphf_server_t *srv, uint64_t req_id, double timeout_s, int *status,
                      double *latency_s, mphf_t **built);
 int mphf_server_stats(mphf_server_t *srv, uint64_t *batches, uint64_t *requests, uint64_t *keys,

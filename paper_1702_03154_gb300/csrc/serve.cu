@@ -511,7 +511,10 @@ void mphf_server_destroy(mphf_server_t *sv) {
     cudaEventSynchronize(b.ev);
     cudaEventDestroy(b.ev);
   }
-  for (auto &kv : sv->reqs) delete kv.second;
+  for (auto &kv : sv->reqs) {  // requests never waited for: their builds are released
+    if (kv.second->built) mphf_free(kv.second->built);
+    delete kv.second;
+  }
   for (auto &d : sv->dtab)
     if (d.p) cudaFree(d.p);
   for (auto *h : sv->htab)
@@ -586,6 +589,7 @@ int mphf_server_wait(mphf_server_t *sv, uint64_t req_id, double timeout_s, int *
   if (status) *status = r->status;
   if (latency_s) *latency_s = r->t_done - r->t_submit;
   if (built) *built = r->built;
+  else if (r->built) mphf_free(r->built);  // a build nobody takes is released here
   sv->reqs.erase(it);
   delete r;
   return MPHF_OK;
