@@ -142,12 +142,12 @@ int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_t n, uint64
 double mphf_bits_per_key(const mphf_t *h);
 
 /* Device memory the handle holds, in bytes.  A and its ranks are stored
- * together in 32-byte sectors (224 bits of A and a 32-bit count of the ones
- * before the sector within its superblock of 2^24 sectors), plus one 64-bit
- * count per superblock and the fallback keys.  A query then reads one sector
- * per level it probes.  The counts cost 1/7 of A, where Sec. 3.1's 64-bit
- * checkpoint per 512 bits costs 1/8 (mphf_bits_per_key counts the paper's).
- * 0 for NULL. */
+ * together (by default in 32-byte sectors: 224 bits of A and a 32-bit count of
+ * the ones before the sector within its superblock of 2^24 sectors, plus one
+ * 64-bit count per superblock; see mphf_set_layout for the other layouts),
+ * and the fallback keys.  A query then reads one sector per level it probes.
+ * The default counts cost 1/7 of A, where Sec. 3.1's 64-bit checkpoint per
+ * 512 bits costs 1/8 (mphf_bits_per_key counts the paper's).  0 for NULL. */
 uint64_t mphf_device_bytes(const mphf_t *h);
 
 /*
@@ -183,8 +183,10 @@ uint64_t mphf_num_fallback(const mphf_t *h);    /* n_fb */
 /* n_d = |F_d|, m_d = |A_d|, off_d = first bit of A_d in A, s_d = level seed. */
 int mphf_level_info(const mphf_t *h, uint32_t d, uint64_t *n_d, uint64_t *m_d, uint64_t *off_d,
                     uint64_t *s_d);
-/* Copy A (M/64 words), the rank checkpoints or the sorted fallback to host memory;
- * `count` must equal the size reported above. */
+/* Copy A (M/64 words, gathered out of the storage layout), the rank checkpoints
+ * (evaluated from the stored counts: ones before bit 512 b) or the sorted
+ * fallback to host memory; `count` must equal the size reported above.  These
+ * wait for the device. */
 int mphf_copy_bits(const mphf_t *h, uint64_t *h_words, uint64_t count);
 int mphf_copy_rank(const mphf_t *h, uint64_t *h_rank, uint64_t count);
 int mphf_copy_fallback(const mphf_t *h, uint64_t *h_keys, uint64_t count);
