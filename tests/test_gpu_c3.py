@@ -26,7 +26,14 @@ def test_config3_1e10_properties():
         pytest.skip(f"needs ~240 GB of free device memory, {free / 2**30:.0f} GB free")
     from paper_1702_03154_gb300 import mphf
     keys = mphf.keygen(N, 4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
     h = mphf.MPHF.build(keys, gamma=2.0, levels=25, seed=0)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"build of 1e10 keys: {e0.elapsed_time(e1) / 1e3:.3f} s "
+          f"({N / (e0.elapsed_time(e1) / 1e3) / 1e9:.2f} Gkeys/s), {h.bits_per_key():.4f} bits/key")
     lv = h.levels()
     sizes = h.level_sizes()
     assert sizes[0] == N
@@ -51,6 +58,20 @@ def test_config3_1e10_properties():
         del idx
     assert bool((hits == 1).all())
     del hits
+    # 1e9 member lookups at random positions (the configuration's query set)
+    sel = torch.randint(0, N, (10**9,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    q = keys[sel]
+    del sel
+    out = torch.empty_like(q)
+    h.lookup(q, out=out)  # warm
+    e0.record()
+    h.lookup(q, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"1e9 random member lookups: {e0.elapsed_time(e1):.1f} ms "
+          f"({1e9 / (e0.elapsed_time(e1) / 1e3) / 1e9:.2f} Gkeys/s)")
+    assert int(out.min()) >= 0 and int(out.max()) < N
+    del q, out
     total_placed = N - h.num_fallback
     assert total_placed + h.num_fallback == N
     # The same function built without storing any key (Sec. 3.4, second
