@@ -294,7 +294,9 @@ def run_batched(args, stream):
            "per_set_build_ms": round(t_p, 3), "per_set_build_mkeys_s": round(total / t_p / 1e3, 1),
            "speedup_vs_per_set": round(t_p / t_b, 2),
            "lookup_all_ms": round(t_l, 3), "lookup_mkeys_s": round(total / t_l / 1e3, 1),
-           "autotune_best_ms": round(tune_ms, 3), "kernels_per_batched_build": int(launches),
+           "autotune_best_ms": round(tune_ms, 3),
+           "autotune_choice": mphf.batched_tuning(S, total),
+           "kernels_per_batched_build": int(launches),
            "handles_by_path": {str(k): v for k, v in sorted(paths.items())}}
     del hs, keys, out
     torch.cuda.empty_cache()

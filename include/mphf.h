@@ -115,6 +115,22 @@ int mphf_autotune_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uin
                           double gamma, uint32_t levels, uint64_t seed, void *stream,
                           double *best_ms);
 
+/* The choice mphf_autotune_batched made for S sets of total_keys keys: the
+ * largest bucket width (positions), the most buckets per set and the tail
+ * shape (keys handed to the single-CTA tail: 4096 on 256 threads or 8192 on
+ * 512).  MPHF_EINVAL (and the defaults) if that size class was never tuned. */
+int mphf_batched_tuning(uint32_t S, uint64_t total_keys, uint64_t *pmax, uint64_t *bset_max,
+                        uint64_t *tail_keys);
+
+/* Sets the choice for the size class of S sets of total_keys keys (both
+ * rounded up to powers of two), e.g. one saved from an earlier
+ * mphf_autotune_batched: pmax a power of two in [4096, 262144], bset_max in
+ * [1, 2048], tail_keys 4096 or 8192.  Results never depend on it; a choice
+ * whose buckets overflow costs a re-build of the sets concerned.
+ * MPHF_EINVAL for values out of range. */
+int mphf_batched_set_tuning(uint32_t S, uint64_t total_keys, uint64_t pmax, uint64_t bset_max,
+                            uint64_t tail_keys);
+
 /* Test hook: scales the bucket capacities of mphf_build_batched (default 1;
  * values < 1 make sets overflow and exercise their individual rebuild). */
 int mphf_batched_debug_config(double cap_scale);

@@ -617,13 +617,12 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
 // Single-CTA tail of every set (sets that never left shared memory start at
 // level 0 from the caller's keys).
 // ---------------------------------------------------------------------------
-// Batched tails are small: sets join the tail at kBTailKeys keys and run on
-// kBTailThreads threads with ~kBTailKeys * 8 bytes of shared memory, so that
-// several tails share an SM (the tail is a chain of short, barrier-bound levels).
-static constexpr int kBTailThreads = 512;
-static constexpr int kBTailKeys = 8192;
-
-__global__ void __launch_bounds__(kBTailThreads) k_btail(BCfg c, u64 mcap, int dlim) {
+// Batched tails are small: sets join the tail at MAXK keys and run on NT
+// threads with ~MAXK * 8 bytes of shared memory, so that several tails share
+// an SM (the tail is a chain of short, barrier-bound levels).  Two shapes are
+// compiled; the autotuner picks one per size class.
+template <int NT, int MAXK>
+__global__ void __launch_bounds__(NT) k_btail(BCfg c, u64 mcap, int dlim) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned s = blockIdx.x;
   BSet *st = &c.sets[s];
@@ -644,11 +643,11 @@ __global__ void __launch_bounds__(kBTailThreads) k_btail(BCfg c, u64 mcap, int d
       return;
     }
   }
-  if (n > (u64)kBTailKeys) {  // a fallback too large to sort here
+  if (n > (u64)MAXK) {  // a fallback too large to sort here
     if (threadIdx.x == 0) fail_set(st);
     return;
   }
-  TailSmem sm = carve_tail(smem, mcap, kBTailKeys);
+  TailSmem sm = carve_tail(smem, mcap, MAXK);
   const u64 *src = st->small ? c.keys + st->key_off : c.flat + st->flat_off;
   for (unsigned i = threadIdx.x; i < n; i += blockDim.x) sm.keys[i] = src[i];
   if (threadIdx.x == 0) {
@@ -656,7 +655,7 @@ __global__ void __launch_bounds__(kBTailThreads) k_btail(BCfg c, u64 mcap, int d
     hist[st->small ? 0 : t].off = off;
   }
   __syncthreads();
-  const unsigned used = cta_levels<kBTailThreads, kBTailKeys>(
+  const unsigned used = cta_levels<NT, MAXK>(
       sm, n, st->small ? 0 : (int)t, off, hist, c.gamma, c.L, c.seed,
                                    c.A0 + st->a0_off, c.arena + st->at_off, st->m0, st->at_words,
                                    c.flat + st->flat_off, &st->n_fb, &st->status);
@@ -757,7 +756,15 @@ __global__ void __launch_bounds__(kSectT) k_bsectors(const BOut *__restrict__ ou
 struct BatchTune {
   u64 Pmax = 128 * 1024;
   u64 Bset_max = 64;
+  u64 tail_keys = 8192;  // tail shape: 8192 keys on 512 threads, or 4096 on 256
 };
+
+static cudaError_t launch_btail(const BatchTune &t, const BCfg &c, u64 mcap, size_t smem, int dlim,
+                                cudaStream_t st) {
+  if (t.tail_keys == 4096) k_btail<256, 4096><<<c.S, 256, smem, st>>>(c, mcap, dlim);
+  else k_btail<512, 8192><<<c.S, 512, smem, st>>>(c, mcap, dlim);
+  return cudaGetLastError();
+}
 
 static std::mutex g_bmu;
 static std::map<u64, BatchTune> g_tuned;  // key: size class
@@ -869,10 +876,10 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   const size_t comp_b = split_smem_bytes((unsigned)tune.Bset_max, kTile + kIn) + kPmax / 8;
   const size_t comp_max = split_smem_bytes((unsigned)kBmax, kTile + kIn) + kPmax / 8;
   u64 mcap = 0;
-  u64 T = kBTailKeys;  // keep a tail's shared memory small enough for several CTAs per SM
-  while (T > 64 && tail_smem_bytes(level_bits(T, gamma), kBTailKeys) > 96 * 1024) T >>= 1;
+  u64 T = tune.tail_keys;  // keep a tail's shared memory small enough for several CTAs per SM
+  while (T > 64 && tail_smem_bytes(level_bits(T, gamma), tune.tail_keys) > 96 * 1024) T >>= 1;
   mcap = level_bits(T, gamma);
-  const size_t tail_b = tail_smem_bytes(mcap, kBTailKeys);
+  const size_t tail_b = tail_smem_bytes(mcap, tune.tail_keys);
   if (!attr) {
     MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)split_b));
@@ -880,8 +887,11 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
                                    (int)comp_max));
     MPHF_CUDA(cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(kPmax / 4)));
-    MPHF_CUDA(cudaFuncSetAttribute(k_btail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   100 * 1024));  // tail_b <= 96 KB by the choice of T above
+    // tail_b <= 96 KB by the choice of T above
+    MPHF_CUDA(cudaFuncSetAttribute(k_btail<512, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   100 * 1024));
+    MPHF_CUDA(cudaFuncSetAttribute(k_btail<256, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   100 * 1024));
     attr = true;
   }
   for (unsigned s = 0; s < S; s++) out[s] = nullptr;
@@ -1042,9 +1052,8 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
         nk_rec += 3;
       }
     }
-    k_btail<<<S, kBTailThreads, tail_b, st>>>(c, mcap, Dl + 1);
     nk_rec++;
-    return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
+    return launch_btail(tune, c, mcap, tail_b, Dl + 1, st) == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
   };
   // replay the recorded loop when the configuration is unchanged
   GraphCache &gc = g_ws.g;
@@ -1128,7 +1137,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     }
     {
       LaunchScope ls("btail", st);
-      k_btail<<<S, kBTailThreads, tail_b, st>>>(c, mcap, D + 1);
+      MPHF_CUDA(launch_btail(tune, c, mcap, tail_b, D + 1, st));
     }
     MPHF_CUDA(cudaGetLastError());
     MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
@@ -1316,12 +1325,14 @@ extern "C" int mphf_autotune_batched(const uint64_t *d_keys, const uint64_t *h_o
   const u64 total = h_offsets[S] - h_offsets[0];
   std::vector<BatchTune> cands;
   for (u64 P : {32768ull, 65536ull, 131072ull, 262144ull})
-    for (u64 B : {16ull, 64ull}) {
-      BatchTune t;
-      t.Pmax = P;
-      t.Bset_max = B;
-      cands.push_back(t);
-    }
+    for (u64 B : {16ull, 64ull})
+      for (u64 tk : {4096ull, 8192ull}) {
+        BatchTune t;
+        t.Pmax = P;
+        t.Bset_max = B;
+        t.tail_keys = tk;
+        cands.push_back(t);
+      }
   std::vector<mphf_t *> outs(S, nullptr);
   double best = 1e30;
   BatchTune bt;
@@ -1362,6 +1373,31 @@ extern "C" int mphf_autotune_batched(const uint64_t *d_keys, const uint64_t *h_o
   cudaEventDestroy(e1);
   g_tuned[size_class(S, total)] = bt;
   if (best_ms) *best_ms = best;
+  return MPHF_OK;
+}
+
+extern "C" int mphf_batched_tuning(uint32_t S, uint64_t total_keys, uint64_t *pmax,
+                                   uint64_t *bset_max, uint64_t *tail_keys) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  auto it = g_tuned.find(size_class(S, total_keys));
+  const BatchTune t = it != g_tuned.end() ? it->second : BatchTune();
+  if (pmax) *pmax = t.Pmax;
+  if (bset_max) *bset_max = t.Bset_max;
+  if (tail_keys) *tail_keys = t.tail_keys;
+  return it != g_tuned.end() ? MPHF_OK : MPHF_EINVAL;
+}
+
+extern "C" int mphf_batched_set_tuning(uint32_t S, uint64_t total_keys, uint64_t pmax,
+                                       uint64_t bset_max, uint64_t tail_keys) {
+  if (pmax < 4096 || pmax > kPmax || (pmax & (pmax - 1))) return MPHF_EINVAL;
+  if (bset_max < 1 || bset_max > kBmax) return MPHF_EINVAL;
+  if (tail_keys != 4096 && tail_keys != 8192) return MPHF_EINVAL;
+  BatchTune t;
+  t.Pmax = pmax;
+  t.Bset_max = bset_max;
+  t.tail_keys = tail_keys;
+  std::lock_guard<std::mutex> lk(g_bmu);
+  g_tuned[size_class(S, total_keys)] = t;
   return MPHF_OK;
 }
 

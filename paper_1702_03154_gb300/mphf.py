@@ -83,6 +83,8 @@ def lib():
         "mphf_build_batched": ([vp, vp, u32, dbl, u32, u64, vp, vp], i32),
         "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
         "mphf_batched_debug_config": ([dbl], i32),
+        "mphf_batched_tuning": ([u32, u64, pu64, pu64, pu64], i32),
+        "mphf_batched_set_tuning": ([u32, u64, u64, u64, u64], i32),
         "mphf_workspace_release": ([], None),
         "mphf_rank_table_noalloc": ([vp, u64, vp, vp, vp], i32),
         "mphf_lookup_multi": ([vp, vp, vp, vp, u32, vp], i32),
@@ -378,6 +380,23 @@ def autotune_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: 
                                      _stream_ptr(stream), ctypes.byref(best))
     _check(rc, "mphf_autotune_batched")
     return best.value
+
+
+def batched_tuning(S: int, total_keys: int) -> dict:
+    """What mphf_autotune_batched chose for S sets of total_keys keys (None if never tuned)."""
+    v = [ctypes.c_uint64() for _ in range(3)]
+    rc = lib().mphf_batched_tuning(int(S), int(total_keys), *[ctypes.byref(x) for x in v])
+    if rc != OK:
+        return None
+    return dict(zip(("bucket_width_max", "buckets_per_set_max", "tail_keys"), (x.value for x in v)))
+
+
+def batched_set_tuning(S: int, total_keys: int, bucket_width_max: int,
+                       buckets_per_set_max: int, tail_keys: int) -> None:
+    """Pins the batched build's choice for this size class (see batched_tuning)."""
+    _check(lib().mphf_batched_set_tuning(int(S), int(total_keys), int(bucket_width_max),
+                                         int(buckets_per_set_max), int(tail_keys)),
+           "mphf_batched_set_tuning")
 
 
 def batched_debug_config(cap_scale: float = 1.0):

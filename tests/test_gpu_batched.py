@@ -143,3 +143,40 @@ def test_batched_config4_full_size_sampled(M):
         k = M.to_u64(keys_d[a:b])
         o = oracle.build(k, gamma=2.0, levels=25, seed=0)
         same(hs[s], o)
+
+
+@pytest.mark.parametrize("pmax,bset,tail", [(4096, 1, 4096), (32768, 16, 4096), (262144, 2048, 8192),
+                                            (65536, 64, 8192)])
+def test_every_tuning_gives_the_oracle_result(M, pmax, bset, tail):
+    # the tuning moves bucket widths, buckets per set and the tail block shape;
+    # the function stays the paper's (narrow choices overflow and re-build)
+    keys, off = make_sets(30, 2000, 120000, 29)
+    S, total = len(off) - 1, int(off[-1])
+    M.batched_set_tuning(S, total, pmax, bset, tail)
+    assert M.batched_tuning(S, total) == {"bucket_width_max": pmax, "buckets_per_set_max": bset,
+                                          "tail_keys": tail}
+    hs = M.build_batched(dev(keys), off, gamma=2.0, levels=25, seed=8)
+    for s in (0, 7, 18, 29):
+        k = keys[int(off[s]):int(off[s + 1])]
+        o = oracle.build(k, gamma=2.0, levels=25, seed=8)
+        assert np.array_equal(hs[s].bits(), o.bits())
+        assert np.array_equal(hs[s].fallback(), o.fallback())
+        assert np.array_equal(M.to_u64(hs[s].lookup(dev(k))), o.lookup(k))
+    M.batched_set_tuning(S, total, 131072, 64, 8192)
+
+
+def test_autotune_choice_is_reported(M):
+    keys, off = make_sets(16, 1000, 90000, 31)
+    S, total = len(off) - 1, int(off[-1])
+    M.autotune_batched(dev(keys), off, gamma=2.0, levels=25, seed=1)
+    t = M.batched_tuning(S, total)
+    assert t["bucket_width_max"] in (32768, 65536, 131072, 262144)
+    assert t["buckets_per_set_max"] in (16, 64) and t["tail_keys"] in (4096, 8192)
+
+
+def test_bad_tuning_is_refused(M):
+    for args in ((4095, 64, 8192), (3 * 4096, 64, 8192), (524288, 64, 8192), (65536, 0, 8192),
+                 (65536, 4096, 8192), (65536, 64, 2048)):
+        with pytest.raises(M.MPHFError) as e:
+            M.batched_set_tuning(10, 10**6, *args)
+        assert e.value.code == M.EINVAL
