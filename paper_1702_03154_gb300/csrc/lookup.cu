@@ -49,14 +49,22 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
   return MPHF_NOT_FOUND;
 }
 
-template <int kSlots, int W>
+// kNarrow: every m_d < 2^32 and A short enough that bit g's word index
+// g >> kQShift is below 2^32 (A below 2^36 bits); then a probe's position
+// arithmetic is 32-bit: with off_d a multiple of 64,
+//   g >> kQShift = (off_d >> kQShift) + (p >> kQShift),  g & mask = p & mask.
+template <int kSlots, int W, bool kNarrow>
 __global__ void __launch_bounds__(kLookupThreads)
 k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
+  using LW = Lay<W>;
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
+  __shared__ unsigned tm32[MPHF_MAX_LEVELS], toq[MPHF_MAX_LEVELS];
   for (unsigned i = threadIdx.x; i < a.L_used; i += kLookupThreads) {
     ts[i] = t.s[i];
     tm[i] = t.m[i];
     toff[i] = t.off[i];
+    tm32[i] = (unsigned)t.m[i];
+    toq[i] = (unsigned)(t.off[i] >> LW::kQShift);
   }
   __syncthreads();
 
@@ -82,7 +90,29 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
   }
 
   for (;;) {
-    // refill retired slots from the warp's input stream (warp-uniform control)
+    // refill retired slots from the warp's input stream (warp-uniform
+    // control); while the current chunk holds a key for every free slot they
+    // are ranked lane by lane, slot 0 first, and filled in one pass
+    unsigned rk[kSlots], nfree = 0;
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      const unsigned need = __ballot_sync(0xffffffffu, !act[s]);
+      rk[s] = nfree + __popc(need & lt);
+      nfree += __popc(need);
+    }
+    if (nfree && cend - cursor >= nfree) {
+#pragma unroll
+      for (int s = 0; s < kSlots; s++) {
+        if (!act[s]) {
+          const u64 i = cursor + rk[s];
+          idx[s] = i;
+          x[s] = __ldcs(keys + i);
+          lvl[s] = 0;
+          act[s] = true;
+        }
+      }
+      cursor += nfree;
+    }
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       unsigned need = __ballot_sync(0xffffffffu, !act[s]);
@@ -116,14 +146,22 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
     if (!__any_sync(0xffffffffu, any)) break;
 
     // one probe per active slot: issue all loads, then resolve
-    using LW = Lay<W>;
     typename LW::Pos p[kSlots];
     typename LW::Data v[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (act[s]) {
         const unsigned d = lvl[s];
-        p[s] = LW::pos(toff[d] + level_pos(x[s], ts[d], tm[d]));
+        if (kNarrow) {
+          // reduce_range for m < 2^32, kept in 32 bits
+          const u64 h = mix64(x[s] ^ ts[d]);
+          const unsigned m32 = tm32[d];
+          const u64 lo = ((u64)(unsigned)h * m32) >> 32;
+          const unsigned pd = (unsigned)(((u64)(unsigned)(h >> 32) * m32 + lo) >> 32);
+          p[s] = LW::pos_q(toq[d] + (pd >> LW::kQShift), pd & ((1u << LW::kQShift) - 1u));
+        } else {
+          p[s] = LW::pos(toff[d] + level_pos(x[s], ts[d], tm[d]));
+        }
         v[s] = LW::load(a.S, p[s]);
       }
     }
@@ -161,20 +199,20 @@ static void fill_tables(const mphf_t *h, LookupArgs &a, LevelTable &t) {
 // for more, but measured on a GB300 3, 4 or 6 slots run slower than 2.)
 static constexpr int kUnitSlots = 2;
 
-template <int SLOTS, int W>
+template <int SLOTS, int W, bool NARROW>
 static int launch_lookup(const u64 *keys, u64 n, u64 *out, const LookupArgs &a,
                          const LevelTable &t, cudaStream_t s) {
   // one wave of resident CTAs: warps take chunks in a fixed order, so a
   // second wave would only start after the first has drained
   static unsigned mb = 0;
-  if (!mb) mb = resident_grid(k_lookup<SLOTS, W>, kLookupThreads, 0);
+  if (!mb) mb = resident_grid(k_lookup<SLOTS, W, NARROW>, kLookupThreads, 0);
   const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
   const unsigned per_block = kLookupThreads / 32;
   u64 grid = (nwarps_needed + per_block - 1) / per_block;
   if (grid > mb) grid = mb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  k_lookup<SLOTS, W><<<(unsigned)grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
+  k_lookup<SLOTS, W, NARROW><<<(unsigned)grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
@@ -183,9 +221,16 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   LookupArgs a;
   LevelTable t;
   fill_tables(h, a, t);
-  if (h->sw == kSectWordsMini) return launch_lookup<2, kSectWordsMini>(keys, n, out, a, t, s);
-  if (h->sw == kUnitBits) return launch_lookup<kUnitSlots, kUnitBits>(keys, n, out, a, t, s);
-  return launch_lookup<2, kSectWords>(keys, n, out, a, t, s);
+  bool narrow = (h->M >> 36) == 0;
+  for (uint32_t d = 0; d < h->L_used; d++) narrow = narrow && (h->m[d] >> 32) == 0;
+  if (h->sw == kSectWordsMini)
+    return narrow ? launch_lookup<2, kSectWordsMini, true>(keys, n, out, a, t, s)
+                  : launch_lookup<2, kSectWordsMini, false>(keys, n, out, a, t, s);
+  if (h->sw == kUnitBits)
+    return narrow ? launch_lookup<kUnitSlots, kUnitBits, true>(keys, n, out, a, t, s)
+                  : launch_lookup<kUnitSlots, kUnitBits, false>(keys, n, out, a, t, s);
+  return narrow ? launch_lookup<2, kSectWords, true>(keys, n, out, a, t, s)
+                : launch_lookup<2, kSectWords, false>(keys, n, out, a, t, s);
 }
 
 }  // namespace bbh

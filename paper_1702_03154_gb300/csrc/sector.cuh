@@ -170,11 +170,17 @@ __device__ __forceinline__ u64 sect_rank(const Sect<W> &v, const SectPos &p, uns
 //   Lay<W>::hit(v, p, w)             bit g of A (w: the A word, for rank)
 //   Lay<W>::rank(v, p, w, SB)        ones of A before bit g
 // ---------------------------------------------------------------------------
+//   Pos p = Lay<W>::pos_q(q, lo);    the same for g = q 2^kQShift + lo, q < 2^32
 template <int W>
 struct Lay {
   using Pos = SectPos;
   using Data = Sect<W>;
+  static constexpr unsigned kQShift = 5;  // q: the 32-bit word of A holding bit g
   static __device__ __forceinline__ Pos pos(u64 g) { return sect_pos<W>(g); }
+  static __device__ __forceinline__ Pos pos_q(unsigned q, unsigned lo) {
+    const unsigned t = div_sector<W>(q);
+    return SectPos{t, q - t * (unsigned)W, lo};
+  }
   static __device__ __forceinline__ Data load(const unsigned *__restrict__ S, const Pos &p) {
     return sect_load<W>(S, p.t);
   }
@@ -202,6 +208,11 @@ struct Lay<(int)kUnitBits> {
     const u64 q = g >> 4;
     const u64 u = (q >> 32) == 0 ? (u64)(__umulhi((unsigned)q, 0xAAAAAAABu) >> 1) : q / 3;
     return UnitPos{u, (unsigned)(g - u * kUnitBits)};
+  }
+  static constexpr unsigned kQShift = 4;  // q: the 16-bit piece of A holding bit g
+  static __device__ __forceinline__ Pos pos_q(unsigned q, unsigned lo) {
+    const unsigned u = __umulhi(q, 0xAAAAAAABu) >> 1;
+    return UnitPos{u, 16u * (q - 3u * u) + lo};
   }
   // an ordinary cached load: measured on a GB300, the same 8-byte probes with
   // an L1 no-allocate hint ran 1.6x slower
