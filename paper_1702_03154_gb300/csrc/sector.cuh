@@ -143,21 +143,44 @@ __device__ __forceinline__ SectPos sect_pos(u64 g) {
   return SectPos{t, (unsigned)(q - t * W), (unsigned)g & 31u};
 }
 
-template <int W>
-__device__ __forceinline__ unsigned sect_word(const Sect<W> &v, unsigned j) {
-  unsigned x = v.w[0];
+// Element j (< N, N a power of two) of a[0..N-1] by a tree of selects on j's
+// bits: N - 1 selects, where comparing j with every index costs a compare
+// and a select per element.
+template <int N>
+__device__ __forceinline__ unsigned select_tree(const unsigned (&a)[N], unsigned j) {
+  unsigned x[N];
 #pragma unroll
-  for (unsigned i = 1; i < (unsigned)W; i++) x = (j == i) ? v.w[i] : x;
-  return x;
+  for (int i = 0; i < N; i++) x[i] = a[i];
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1) {
+    const bool bit = (j & (unsigned)h) != 0u;
+#pragma unroll
+    for (int i = 0; i < N / (2 * h); i++) x[i] = bit ? x[2 * i + 1] : x[2 * i];
+  }
+  return x[0];
 }
 
-// Ones of A before bit (t, j, b), given the sector and SB.
+template <int W>
+__device__ __forceinline__ unsigned sect_word(const Sect<W> &v, unsigned j) {
+  unsigned a[W + 1];
+#pragma unroll
+  for (int i = 0; i < W; i++) a[i] = v.w[i];
+  a[W] = v.w[W - 1];
+  return select_tree<W + 1>(a, j);
+}
+
+// Ones of A before bit (t, j, b), given the sector and SB: the count of the
+// sector plus the prefix counts of its words, the one before word j picked by
+// the same select tree.
 template <int W>
 __device__ __forceinline__ u64 sect_rank(const Sect<W> &v, const SectPos &p, unsigned word,
                                          const u64 *__restrict__ SB) {
-  unsigned c = v.r;
+  unsigned pre[W + 1];
+  pre[0] = v.r;
 #pragma unroll
-  for (unsigned i = 0; i + 1 < (unsigned)W; i++) c += (i < p.j) ? __popc(v.w[i]) : 0u;
+  for (int i = 0; i + 1 < W; i++) pre[i + 1] = pre[i] + __popc(v.w[i]);
+  pre[W] = pre[W - 1];
+  unsigned c = select_tree<W + 1>(pre, p.j);
   c += __popc(word & ((1u << p.b) - 1u));
   const u64 k = p.t >> kSBShift;
   return (k ? __ldg(SB + k) : 0ull) + c;
