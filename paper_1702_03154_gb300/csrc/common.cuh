@@ -197,3 +197,13 @@ struct mphf {
   mphf_shared *shared = nullptr;  // set: S/SB/fb live in a batched arena
   bbh::DevBuf ldesc;     // device descriptor for multi-function lookups (made on first use)
 };
+
+namespace bbh {
+// Every level below 2^32 bits and A below 2^36 bits: a probe's position
+// arithmetic fits 32 bits (word index g >> 5 or piece index g >> 4 < 2^32).
+inline bool narrow_positions(const mphf *h) {
+  bool narrow = (h->M >> 36) == 0;
+  for (uint32_t d = 0; d < h->L_used; d++) narrow = narrow && (h->m[d] >> 32) == 0;
+  return narrow;
+}
+}  // namespace bbh

@@ -221,8 +221,7 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
   LookupArgs a;
   LevelTable t;
   fill_tables(h, a, t);
-  bool narrow = (h->M >> 36) == 0;
-  for (uint32_t d = 0; d < h->L_used; d++) narrow = narrow && (h->m[d] >> 32) == 0;
+  const bool narrow = narrow_positions(h);
   if (h->sw == kSectWordsMini)
     return narrow ? launch_lookup<2, kSectWordsMini, true>(keys, n, out, a, t, s)
                   : launch_lookup<2, kSectWordsMini, false>(keys, n, out, a, t, s);

@@ -37,6 +37,8 @@ struct LookupDev {
   u64 n_fb, N;
   uint32_t L_used, sw;  // levels, A words per sector
   u64 s[MPHF_MAX_LEVELS], m[MPHF_MAX_LEVELS], off[MPHF_MAX_LEVELS];
+  // for functions with narrow_positions: m_d and off_d >> kQShift in 32 bits
+  unsigned m32[MPHF_MAX_LEVELS], oq[MPHF_MAX_LEVELS];
 };
 
 struct ReqDev {
@@ -64,6 +66,9 @@ int ensure_lookup_desc(mphf_t *h) {
     d.s[i] = h->s[i];
     d.m[i] = h->m[i];
     d.off[i] = h->off[i];
+    d.m32[i] = (unsigned)h->m[i];
+    d.oq[i] = (unsigned)(h->off[i] >> (h->sw == kUnitBits ? Lay<(int)kUnitBits>::kQShift
+                                                          : Lay<(int)kSectWords>::kQShift));
   }
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, sizeof(d));
@@ -99,9 +104,12 @@ static constexpr unsigned kMultiChunk = 32 * 64;
 // Lookups of a batch of requests against different functions: the keys of all
 // requests form one index space [0, total); warps take chunks of it and keep
 // kMultiSlots query slots per lane, each slot carrying its request's function.
-template <int W>
+// NARROW: every function of the batch has narrow_positions (32-bit probe
+// arithmetic, as in k_lookup).
+template <int W, bool NARROW>
 __global__ void __launch_bounds__(kMultiThreads)
 k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
+  using LW = Lay<W>;
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const u64 nchunks = (total + kMultiChunk - 1) / kMultiChunk;
@@ -140,6 +148,37 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
     hd[s] = nullptr;
   }
   for (;;) {
+    // free slots ranked lane by lane, slot 0 first, filled in one pass while
+    // the chunk holds a key for each; the rest by the loop below
+    unsigned rk[kMultiSlots], nfree = 0;
+#pragma unroll
+    for (int s = 0; s < kMultiSlots; s++) {
+      const unsigned need = __ballot_sync(0xffffffffu, !act[s]);
+      rk[s] = nfree + __popc(need & lt);
+      nfree += __popc(need);
+    }
+    if (nfree && cend - cursor >= nfree) {
+#pragma unroll
+      for (int s = 0; s < kMultiSlots; s++) {
+        if (!act[s]) {
+          const u64 gi = cursor + rk[s];
+          unsigned q = rcur;
+          while (q + 1 < nreq && reqs[q + 1].start <= gi) q++;
+          const ReqDev rd = reqs[q];
+          x[s] = __ldcs(rd.keys + (gi - rd.start));
+          optr[s] = rd.out + (gi - rd.start);
+          hd[s] = rd.h;
+          lvl[s] = 0;
+          act[s] = true;
+        }
+      }
+      cursor += nfree;
+      if (cursor < total) {
+        unsigned q = rcur;
+        while (q + 1 < nreq && reqs[q + 1].start <= cursor) q++;
+        rcur = q;
+      }
+    }
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) {
       unsigned need = __ballot_sync(0xffffffffu, !act[s]);
@@ -183,7 +222,6 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
 #pragma unroll
     for (int s = 0; s < kMultiSlots; s++) any |= act[s];
     if (!__any_sync(0xffffffffu, any)) break;
-    using LW = Lay<W>;
     typename LW::Pos p[kMultiSlots];
     typename LW::Data v[kMultiSlots];
 #pragma unroll
@@ -191,7 +229,16 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
       if (act[s]) {
         const unsigned d = lvl[s];
         const LookupDev *h = hd[s];
-        p[s] = LW::pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        if (NARROW) {
+          const u64 hh = mix64(x[s] ^ __ldg(h->s + d));
+          const unsigned m32 = __ldg(h->m32 + d);
+          const u64 lo = ((u64)(unsigned)hh * m32) >> 32;
+          const unsigned pd = (unsigned)(((u64)(unsigned)(hh >> 32) * m32 + lo) >> 32);
+          p[s] = LW::pos_q(__ldg(h->oq + d) + (pd >> LW::kQShift),
+                           pd & ((1u << LW::kQShift) - 1u));
+        } else {
+          p[s] = LW::pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        }
         v[s] = LW::load(h->S, p[s]);
       }
     }
@@ -212,19 +259,26 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
   }
 }
 
-template <int W>
-static int launch_multi_w(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
-  if (total == 0 || nreq == 0) return MPHF_OK;
+template <int W, bool NARROW>
+static int launch_multi_wn(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
   const u64 chunks = (total + kMultiChunk - 1) / kMultiChunk;
   u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
   static u64 maxb = 0;  // one wave of resident CTAs
-  if (!maxb) maxb = resident_grid(k_lookup_multi<W>, kMultiThreads, 0);
+  if (!maxb) maxb = resident_grid(k_lookup_multi<W, NARROW>, kMultiThreads, 0);
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup_multi", s);
-  k_lookup_multi<W><<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total);
+  k_lookup_multi<W, NARROW><<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
+}
+
+template <int W>
+static int launch_multi_w(const ReqDev *d_reqs, unsigned nreq, u64 total, bool narrow,
+                          cudaStream_t s) {
+  if (total == 0 || nreq == 0) return MPHF_OK;
+  return narrow ? launch_multi_wn<W, true>(d_reqs, nreq, total, s)
+                : launch_multi_wn<W, false>(d_reqs, nreq, total, s);
 }
 
 // Request table of a batch, grouped by layout: the default-layout requests
@@ -238,6 +292,7 @@ __host__ inline int layout_group(unsigned sw) {
 struct TableGroups {
   unsigned n[kLayouts] = {0, 0, 0};
   u64 total[kLayouts] = {0, 0, 0};
+  bool narrow[kLayouts] = {true, true, true};  // every function of the group
 };
 template <class GetH, class GetKeys, class GetOut, class GetN>
 static TableGroups fill_table(ReqDev *t, size_t nreq, GetH geth, GetKeys getk, GetOut geto,
@@ -255,16 +310,18 @@ static TableGroups fill_table(ReqDev *t, size_t nreq, GetH geth, GetKeys getk, G
       r.start = g.total[grp];
       g.total[grp] += getn(i);
       g.n[grp]++;
+      g.narrow[grp] = g.narrow[grp] && narrow_positions(h);
     }
   }
   return g;
 }
 
 static int launch_lookup_multi(const ReqDev *d_reqs, const TableGroups &g, cudaStream_t s) {
-  int rc = launch_multi_w<kSectWords>(d_reqs, g.n[0], g.total[0], s);
-  if (rc == MPHF_OK) rc = launch_multi_w<kSectWordsMini>(d_reqs + g.n[0], g.n[1], g.total[1], s);
+  int rc = launch_multi_w<kSectWords>(d_reqs, g.n[0], g.total[0], g.narrow[0], s);
   if (rc == MPHF_OK)
-    rc = launch_multi_w<kUnitBits>(d_reqs + g.n[0] + g.n[1], g.n[2], g.total[2], s);
+    rc = launch_multi_w<kSectWordsMini>(d_reqs + g.n[0], g.n[1], g.total[1], g.narrow[1], s);
+  if (rc == MPHF_OK)
+    rc = launch_multi_w<kUnitBits>(d_reqs + g.n[0] + g.n[1], g.n[2], g.total[2], g.narrow[2], s);
   return rc;
 }
 
