@@ -357,6 +357,12 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     const u64 e0 = (u64)(u - ubase) * kIn + (u64)threadIdx.x * kInPT;
     const unsigned *pe = parena + (u64)b * lv.cap + e0;
     const u64 *ke = arena + (u64)b * lv.cap + e0;
+    // pull this thread's entries of the next unit of the bucket into L2 now, so
+    // that their loads one unit later do not wait for HBM
+    if (u + 1 < u1 && u + 1 < bnext && e0 + kIn < nk) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ke + kIn));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(pe + kIn));
+    }
     unsigned pk[kInPT];
     u64 xk[kInPT];
     if (e0 + kInPT <= nk) {
