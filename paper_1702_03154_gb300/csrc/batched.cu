@@ -556,6 +556,11 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
     const u64 e0 = (u64)(u - ubase) * kIn + (u64)threadIdx.x * kInPT;
     const unsigned *pe = c.XP[sl] + b_kbase + e0;
     const u64 *ke = c.X[sl] + b_kbase + e0;
+    // next unit of the bucket into L2 now (its loads come one unit later)
+    if (u + 1 < u1 && u + 1 < bnext && e0 + kIn < nk) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ke + kIn));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(pe + kIn));
+    }
     unsigned pk[kInPT];
     u64 xk[kInPT];
     if (e0 + kInPT <= nk) {
