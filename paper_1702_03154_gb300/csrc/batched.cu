@@ -124,6 +124,7 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
   __shared__ u64 t_m, t_base;  // one bucketed set in the tile: its m and first bucket - gb0
   __shared__ unsigned t_sh, t_one;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  split_clear(sm, (unsigned)kBmax);  // ordered by the first tile's barrier
   const u64 s0 = level_seed(c.seed, 0);
   const u64 ntiles = ceil_div(total, kTile);
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -207,7 +208,7 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
         }
       }
     }
-    multisplit_write<true>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
+    multisplit_write<true, false>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
                            PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], t_gb0}, c.status);
   }
 }
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
   // destinations of one flush: the next-level buckets of one set (at most
   // Bset_max); the stage holds kTile + kIn survivors of that set
   SplitSmem sm = carve_split(smem, (unsigned)c.Bset_max, kTile + kIn);
+  split_clear(sm, (unsigned)c.Bset_max);  // every flush follows a block barrier
   u64 *segA = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)c.Bset_max, kTile + kIn));
   u64 *stage = sm.sorted;
   const u64 s_n = level_seed(c.seed, d + 1);
@@ -481,10 +483,10 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
     }
     __syncthreads();  // the staging area is reused by the writer
     if (flat)
-      multisplit_write<false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
+      multisplit_write<false, false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
                               SetFlatDest{&st->n_flat, st->flat_off, st->flat_cap}, &st->status);
     else
-      multisplit_write<true>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
+      multisplit_write<true, false>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
                              SetBucketDest{c.cnt[nl], nx.bbase, nx.aoff, nx.cap}, &st->status);
   };
 

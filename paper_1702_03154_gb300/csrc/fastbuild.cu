@@ -44,6 +44,8 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
   const FLevel lv = meta->lv[0];
   const unsigned nb = (unsigned)lv.B;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
+  split_clear(sm, nb);
+  __syncthreads();
   u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
   auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * kTT + threadIdx.x) + (k & 1); };
   const u64 s0 = level_seed(cfg.seed, 0);
@@ -94,7 +96,7 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
       dst[k] = (unsigned)(p >> sh);
       lp[k] = (unsigned)p & mask;
     }
-    multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
+    multisplit_write<true, true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
                            &meta->status);
   }
   cp_async_wait0();
@@ -308,6 +310,7 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     for (u64 w = w0 + threadIdx.x; w < wend; w += kTT) segA[w - w0] = Alev[w];
   };
   if (threadIdx.x < 3) scnt[threadIdx.x] = 0;
+  split_clear(sm, nb);
   load_segA(b);
   __syncthreads();
 
@@ -331,10 +334,10 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     }
     __syncthreads();  // the staging area is reused by the writer
     if (flat)
-      multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+      multisplit_write<false, true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                               &meta->status);
     else
-      multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+      multisplit_write<true, true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                              &meta->status);
   };
 

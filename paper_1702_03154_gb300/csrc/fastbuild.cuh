@@ -183,40 +183,71 @@ struct UniformDest {
 // capacity.  Slots are reserved with one atomicAdd per non-empty destination;
 // the entries of one destination leave as one contiguous run.  Entries past a
 // bucket's capacity are dropped and ST_OVERFLOW is raised.
-template <bool WITH_POS, class Dest>
+template <bool WITH_POS, bool GROUPED, class Dest>
 __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
                                  const unsigned (&dst)[kKPT], const bool (&ok)[kKPT], unsigned nb,
                                  const SplitSmem &sm, u64 *__restrict__ arena,
                                  unsigned *__restrict__ parena, const Dest &dest,
                                  unsigned *__restrict__ status) {
-  for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;
-  __syncthreads();
+  // sm.cnt[0, nb) is zero on entry (split_clear before the first call; every
+  // call clears what it used while writing out, behind its last barrier)
   unsigned rk[kKPT];
 #pragma unroll
   for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
   __syncthreads();
   // exclusive scan of the counts (each thread owns a run of entries), then
   // reserve each destination's slots and precompute where its run goes
+  // GROUPED: nb <= kBmax, so a thread owns at most kBmax / kTT destinations,
+  // and their reservations are issued together instead of one round trip
+  // after another (more registers: kernels already at their register limit
+  // take the plain loop)
   const unsigned per = (nb + kTT - 1) / kTT;
   const unsigned lo = threadIdx.x * per;
   const unsigned hi = min(lo + per, nb);
-  unsigned s = 0;
-  for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
   unsigned total;
-  unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
-  for (unsigned i = lo; i < hi; i++) {
-    const unsigned c = sm.cnt[i];
-    u64 b0 = 0, room = 0, base = 0;
-    if (c) {
-      const DestRun r = dest(i);
-      b0 = atomicAdd(r.counter, (u64)c);
-      room = b0 < r.cap ? r.cap - b0 : 0;
-      base = r.base;
+  if (GROUPED) {
+    constexpr unsigned kPer = (unsigned)(kBmax / kTT);
+    static_assert(kBmax % kTT == 0, "destinations per thread");
+    unsigned c[kPer], s = 0;
+#pragma unroll
+    for (unsigned k = 0; k < kPer; k++) {
+      c[k] = lo + k < hi ? sm.cnt[lo + k] : 0u;
+      s += c[k];
     }
-    sm.cnt[i] = pre;
-    sm.lim[i] = pre + (unsigned)(room < c ? room : c);
-    sm.dbase[i] = base + b0 - pre;
-    pre += c;
+    unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+    u64 b0[kPer];
+#pragma unroll
+    for (unsigned k = 0; k < kPer; k++)
+      b0[k] = c[k] ? atomicAdd(dest(lo + k).counter, (u64)c[k]) : 0;
+#pragma unroll
+    for (unsigned k = 0; k < kPer; k++) {
+      if (lo + k < hi) {
+        const DestRun r = dest(lo + k);
+        const u64 room = c[k] && b0[k] < r.cap ? r.cap - b0[k] : 0;
+        sm.cnt[lo + k] = pre;
+        sm.lim[lo + k] = pre + (unsigned)(room < c[k] ? room : c[k]);
+        sm.dbase[lo + k] = (c[k] ? r.base + b0[k] : 0) - pre;
+        pre += c[k];
+      }
+    }
+  } else {
+    unsigned s = 0;
+    for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
+    unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+    for (unsigned i = lo; i < hi; i++) {
+      const unsigned c = sm.cnt[i];
+      u64 b0 = 0, room = 0, base = 0;
+      if (c) {
+        const DestRun r = dest(i);
+        b0 = atomicAdd(r.counter, (u64)c);
+        room = b0 < r.cap ? r.cap - b0 : 0;
+        base = r.base;
+      }
+      sm.cnt[i] = pre;
+      sm.lim[i] = pre + (unsigned)(room < c ? room : c);
+      sm.dbase[i] = base + b0 - pre;
+      pre += c;
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -239,7 +270,14 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
       atomicOr(status, ST_OVERFLOW);
     }
   }
+  for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;  // last read before the scatter
   __syncthreads();
+}
+
+// Zero the destination counts before a kernel's first multisplit_write (the
+// caller synchronises the block before that call).
+__device__ __forceinline__ void split_clear(const SplitSmem &sm, unsigned nb_cap) {
+  for (unsigned i = threadIdx.x; i < nb_cap; i += kTT) sm.cnt[i] = 0;
 }
 
 // sorted_cap >= kTile entries of `sorted` (a caller may stage more keys there
