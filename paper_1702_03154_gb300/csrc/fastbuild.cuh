@@ -151,6 +151,34 @@ __device__ __forceinline__ unsigned block_scan_u32(unsigned v, unsigned *red, un
   return before + x - v;
 }
 
+// The same scan with two barriers instead of four, for callers that put a
+// block barrier between one call's reads of red and the next call's writes.
+template <int NT>
+__device__ __forceinline__ unsigned block_scan_u32_fenced(unsigned v, unsigned *red,
+                                                          unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < NT / 32 ? red[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) red[lane] = w;
+  }
+  __syncthreads();
+  *total = red[NT / 32 - 1];
+  return (warp ? red[warp - 1] : 0u) + x - v;
+}
+
 // Shared memory of the multisplit writer.
 struct SplitSmem {
   unsigned *cnt;         // [nb] entries per destination in this tile, then their local start
@@ -196,7 +224,9 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
   __syncthreads();
   // exclusive scan of the counts (each thread owns a run of entries), then
-  // reserve each destination's slots and precompute where its run goes
+  // reserve each destination's slots and precompute where its run goes; sm.red
+  // is only touched by this scan, and the barriers below separate its reads
+  // from the next call's writes
   // GROUPED: nb <= kBmax, so a thread owns at most kBmax / kTT destinations,
   // and their reservations are issued together instead of one round trip
   // after another (more registers: kernels already at their register limit
@@ -214,7 +244,7 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
       c[k] = lo + k < hi ? sm.cnt[lo + k] : 0u;
       s += c[k];
     }
-    unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+    unsigned pre = block_scan_u32_fenced<kTT>(s, sm.red, &total);
     u64 b0[kPer];
 #pragma unroll
     for (unsigned k = 0; k < kPer; k++)
@@ -233,7 +263,7 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   } else {
     unsigned s = 0;
     for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
-    unsigned pre = block_scan_u32<kTT>(s, sm.red, &total);
+    unsigned pre = block_scan_u32_fenced<kTT>(s, sm.red, &total);
     for (unsigned i = lo; i < hi; i++) {
       const unsigned c = sm.cnt[i];
       u64 b0 = 0, room = 0, base = 0;
