@@ -120,7 +120,7 @@ __device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
     meta->levels_used = d + 1;
   } else if ((uint32_t)(d + 1) == cfg.L) {
     nx.mode = LM_FLAT;  // fallback
-    if (d > 0 && nn > cfg.flat_cap) atomicOr(&meta->status, ST_OVERFLOW);
+    if (nn > cfg.flat_cap) atomicOr(&meta->status, ST_OVERFLOW);
   } else if (nn <= cfg.T) {
     nx.mode = LM_FLAT;  // tail
     nx.m = level_bits(nn, cfg.gamma);
@@ -128,9 +128,11 @@ __device__ void finish_level(FastMeta *meta, int d, const FastCfg &cfg) {
     size_bucketed(nx, nn, cfg.gamma, cfg.Pmin, cfg.Pmax, cfg.Btarget, cfg.cap_scale);
     nx.off = vl[d].off + m;
     nx.mode = LM_BUCKETED;
-    // level 1's arena is allocated by the host from these sizes (after level 0)
+    // the arenas were allocated before level 0 ran (level 1's from a bound on
+    // |F_1|): a level that does not fit sends the build to the unbucketed path
     const u64 acap = ((d + 1) & 1) ? cfg.capY : cfg.capX;
-    if (nx.B > cfg.Bmax || (d > 0 && nx.B * nx.cap > acap)) {
+    const bool a_fits = ((nx.off - cfg.m0) >> 6) + (nx.m >> 6) <= cfg.arena_words;
+    if (nx.B > cfg.Bmax || nx.B * nx.cap > acap || !a_fits) {
       atomicOr(&meta->status, ST_OVERFLOW);
       nx.mode = LM_NONE;
     }
@@ -565,6 +567,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
   cfg.m0 = m0;
   FastMeta *meta = nullptr;
   int dlim = 0;
+  int D = 1;  // levels (from 0) launched before the first look at the device's progress
   size_t comp_bytes = g_compact_bytes;  // compaction's shared memory for this build
 
 #define FTRY(x)                    \
@@ -626,6 +629,51 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
     cfg.X = (u64 *)sc.X.p;
     cfg.cntX = (u64 *)sc.cntX.p;
     cfg.cntY = (u64 *)sc.cntY.p;
+    {
+      // Level 1 is sized on the device by the last CTA of level 0's fill; its
+      // buffers come from a bound on |F_1| so that no host round trip sits
+      // between the levels.  |F_1| (keys not alone in their bin at level 0)
+      // has mean N - N (1 - 1/m_0)^(N-1) and a standard deviation below
+      // sqrt(N); the bound adds 10 of those.  With n1 <= n1_hi, any level
+      // size the device picks (B buckets of cap slots, B <= Bb) fits
+      //   capY = n1_hi + Pmax + 8 sqrt(Bb (n1_hi + Pmax)) + 64 Bb (+ rounding),
+      // since the bucket means sum to at most n + P and sqrt is concave.  A
+      // level that does not fit anyway (duplicate-heavy input) is caught by
+      // finish_level and the build is redone by the unbucketed path.
+      const double ev1 = expect_next((double)N, gamma);  // E|F_1|
+      u64 n1_hi = (u64)ceil(ev1 + 10.0 * sqrt((double)N) + 256.0);
+      if (n1_hi > N) n1_hi = N;
+      const u64 m1_hi = level_bits(n1_hi, gamma);
+      u64 Bb = ceil_div(m1_hi, cfg.Pmax);
+      if (Bb < cfg.Btarget) Bb = cfg.Btarget;
+      const double tot = (double)(n1_hi + cfg.Pmax);
+      cfg.capY = (u64)(cfg.cap_scale * (tot + 8.0 * sqrt((double)Bb * tot) + 64.0 * (double)Bb)) +
+                 4 * Bb + 64;
+      FTRY(dev_alloc(sc.Y, cfg.capY * 8, st));
+      FTRY(dev_alloc(sc.YP, cfg.capY * 4, st));
+      cfg.Y = (u64 *)sc.Y.p;
+      cfg.YP = (unsigned *)sc.YP.p;
+      cfg.flat_cap = n1_hi < (1ull << 22) ? n1_hi : (1ull << 22);
+      if (cfg.flat_cap < T) cfg.flat_cap = T;
+      FTRY(dev_alloc(sc.flat, cfg.flat_cap * 8, st));
+      cfg.flat = (u64 *)sc.flat.p;
+      cfg.arena_words = (u64)(L > 1 ? L - 1 : 1) * (m1_hi / 64);
+      FTRY(dev_alloc(sc.arena, cfg.arena_words * 8, st));
+      cfg.arena = (u64 *)sc.arena.p;
+      // destination buckets of any compaction: level 1 has the most keys of
+      // the levels >= 1, and a smaller level never takes more than Btarget
+      // buckets (its width shrinks first), so Bb bounds them all; the
+      // compaction checks it and falls back if ever exceeded
+      cfg.nbcap = Bb < kBmax ? Bb : kBmax;
+      comp_bytes = split_smem_bytes((unsigned)cfg.nbcap, kTile + kIn) + kPmax / 8;
+      // predicted number of bucketed levels after level 0
+      double e = ev1;
+      D = 1;
+      while (e > (double)T && D < (int)L) {
+        e = expect_next(e, gamma);
+        D++;
+      }
+    }
     FCUDA(cudaMemsetAsync(sc.cntX.p, 0, kBmax * 8, st));
     FCUDA(cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st));
     // Level-0 partition.  Keys still arriving from the host are partitioned
@@ -651,52 +699,7 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
                        (size_t)(hm.lv[0].P / 4), st>>>(meta, 0, cfg);
     }
     FCUDA(cudaGetLastError());
-    FCUDA(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, st));
-    FCUDA(cudaStreamSynchronize(st));
-    if (hm.status & ST_OVERFLOW) {
-      *fallback_needed = true;
-      sc.release(st);
-      return MPHF_OK;
-    }
-    if (hm.status) {
-      rc = MPHF_EINTERNAL;
-      goto fail;
-    }
-    const u64 n1 = hm.lv[1].n;
-    if (n1 > 0) {
-      const u64 m1 = level_bits(n1, gamma);
-      cfg.capY = hm.lv[1].mode == LM_BUCKETED ? hm.lv[1].B * hm.lv[1].cap : 0;
-      if (cfg.capY) {
-        FTRY(dev_alloc(sc.Y, cfg.capY * 8, st));
-        FTRY(dev_alloc(sc.YP, cfg.capY * 4, st));
-        cfg.Y = (u64 *)sc.Y.p;
-        cfg.YP = (unsigned *)sc.YP.p;
-      }
-      cfg.flat_cap = n1 < (1ull << 22) ? n1 : (1ull << 22);
-      if (cfg.flat_cap < T) cfg.flat_cap = T;
-      FTRY(dev_alloc(sc.flat, cfg.flat_cap * 8, st));
-      cfg.flat = (u64 *)sc.flat.p;
-      cfg.arena_words = (u64)(L > 1 ? L - 1 : 1) * (m1 / 64);
-      FTRY(dev_alloc(sc.arena, cfg.arena_words * 8, st));
-      cfg.arena = (u64 *)sc.arena.p;
-      // Destination buckets of any compaction: level 1 has the most keys of the
-      // levels >= 1, and a smaller level never takes more than Btarget buckets
-      // (its width shrinks first), so max(B_1, Btarget) bounds them all; the
-      // compaction checks it and falls back if ever exceeded.
-      {
-        u64 nbc = hm.lv[1].mode == LM_BUCKETED ? hm.lv[1].B : 1;
-        if (nbc < cfg.Btarget) nbc = cfg.Btarget;
-        if (nbc > kBmax) nbc = kBmax;
-        cfg.nbcap = nbc;
-        comp_bytes = split_smem_bytes((unsigned)nbc, kTile + kIn) + kPmax / 8;
-      }
-      // predicted number of bucketed levels after level 0
-      double e = (double)n1;
-      int D = 1;
-      while (e > (double)T && D < (int)L) {
-        e = expect_next(e, gamma);
-        D++;
-      }
+    {
       for (int round = 0; round < 64; round++) {
         for (; dlim < D && dlim < (int)L; dlim++) {
           {
@@ -719,9 +722,6 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
         if (hm.status || hm.tail_done || dlim >= (int)L) break;
         D = dlim + 2;
       }
-    } else {
-      hm.tail_done = 1;
-      hm.levels_used = 1;
     }
   }
   if (N <= T) {
