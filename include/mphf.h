@@ -89,6 +89,23 @@ int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t l
                     uint64_t seed, void *stream, mphf_t **out);
 
 /*
+ * mphf_build_host followed by mphf_lookup_host in one call, with the host
+ * link kept busy: the queries are copied right behind the keys while the
+ * levels after the first are built, and each chunk of queries is looked up
+ * as soon as it has landed while the indices of the previous chunk are
+ * copied back.  Same results as the two calls.
+ *   h_keys, n        the key set (host memory; page-locked is faster)
+ *   h_queries, nq    the keys to look up (host), h_out receives nq indices
+ *                    (host), as mphf_lookup writes them
+ *   out              receives the function (release with mphf_free)
+ * Waits for the results.  Errors as mphf_build and mphf_lookup; on error
+ * nothing is leaked and *out is NULL.
+ */
+int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t levels,
+                           uint64_t seed, const uint64_t *h_queries, uint64_t nq,
+                           uint64_t *h_out, void *stream, mphf_t **out);
+
+/*
  * Build S independent functions at once, one per key set (the same method
  * and conventions as mphf_build, applied to each set separately; set s gets
  * exactly the function mphf_build would give it with the same arguments).

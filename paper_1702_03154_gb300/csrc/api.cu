@@ -127,6 +127,18 @@ int KeyFeed::ensure(u64 upto, cudaStream_t st) {
   }
   MPHF_CUDA(cudaEventRecord(ev, cs));
   MPHF_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  if (issued == n && hq && !q_issued) return issue_queries();
+  return MPHF_OK;
+}
+
+int KeyFeed::issue_queries() {
+  q_issued = true;
+  u64 i = 0;
+  for (u64 c0 = 0; c0 < nq; c0 += qchunk, i++) {
+    const u64 c = nq - c0 < qchunk ? nq - c0 : qchunk;
+    MPHF_CUDA(cudaMemcpyAsync(dq + c0, hq + c0, c * 8, cudaMemcpyHostToDevice, cs));
+    MPHF_CUDA(cudaEventRecord(qev[i], cs));
+  }
   return MPHF_OK;
 }
 

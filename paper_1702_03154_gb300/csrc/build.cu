@@ -586,6 +586,108 @@ extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma,
   return rc;
 }
 
+// Build and query in one call, with every transfer on the host link kept
+// busy: the keys stream in chunk by chunk behind the level-0 partition (as in
+// mphf_build_host), the queries follow them on the same copy stream while
+// the remaining levels are built, and once the function exists the lookup of
+// query chunk c runs as soon as that chunk has landed while the indices of
+// chunk c-1 stream back on a third stream.
+extern "C" int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double gamma,
+                                      uint32_t levels, uint64_t seed, const uint64_t *h_queries,
+                                      uint64_t nq, uint64_t *h_out, void *stream, mphf_t **out) {
+  if (!out) return MPHF_EINVAL;
+  *out = nullptr;
+  if (!(gamma >= 1.0) || isinf(gamma) || levels < 1 || levels > MPHF_MAX_LEVELS ||
+      (n > 0 && !h_keys) || (nq > 0 && (!h_queries || !h_out)))
+    return MPHF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const u64 qchunk = nq ? (feed_chunk(nq) ? feed_chunk(nq) : nq) : 1;
+  const u64 nqc = nq ? (nq + qchunk - 1) / qchunk : 0;
+  std::vector<cudaEvent_t> qev(nqc, nullptr);
+  DevBuf kb, qb, ob;
+  KeyFeed f;
+  cudaStream_t co = nullptr;
+  cudaEvent_t ev_k = nullptr;
+  cudaError_t e = cudaSuccess;
+  int rc = dev_alloc(kb, n * 8, st);
+  if (rc == MPHF_OK) rc = dev_alloc(qb, nq * 8, st);
+  if (rc == MPHF_OK) rc = dev_alloc(ob, nq * 8, st);
+  if (rc == MPHF_OK) {
+    f.h = (const u64 *)h_keys;
+    f.d = (u64 *)kb.p;
+    f.n = n;
+    f.chunk = feed_chunk(n);
+    f.hq = (const u64 *)h_queries;
+    f.dq = (u64 *)qb.p;
+    f.nq = nq;
+    f.qchunk = qchunk;
+    f.qev = qev.data();
+    e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k, cudaEventDisableTiming);
+    for (u64 i = 0; i < nqc && e == cudaSuccess; i++)
+      e = cudaEventCreateWithFlags(&qev[i], cudaEventDisableTiming);
+    // the copies must not start before the buffers' allocation in st's order
+    if (e == cudaSuccess) e = cudaEventRecord(f.ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(f.cs, f.ev, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "mphf_build_lookup_host (streams)");
+  }
+  if (rc == MPHF_OK) rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out, &f);
+  if (rc == MPHF_OK && !f.q_issued) rc = f.issue_queries();
+  if (rc == MPHF_OK && nq) {
+    // chunk c: wait for its copy, look it up; its indices leave on co after
+    // the lookup of chunk c+1 is queued
+    u64 prev0 = 0, prevn = 0, i = 0;
+    u64 *dq = (u64 *)qb.p, *dout = (u64 *)ob.p;
+    for (u64 c0 = 0; c0 < nq && rc == MPHF_OK && e == cudaSuccess; c0 += qchunk, i++) {
+      const u64 cn = nq - c0 < qchunk ? nq - c0 : qchunk;
+      e = cudaStreamWaitEvent(st, qev[i], 0);
+      if (e != cudaSuccess) break;
+      rc = mphf_lookup(*out, (const uint64_t *)(dq + c0), cn, (uint64_t *)(dout + c0), stream);
+      if (rc != MPHF_OK) break;
+      e = cudaEventRecord(ev_k, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(co, ev_k, 0);
+      if (e == cudaSuccess && prevn)
+        e = cudaMemcpyAsync(h_out + prev0, dout + prev0, prevn * 8, cudaMemcpyDeviceToHost, co);
+      prev0 = c0;
+      prevn = cn;
+    }
+    if (e == cudaSuccess && rc == MPHF_OK && prevn)
+      e = cudaMemcpyAsync(h_out + prev0, dout + prev0, prevn * 8, cudaMemcpyDeviceToHost, co);
+    if (e != cudaSuccess && rc == MPHF_OK) rc = cuda_fail(e, "mphf_build_lookup_host");
+  }
+  // everything enqueued on the side streams is ordered before the frees
+  if (f.cs && f.ev) {
+    cudaEventRecord(f.ev, f.cs);
+    cudaStreamWaitEvent(st, f.ev, 0);
+  }
+  if (co && ev_k) {
+    cudaEventRecord(ev_k, co);
+    cudaStreamWaitEvent(st, ev_k, 0);
+  }
+  if (!f.ev || !ev_k) {  // setup failed part-way: nothing can order the streams
+    if (f.cs) cudaStreamSynchronize(f.cs);
+    if (co) cudaStreamSynchronize(co);
+  }
+  dev_free(ob, st);
+  dev_free(qb, st);
+  dev_free(kb, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (rc == MPHF_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "mphf_build_lookup_host");
+  for (cudaEvent_t q : qev)
+    if (q) cudaEventDestroy(q);
+  if (f.ev) cudaEventDestroy(f.ev);
+  if (ev_k) cudaEventDestroy(ev_k);
+  if (f.cs) cudaStreamDestroy(f.cs);
+  if (co) cudaStreamDestroy(co);
+  if (rc != MPHF_OK && *out) {
+    mphf_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
 extern "C" int mphf_debug_config(int path, double cap_scale) {
   if (path < 0 || path > 1 || !(cap_scale > 0.0) || cap_scale > 16.0) return MPHF_EINVAL;
   bbh::g_build_path = path;

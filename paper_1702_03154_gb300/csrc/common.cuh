@@ -158,7 +158,16 @@ struct KeyFeed {
   u64 issued = 0;          // keys whose copy is enqueued (and awaited by the main stream)
   cudaStream_t cs = nullptr;
   cudaEvent_t ev = nullptr;
+  // Optional second array copied on cs right behind the last key chunk, one
+  // event per chunk (mphf_build_lookup_host: the queries cross the host link
+  // while the levels are built).  The main stream never waits for them here.
+  const u64 *hq = nullptr;
+  u64 *dq = nullptr;
+  u64 nq = 0, qchunk = 0;        // qchunk: keys per query chunk (> 0)
+  cudaEvent_t *qev = nullptr;    // ceil(nq / qchunk) events
+  bool q_issued = false;
   int ensure(u64 upto, cudaStream_t st);
+  int issue_queries();
 };
 // Keys per chunk for n keys (0 = copy in one piece: too few keys to pipeline).
 u64 feed_chunk(u64 n);

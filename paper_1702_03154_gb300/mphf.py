@@ -65,6 +65,7 @@ def lib():
         "mphf_build_host": ([vp, u64, dbl, u32, u64, vp, pvp], i32),
         "mphf_lookup": ([vp, vp, u64, vp, vp], i32),
         "mphf_lookup_host": ([vp, vp, u64, vp, vp], i32),
+        "mphf_build_lookup_host": ([vp, u64, dbl, u32, u64, vp, u64, vp, vp, pvp], i32),
         "mphf_bits_per_key": ([vp], dbl),
         "mphf_device_bytes": ([vp], u64),
         "mphf_free": ([vp], None),
@@ -173,6 +174,26 @@ class MPHF:
                                    int(seed) & NOT_FOUND, _stream_ptr(stream), ctypes.byref(h))
         _check(rc, "mphf_build_host")
         return cls(h)
+
+    @classmethod
+    def build_lookup_host(cls, keys, queries, out: Optional[np.ndarray] = None,
+                          gamma: float = 2.0, levels: int = 25, seed: int = 0, stream=None):
+        """Build from host keys and look up host queries in one pipelined call.
+
+        Returns (function, indices): the same as build_host then lookup_host."""
+        a = keys if isinstance(keys, np.ndarray) and keys.dtype == np.uint64 else _host_u64(keys)
+        qa = (queries if isinstance(queries, np.ndarray) and queries.dtype == np.uint64
+              else _host_u64(queries))
+        if out is None:
+            out = np.empty(qa.size, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_lookup_host(_host_ptr(keys, a) if a.size else None, a.size,
+                                          float(gamma), int(levels), int(seed) & NOT_FOUND,
+                                          _host_ptr(queries, qa) if qa.size else None, qa.size,
+                                          _host_ptr(out, out) if qa.size else None,
+                                          _stream_ptr(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_lookup_host")
+        return cls(h), out
 
     @classmethod
     def build_nodisk(cls, keys, gamma: float = 2.0, levels: int = 25, seed: int = 0,

@@ -312,3 +312,45 @@ def test_large_fallback_at_scale(M):
     keys = inputs.splitmix64_keys(2 * 10**6, 122)
     g, o = check(M, keys, 1.0, 1, 13)
     assert g.num_fallback > 10**6
+
+
+@pytest.mark.parametrize("n,nq,pinned", [((1 << 22) + 12345, (1 << 22) + 999, True),
+                                         ((1 << 22) + 3, 5000, False),
+                                         (200001, (1 << 22) + 77, True),
+                                         (777, 1000, False)])
+def test_build_lookup_host_is_build_then_lookup(M, n, nq, pinned):
+    # The pipelined call (queries copied behind the keys while the levels are
+    # built, lookups chunk by chunk) gives the function and the indices of the
+    # two separate calls, chunked or not on either side.
+    keys = inputs.splitmix64_keys(n, 52)
+    extra = inputs.splitmix64_keys(nq, 53)
+    q = np.concatenate([inputs.shuffled(keys, 6)[: nq // 2], extra[: nq - min(nq // 2, n)]])
+    q = q[:nq]
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=10)
+    ks = torch.from_numpy(keys.view(np.int64)).pin_memory() if pinned else keys
+    qs = torch.from_numpy(q.view(np.int64)).pin_memory() if pinned else q
+    if pinned:
+        ot = torch.empty(q.size, dtype=torch.int64).pin_memory()
+        g, _ = M.MPHF.build_lookup_host(ks, qs, out=ot.numpy().view(np.uint64), gamma=2.0,
+                                        levels=25, seed=10)
+        out = ot.numpy().view(np.uint64).copy()
+    else:
+        g, out = M.MPHF.build_lookup_host(ks, qs, gamma=2.0, levels=25, seed=10)
+    assert_same_structure(g, o)
+    assert np.array_equal(out, o.lookup(q))
+
+
+def test_build_lookup_host_edges(M):
+    # no keys: every query misses; no queries: just the function
+    g, out = M.MPHF.build_lookup_host(np.empty(0, dtype=np.uint64),
+                                      inputs.splitmix64_keys(1000, 54))
+    assert g.N == 0 and np.all(out == np.uint64(U64))
+    keys = inputs.splitmix64_keys(5000, 55)
+    g, out = M.MPHF.build_lookup_host(keys, np.empty(0, dtype=np.uint64), seed=3)
+    assert out.size == 0
+    assert_same_structure(g, oracle.build(keys, gamma=2.0, levels=25, seed=3))
+    # duplicates: reported, no function returned
+    dup = np.concatenate([keys, keys[:10]])
+    with pytest.raises(M.MPHFError) as e:
+        M.MPHF.build_lookup_host(dup, keys)
+    assert e.value.code == M.EDUPLICATE
