@@ -89,7 +89,8 @@ int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma, uint32_t l
                     uint64_t seed, void *stream, mphf_t **out);
 
 /*
- * mphf_build_host followed by mphf_lookup_host in one call, with the host
+ * mphf_build_host followed by mphf_lookup_host in one call (construction,
+ * Algorithms 1-2; query, Algorithm 3 with the ranks of Sec. 3.1), with the host
  * link kept busy: the queries are copied right behind the keys while the
  * levels after the first are built, and each chunk of queries is looked up
  * as soon as it has landed while the indices of the previous chunk are

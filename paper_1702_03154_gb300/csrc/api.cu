@@ -117,6 +117,29 @@ u64 feed_chunk(u64 n) {
   return c < kMin ? kMin : c;
 }
 
+int side_set(size_t n_events, SideSet *out) {
+  struct Pool {
+    cudaStream_t s[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;
+  };
+  thread_local std::vector<Pool> pools;  // by device; kept for the thread's life
+  int dev = 0;
+  MPHF_CUDA(cudaGetDevice(&dev));
+  if ((int)pools.size() <= dev) pools.resize(dev + 1);
+  Pool &p = pools[dev];
+  for (cudaStream_t &x : p.s)
+    if (!x) MPHF_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  while (p.ev.size() < n_events) {
+    cudaEvent_t e = nullptr;
+    MPHF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p.ev.push_back(e);
+  }
+  out->s[0] = p.s[0];
+  out->s[1] = p.s[1];
+  out->ev = p.ev.data();
+  return MPHF_OK;
+}
+
 int KeyFeed::ensure(u64 upto, cudaStream_t st) {
   if (upto > n) upto = n;
   if (issued >= upto) return MPHF_OK;

@@ -564,10 +564,16 @@ extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma,
   f.d = (u64 *)kb.p;
   f.n = n;
   f.chunk = chunk;
-  cudaError_t e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
+  SideSet ss;
+  rc = side_set(1, &ss);
+  if (rc != MPHF_OK) {
+    dev_free(kb, st);
+    return rc;
+  }
+  f.cs = ss.s[0];
+  f.ev = ss.ev[0];
   // the copies must not start before the buffer's allocation in st's order
-  if (e == cudaSuccess) e = cudaEventRecord(f.ev, st);
+  cudaError_t e = cudaEventRecord(f.ev, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(f.cs, f.ev, 0);
   if (e == cudaSuccess) {
     rc = build_impl((const u64 *)kb.p, n, gamma, levels, seed, st, out, &f);
@@ -576,13 +582,9 @@ extern "C" int mphf_build_host(const uint64_t *h_keys, uint64_t n, double gamma,
     cudaStreamWaitEvent(st, f.ev, 0);
   } else {
     rc = cuda_fail(e, "mphf_build_host (copy stream)");
+    cudaStreamSynchronize(f.cs);
   }
   dev_free(kb, st);
-  if (f.ev) cudaEventDestroy(f.ev);
-  if (f.cs) {
-    if (e != cudaSuccess) cudaStreamSynchronize(f.cs);
-    cudaStreamDestroy(f.cs);
-  }
   return rc;
 }
 
@@ -603,15 +605,21 @@ extern "C" int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double
   cudaStream_t st = (cudaStream_t)stream;
   const u64 qchunk = nq ? (feed_chunk(nq) ? feed_chunk(nq) : nq) : 1;
   const u64 nqc = nq ? (nq + qchunk - 1) / qchunk : 0;
-  std::vector<cudaEvent_t> qev(nqc, nullptr);
   DevBuf kb, qb, ob;
   KeyFeed f;
+  SideSet ss;
   cudaStream_t co = nullptr;
   cudaEvent_t ev_k = nullptr;
   cudaError_t e = cudaSuccess;
-  int rc = dev_alloc(kb, n * 8, st);
+  int rc = side_set((size_t)nqc + 2, &ss);
+  if (rc != MPHF_OK) return rc;
+  rc = dev_alloc(kb, n * 8, st);
   if (rc == MPHF_OK) rc = dev_alloc(qb, nq * 8, st);
   if (rc == MPHF_OK) rc = dev_alloc(ob, nq * 8, st);
+  f.cs = ss.s[0];
+  co = ss.s[1];
+  f.ev = ss.ev[0];
+  ev_k = ss.ev[1];
   if (rc == MPHF_OK) {
     f.h = (const u64 *)h_keys;
     f.d = (u64 *)kb.p;
@@ -621,15 +629,9 @@ extern "C" int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double
     f.dq = (u64 *)qb.p;
     f.nq = nq;
     f.qchunk = qchunk;
-    f.qev = qev.data();
-    e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k, cudaEventDisableTiming);
-    for (u64 i = 0; i < nqc && e == cudaSuccess; i++)
-      e = cudaEventCreateWithFlags(&qev[i], cudaEventDisableTiming);
+    f.qev = ss.ev + 2;
     // the copies must not start before the buffers' allocation in st's order
-    if (e == cudaSuccess) e = cudaEventRecord(f.ev, st);
+    e = cudaEventRecord(f.ev, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(f.cs, f.ev, 0);
     if (e != cudaSuccess) rc = cuda_fail(e, "mphf_build_lookup_host (streams)");
   }
@@ -642,7 +644,7 @@ extern "C" int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double
     u64 *dq = (u64 *)qb.p, *dout = (u64 *)ob.p;
     for (u64 c0 = 0; c0 < nq && rc == MPHF_OK && e == cudaSuccess; c0 += qchunk, i++) {
       const u64 cn = nq - c0 < qchunk ? nq - c0 : qchunk;
-      e = cudaStreamWaitEvent(st, qev[i], 0);
+      e = cudaStreamWaitEvent(st, f.qev[i], 0);
       if (e != cudaSuccess) break;
       rc = mphf_lookup(*out, (const uint64_t *)(dq + c0), cn, (uint64_t *)(dout + c0), stream);
       if (rc != MPHF_OK) break;
@@ -658,29 +660,15 @@ extern "C" int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double
     if (e != cudaSuccess && rc == MPHF_OK) rc = cuda_fail(e, "mphf_build_lookup_host");
   }
   // everything enqueued on the side streams is ordered before the frees
-  if (f.cs && f.ev) {
-    cudaEventRecord(f.ev, f.cs);
-    cudaStreamWaitEvent(st, f.ev, 0);
-  }
-  if (co && ev_k) {
-    cudaEventRecord(ev_k, co);
-    cudaStreamWaitEvent(st, ev_k, 0);
-  }
-  if (!f.ev || !ev_k) {  // setup failed part-way: nothing can order the streams
-    if (f.cs) cudaStreamSynchronize(f.cs);
-    if (co) cudaStreamSynchronize(co);
-  }
+  cudaEventRecord(f.ev, f.cs);
+  cudaStreamWaitEvent(st, f.ev, 0);
+  cudaEventRecord(ev_k, co);
+  cudaStreamWaitEvent(st, ev_k, 0);
   dev_free(ob, st);
   dev_free(qb, st);
   dev_free(kb, st);
   const cudaError_t e2 = cudaStreamSynchronize(st);
   if (rc == MPHF_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "mphf_build_lookup_host");
-  for (cudaEvent_t q : qev)
-    if (q) cudaEventDestroy(q);
-  if (f.ev) cudaEventDestroy(f.ev);
-  if (ev_k) cudaEventDestroy(ev_k);
-  if (f.cs) cudaStreamDestroy(f.cs);
-  if (co) cudaStreamDestroy(co);
   if (rc != MPHF_OK && *out) {
     mphf_free(*out);
     *out = nullptr;

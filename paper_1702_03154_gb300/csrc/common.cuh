@@ -172,6 +172,17 @@ struct KeyFeed {
 // Keys per chunk for n keys (0 = copy in one piece: too few keys to pipeline).
 u64 feed_chunk(u64 n);
 
+// Side streams and events of the host-buffer entry points, created once per
+// host thread and device and reused by every call (creating and destroying
+// them per call cost about as much as copying a chunk).  A call joins all it
+// enqueued on them into its own stream before it returns, so one thread's
+// consecutive calls never overlap on them.
+struct SideSet {
+  cudaStream_t s[2];
+  cudaEvent_t *ev;  // n_events events (timing disabled)
+};
+int side_set(size_t n_events, SideSet *out);
+
 // Sort n keys ascending in place and flag equal neighbours (sort.cu).
 int sort_fallback(u64 *keys, u64 n, unsigned int *d_dup_flag, cudaStream_t s);
 

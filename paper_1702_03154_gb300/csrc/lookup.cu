@@ -279,15 +279,18 @@ extern "C" int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_
       if (rc == MPHF_OK) e = cudaMemcpyAsync(h_out, ob.p, n * 8, cudaMemcpyDeviceToHost, s);
     }
   } else {
-    cudaStream_t ci = nullptr, co = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_k = nullptr;
+    SideSet ss;
+    rc = side_set(2, &ss);
+    if (rc != MPHF_OK) {
+      dev_free(kb, s);
+      dev_free(ob, s);
+      return rc;
+    }
+    cudaStream_t ci = ss.s[0], co = ss.s[1];
+    cudaEvent_t ev_in = ss.ev[0], ev_k = ss.ev[1];
     u64 *dk = (u64 *)kb.p, *dout = (u64 *)ob.p;
-    e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_k, cudaEventDisableTiming);
     // both buffers were allocated in s's order: the side streams start after
-    if (e == cudaSuccess) e = cudaEventRecord(ev_in, s);
+    e = cudaEventRecord(ev_in, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev_in, 0);
     u64 prev0 = 0, prevn = 0;  // chunk whose copy out is still to be enqueued
     for (u64 c0 = 0; c0 < n && e == cudaSuccess && rc == MPHF_OK; c0 += chunk) {
@@ -308,22 +311,10 @@ extern "C" int mphf_lookup_host(const mphf_t *h, const uint64_t *h_keys, uint64_
     if (e == cudaSuccess && rc == MPHF_OK && prevn)
       e = cudaMemcpyAsync((u64 *)h_out + prev0, dout + prev0, prevn * 8, cudaMemcpyDeviceToHost, co);
     // everything enqueued on the side streams is ordered before the frees
-    if (ci && ev_in) {
-      cudaEventRecord(ev_in, ci);
-      cudaStreamWaitEvent(s, ev_in, 0);
-    }
-    if (co && ev_k) {
-      cudaEventRecord(ev_k, co);
-      cudaStreamWaitEvent(s, ev_k, 0);
-    }
-    if (!ev_in || !ev_k) {  // setup failed part-way: nothing can order the streams
-      if (ci) cudaStreamSynchronize(ci);
-      if (co) cudaStreamSynchronize(co);
-    }
-    if (ev_in) cudaEventDestroy(ev_in);
-    if (ev_k) cudaEventDestroy(ev_k);
-    if (ci) cudaStreamDestroy(ci);
-    if (co) cudaStreamDestroy(co);
+    cudaEventRecord(ev_in, ci);
+    cudaStreamWaitEvent(s, ev_in, 0);
+    cudaEventRecord(ev_k, co);
+    cudaStreamWaitEvent(s, ev_k, 0);
   }
   dev_free(kb, s);
   dev_free(ob, s);
