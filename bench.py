@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--levels", type=int, default=25)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--sweep", action="store_true", help="also time gamma = 1 and 5")
+    p.add_argument("--no-sweep", action="store_true", help="skip timing gamma = 1 and 5")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-seconds", type=float, default=3.0)
@@ -159,6 +159,28 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- CPU baselines
+def host_cpu() -> dict:
+    """The host the CPU oracle runs on: logical cores and the processor name."""
+    name, part = None, None
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1",
+                 "0xd0c": "Arm Neoverse N1", "0xd49": "Arm Neoverse N2",
+                 "0xd8e": "Arm Neoverse N3", "0xd84": "Arm Neoverse V3"}
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "hardware", "cpu model") and name is None:
+                name = line.split(":", 1)[1].strip()
+            if k == "cpu part" and part is None:
+                part = line.split(":", 1)[1].strip().lower()
+    except OSError:
+        pass
+    if name is None and part is not None:
+        name = arm_parts.get(part, f"Arm CPU part {part}")
+    import platform
+    return {"nproc": os.cpu_count(), "cpu": name or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
 def cpu_baseline(n_sample: int, gamma: float, levels: int):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -171,6 +193,7 @@ def cpu_baseline(n_sample: int, gamma: float, levels: int):
     h.lookup(q)
     t2 = time.perf_counter()
     return {"value": n_sample / (t2 - t0) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"build over the first {n_sample:.0e} keys of the workload + lookup of all of "
                       f"them in shuffled order (gamma={gamma}, L={levels}); build {t1 - t0:.2f} s, "
                       f"lookup {t2 - t1:.2f} s, single-threaded C"}
@@ -206,7 +229,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": workload_config(int(args.n), args.gamma, args.levels),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "host": r["host"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -525,6 +548,32 @@ def run_ours(args):
                                    "GB300 (microbenchmark; 8-byte loads reach ~600 G/s)"}
     last.free()
 
+    sweep = {}
+    if not args.no_sweep:
+        # the N = 1e8 workload at the other two gamma of its configuration:
+        # build, then the same shuffled member lookups (median of 3 after 1)
+        for g2 in (1.0, 5.0):
+            tb, tl = [], []
+            for i in range(4):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                ev[0].record(stream)
+                h = mphf.MPHF.build(keys, gamma=g2, levels=L, seed=0)
+                ev[1].record(stream)
+                h.lookup(q, out=out)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                if i:
+                    tb.append(ev[0].elapsed_time(ev[1]))
+                    tl.append(ev[1].elapsed_time(ev[2]))
+                bpk = h.bits_per_key()
+                h.free()
+            b_ms, l_ms = float(np.median(tb)), float(np.median(tl))
+            sweep[f"gamma={g2:g}"] = {"build_ms": round(b_ms, 3), "lookup_ms": round(l_ms, 3),
+                                      "build_mkeys_s": round(N / b_ms / 1e3, 1),
+                                      "lookup_mkeys_s": round(N / l_ms / 1e3, 1),
+                                      "step_mkeys_s": round(N / (b_ms + l_ms) / 1e3, 1),
+                                      "bits_per_key": round(bpk, 4)}
+
     e2e = None
     if not args.no_e2e:
         kh = torch.empty(N, dtype=torch.int64, pin_memory=True)
@@ -570,24 +619,6 @@ def run_ours(args):
                       "pinned host buffers",
                "two_calls": {"api": "mphf_build_host + mphf_lookup_host",
                              "value": job_value(N, world, sep_max), "ms_per_step": sep_max}}
-
-    sweep = {}
-    if args.sweep:
-        for g2 in (1.0, 5.0):
-            ts = []
-            for i in range(4):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                kk = keys
-                e0.record(stream)
-                h = mphf.MPHF.build(kk, gamma=g2, levels=L, seed=0)
-                h.lookup(kk, out=out)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                if i:
-                    ts.append(e0.elapsed_time(e1))
-                h.free()
-            sweep[f"gamma={g2:g}"] = {"mkeys_s": round(N / (np.median(ts) / 1e3) / 1e6, 1),
-                                      "ms": round(float(np.median(ts)), 3)}
 
     batched = None
     if not args.no_batched:
