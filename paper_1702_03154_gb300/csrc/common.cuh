@@ -128,6 +128,16 @@ inline unsigned int resident_grid(K kernel, int threads, size_t smem) {
   return (unsigned int)(per_sm * sm_count());
 }
 
+// Keys a lookup warp takes from its batch at a time: 2048 once the batch has
+// that many for every resident warp, otherwise fewer (a multiple of 64, at
+// least 128), so that a small batch still spreads over the whole GPU instead
+// of queueing on a few warps.
+inline u64 lookup_chunk(u64 n, u64 resident_warps) {
+  u64 c = (n + resident_warps - 1) / (resident_warps ? resident_warps : 1);
+  c = (c + 63) & ~63ull;
+  return c < 128 ? 128 : c > 2048 ? 2048 : c;
+}
+
 inline unsigned int grid_for(u64 items, unsigned int per_block, unsigned int max_blocks) {
   u64 b = (items + per_block - 1) / per_block;
   if (b < 1) b = 1;

@@ -21,7 +21,6 @@
 namespace bbh {
 
 static constexpr int kLookupThreads = 256;
-static constexpr unsigned kChunk = 32 * 64;  // keys a warp takes from the input at a time
 
 struct LevelTable {
   u64 s[MPHF_MAX_LEVELS];
@@ -55,7 +54,8 @@ __device__ __forceinline__ u64 fallback_index(const LookupArgs &a, u64 x) {
 //   g >> kQShift = (off_d >> kQShift) + (p >> kQShift),  g & mask = p & mask.
 template <int kSlots, int W, bool kNarrow>
 __global__ void __launch_bounds__(kLookupThreads)
-k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs a, LevelTable t) {
+k_lookup(const u64 *__restrict__ keys, u64 n, u64 csz, u64 *__restrict__ out, LookupArgs a,
+         LevelTable t) {
   using LW = Lay<W>;
   __shared__ u64 ts[MPHF_MAX_LEVELS], tm[MPHF_MAX_LEVELS], toff[MPHF_MAX_LEVELS];
   __shared__ unsigned tm32[MPHF_MAX_LEVELS], toq[MPHF_MAX_LEVELS];
@@ -70,12 +70,12 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
 
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const u64 nchunks = (n + kChunk - 1) / kChunk;
+  const u64 nchunks = (n + csz - 1) / csz;
   const u64 warp_id = ((u64)blockIdx.x * kLookupThreads + threadIdx.x) >> 5;
   const u64 nwarps = ((u64)gridDim.x * kLookupThreads) >> 5;
   u64 chunk = warp_id;
-  u64 cursor = chunk * kChunk;
-  u64 cend = chunk < nchunks ? min(cursor + kChunk, n) : cursor;
+  u64 cursor = chunk * csz;
+  u64 cend = chunk < nchunks ? min(cursor + csz, n) : cursor;
   bool more = chunk < nchunks;
 
   u64 x[kSlots], idx[kSlots];
@@ -123,8 +123,8 @@ k_lookup(const u64 *__restrict__ keys, u64 n, u64 *__restrict__ out, LookupArgs 
             more = false;
             break;
           }
-          cursor = chunk * kChunk;
-          cend = min(cursor + kChunk, n);
+          cursor = chunk * csz;
+          cend = min(cursor + csz, n);
         }
         const u64 avail = cend - cursor;
         const unsigned r = __popc(need & lt);
@@ -206,13 +206,15 @@ static int launch_lookup(const u64 *keys, u64 n, u64 *out, const LookupArgs &a,
   // second wave would only start after the first has drained
   static unsigned mb = 0;
   if (!mb) mb = resident_grid(k_lookup<SLOTS, W, NARROW>, kLookupThreads, 0);
-  const u64 nwarps_needed = (n + kChunk - 1) / kChunk;
+  const u64 csz = lookup_chunk(n, (u64)mb * (kLookupThreads / 32));
+  const u64 nwarps_needed = (n + csz - 1) / csz;
   const unsigned per_block = kLookupThreads / 32;
   u64 grid = (nwarps_needed + per_block - 1) / per_block;
   if (grid > mb) grid = mb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup", s);
-  k_lookup<SLOTS, W, NARROW><<<(unsigned)grid, kLookupThreads, 0, s>>>(keys, n, out, a, t);
+  k_lookup<SLOTS, W, NARROW><<<(unsigned)grid, kLookupThreads, 0, s>>>(keys, n, csz, out, a,
+                                                                       t);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }

@@ -99,7 +99,6 @@ __device__ __forceinline__ u64 fallback_index_m(const LookupDev *h, u64 x) {
 
 static constexpr int kMultiThreads = 256;
 static constexpr int kMultiSlots = 2;
-static constexpr unsigned kMultiChunk = 32 * 64;
 
 // Lookups of a batch of requests against different functions: the keys of all
 // requests form one index space [0, total); warps take chunks of it and keep
@@ -108,15 +107,15 @@ static constexpr unsigned kMultiChunk = 32 * 64;
 // arithmetic, as in k_lookup).
 template <int W, bool NARROW>
 __global__ void __launch_bounds__(kMultiThreads)
-k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
+k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total, u64 csz) {
   using LW = Lay<W>;
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const u64 nchunks = (total + kMultiChunk - 1) / kMultiChunk;
+  const u64 nchunks = (total + csz - 1) / csz;
   const u64 nwarps = ((u64)gridDim.x * kMultiThreads) >> 5;
   u64 chunk = ((u64)blockIdx.x * kMultiThreads + threadIdx.x) >> 5;
-  u64 cursor = chunk * kMultiChunk;
-  u64 cend = chunk < nchunks ? min(cursor + kMultiChunk, total) : cursor;
+  u64 cursor = chunk * csz;
+  u64 cend = chunk < nchunks ? min(cursor + csz, total) : cursor;
   bool more = chunk < nchunks;
   unsigned rcur = 0;  // request holding `cursor` (warp-uniform), found by search
   auto find_req = [&](u64 i, unsigned from) -> unsigned {
@@ -189,8 +188,8 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
             more = false;
             break;
           }
-          cursor = chunk * kMultiChunk;
-          cend = min(cursor + kMultiChunk, total);
+          cursor = chunk * csz;
+          cend = min(cursor + csz, total);
           rcur = find_req(cursor, rcur);
         }
         const u64 avail = cend - cursor;
@@ -261,14 +260,16 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total) {
 
 template <int W, bool NARROW>
 static int launch_multi_wn(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
-  const u64 chunks = (total + kMultiChunk - 1) / kMultiChunk;
-  u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
   static u64 maxb = 0;  // one wave of resident CTAs
   if (!maxb) maxb = resident_grid(k_lookup_multi<W, NARROW>, kMultiThreads, 0);
+  const u64 csz = lookup_chunk(total, maxb * (kMultiThreads / 32));
+  const u64 chunks = (total + csz - 1) / csz;
+  u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
   if (grid > maxb) grid = maxb;
   if (grid < 1) grid = 1;
   LaunchScope ls("lookup_multi", s);
-  k_lookup_multi<W, NARROW><<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total);
+  k_lookup_multi<W, NARROW><<<(unsigned)grid, kMultiThreads, 0, s>>>(d_reqs, nreq, total,
+                                                                      csz);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
@@ -486,8 +487,12 @@ static void scheduler(mphf_server *sv) {
 
 static void build_worker(mphf_server *sv) {
   cudaSetDevice(sv->device);
+  // builds run at the lowest stream priority: when SMs free up, the block
+  // scheduler takes the pending CTAs of lookup batches first
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   cudaStream_t s;
-  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least);
   for (;;) {
     Req *r = nullptr;
     {
@@ -536,8 +541,12 @@ int mphf_server_create(uint64_t max_batch_keys, uint32_t max_batch_reqs, int max
   sv->mem_reserve = mem_reserve_bytes;
   cudaGetDevice(&sv->device);
   int rc = MPHF_OK;
+  // lookup batches at the highest stream priority (builds take the lowest)
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (int i = 0; i < 2 && rc == MPHF_OK; i++)
-    if (cudaStreamCreateWithFlags(&sv->lstream[i], cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithPriority(&sv->lstream[i], cudaStreamNonBlocking, greatest) !=
+        cudaSuccess)
       rc = cuda_fail(cudaGetLastError(), "cudaStreamCreate");
   sv->dtab.resize(max_inflight);
   sv->htab.resize(max_inflight, nullptr);
