@@ -210,12 +210,12 @@ int oracle_build_hooked(const uint64_t *keys, uint64_t N, double gamma, uint32_t
             free(F); free(Fnext); free(Alev); oracle_free(h);
             return ORACLE_ENOMEM;
         }
-        array_fill(h, i, F, n, A, C);   /* A_i = ArrayFill(F_i, gamma) */
+        array_fill(h, i, F, n, A, C);   /* level i's bit array from its keys (Algorithm 2) */
         uint64_t nn = 0;
         for (uint64_t k = 0; k < n; k++) {
             uint64_t p = position(h, i, F[k]);
             if (A[p] == 0)
-                Fnext[nn++] = F[k];      /* F_{i+1}.add(x) */
+                Fnext[nn++] = F[k];      /* not placed: the key goes on to level i+1 */
         }
         Alev[i] = A;
         h->bitC[i] = C;

@@ -9,8 +9,8 @@
 // the same L2 sector.  Extraction then computes A_d = hit & ~collision into
 // the concatenated A, counts weight(A_d), and derives |F_{d+1}| = |F_d| -
 // weight(A_d) before any key is moved.  Compaction of level d streams F_d
-// again, keeps the keys whose A_d bit is 0 (Algorithm 1, "if A_i[h] == 0
-// then F_{i+1}.add(x)"), packs them with warp ballots + a block scan, and --
+// again, keeps the keys whose A_d bit is 0 (they form F_{d+1}, Algorithm 1),
+// packs them with warp ballots + a block scan, and --
 // since |A_{d+1}| is already known -- runs level d+1's ArrayFill on the
 // survivors in the same pass, so F_{d+1} is read once less.
 #include <cuda_runtime.h>
