@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fastbuild.cuh"
 #include "sector.cuh"
 
 namespace bbh {
@@ -61,7 +62,7 @@ k_fill_vec(const uint4 *__restrict__ keys2, u64 npairs, u64 s, u64 m, u64 *__res
 #pragma unroll
     for (int u = 0; u < kFillUnroll; u++) {
       u64 i = base + (u64)u * kFillThreads;
-      if (i < npairs) v[u] = load_stream(keys2 + i);
+      v[u] = i < npairs ? load_stream(keys2 + i) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kFillUnroll; u++) {
@@ -238,15 +239,127 @@ k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restri
 }
 
 // ---------------------------------------------------------------------------
+// Slab order.  When a level's AC array is far larger than L2, random atomics
+// on it go to HBM one sector at a time.  Its keys are then first grouped by
+// slab (2^27 consecutive positions, a 32 MB stretch of AC): a count
+// per slab, then a multisplit into exact slab ranges.  The fill and the
+// compaction stream the grouped keys in order, so all CTAs work inside one or
+// two slabs at any moment and the atomics and bit tests hit L2.  The grouping
+// changes no result: ArrayFill and the compaction depend on the key set only.
+// ---------------------------------------------------------------------------
+static unsigned g_slab_shift = 27;           // positions per slab: 2^27
+static u64 g_slab_min_ac = 64ull << 20;       // group levels whose AC exceeds this (bytes)
+static constexpr unsigned kSlabMax = (unsigned)kBmax; // slabs a multisplit can take
+static constexpr int kSlabCountThreads = 256;
+
+__global__ void __launch_bounds__(kSlabCountThreads)
+k_slab_count(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift, unsigned nslab,
+             u64 *__restrict__ counts) {
+  __shared__ unsigned hist[kSlabMax];
+  for (unsigned i = threadIdx.x; i < nslab; i += kSlabCountThreads) hist[i] = 0;
+  __syncthreads();
+  const u64 stride = (u64)gridDim.x * kSlabCountThreads;
+  for (u64 i = (u64)blockIdx.x * kSlabCountThreads + threadIdx.x; i < n; i += stride)
+    atomicAdd(&hist[(unsigned)(level_pos(__ldcs(keys + i), s, m) >> shift)], 1u);
+  __syncthreads();
+  for (unsigned i = threadIdx.x; i < nslab; i += kSlabCountThreads)
+    if (hist[i]) atomicAdd(counts + i, (u64)hist[i]);
+}
+
+// Destination slab i of the multisplit: cursor[i] starts at the slab's first
+// index and end[i] is one past its last.
+struct SlabDest {
+  u64 *cursor;
+  const u64 *end;
+  __device__ __forceinline__ DestRun operator()(unsigned i) const {
+    return DestRun{cursor + i, 0, end[i]};
+  }
+};
+
+__global__ void __launch_bounds__(kTT, 2)
+k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift, unsigned nslab,
+               u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
+               unsigned *__restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SplitSmem sm = carve_split(smem, nslab);
+  split_clear(sm, nslab);
+  __syncthreads();
+  const u64 ntiles = (n + kTile - 1) / kTile;
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    u64 x[kKPT];
+    unsigned dst[kKPT], lp[kKPT];
+    bool ok[kKPT];
+#pragma unroll
+    for (int k = 0; k < kKPT; k++) {
+      const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
+      ok[k] = i < n;
+      x[k] = ok[k] ? __ldcs(keys + i) : 0;
+      dst[k] = ok[k] ? (unsigned)(level_pos(x[k], s, m) >> shift) : 0u;
+      lp[k] = 0;
+    }
+    multisplit_write<false, false>(x, lp, dst, ok, nslab, sm, out, nullptr,
+                                   SlabDest{cursor, end}, status);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host orchestration.
 // ---------------------------------------------------------------------------
 struct Scratch {
-  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag;
+  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag, R, slab;
   void release(cudaStream_t s) {
     dev_free(meta, s); dev_free(AC0, s); dev_free(AC1, s); dev_free(A0, s);
     dev_free(arena, s); dev_free(F1, s); dev_free(F2, s); dev_free(dupflag, s);
+    dev_free(R, s); dev_free(slab, s);
   }
 };
+
+// Slabs of a level of m positions, or 0 if its keys are left in their order.
+static unsigned slab_count_for(u64 m) {
+  if (m / 4 <= g_slab_min_ac) return 0;  // the AC array (2 bits a position) is L2-sized
+  const u64 ns = (m + (1ull << g_slab_shift) - 1) >> g_slab_shift;
+  return ns <= kSlabMax ? (unsigned)ns : 0u;
+}
+
+// R <- the n keys of F grouped by slab of level (s, m).  slab: 3 * kSlabMax u64.
+static int slab_order(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *R, u64 *slab,
+                      unsigned *status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)split_smem_bytes(kSlabMax)));
+    attr = true;
+  }
+  u64 *counts = slab, *cursor = slab + kSlabMax, *end = slab + 2 * kSlabMax;
+  MPHF_CUDA(cudaMemsetAsync(counts, 0, nslab * 8, st));
+  {
+    LaunchScope ls("slab_count", st);
+    k_slab_count<<<grid_for(n, kSlabCountThreads * 16, (unsigned)sm_count() * 8),
+                   kSlabCountThreads, 0, st>>>(F, n, s, m, g_slab_shift, nslab, counts);
+  }
+  std::vector<u64> c(nslab), se(2 * (size_t)nslab);
+  MPHF_CUDA(cudaMemcpyAsync(c.data(), counts, nslab * 8, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  u64 run = 0;
+  for (unsigned i = 0; i < nslab; i++) {
+    se[i] = run;
+    run += c[i];
+    se[nslab + i] = run;
+  }
+  if (run != n) return MPHF_EINTERNAL;
+  MPHF_CUDA(cudaMemcpyAsync(cursor, se.data(), nslab * 8, cudaMemcpyHostToDevice, st));
+  MPHF_CUDA(cudaMemcpyAsync(end, se.data() + nslab, nslab * 8, cudaMemcpyHostToDevice, st));
+  {
+    LaunchScope ls("slab_scatter", st);
+    k_slab_scatter<<<grid_for(n, kTile, (unsigned)sm_count() * 2), kTT,
+                     split_smem_bytes(nslab), st>>>(F, n, s, m, g_slab_shift, nslab, cursor, end,
+                                                    R, status);
+  }
+  // the host copies of the offsets are read by the copies above before return
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
 
 static void release_handle(mphf_t *h, cudaStream_t s) {
   if (!h) return;
@@ -331,6 +444,9 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   u64 *Ffb = nullptr;
   BuildMeta *meta = nullptr;
   unsigned int *dflag = nullptr;
+  unsigned nslab0 = 0;
+  unsigned *slab_status = nullptr;
+  const u64 *F0 = keys;
 
 #define TRY(x)                  \
   do {                          \
@@ -342,20 +458,38 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   meta = (BuildMeta *)sc.meta.p;
   TRY(dev_alloc(sc.AC0, m0 / 32 * 8, st));
   TRY(dev_alloc(sc.A0, m0 / 64 * 8, st));
-  TRY(dev_alloc(sc.dupflag, 16, st));
+  TRY(dev_alloc(sc.dupflag, 32, st));  // dup flag, rank total, slab overflow
   dflag = (unsigned int *)sc.dupflag.p;
   if ((rc = cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     rc = cuda_fail((cudaError_t)rc, "cudaMemcpyAsync(meta)");
     goto fail;
   }
   if (cudaMemsetAsync(sc.AC0.p, 0, sc.AC0.bytes, st) != cudaSuccess ||
-      cudaMemsetAsync(dflag, 0, 16, st) != cudaSuccess) {
+      cudaMemsetAsync(dflag, 0, 32, st) != cudaSuccess) {
     rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
     goto fail;
   }
+  // Levels too large for L2 are grouped by slab first (levels only shrink, so
+  // they are a prefix of the levels).  R holds the grouped keys; without room
+  // for it the keys stay in their order.
+  nslab0 = slab_count_for(m0);
+  if (nslab0) {
+    if (dev_alloc(sc.R, N * 8, st) != MPHF_OK || dev_alloc(sc.slab, 3 * kSlabMax * 8, st) != MPHF_OK) {
+      cudaGetLastError();
+      dev_free(sc.R, st);
+      dev_free(sc.slab, st);
+      nslab0 = 0;
+    }
+  }
+  slab_status = (unsigned *)((u64 *)sc.dupflag.p + 2);
+  if (nslab0) {
+    TRY(slab_order(keys, N, h->s[0], m0, nslab0, (u64 *)sc.R.p, (u64 *)sc.slab.p, slab_status,
+                   st));
+    F0 = (const u64 *)sc.R.p;
+  }
 
-  // Level 0: ArrayFill over the caller's keys, then extraction.
-  TRY(launch_fill0(keys, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
+  // Level 0: ArrayFill over the (grouped) keys, then extraction.
+  TRY(launch_fill0(F0, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
   TRY(launch_extract((u64 *)sc.AC0.p, m0, (u64 *)sc.A0.p, nullptr, meta, 0, (int)L, gamma, st));
   TRY(read_u64(&meta->n[1], &n1, st));
 
@@ -363,7 +497,8 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     // Every later level holds at most n1 keys, so these bounds are exact worst cases.
     const u64 m1 = level_bits(n1, gamma);
     TRY(dev_alloc(sc.F1, n1 * 8, st));
-    if (L > 1) TRY(dev_alloc(sc.F2, n1 * 8, st));
+    // with grouped levels, R (N keys) is the second buffer of the level loop
+    if (L > 1 && !nslab0) TRY(dev_alloc(sc.F2, n1 * 8, st));
     if (L > 1) {
       TRY(dev_alloc(sc.AC1, m1 / 32 * 8, st));
       TRY(dev_alloc(sc.arena, (u64)(L - 1) * (m1 / 64) * 8, st));
@@ -377,29 +512,43 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   {
     // Level loop: compaction of d (+ fill of d+1), extraction of d+1.
     u64 n_next = n1;  // |F_{d+1}|
-    const u64 *Fin = keys;
+    const u64 *Fin = F0;
     int d = 0;
     for (;;) {
       if (n_next == 0) {
         last_level = d;
         break;
       }
-      u64 *Fout = ((d + 1) & 1) ? (u64 *)sc.F1.p : (u64 *)sc.F2.p;
+      // F_{d+1} goes to the buffer F_d is not read from: F1 and F2, or F1 and R
+      // (grouped levels, a prefix of the levels, read R and write F1)
+      u64 *other = nslab0 ? (u64 *)sc.R.p : (u64 *)sc.F2.p;
+      u64 *Fout = (Fin == (const u64 *)sc.F1.p) ? other : (u64 *)sc.F1.p;
       const bool to_fallback = (uint32_t)(d + 1) == L;
       u64 *ACnext = ((d + 1) & 1) ? (u64 *)sc.AC1.p : (u64 *)sc.AC0.p;
+      // a grouped next level is filled after its keys are grouped, not here
+      const u64 m_next = to_fallback ? 0 : level_bits(n_next, gamma);
+      const unsigned nslab = (nslab0 && !to_fallback) ? slab_count_for(m_next) : 0u;
+      const int fuse = (to_fallback || nslab) ? 0 : 1;
       TRY(launch_compact(Fin, d == 0 ? N : n1, Fout, n1, (const u64 *)sc.A0.p,
-                         (const u64 *)sc.arena.p, to_fallback ? nullptr : ACnext, meta, d,
-                         h->s[d], to_fallback ? 0 : h->s[d + 1], to_fallback ? 0 : 1, st));
+                         (const u64 *)sc.arena.p, fuse ? ACnext : nullptr, meta, d, h->s[d],
+                         fuse ? h->s[d + 1] : 0, fuse, st));
       if (to_fallback) {
         last_level = d;
         Ffb = Fout;
         n_fb = n_next;
         break;
       }
+      const u64 *Fnext = Fout;
+      if (nslab) {
+        TRY(slab_order(Fout, n_next, h->s[d + 1], m_next, nslab, (u64 *)sc.R.p,
+                       (u64 *)sc.slab.p, slab_status, st));
+        Fnext = (const u64 *)sc.R.p;
+        TRY(launch_fill0(Fnext, n_next, h->s[d + 1], m_next, ACnext, st));
+      }
       TRY(launch_extract(ACnext, level_bits(n1, gamma), (u64 *)sc.A0.p, (u64 *)sc.arena.p, meta,
                          d + 1, (int)L, gamma, st));
       TRY(read_u64(&meta->n[d + 2], &n_next, st));
-      Fin = Fout;
+      Fin = Fnext;
       d++;
     }
   }
@@ -441,10 +590,14 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     }
   }
   {
-    u64 flags[2] = {0, 0};
-    if (cudaMemcpyAsync(flags, sc.dupflag.p, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    u64 flags[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(flags, sc.dupflag.p, 24, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       rc = cuda_fail(cudaGetLastError(), "dup flag");
+      goto fail;
+    }
+    if ((unsigned)flags[2]) {  // a grouping overflowed a slab range: cannot happen
+      rc = MPHF_EINTERNAL;
       goto fail;
     }
     if ((unsigned)flags[0]) {
@@ -684,3 +837,10 @@ extern "C" int mphf_debug_config(int path, double cap_scale) {
 }
 
 extern "C" int mphf_build_path(const mphf_t *h) { return h ? h->path : 0; }
+
+extern "C" int mphf_debug_slabs(uint32_t shift, uint64_t min_ac_bytes) {
+  if (shift < 6 || shift > 40) return MPHF_EINVAL;
+  bbh::g_slab_shift = shift;
+  bbh::g_slab_min_ac = min_ac_bytes;
+  return MPHF_OK;
+}

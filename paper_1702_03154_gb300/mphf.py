@@ -84,6 +84,7 @@ def lib():
         "mphf_build_batched": ([vp, vp, u32, dbl, u32, u64, vp, vp], i32),
         "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
         "mphf_batched_debug_config": ([dbl], i32),
+        "mphf_debug_slabs": ([u32, u64], i32),
         "mphf_batched_tuning": ([u32, u64, pu64, pu64, pu64], i32),
         "mphf_batched_set_tuning": ([u32, u64, u64, u64, u64], i32),
         "mphf_workspace_release": ([], None),
@@ -401,6 +402,11 @@ def autotune_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: 
                                      _stream_ptr(stream), ctypes.byref(best))
     _check(rc, "mphf_autotune_batched")
     return best.value
+
+
+def debug_slabs(shift: int = 27, min_ac_bytes: int = 64 << 20) -> None:
+    """Test hook: slab size and threshold of the unbucketed path's key grouping."""
+    _check(lib().mphf_debug_slabs(int(shift), int(min_ac_bytes)), "mphf_debug_slabs")
 
 
 def batched_tuning(S: int, total_keys: int) -> dict:

@@ -354,3 +354,48 @@ def test_build_lookup_host_edges(M):
     with pytest.raises(M.MPHFError) as e:
         M.MPHF.build_lookup_host(dup, keys)
     assert e.value.code == M.EDUPLICATE
+
+
+@pytest.mark.parametrize("gamma,levels,shift", [(2.0, 25, 12), (1.0, 25, 10), (5.0, 25, 14),
+                                                (1.0, 3, 12), (2.0, 25, 6)])
+def test_unbucketed_slab_grouping(M, gamma, levels, shift):
+    # The unbucketed path groups a level's keys by slabs of 2^shift positions
+    # before filling it (all levels here: threshold 0); shift 6 gives more
+    # slabs than a multisplit takes, so level 0 is left ungrouped.
+    keys = inputs.splitmix64_keys(200001, 56)
+    q = np.concatenate([inputs.shuffled(keys, 7), inputs.splitmix64_keys(5000, 57)])
+    o = oracle.build(keys, gamma=gamma, levels=levels, seed=11)
+    M.debug_config(1, 1.0)
+    M.debug_slabs(shift, 0)
+    try:
+        g = M.MPHF.build(dev(keys), gamma=gamma, levels=levels, seed=11)
+        dup = np.concatenate([keys, keys[:7]])
+        with pytest.raises(M.MPHFError) as e:
+            M.MPHF.build(dev(dup), gamma=gamma, levels=levels, seed=11)
+        assert e.value.code == M.EDUPLICATE
+    finally:
+        M.debug_slabs()
+        M.debug_config(0, 1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(M.to_u64(g.lookup(dev(q))), o.lookup(q))
+
+
+def test_unbucketed_slab_grouping_at_scale(M):
+    # 1.5e8 keys at gamma 2: level 0's hit/collision array (75 MB) is past the
+    # default threshold, so the unbucketed path groups it into 3 slabs; the
+    # function equals the bucketed build's (itself the oracle's at smaller N).
+    keys = M.keygen(150_000_000, 58)
+    a = M.MPHF.build(keys, gamma=2.0, levels=25, seed=12)
+    M.debug_config(1, 1.0)
+    try:
+        b = M.MPHF.build(keys, gamma=2.0, levels=25, seed=12)
+    finally:
+        M.debug_config(0, 1.0)
+    assert a.build_path == 1 and b.build_path == 2
+    assert a.levels() == b.levels()
+    assert np.array_equal(a.bits(), b.bits())
+    assert np.array_equal(a.rank(), b.rank())
+    assert np.array_equal(a.fallback(), b.fallback())
+    sel = keys[::997]
+    assert torch.equal(a.lookup(sel), b.lookup(sel))
