@@ -151,9 +151,9 @@ int mphf_batched_set_tuning(uint32_t S, uint64_t total_keys, uint64_t pmax, uint
 
 /* Test hook for the unbucketed construction: a level whose hit/collision
  * array (2 bits a position) exceeds min_ac_bytes has its keys grouped by slabs
- * of 2^shift positions before it is filled (defaults 27 and 64 MiB), which
- * keeps its atomics in L2 and changes no result.  shift in [6, 40];
- * MPHF_EINVAL otherwise. */
+ * of 2^shift positions, and each slab's keys by fine slabs of 2^18 positions
+ * filled in shared memory (defaults 27 and 64 MiB); no result changes.
+ * shift in [6, 29]; MPHF_EINVAL otherwise. */
 int mphf_debug_slabs(uint32_t shift, uint64_t min_ac_bytes);
 
 /* Test hook: scales the bucket capacities of mphf_build_batched (default 1;

@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -84,6 +85,22 @@ k_fill_scalar(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 *__restrict
     fill_position(AC, level_pos(__ldcs(keys + i), s, m));
 }
 
+// |F_{d+1}| = |F_d| - weight(A_d) and the next level's size and offset.
+__device__ void size_next_level(BuildMeta *meta, int d, int L, double gamma) {
+  volatile BuildMeta *vm = meta;
+  const u64 m = vm->m[d];
+  u64 wgt = vm->weight[d];
+  u64 n = vm->n[d];
+  if (wgt > n) {  // cannot happen: every set bit is one distinct key
+    atomicExch(&meta->status, (unsigned)MPHF_EINTERNAL);
+    wgt = n;
+  }
+  u64 nn = n - wgt;
+  vm->n[d + 1] = nn;
+  vm->off[d + 1] = vm->off[d] + m;
+  vm->m[d + 1] = (nn > 0 && d + 1 < L) ? level_bits(nn, gamma) : 0;
+}
+
 // ---------------------------------------------------------------------------
 // Extract A_d = hit & ~collision, count weight(A_d), zero the AC array for
 // reuse two levels later, and (last block) size level d+1.
@@ -124,18 +141,14 @@ k_extract(u64 *__restrict__ AC, u64 *__restrict__ A0, u64 *__restrict__ Aarena,
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    volatile BuildMeta *vm = meta;
-    u64 wgt = vm->weight[d];
-    u64 n = vm->n[d];
-    if (wgt > n) {  // cannot happen: every set bit is one distinct key
-      atomicExch(&meta->status, (unsigned)MPHF_EINTERNAL);
-      wgt = n;
-    }
-    u64 nn = n - wgt;
-    vm->n[d + 1] = nn;
-    vm->off[d + 1] = vm->off[d] + m;
-    vm->m[d + 1] = (nn > 0 && d + 1 < L) ? level_bits(nn, gamma) : 0;
+    size_next_level(meta, d, L, gamma);
   }
+}
+
+// One thread: level d+1's size once weight(A_d) is complete (grouped levels).
+__global__ void k_level_done(BuildMeta *__restrict__ meta, int d, int L, double gamma) {
+  __threadfence();
+  size_next_level(meta, d, L, gamma);
 }
 
 // ---------------------------------------------------------------------------
@@ -253,14 +266,14 @@ static constexpr unsigned kSlabMax = (unsigned)kBmax; // slabs a multisplit can 
 static constexpr int kSlabCountThreads = 256;
 
 __global__ void __launch_bounds__(kSlabCountThreads)
-k_slab_count(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift, unsigned nslab,
-             u64 *__restrict__ counts) {
+k_slab_count(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
+             unsigned nslab, u64 *__restrict__ counts) {
   __shared__ unsigned hist[kSlabMax];
   for (unsigned i = threadIdx.x; i < nslab; i += kSlabCountThreads) hist[i] = 0;
   __syncthreads();
   const u64 stride = (u64)gridDim.x * kSlabCountThreads;
   for (u64 i = (u64)blockIdx.x * kSlabCountThreads + threadIdx.x; i < n; i += stride)
-    atomicAdd(&hist[(unsigned)(level_pos(__ldcs(keys + i), s, m) >> shift)], 1u);
+    atomicAdd(&hist[(unsigned)((level_pos(__ldcs(keys + i), s, m) - base) >> shift)], 1u);
   __syncthreads();
   for (unsigned i = threadIdx.x; i < nslab; i += kSlabCountThreads)
     if (hist[i]) atomicAdd(counts + i, (u64)hist[i]);
@@ -277,8 +290,8 @@ struct SlabDest {
 };
 
 __global__ void __launch_bounds__(kTT, 2)
-k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift, unsigned nslab,
-               u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
+k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
+               unsigned nslab, u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
                unsigned *__restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   SplitSmem sm = carve_split(smem, nslab);
@@ -294,7 +307,7 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift
       const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
       ok[k] = i < n;
       x[k] = ok[k] ? __ldcs(keys + i) : 0;
-      dst[k] = ok[k] ? (unsigned)(level_pos(x[k], s, m) >> shift) : 0u;
+      dst[k] = ok[k] ? (unsigned)((level_pos(x[k], s, m) - base) >> shift) : 0u;
       lp[k] = 0;
     }
     multisplit_write<false, false>(x, lp, dst, ok, nslab, sm, out, nullptr,
@@ -302,15 +315,60 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, unsigned shift
   }
 }
 
+// ArrayFill of one fine slab of a grouped level in shared memory: CTA f takes
+// the keys T[fstart[f], fend[f]) of positions [p0, min(p0 + 2^kFineShift,
+// lim)), p0 = base + f 2^kFineShift, sets hit and collision bits there (Algorithm 2, the
+// same three implications as fill_position), writes A_d's words of the range
+// and adds their ones to weight(A_d).
+static constexpr unsigned kFineShift = 18;
+static constexpr int kFineThreads = 512;
+static constexpr size_t kFineSmem = 2 * ((size_t)1 << kFineShift) / 8;  // hit + collision bits
+
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64 *__restrict__ fend,
+            u64 s, u64 m, u64 base, u64 lim, u64 *__restrict__ Alev, u64 *__restrict__ weight) {
+  extern __shared__ __align__(16) unsigned fsm[];
+  __shared__ u64 red[kFineThreads / 32];
+  constexpr unsigned kWords = (1u << kFineShift) / 32;
+  unsigned *hit = fsm, *col = fsm + kWords;
+  const u64 p0 = base + ((u64)blockIdx.x << kFineShift);
+  const u64 np = min((u64)1 << kFineShift, lim - p0);  // lim: end of the slab, a multiple of 64
+  for (unsigned i = threadIdx.x; i < 2 * kWords; i += kFineThreads) fsm[i] = 0;
+  __syncthreads();
+  const u64 i1 = fend[blockIdx.x];
+  for (u64 i = fstart[blockIdx.x] + threadIdx.x; i < i1; i += kFineThreads) {
+    const unsigned q = (unsigned)(level_pos(__ldcs(T + i), s, m) - p0);  // < np
+    const unsigned bit = 1u << (q & 31);
+    const unsigned old = atomicOr(hit + (q >> 5), bit);
+    if (old & bit) atomicOr(col + (q >> 5), bit);
+  }
+  __syncthreads();
+  u64 wsum = 0;
+  for (unsigned w = threadIdx.x; w < (unsigned)(np >> 6); w += kFineThreads) {
+    const u64 a = (u64)(hit[2 * w] & ~col[2 * w]) | ((u64)(hit[2 * w + 1] & ~col[2 * w + 1]) << 32);
+    Alev[(p0 >> 6) + w] = a;
+    wsum += __popcll(a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int i = 0; i < kFineThreads / 32; i++) t += red[i];
+    if (t) atomicAdd(weight, t);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host orchestration.
 // ---------------------------------------------------------------------------
 struct Scratch {
-  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag, R, slab;
+  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag, R, slab, T;
   void release(cudaStream_t s) {
     dev_free(meta, s); dev_free(AC0, s); dev_free(AC1, s); dev_free(A0, s);
     dev_free(arena, s); dev_free(F1, s); dev_free(F2, s); dev_free(dupflag, s);
-    dev_free(R, s); dev_free(slab, s);
+    dev_free(R, s); dev_free(slab, s); dev_free(T, s);
   }
 };
 
@@ -321,13 +379,18 @@ static unsigned slab_count_for(u64 m) {
   return ns <= kSlabMax ? (unsigned)ns : 0u;
 }
 
-// R <- the n keys of F grouped by slab of level (s, m).  slab: 3 * kSlabMax u64.
-static int slab_order(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *R, u64 *slab,
-                      unsigned *status, cudaStream_t st) {
+// out <- the n keys of F grouped by slab: position p of level (s, m) goes to
+// slab (p - base) >> shift, nslab slabs; se[i], se[nslab + i] receive slab i's
+// range of out.  slab: 4 * kSlabMax u64 of device scratch.
+static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,
+                      unsigned nslab, u64 *out, u64 *slab, unsigned *status,
+                      std::vector<u64> &se, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)split_smem_bytes(kSlabMax)));
+    MPHF_CUDA(cudaFuncSetAttribute(k_fine_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFineSmem));
     attr = true;
   }
   u64 *counts = slab, *cursor = slab + kSlabMax, *end = slab + 2 * kSlabMax;
@@ -335,9 +398,10 @@ static int slab_order(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *R,
   {
     LaunchScope ls("slab_count", st);
     k_slab_count<<<grid_for(n, kSlabCountThreads * 16, (unsigned)sm_count() * 8),
-                   kSlabCountThreads, 0, st>>>(F, n, s, m, g_slab_shift, nslab, counts);
+                   kSlabCountThreads, 0, st>>>(F, n, s, m, base, shift, nslab, counts);
   }
-  std::vector<u64> c(nslab), se(2 * (size_t)nslab);
+  std::vector<u64> c(nslab);
+  se.assign(2 * (size_t)nslab, 0);
   MPHF_CUDA(cudaMemcpyAsync(c.data(), counts, nslab * 8, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaStreamSynchronize(st));
   u64 run = 0;
@@ -347,16 +411,61 @@ static int slab_order(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *R,
     se[nslab + i] = run;
   }
   if (run != n) return MPHF_EINTERNAL;
+  // pageable copies: the host data is staged before each call returns
   MPHF_CUDA(cudaMemcpyAsync(cursor, se.data(), nslab * 8, cudaMemcpyHostToDevice, st));
   MPHF_CUDA(cudaMemcpyAsync(end, se.data() + nslab, nslab * 8, cudaMemcpyHostToDevice, st));
   {
     LaunchScope ls("slab_scatter", st);
     k_slab_scatter<<<grid_for(n, kTile, (unsigned)sm_count() * 2), kTT,
-                     split_smem_bytes(nslab), st>>>(F, n, s, m, g_slab_shift, nslab, cursor, end,
-                                                    R, status);
+                     split_smem_bytes(nslab), st>>>(F, n, s, m, base, shift, nslab, cursor, end,
+                                                    out, status);
   }
-  // the host copies of the offsets are read by the copies above before return
-  MPHF_CUDA(cudaStreamSynchronize(st));
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+// ArrayFill of a level whose keys R are grouped by slab (ranges se):
+// each slab's keys are grouped again into fine slabs of 2^kFineShift positions
+// (into T) and filled in shared memory; A_d and weight(A_d) are written
+// directly, then level d+1 is sized.
+static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::vector<u64> &se,
+                        Scratch &sc, u64 *Alev, BuildMeta *meta, int d, int L, double gamma,
+                        unsigned *status, cudaStream_t st) {
+  u64 need = 0;
+  for (unsigned c = 0; c < nslab; c++) need = std::max(need, se[nslab + c] - se[c]);
+  if (sc.T.bytes < need * 8) {
+    dev_free(sc.T, st);
+    int rc = dev_alloc(sc.T, need * 8, st);
+    if (rc != MPHF_OK) return rc;
+  }
+  u64 *T = (u64 *)sc.T.p;
+  u64 *fstart = (u64 *)sc.slab.p + 3 * kSlabMax;
+  std::vector<u64> fse;
+  for (unsigned c = 0; c < nslab; c++) {
+    const u64 a = se[c], b = se[nslab + c];
+    const u64 base = (u64)c << g_slab_shift;
+    const u64 range = std::min((u64)1 << g_slab_shift, m - base);
+    if (a == b) {  // no key in the slab: its stretch of A_d is all zero
+      MPHF_CUDA(cudaMemsetAsync(Alev + (base >> 6), 0, range / 8, st));
+      continue;
+    }
+    const unsigned nf = (unsigned)((range + ((u64)1 << kFineShift) - 1) >> kFineShift);
+    int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, (u64 *)sc.slab.p, status,
+                        fse, st);
+    if (rc != MPHF_OK) return rc;
+    MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
+    {
+      LaunchScope ls("fine_fill", st);
+      k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, fstart, (u64 *)sc.slab.p + 2 * kSlabMax,
+                                                       s, m, base, base + range, Alev,
+                                                       &meta->weight[d]);
+    }
+    MPHF_CUDA(cudaGetLastError());
+  }
+  {
+    LaunchScope ls("extract", st);
+    k_level_done<<<1, 1, 0, st>>>(meta, d, L, gamma);
+  }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
@@ -447,6 +556,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   unsigned nslab0 = 0;
   unsigned *slab_status = nullptr;
   const u64 *F0 = keys;
+  std::vector<u64> se;  // slab ranges of the grouped keys
 
 #define TRY(x)                  \
   do {                          \
@@ -474,7 +584,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   // for it the keys stay in their order.
   nslab0 = slab_count_for(m0);
   if (nslab0) {
-    if (dev_alloc(sc.R, N * 8, st) != MPHF_OK || dev_alloc(sc.slab, 3 * kSlabMax * 8, st) != MPHF_OK) {
+    if (dev_alloc(sc.R, N * 8, st) != MPHF_OK || dev_alloc(sc.slab, 4 * kSlabMax * 8, st) != MPHF_OK) {
       cudaGetLastError();
       dev_free(sc.R, st);
       dev_free(sc.slab, st);
@@ -482,15 +592,19 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     }
   }
   slab_status = (unsigned *)((u64 *)sc.dupflag.p + 2);
+  // Level 0: ArrayFill over the caller's keys (grouped by slab: in shared
+  // memory, fine slab by fine slab), then extraction.
   if (nslab0) {
-    TRY(slab_order(keys, N, h->s[0], m0, nslab0, (u64 *)sc.R.p, (u64 *)sc.slab.p, slab_status,
-                   st));
+    TRY(group_keys(keys, N, h->s[0], m0, 0, g_slab_shift, nslab0, (u64 *)sc.R.p,
+                   (u64 *)sc.slab.p, slab_status, se, st));
     F0 = (const u64 *)sc.R.p;
+    TRY(fill_grouped(F0, h->s[0], m0, nslab0, se, sc, (u64 *)sc.A0.p, meta, 0, (int)L, gamma,
+                     slab_status, st));
+  } else {
+    TRY(launch_fill0(F0, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
+    TRY(launch_extract((u64 *)sc.AC0.p, m0, (u64 *)sc.A0.p, nullptr, meta, 0, (int)L, gamma,
+                       st));
   }
-
-  // Level 0: ArrayFill over the (grouped) keys, then extraction.
-  TRY(launch_fill0(F0, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
-  TRY(launch_extract((u64 *)sc.AC0.p, m0, (u64 *)sc.A0.p, nullptr, meta, 0, (int)L, gamma, st));
   TRY(read_u64(&meta->n[1], &n1, st));
 
   if (n1 > 0) {
@@ -512,6 +626,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   {
     // Level loop: compaction of d (+ fill of d+1), extraction of d+1.
     u64 n_next = n1;  // |F_{d+1}|
+    u64 off_next = 0;
     const u64 *Fin = F0;
     int d = 0;
     for (;;) {
@@ -540,13 +655,17 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
       }
       const u64 *Fnext = Fout;
       if (nslab) {
-        TRY(slab_order(Fout, n_next, h->s[d + 1], m_next, nslab, (u64 *)sc.R.p,
-                       (u64 *)sc.slab.p, slab_status, st));
+        TRY(group_keys(Fout, n_next, h->s[d + 1], m_next, 0, g_slab_shift, nslab,
+                       (u64 *)sc.R.p, (u64 *)sc.slab.p, slab_status, se, st));
         Fnext = (const u64 *)sc.R.p;
-        TRY(launch_fill0(Fnext, n_next, h->s[d + 1], m_next, ACnext, st));
+        TRY(read_u64(&meta->off[d + 1], &off_next, st));
+        TRY(fill_grouped(Fnext, h->s[d + 1], m_next, nslab, se, sc,
+                         (u64 *)sc.arena.p + ((off_next - m0) >> 6), meta, d + 1, (int)L, gamma,
+                         slab_status, st));
+      } else {
+        TRY(launch_extract(ACnext, level_bits(n1, gamma), (u64 *)sc.A0.p, (u64 *)sc.arena.p,
+                           meta, d + 1, (int)L, gamma, st));
       }
-      TRY(launch_extract(ACnext, level_bits(n1, gamma), (u64 *)sc.A0.p, (u64 *)sc.arena.p, meta,
-                         d + 1, (int)L, gamma, st));
       TRY(read_u64(&meta->n[d + 2], &n_next, st));
       Fin = Fnext;
       d++;
@@ -839,7 +958,7 @@ extern "C" int mphf_debug_config(int path, double cap_scale) {
 extern "C" int mphf_build_path(const mphf_t *h) { return h ? h->path : 0; }
 
 extern "C" int mphf_debug_slabs(uint32_t shift, uint64_t min_ac_bytes) {
-  if (shift < 6 || shift > 40) return MPHF_EINVAL;
+  if (shift < 6 || shift > 29) return MPHF_EINVAL;  // at most 2048 fine slabs of 2^18 a slab
   bbh::g_slab_shift = shift;
   bbh::g_slab_min_ac = min_ac_bytes;
   return MPHF_OK;
