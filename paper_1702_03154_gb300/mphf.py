@@ -498,7 +498,7 @@ class Server:
     """The C serving loop (continuous batching of lookups, admitted builds)."""
 
     def __init__(self, max_batch_keys=1 << 22, max_batch_reqs=4096, max_inflight=3,
-                 build_workers=2, mem_reserve=2 << 30):
+                 build_workers=1, mem_reserve=2 << 30):
         p = ctypes.c_void_p()
         _check(lib().mphf_server_create(int(max_batch_keys), int(max_batch_reqs),
                                         int(max_inflight), int(build_workers), int(mem_reserve),
