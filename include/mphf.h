@@ -149,6 +149,11 @@ int mphf_batched_tuning(uint32_t S, uint64_t total_keys, uint64_t *pmax, uint64_
 int mphf_batched_set_tuning(uint32_t S, uint64_t total_keys, uint64_t pmax, uint64_t bset_max,
                             uint64_t tail_keys);
 
+/* Test hook: nonzero sends every lookup through the kernels with 64-bit
+ * position arithmetic, which otherwise only functions with a level of 2^32
+ * bits or more, or 2^36 bits of A, take.  Results never depend on it. */
+int mphf_debug_lookup_wide(int on);
+
 /* Test hook for the unbucketed construction: a level whose hit/collision
  * array (2 bits a position) exceeds min_ac_bytes has its keys grouped by slabs
  * of 2^shift positions, and each slab's keys by fine slabs of 2^18 positions

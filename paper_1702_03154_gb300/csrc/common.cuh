@@ -231,7 +231,9 @@ struct mphf {
 namespace bbh {
 // Every level below 2^32 bits and A below 2^36 bits: a probe's position
 // arithmetic fits 32 bits (word index g >> 5 or piece index g >> 4 < 2^32).
+extern int g_lookup_wide;  // test hook: 1 sends every lookup through the 64-bit kernels
 inline bool narrow_positions(const mphf *h) {
+  if (g_lookup_wide) return false;
   bool narrow = (h->M >> 36) == 0;
   for (uint32_t d = 0; d < h->L_used; d++) narrow = narrow && (h->m[d] >> 32) == 0;
   return narrow;

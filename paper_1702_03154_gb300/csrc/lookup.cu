@@ -236,7 +236,14 @@ int lookup_impl(const mphf_t *h, const u64 *keys, u64 n, u64 *out, cudaStream_t 
 
 }  // namespace bbh
 
+int bbh::g_lookup_wide = 0;
+
 using namespace bbh;
+
+extern "C" int mphf_debug_lookup_wide(int on) {
+  g_lookup_wide = on ? 1 : 0;
+  return MPHF_OK;
+}
 
 extern "C" int mphf_lookup(const mphf_t *h, const uint64_t *d_keys, uint64_t n, uint64_t *d_out,
                            void *stream) {

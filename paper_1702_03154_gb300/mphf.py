@@ -85,6 +85,7 @@ def lib():
         "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
         "mphf_batched_debug_config": ([dbl], i32),
         "mphf_debug_slabs": ([u32, u64], i32),
+        "mphf_debug_lookup_wide": ([i32], i32),
         "mphf_batched_tuning": ([u32, u64, pu64, pu64, pu64], i32),
         "mphf_batched_set_tuning": ([u32, u64, u64, u64, u64], i32),
         "mphf_workspace_release": ([], None),
@@ -402,6 +403,11 @@ def autotune_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: 
                                      _stream_ptr(stream), ctypes.byref(best))
     _check(rc, "mphf_autotune_batched")
     return best.value
+
+
+def debug_lookup_wide(on: bool = True) -> None:
+    """Test hook: every lookup through the 64-bit position kernels."""
+    _check(lib().mphf_debug_lookup_wide(1 if on else 0), "mphf_debug_lookup_wide")
 
 
 def debug_slabs(shift: int = 27, min_ac_bytes: int = 64 << 20) -> None:

@@ -125,3 +125,25 @@ def test_bad_sector_size_is_refused(M):
         with pytest.raises(M.MPHFError) as e:
             g.set_layout(b)
         assert e.value.code == M.EINVAL
+
+
+def test_wide_position_kernels_every_layout(M):
+    # The kernels with 64-bit position arithmetic (taken on their own only by
+    # functions past 2^32-bit levels or 2^36 bits of A) give the same indices
+    # in every layout, single- and multi-function.
+    keys = inputs.splitmix64_keys(300007, 118)
+    q = np.concatenate([inputs.shuffled(keys, 9), inputs.splitmix64_keys(9999, 119)])
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=13)
+    want = o.lookup(q)
+    hs = [M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=13) for _ in range(3)]
+    hs[1].set_layout(64)
+    hs[2].set_layout(8)
+    M.debug_lookup_wide(True)
+    try:
+        for h in hs:
+            assert np.array_equal(M.to_u64(h.lookup(dev(q))), want)
+        outs = M.lookup_multi(hs, [dev(q)] * 3)
+    finally:
+        M.debug_lookup_wide(False)
+    for out in outs:
+        assert np.array_equal(M.to_u64(out), want)
