@@ -326,7 +326,8 @@ static constexpr size_t kFineSmem = 2 * ((size_t)1 << kFineShift) / 8;  // hit +
 
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64 *__restrict__ fend,
-            u64 s, u64 m, u64 base, u64 lim, u64 *__restrict__ Alev, u64 *__restrict__ weight) {
+            const u64 *__restrict__ fcap, u64 s, u64 m, u64 base, u64 lim,
+            u64 *__restrict__ Alev, u64 *__restrict__ weight) {
   extern __shared__ __align__(16) unsigned fsm[];
   __shared__ u64 red[kFineThreads / 32];
   constexpr unsigned kWords = (1u << kFineShift) / 32;
@@ -335,7 +336,7 @@ k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64
   const u64 np = min((u64)1 << kFineShift, lim - p0);  // lim: end of the slab, a multiple of 64
   for (unsigned i = threadIdx.x; i < 2 * kWords; i += kFineThreads) fsm[i] = 0;
   __syncthreads();
-  const u64 i1 = fend[blockIdx.x];
+  const u64 i1 = min(fend[blockIdx.x], fcap[blockIdx.x]);  // an overflowed range stops at its end
   for (u64 i = fstart[blockIdx.x] + threadIdx.x; i < i1; i += kFineThreads) {
     const unsigned q = (unsigned)(level_pos(__ldcs(T + i), s, m) - p0);  // < np
     const unsigned bit = 1u << (q & 31);
@@ -357,6 +358,18 @@ k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64
     u64 t = 0;
     for (int i = 0; i < kFineThreads / 32; i++) t += red[i];
     if (t) atomicAdd(weight, t);
+  }
+}
+
+// Fine slab f of a slab takes T[f cap, (f + 1) cap): a cap of mean + 8 sigma
+// + 64 keys, so no count pass is needed; a slab whose keys overflow a range
+// (raised in status by the multisplit) is redone with exact counts.
+__global__ void k_fine_ranges(u64 *__restrict__ cursor, u64 *__restrict__ end,
+                              u64 *__restrict__ start, unsigned nf, u64 cap) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < nf) {
+    start[f] = cursor[f] = (u64)f * cap;
+    end[f] = (u64)(f + 1) * cap;
   }
 }
 
@@ -431,36 +444,74 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
 static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::vector<u64> &se,
                         Scratch &sc, u64 *Alev, BuildMeta *meta, int d, int L, double gamma,
                         unsigned *status, cudaStream_t st) {
+  const u64 fine = (u64)1 << kFineShift;
+  auto fine_count = [&](unsigned c) -> unsigned {
+    const u64 base = (u64)c << g_slab_shift;
+    const u64 range = std::min((u64)1 << g_slab_shift, m - base);
+    return (unsigned)((range + fine - 1) >> kFineShift);
+  };
+  auto fine_cap = [&](unsigned c) -> u64 {
+    // keys expected in a whole fine slab: the slab's keys spread over its range
+    const u64 base = (u64)c << g_slab_shift;
+    const u64 range = std::min((u64)1 << g_slab_shift, m - base);
+    const double mean = (double)(se[nslab + c] - se[c]) * (double)std::min(fine, range) /
+                        (double)range;
+    const u64 cap = (u64)(g_cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));  // scale: tests only
+    return (cap + 3) & ~3ull;
+  };
+  // T holds one slab's keys in either form: fixed-capacity ranges, or the
+  // exact ranges of a redo
   u64 need = 0;
-  for (unsigned c = 0; c < nslab; c++) need = std::max(need, se[nslab + c] - se[c]);
+  for (unsigned c = 0; c < nslab; c++)
+    if (se[nslab + c] > se[c])
+      need = std::max(need, std::max((u64)fine_count(c) * fine_cap(c), se[nslab + c] - se[c]));
   if (sc.T.bytes < need * 8) {
     dev_free(sc.T, st);
     int rc = dev_alloc(sc.T, need * 8, st);
     if (rc != MPHF_OK) return rc;
   }
   u64 *T = (u64 *)sc.T.p;
+  u64 *cursor = (u64 *)sc.slab.p + kSlabMax, *end = (u64 *)sc.slab.p + 2 * kSlabMax;
   u64 *fstart = (u64 *)sc.slab.p + 3 * kSlabMax;
   std::vector<u64> fse;
-  for (unsigned c = 0; c < nslab; c++) {
-    const u64 a = se[c], b = se[nslab + c];
-    const u64 base = (u64)c << g_slab_shift;
-    const u64 range = std::min((u64)1 << g_slab_shift, m - base);
-    if (a == b) {  // no key in the slab: its stretch of A_d is all zero
-      MPHF_CUDA(cudaMemsetAsync(Alev + (base >> 6), 0, range / 8, st));
-      continue;
+  // exact = false: fine ranges of a fixed capacity; true: counted first
+  for (int exact = 0; exact < 2; exact++) {
+    for (unsigned c = 0; c < nslab; c++) {
+      const u64 a = se[c], b = se[nslab + c];
+      const u64 base = (u64)c << g_slab_shift;
+      const u64 range = std::min((u64)1 << g_slab_shift, m - base);
+      if (a == b) {  // no key in the slab: its stretch of A_d is all zero
+        MPHF_CUDA(cudaMemsetAsync(Alev + (base >> 6), 0, range / 8, st));
+        continue;
+      }
+      const unsigned nf = fine_count(c);
+      if (exact) {
+        int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, (u64 *)sc.slab.p,
+                            status, fse, st);
+        if (rc != MPHF_OK) return rc;
+        MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
+      } else {
+        k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
+        LaunchScope ls("slab_scatter", st);
+        k_slab_scatter<<<grid_for(b - a, kTile, (unsigned)sm_count() * 2), kTT,
+                         split_smem_bytes(nf), st>>>(R + a, b - a, s, m, base, kFineShift, nf,
+                                                     cursor, end, T, status);
+      }
+      {
+        LaunchScope ls("fine_fill", st);
+        k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, fstart, cursor, end, s, m, base,
+                                                         base + range, Alev, &meta->weight[d]);
+      }
+      MPHF_CUDA(cudaGetLastError());
     }
-    const unsigned nf = (unsigned)((range + ((u64)1 << kFineShift) - 1) >> kFineShift);
-    int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, (u64 *)sc.slab.p, status,
-                        fse, st);
-    if (rc != MPHF_OK) return rc;
-    MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
-    {
-      LaunchScope ls("fine_fill", st);
-      k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, fstart, (u64 *)sc.slab.p + 2 * kSlabMax,
-                                                       s, m, base, base + range, Alev,
-                                                       &meta->weight[d]);
-    }
-    MPHF_CUDA(cudaGetLastError());
+    if (exact) break;
+    // a fixed-capacity range overflowed (duplicate-heavy input): redo the level
+    unsigned flag = 0;
+    MPHF_CUDA(cudaMemcpyAsync(&flag, status, 4, cudaMemcpyDeviceToHost, st));
+    MPHF_CUDA(cudaStreamSynchronize(st));
+    if (!flag) break;
+    MPHF_CUDA(cudaMemsetAsync(status, 0, 4, st));
+    MPHF_CUDA(cudaMemsetAsync(&meta->weight[d], 0, 8, st));
   }
   {
     LaunchScope ls("extract", st);

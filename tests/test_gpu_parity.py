@@ -381,6 +381,29 @@ def test_unbucketed_slab_grouping(M, gamma, levels, shift):
     assert np.array_equal(M.to_u64(g.lookup(dev(q))), o.lookup(q))
 
 
+@pytest.mark.parametrize("cap_scale", [1.0, 0.3])
+def test_unbucketed_grouping_overflow_redo(M, cap_scale):
+    # Fine slabs take fixed-capacity ranges; a range that overflows (capacity
+    # scaled down here, or thousands of copies of one key) makes the level
+    # redo its grouping with exact counts: same function, duplicates reported.
+    keys = inputs.splitmix64_keys(300007, 60)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=14)
+    M.debug_config(1, cap_scale)
+    M.debug_slabs(20, 0)
+    try:
+        g = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=14)
+        dup = np.concatenate([keys, np.full(5000, keys[3], dtype=np.uint64)])
+        with pytest.raises(M.MPHFError) as e:
+            M.MPHF.build(dev(dup), gamma=2.0, levels=25, seed=14)
+        assert e.value.code == M.EDUPLICATE
+    finally:
+        M.debug_slabs()
+        M.debug_config(0, 1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(M.to_u64(g.lookup(dev(keys))), o.lookup(keys))
+
+
 def test_unbucketed_slab_grouping_at_scale(M):
     # 1.5e8 keys at gamma 2: level 0's hit/collision array (75 MB) is past the
     # default threshold, so the unbucketed path groups it into 3 slabs; the
