@@ -491,7 +491,10 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
         if (rc != MPHF_OK) return rc;
         MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
       } else {
-        k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
+        {
+          LaunchScope lr("slab_ranges", st);
+          k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
+        }
         LaunchScope ls("slab_scatter", st);
         k_slab_scatter<<<grid_for(b - a, kTile, (unsigned)sm_count() * 2), kTT,
                          split_smem_bytes(nf), st>>>(R + a, b - a, s, m, base, kFineShift, nf,
