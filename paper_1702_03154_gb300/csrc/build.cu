@@ -395,9 +395,7 @@ static unsigned slab_count_for(u64 m) {
 // out <- the n keys of F grouped by slab: position p of level (s, m) goes to
 // slab (p - base) >> shift, nslab slabs; se[i], se[nslab + i] receive slab i's
 // range of out.  slab: 4 * kSlabMax u64 of device scratch.
-static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,
-                      unsigned nslab, u64 *out, u64 *slab, unsigned *status,
-                      std::vector<u64> &se, cudaStream_t st) {
+static int slab_attrs() {
   static bool attr = false;
   if (!attr) {
     MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -406,6 +404,14 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
                                    (int)kFineSmem));
     attr = true;
   }
+  return MPHF_OK;
+}
+
+static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,
+                      unsigned nslab, u64 *out, u64 *slab, unsigned *status,
+                      std::vector<u64> &se, cudaStream_t st) {
+  int rc0 = slab_attrs();
+  if (rc0 != MPHF_OK) return rc0;
   u64 *counts = slab, *cursor = slab + kSlabMax, *end = slab + 2 * kSlabMax;
   MPHF_CUDA(cudaMemsetAsync(counts, 0, nslab * 8, st));
   {
@@ -444,6 +450,8 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
 static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::vector<u64> &se,
                         Scratch &sc, u64 *Alev, BuildMeta *meta, int d, int L, double gamma,
                         unsigned *status, cudaStream_t st) {
+  int rc0 = slab_attrs();
+  if (rc0 != MPHF_OK) return rc0;
   const u64 fine = (u64)1 << kFineShift;
   auto fine_count = [&](unsigned c) -> unsigned {
     const u64 base = (u64)c << g_slab_shift;
