@@ -149,6 +149,19 @@ int mphf_batched_tuning(uint32_t S, uint64_t total_keys, uint64_t *pmax, uint64_
 int mphf_batched_set_tuning(uint32_t S, uint64_t total_keys, uint64_t pmax, uint64_t bset_max,
                             uint64_t tail_keys);
 
+/* Test hooks, host arithmetic only (no device work).  mphf_debug_size_level:
+ * the bucketed construction's choice for a level of n keys with a target of
+ * btarget buckets: B buckets of P positions (a power of two) and cap key slots
+ * each.  mphf_debug_level1_bound: for a bucketed build of N keys, the bound
+ * n1_hi on |F_1| and the slots capY (and buckets Bb) of level 1's arena,
+ * allocated before level 0 runs: every level size of n <= n1_hi keys must fit
+ * (B <= Bb, B cap <= capY).  MPHF_EINVAL for NULL outputs, gamma < 1 or
+ * btarget = 0. */
+int mphf_debug_size_level(uint64_t n, double gamma, uint64_t btarget, uint64_t *B, uint64_t *cap,
+                          uint64_t *P);
+int mphf_debug_level1_bound(uint64_t N, double gamma, uint64_t btarget, uint64_t *n1_hi,
+                            uint64_t *capY, uint64_t *Bb);
+
 /* Test hook: nonzero sends every lookup through the kernels with 64-bit
  * position arithmetic, which otherwise only functions with a level of 2^32
  * bits or more, or 2^36 bits of A, take.  Results never depend on it. */

@@ -524,6 +524,25 @@ struct FastScratch {
   }
 };
 
+// Level 1's bucket arena, allocated before level 0 runs: slots for any level
+// size the device may pick for |F_1| <= n1_hi = E|F_1| + 10 sqrt(N) + 256
+// (|F_1| has a standard deviation below sqrt(N)).  With B <= Bb buckets of
+// cap = cap_scale (mean + 8 sqrt(mean) + 64) slots, the means summing to at
+// most n + P, B cap <= cap_scale (n + P + 8 sqrt(B (n + P)) + 64 B) + 4 B.
+static u64 level1_bound(u64 N, double gamma, u64 Btarget, u64 Pmax, double cap_scale,
+                        u64 *n1_hi_out, u64 *Bb_out) {
+  const double ev1 = expect_next((double)N, gamma);  // E|F_1|
+  u64 n1_hi = (u64)ceil(ev1 + 10.0 * sqrt((double)N) + 256.0);
+  if (n1_hi > N) n1_hi = N;
+  const u64 m1_hi = level_bits(n1_hi, gamma);
+  u64 Bb = ceil_div(m1_hi, Pmax);
+  if (Bb < Btarget) Bb = Btarget;
+  const double tot = (double)(n1_hi + Pmax);
+  *n1_hi_out = n1_hi;
+  *Bb_out = Bb;
+  return (u64)(cap_scale * (tot + 8.0 * sqrt((double)Bb * tot) + 64.0 * (double)Bb)) + 4 * Bb + 64;
+}
+
 // Largest level size the tail may take for this gamma (keys + 2 bit arrays in 200 KB).
 static u64 tail_limit(double gamma, u64 *mcap_out) {
   u64 T = kTailMaxKeys;
@@ -641,14 +660,9 @@ int fast_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaS
       // level that does not fit anyway (duplicate-heavy input) is caught by
       // finish_level and the build is redone by the unbucketed path.
       const double ev1 = expect_next((double)N, gamma);  // E|F_1|
-      u64 n1_hi = (u64)ceil(ev1 + 10.0 * sqrt((double)N) + 256.0);
-      if (n1_hi > N) n1_hi = N;
+      u64 n1_hi = 0, Bb = 0;
+      cfg.capY = level1_bound(N, gamma, cfg.Btarget, cfg.Pmax, cfg.cap_scale, &n1_hi, &Bb);
       const u64 m1_hi = level_bits(n1_hi, gamma);
-      u64 Bb = ceil_div(m1_hi, cfg.Pmax);
-      if (Bb < cfg.Btarget) Bb = cfg.Btarget;
-      const double tot = (double)(n1_hi + cfg.Pmax);
-      cfg.capY = (u64)(cfg.cap_scale * (tot + 8.0 * sqrt((double)Bb * tot) + 64.0 * (double)Bb)) +
-                 4 * Bb + 64;
       FTRY(dev_alloc(sc.Y, cfg.capY * 8, st));
       FTRY(dev_alloc(sc.YP, cfg.capY * 4, st));
       cfg.Y = (u64 *)sc.Y.p;
@@ -798,3 +812,27 @@ fail:
 }
 
 }  // namespace bbh
+
+// Test hooks (host arithmetic only, no device work): the bucketed level size
+// the device picks for n keys, and the level-1 arena bound of an N-key build.
+extern "C" int mphf_debug_size_level(uint64_t n, double gamma, uint64_t btarget, uint64_t *B,
+                                     uint64_t *cap, uint64_t *P) {
+  if (!B || !cap || !P || !(gamma >= 1.0) || btarget == 0) return MPHF_EINVAL;
+  bbh::FLevel lv;
+  memset(&lv, 0, sizeof(lv));
+  bbh::size_bucketed(lv, n, gamma, 4096, bbh::kPmax, btarget, 1.0);
+  *B = lv.B;
+  *cap = lv.cap;
+  *P = lv.P;
+  return MPHF_OK;
+}
+
+extern "C" int mphf_debug_level1_bound(uint64_t N, double gamma, uint64_t btarget,
+                                       uint64_t *n1_hi, uint64_t *capY, uint64_t *Bb) {
+  if (!n1_hi || !capY || !Bb || !(gamma >= 1.0) || btarget == 0) return MPHF_EINVAL;
+  bbh::u64 nh = 0, bb = 0;
+  *capY = bbh::level1_bound(N, gamma, btarget, bbh::kPmax, 1.0, &nh, &bb);
+  *n1_hi = nh;
+  *Bb = bb;
+  return MPHF_OK;
+}

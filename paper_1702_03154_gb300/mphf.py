@@ -86,6 +86,8 @@ def lib():
         "mphf_batched_debug_config": ([dbl], i32),
         "mphf_debug_slabs": ([u32, u64], i32),
         "mphf_debug_lookup_wide": ([i32], i32),
+        "mphf_debug_size_level": ([u64, dbl, u64, pu64, pu64, pu64], i32),
+        "mphf_debug_level1_bound": ([u64, dbl, u64, pu64, pu64, pu64], i32),
         "mphf_batched_tuning": ([u32, u64, pu64, pu64, pu64], i32),
         "mphf_batched_set_tuning": ([u32, u64, u64, u64, u64], i32),
         "mphf_workspace_release": ([], None),
@@ -403,6 +405,22 @@ def autotune_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: 
                                      _stream_ptr(stream), ctypes.byref(best))
     _check(rc, "mphf_autotune_batched")
     return best.value
+
+
+def debug_size_level(n: int, gamma: float, btarget: int) -> tuple:
+    """(B, cap, P): the bucketed level size the device picks for n keys."""
+    v = [ctypes.c_uint64() for _ in range(3)]
+    _check(lib().mphf_debug_size_level(int(n), float(gamma), int(btarget),
+                                       *[ctypes.byref(x) for x in v]), "mphf_debug_size_level")
+    return tuple(x.value for x in v)
+
+
+def debug_level1_bound(N: int, gamma: float, btarget: int) -> tuple:
+    """(n1_hi, capY, Bb): level 1's arena bound of a bucketed build of N keys."""
+    v = [ctypes.c_uint64() for _ in range(3)]
+    _check(lib().mphf_debug_level1_bound(int(N), float(gamma), int(btarget),
+                                         *[ctypes.byref(x) for x in v]), "mphf_debug_level1_bound")
+    return tuple(x.value for x in v)
 
 
 def debug_lookup_wide(on: bool = True) -> None:
