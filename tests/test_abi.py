@@ -70,3 +70,38 @@ def test_oracle_and_cuda_sources_share_nothing():
     for f in glob.glob(os.path.join(ROOT, "paper_1702_03154_gb300", "*.py")):
         txt = open(f).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_new_entry_points_validate_without_gpu(libpath):
+    # Host-side argument checks of the later entry points (no CUDA call made).
+    from paper_1702_03154_gb300 import mphf
+    L = mphf.lib()
+    h = ctypes.c_void_p()
+    # build + lookup from host buffers
+    assert L.mphf_build_lookup_host(8, 3, 2.0, 25, 0, 8, 1, 8, None, None) == mphf.EINVAL
+    for gamma, levels in ((0.5, 25), (float("nan"), 25), (2.0, 0), (2.0, 65)):
+        assert L.mphf_build_lookup_host(8, 3, gamma, levels, 0, 8, 1, 8, None,
+                                        ctypes.byref(h)) == mphf.EINVAL
+        assert h.value is None
+    assert L.mphf_build_lookup_host(None, 3, 2.0, 25, 0, 8, 1, 8, None,
+                                    ctypes.byref(h)) == mphf.EINVAL
+    assert L.mphf_build_lookup_host(8, 3, 2.0, 25, 0, None, 1, 8, None,
+                                    ctypes.byref(h)) == mphf.EINVAL
+    assert L.mphf_build_lookup_host(8, 3, 2.0, 25, 0, 8, 1, None, None,
+                                    ctypes.byref(h)) == mphf.EINVAL
+    # batched tuning: values outside what the kernels take are refused
+    for args in ((4095, 64, 8192), (3 * 4096, 64, 8192), (524288, 64, 8192), (65536, 0, 8192),
+                 (65536, 4096, 8192), (65536, 64, 1000)):
+        assert L.mphf_batched_set_tuning(10, 10**6, *args) == mphf.EINVAL
+    v = [ctypes.c_uint64() for _ in range(3)]
+    assert L.mphf_batched_tuning(7, 12345, *[ctypes.byref(x) for x in v]) == mphf.EINVAL
+    assert (v[0].value, v[1].value, v[2].value) == (131072, 64, 8192)  # the defaults
+    assert L.mphf_batched_set_tuning(7, 12345, 65536, 16, 4096) == mphf.OK
+    assert L.mphf_batched_tuning(7, 12345, *[ctypes.byref(x) for x in v]) == mphf.OK
+    assert (v[0].value, v[1].value, v[2].value) == (65536, 16, 4096)
+    assert L.mphf_batched_set_tuning(7, 12345, 131072, 64, 8192) == mphf.OK
+    # test hooks
+    assert L.mphf_debug_slabs(5, 0) == mphf.EINVAL and L.mphf_debug_slabs(30, 0) == mphf.EINVAL
+    assert L.mphf_debug_slabs(27, 64 << 20) == mphf.OK
+    assert L.mphf_debug_size_level(1000, 2.0, 0, *[ctypes.byref(x) for x in v]) == mphf.EINVAL
+    assert L.mphf_debug_level1_bound(1000, 0.5, 608, *[ctypes.byref(x) for x in v]) == mphf.EINVAL
