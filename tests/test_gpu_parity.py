@@ -214,16 +214,20 @@ def test_config2_shape_parity_1e7(M, gamma):
     check(M, keys, gamma, 25, 0, queries=q)
 
 
-def test_config2_full_size_gamma2(M):
-    # N = 1e8, gamma = 2, L = 25, as the benchmark times it: the full structure
-    # (levels, A, rank, fallback) against the oracle, a bijection check of all
-    # 1e8 lookups in shuffled order on the GPU result, and 2e6 sampled lookups
-    # against the oracle.
+@pytest.mark.parametrize("gamma", [2.0, 1.0, 5.0])
+def test_config2_full_size(M, gamma):
+    # N = 1e8, L = 25, as the benchmark times it (gamma = 2; 1 and 5 as its
+    # sweep does; at gamma = 1 about 1e3 keys reach the fallback): the full
+    # structure (levels, A, rank, fallback) against the oracle, a bijection
+    # check of all 1e8 lookups in shuffled order on the GPU result, and 2e6
+    # sampled lookups against the oracle.
     N = 10**8
     keys = inputs.splitmix64_keys(N, 2)
-    o = oracle.build(keys, gamma=2.0, levels=25, seed=0)
+    o = oracle.build(keys, gamma=gamma, levels=25, seed=0)
     kd = dev(keys)
-    g = M.MPHF.build(kd, gamma=2.0, levels=25, seed=0)
+    g = M.MPHF.build(kd, gamma=gamma, levels=25, seed=0)
+    if gamma == 1.0:
+        assert g.num_fallback > 0
     assert_same_structure(g, o)
     perm = torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
     q = kd[perm]
