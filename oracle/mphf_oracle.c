@@ -83,7 +83,7 @@ uint64_t oracle_mix(uint64_t z)
     return z ^ (z >> 31);
 }
 
-/* s_d: seed of the level-d hash function h_d (Sec. 2.1, "a new hash function h_1"). */
+/* s_d: seed of the level-d hash function h_d (Sec. 2.1: every level hashes with its own function). */
 uint64_t oracle_level_seed(uint64_t seed, uint32_t d)
 {
     return oracle_mix(oracle_mix(seed) + (uint64_t)d);
@@ -197,7 +197,7 @@ int oracle_build_hooked(const uint64_t *keys, uint64_t N, double gamma, uint32_t
     uint64_t n = N;
     uint32_t i = 0;
     uint64_t off = 0;
-    while (n > 0 && i < L) {           /* "while F_i not empty and i <= last" */
+    while (n > 0 && i < L) {           /* levels go on while keys remain, at most L of them */
         h->n[i] = n;
         h->s[i] = oracle_level_seed(seed, i);
         h->m[i] = oracle_level_bits(n, gamma);
