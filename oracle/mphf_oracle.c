@@ -13,11 +13,11 @@
  * paper leaves open fixed as follows:
  *
  *   mix(z)      the SplitMix64 finalizer (Steele, Lea, Flood, OOPSLA 2014);
- *               the paper only asks for an "xor-shift based" hash (Sec. 3.3).
+ *               the paper only says its hash is built on xor-shifts (Sec. 3.3).
  *   s_d         level seed  = mix(mix(seed) + d).
  *   h_d(x)      = mix(x XOR s_d).
  *   position    p = floor(h_d(x) * m_d / 2^64) (Lemire's fastrange reduction,
- *               in place of "mod" in Algorithms 1-3).
+ *               in place of the modulo of Algorithms 1-3).
  *   m_d = |A_d| = |C_d| = max(64, ceil(gamma * |F_d|) rounded up to a multiple
  *               of 64), gamma >= 1 real (Sec. 2.2.4); ceil(gamma*n) is taken
  *               from one IEEE-754 double multiply.
@@ -27,7 +27,7 @@
  *               counters (Sec. 3.1): rank[b] = ones in bits [0, 512 b).
  *   levels      L levels numbered 0 .. L-1 (D = 25 by default, Sec. 3.5);
  *               keys still colliding after level L-1 go to the fallback.
- *   fallback    the "regular hash table" of Sec. 3.5 is a sorted array of
+ *   fallback    the table of leftover keys of Sec. 3.5 is a sorted array of
  *               the leftover keys; key at sorted position i gets index
  *               N - n_fb + i (the range Algorithm 1 gives it).
  *   duplicates  identical keys collide at every level, so they reach the
@@ -57,7 +57,7 @@ typedef struct oracle_mphf {
     uint64_t N;
     double gamma;
     uint32_t L;          /* level budget */
-    uint32_t L_used;     /* levels actually built ("last" + 1) */
+    uint32_t L_used;     /* levels actually built (index of the last one + 1) */
     uint64_t seed;
     uint64_t n[ORACLE_MAX_LEVELS + 1]; /* n[d] = |F_d|; n[L_used] = |fallback| */
     uint64_t m[ORACLE_MAX_LEVELS];     /* |A_d| in bits */
@@ -400,7 +400,7 @@ void oracle_copy_fallback(const oracle_mphf *h, uint64_t *out)
  */
 /*
  * The same with one 64-bit counter every rank_block bits: Sec. 3.1's default
- * is 512; the "minirank" setting of Sec. 4.3 (Table 1) samples every 1024.
+ * is 512; the minirank setting of Sec. 4.3 (Table 1) samples every 1024.
  */
 double oracle_bits_per_key_sampled(const oracle_mphf *h, uint64_t rank_block)
 {
