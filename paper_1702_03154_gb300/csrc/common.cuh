@@ -15,7 +15,7 @@ namespace bbh {
 typedef unsigned long long u64;
 
 // ---------------------------------------------------------------------------
-// Level hash (Sec. 3.3 asks for a fast "xor-shift based" hash; this library
+// Level hash (Sec. 3.3 only says the hash is a fast one built on xor-shifts; this library
 // uses the SplitMix64 finalizer, a xor-shift-multiply mixer).
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ u64 mix64(u64 z) {
