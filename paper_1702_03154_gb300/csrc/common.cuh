@@ -15,8 +15,8 @@ namespace bbh {
 typedef unsigned long long u64;
 
 // ---------------------------------------------------------------------------
-// Level hash (Sec. 3.3 only says the hash is a fast one built on xor-shifts; this library
-// uses the SplitMix64 finalizer, a xor-shift-multiply mixer).
+// Level hash (Sec. 3.3 only says the hash is a fast one built on xor-shifts;
+// this library uses the SplitMix64 finalizer, a xor-shift-multiply mixer).
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ u64 mix64(u64 z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
