@@ -118,7 +118,7 @@ struct PartDest {
 __global__ void __launch_bounds__(kTT, 2)
 k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned t_sa, t_sb;
+  __shared__ unsigned t_sa;
   __shared__ u64 t_gb0;
   __shared__ unsigned t_nb;
   __shared__ u64 t_m, t_base;  // one bucketed set in the tile: its m and first bucket - gb0
@@ -140,7 +140,6 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
       unsigned sb = lo;
       while (sb + 1 < c.S && key_off[sb + 1] < t1) sb++;
       t_sa = lo;
-      t_sb = sb;
       // global buckets of the large sets in [sa, sb] are consecutive
       u64 g0 = ~0ull, g1 = 0;
       for (unsigned s = lo; s <= sb; s++) {

@@ -492,7 +492,7 @@ __device__ __forceinline__ TailSmem carve_tail(unsigned char *smem, u64 mcap,
   return t;
 }
 
-static size_t tail_smem_bytes(u64 mcap, u64 maxk = kTailMaxKeys) {
+static inline size_t tail_smem_bytes(u64 mcap, u64 maxk = kTailMaxKeys) {
   return maxk * 8 + 2 * (mcap >> 5) * 4 + 32 * 8 + 40 * 4;
 }
 
