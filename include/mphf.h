@@ -218,8 +218,8 @@ uint64_t mphf_device_bytes(const mphf_t *h);
  *       A, at gamma = 1 the size drops from 3.1 to 2.9 bits/key as in the
  *       paper, and a probe loads both halves of its sector;
  *   8   units of 48 bits of A + a 16-bit count within blocks of 1024 units (a
- *       64-bit count per block): every probe is one 8-byte load, the fastest
- *       lookups, at the price of counts costing 1/3 of A.
+ *       64-bit count per block): every probe is one 8-byte load (lookups as
+ *       fast as with 32-byte sectors), at the price of counts costing 1/3 of A.
  * Builds make 32-byte sectors; mphf_set_layout re-stores a function in
  * another layout, keeping every index unchanged; a handle of a batched build
  * then gets arrays of its own.  mphf_bits_per_key counts one 64-bit counter
