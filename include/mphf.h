@@ -110,21 +110,31 @@ int mphf_build_lookup_host(const uint64_t *h_keys, uint64_t n, double gamma, uin
  * Build S independent functions at once, one per key set (the same method
  * and conventions as mphf_build, applied to each set separately; set s gets
  * exactly the function mphf_build would give it with the same arguments).
- *   d_keys     device array holding the sets back to back.
- *   h_offsets  host array of S + 1 non-decreasing indices into d_keys: set s
- *              is d_keys[h_offsets[s] .. h_offsets[s+1]).
+ *   d_keys     device array holding the sets back to back (8-byte aligned).
+ *   d_offsets  device array of S + 1 non-decreasing indices into d_keys
+ *              (8-byte aligned): set s is d_keys[d_offsets[s] ..
+ *              d_offsets[s+1]).  Read back to the host at the start of the
+ *              call (the plan of the build depends on the set sizes).
+ *   S          number of sets, >= 1.
  *   out        host array of S handles, each released with mphf_free (their
  *              device memory is one shared block, returned when the last is
  *              freed).
  * All sets advance level by level together (one launch per phase per level
  * for all sets, recorded once as a CUDA graph and replayed); sets of at most
  * 16384 keys run every level in one thread block.  Synchronous w.r.t. stream.
- * Errors as mphf_build; on error no handle is returned.  Builds through this
- * call are serialised within a process (they share a device workspace, kept
- * between calls; see mphf_workspace_release).
+ * Errors as mphf_build, and MPHF_EINVAL for decreasing offsets; on error no
+ * handle is returned (every out[s] is NULL).  Builds through this call are
+ * serialised within a process (they share a device workspace, kept between
+ * calls; see mphf_workspace_release).
  */
-int mphf_build_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S, double gamma,
+int mphf_build_batched(const uint64_t *d_keys, const uint64_t *d_offsets, uint32_t S, double gamma,
                        uint32_t levels, uint64_t seed, void *stream, mphf_t **out);
+
+/* As mphf_build_batched with the S + 1 offsets in host memory (h_offsets),
+ * for callers that planned the sets on the host; nothing is read back. */
+int mphf_build_batched_host_offsets(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S,
+                                    double gamma, uint32_t levels, uint64_t seed, void *stream,
+                                    mphf_t **out);
 
 /* Time the candidate bucket widths of mphf_build_batched on this input and keep
  * the fastest for inputs of the same size class (process-wide).  The functions
@@ -235,7 +245,8 @@ void mphf_free(mphf_t *h);
 
 /* ---- introspection (host copies; for tests and tools) ------------------ */
 uint64_t mphf_num_keys(const mphf_t *h);
-uint32_t mphf_num_levels(const mphf_t *h);      /* levels built, last + 1 */
+/* Levels built (index of the last level + 1) into *levels; MPHF_EINVAL for NULL. */
+int mphf_num_levels(const mphf_t *h, uint32_t *levels);
 uint64_t mphf_total_bits(const mphf_t *h);      /* M */
 uint64_t mphf_num_rank(const mphf_t *h);        /* ceil(M / 512) */
 uint64_t mphf_num_fallback(const mphf_t *h);    /* n_fb */
@@ -263,13 +274,12 @@ int mphf_debug_config(int path, double cap_scale);
 
 /*
  * Rank table of a bit array without allocating device memory.  The paper has
- * no counterpart: this is an allocation-free rank-table build over a caller's
- * bit array (Sec. 3.1's 512-bit checkpoints, each beside seven 9-bit in-block
- * counts), for callers that must not call cudaMalloc:
- * code that records work into a CUDA graph (cudaMalloc cannot be captured),
- * serving loops that run under a fixed device-memory budget, and hosts whose
- * own allocator owns the device memory (a direct cudaMalloc there fragments
- * that pool and stalls the device).
+ * no counterpart: the output is one 64-bit count of ones per 512 bits of the
+ * array, next to seven 9-bit in-block counts.  It is for callers that must
+ * not call cudaMalloc: code that records work into a CUDA graph (cudaMalloc
+ * cannot be captured), serving loops that run under a fixed device-memory
+ * budget, and hosts whose own allocator owns the device memory (a direct
+ * cudaMalloc there fragments that pool and stalls the device).
  *   d_words  device array of nwords 64-bit words (16-byte aligned).
  *   d_rank2  device output of 2 * ceil(nwords / 8) words (16-byte aligned):
  *            d_rank2[2b] = ones of the array in bits [0, 512 b), d_rank2[2b+1]
@@ -279,20 +289,21 @@ int mphf_debug_config(int path, double cap_scale);
  * Scratch lives in a fixed array inside the library: at most 2^27 words
  * (2^33 bits) per call; larger inputs return MPHF_EINVAL.  The first call on
  * each device looks up that array's device address (make it before any stream
- * capture that should contain later calls).  All calls share the array:
- * calls whose work may overlap on the GPU (different streams without ordering)
- * race and must be avoided.  Asynchronous on `stream`.
+ * capture that should contain later calls; the address is kept until the
+ * library is unloaded, so the device must not be reset meanwhile).  All calls
+ * share the array: calls whose work may overlap on the GPU (different streams
+ * without ordering) race and must be avoided.  Asynchronous on `stream`.
  */
 int mphf_rank_table_noalloc(const uint64_t *d_words, uint64_t nwords, uint64_t *d_rank2,
                             uint64_t *d_total, void *stream);
 
 /* ---- construction without stored key sets ---------------------------------- */
 /*
- * Build without storing F_d (Sec. 3.4, the second strategy; Sec. 4.4): level d
+ * Build without storing F_d (Sec. 3.4, the second strategy; Sec. 4.5): level d
  * re-reads every input key, asks levels 0..d-1 whether it was placed there
  * (the query of Algorithm 3), and fills A_d with the keys that were not.  The
  * device holds the bit arrays only, until |F_d| <= keep_fraction * n; then F_d
- * is collected once and the remaining levels run on that list (Sec. 4.4
+ * is collected once and the remaining levels run on that list (Sec. 4.5
  * keeps keys in memory below 2%: keep_fraction = 0.02).  The function equals
  * mphf_build's on the same keys, bit for bit.
  *   mphf_build_nodisk     keys in a caller-owned device array (8-byte aligned),
@@ -313,7 +324,7 @@ int mphf_build_generated(uint64_t n, uint64_t key_seed, uint64_t key_start, doub
 
 /* ---- string keys ------------------------------------------------------------ */
 /*
- * 64-bit keys of n byte strings (Sec. 4.3 / Table 2 run the method on n-grams
+ * 64-bit keys of n byte strings (Sec. 4.4 / Table 2 run the method on n-grams
  * and random words; the paper does not fix how a string becomes a key).
  * String i is d_bytes[d_offsets[i] .. d_offsets[i+1]); its key is
  *   h = mix(seed + (len + 1) * 0x9E3779B97F4A7C15), then for each group of 8

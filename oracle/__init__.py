@@ -95,6 +95,12 @@ def lib():
         L.oracle_string_key.argtypes, L.oracle_string_key.restype = [vp, u64, u64], u64
         L.oracle_fill_level.argtypes, L.oracle_fill_level.restype = [vp, u64, u64, u64, vp, vp], None
         L.oracle_merge_fill.argtypes, L.oracle_merge_fill.restype = [vp, vp, vp, vp, u64], None
+        L.oracle_select_window.argtypes = [vp, u64, u64, u64, u64, u64, vp]
+        L.oracle_select_window.restype = u64
+        L.oracle_fill_window.argtypes = [vp, u64, u64, u64, u64, u64, vp, vp]
+        L.oracle_fill_window.restype = None
+        L.oracle_window_ranks.argtypes = [vp, u64, u64, u64, u64, u64, vp, vp]
+        L.oracle_window_ranks.restype = ctypes.c_int
         L.oracle_string_keys.argtypes, L.oracle_string_keys.restype = [vp, vp, u64, u64, vp], None
         _lib = L
     return _lib
@@ -245,6 +251,42 @@ def fill_level(keys, s_d: int, m: int):
     C = np.zeros(m, dtype=np.uint8)
     lib().oracle_fill_level(_ptr(k) if k.size else None, k.size, s_d & MASK64, m, _ptr(A), _ptr(C))
     return A, C
+
+
+def select_window(keys, s_d: int, m: int, lo: int, W: int) -> np.ndarray:
+    """The keys (input order) whose position on a level of m positions with
+    seed s_d lies in [lo, lo + W)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(max(1, k.size), dtype=np.uint64)
+    c = lib().oracle_select_window(_ptr(k) if k.size else None, k.size, s_d & MASK64, m, lo, W,
+                                   _ptr(out)) if k.size else 0
+    return out[:c].copy()
+
+
+def fill_window(keys, s_d: int, m: int, lo: int, W: int):
+    """ArrayFill of one level of m positions restricted to [lo, lo + W):
+    byte arrays (A, C) of W entries; keys hashed elsewhere are skipped."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    A = np.zeros(W, dtype=np.uint8)
+    C = np.zeros(W, dtype=np.uint8)
+    if k.size:
+        lib().oracle_fill_window(_ptr(k), k.size, s_d & MASK64, m, lo, W, _ptr(A), _ptr(C))
+    return A, C
+
+
+def window_ranks(keys, s_d: int, m: int, lo: int, A) -> np.ndarray:
+    """Per key: ones of the window bits A (position lo + t at entry t) before
+    the key's position, if that position is in the window with its bit set;
+    else UINT64_MAX."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    a = np.ascontiguousarray(A, dtype=np.uint8)
+    out = np.empty(k.size, dtype=np.uint64)
+    if k.size:
+        rc = lib().oracle_window_ranks(_ptr(k), k.size, s_d & MASK64, m, lo, a.size, _ptr(a),
+                                       _ptr(out))
+        if rc != OK:
+            raise OracleError(rc)
+    return out
 
 
 def merge_fill(A1, C1, A2, C2):

@@ -34,7 +34,7 @@
  *               fallback; two equal neighbours there -> ORACLE_EDUPLICATE.
  *   non-members Algorithm 3 run as is: the first level whose bit is 1 gives
  *               the rank, else a fallback hit, else UINT64_MAX.
- *   strings     byte-string keys (Sec. 4.3) become 64-bit keys by the rule of
+ *   strings     byte-string keys (Sec. 4.4) become 64-bit keys by the rule of
  *               oracle_string_key below, then take the same path.
  */
 #include <stdint.h>
@@ -417,7 +417,7 @@ double oracle_bits_per_key(const oracle_mphf *h)
 }
 
 /*
- * String keys (Sec. 4.3, Table 2: the method run on n-grams and random words
+ * String keys (Sec. 4.4, Table 2: the method run on n-grams and random words
  * of 18 characters).  The method itself takes 64-bit keys; a string is first
  * turned into one by this library's convention (the paper does not give its
  * string hash):
@@ -467,6 +467,67 @@ void oracle_fill_level(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t 
 {
     for (uint64_t i = 0; i < n; i++)
         fill_one(A, C, oracle_fastrange(oracle_hash(keys[i], s_d), m));
+}
+
+/*
+ * The keys whose level position p = fastrange(h_d(x), m) falls inside the
+ * window [lo, lo + W) of a level of m positions; they are copied, in input
+ * order, to out (room for n keys).  Returns how many there are.  ArrayFill
+ * decides every position from the keys hashed to it alone, so these keys
+ * and nothing else fix A_d and C_d inside the window.
+ */
+uint64_t oracle_select_window(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t m,
+                              uint64_t lo, uint64_t W, uint64_t *out)
+{
+    uint64_t c = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = oracle_fastrange(oracle_hash(keys[i], s_d), m);
+        if (p >= lo && p - lo < W)
+            out[c++] = keys[i];
+    }
+    return c;
+}
+
+/*
+ * Algorithm 2 (ArrayFill) restricted to the window [lo, lo + W) of a level of
+ * m positions: A and C hold W entries (position lo + t at entry t, zeroed by
+ * the caller); keys hashed outside the window are skipped.
+ */
+void oracle_fill_window(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t m, uint64_t lo,
+                        uint64_t W, unsigned char *A, unsigned char *C)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = oracle_fastrange(oracle_hash(keys[i], s_d), m);
+        if (p >= lo && p - lo < W)
+            fill_one(A, C, p - lo);
+    }
+}
+
+/*
+ * Exclusive rank inside a window (Sec. 2.2.3 restricted to [lo, lo + W) of a
+ * level of m positions whose window bits are A, W entries): for each key whose
+ * position p lies in the window with A[p - lo] = 1, out = ones of A in
+ * [lo, p); other keys get UINT64_MAX.  For the window at the very start of
+ * the concatenated bit array this is the key's index.
+ */
+int oracle_window_ranks(const uint64_t *keys, uint64_t n, uint64_t s_d, uint64_t m, uint64_t lo,
+                        uint64_t W, const unsigned char *A, uint64_t *out)
+{
+    uint64_t *before = (uint64_t *)malloc((W + 1) * sizeof(uint64_t));
+    if (!before)
+        return ORACLE_ENOMEM;
+    before[0] = 0;
+    for (uint64_t t = 0; t < W; t++)
+        before[t + 1] = before[t] + A[t];
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = oracle_fastrange(oracle_hash(keys[i], s_d), m);
+        if (p >= lo && p - lo < W && A[p - lo] == 1)
+            out[i] = before[p - lo];
+        else
+            out[i] = UINT64_MAX;
+    }
+    free(before);
+    return ORACLE_OK;
 }
 
 /*

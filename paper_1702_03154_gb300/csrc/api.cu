@@ -198,7 +198,7 @@ const char *mphf_strerror(int code) {
 
 const char *mphf_last_cuda_error(void) { return g_err_text; }
 
-int mphf_abi_version(void) { return 1; }
+int mphf_abi_version(void) { return 2; }
 
 void mphf_free(mphf_t *h) {
   if (!h) return;
@@ -228,7 +228,11 @@ double mphf_bits_per_key(const mphf_t *h) {
 }
 
 uint64_t mphf_num_keys(const mphf_t *h) { return h ? h->N : 0; }
-uint32_t mphf_num_levels(const mphf_t *h) { return h ? h->L_used : 0; }
+int mphf_num_levels(const mphf_t *h, uint32_t *levels) {
+  if (!h || !levels) return MPHF_EINVAL;
+  *levels = h->L_used;
+  return MPHF_OK;
+}
 uint64_t mphf_total_bits(const mphf_t *h) { return h ? h->M : 0; }
 uint64_t mphf_num_rank(const mphf_t *h) { return h ? h->n_rank : 0; }
 uint64_t mphf_num_fallback(const mphf_t *h) { return h ? h->n_fb : 0; }

@@ -788,6 +788,8 @@ struct GraphCache {
   BCfg cfg;
   int D = -1;
   u64 total = 0, nbk = 0, mcap = 0;
+  u64 tail_keys = 0;   // tail shape and its shared memory: a new tuning re-records
+  size_t tail_b = 0;
   unsigned kernels = 0;
   cudaStream_t stream = nullptr;
 };
@@ -1064,7 +1066,8 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   // replay the recorded loop when the configuration is unchanged
   GraphCache &gc = g_ws.g;
   bool reuse = gc.exec && gc.D == D && gc.stream == st && gc.total == total && gc.nbk == nbk &&
-               gc.mcap == mcap && memcmp(&gc.cfg, &c, sizeof(c)) == 0;
+               gc.mcap == mcap && gc.tail_keys == tune.tail_keys && gc.tail_b == tail_b &&
+               memcmp(&gc.cfg, &c, sizeof(c)) == 0;
   if (!reuse) {
     if (gc.exec) {
       cudaGraphExecDestroy(gc.exec);
@@ -1097,6 +1100,8 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     gc.total = total;
     gc.nbk = nbk;
     gc.mcap = mcap;
+    gc.tail_keys = tune.tail_keys;
+    gc.tail_b = tail_b;
     gc.kernels = nk_rec;
     gc.stream = st;
   }
@@ -1292,9 +1297,9 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
 
 using namespace bbh;
 
-extern "C" int mphf_build_batched(const uint64_t *d_keys, const uint64_t *h_offsets, uint32_t S,
-                                  double gamma, uint32_t levels, uint64_t seed, void *stream,
-                                  mphf_t **out) {
+extern "C" int mphf_build_batched_host_offsets(const uint64_t *d_keys, const uint64_t *h_offsets,
+                                               uint32_t S, double gamma, uint32_t levels,
+                                               uint64_t seed, void *stream, mphf_t **out) {
   if (!out || !h_offsets || S == 0) return MPHF_EINVAL;
   for (uint32_t s = 0; s < S; s++) out[s] = nullptr;
   if (!(gamma >= 1.0) || isinf(gamma) || levels < 1 || levels > MPHF_MAX_LEVELS) return MPHF_EINVAL;
@@ -1427,4 +1432,19 @@ extern "C" void mphf_workspace_release(void) {
   if (g_ws.pin) cudaFreeHost(g_ws.pin);
   g_ws.pin = nullptr;
   g_ws.pin_bytes = 0;
+}
+
+// The offsets in device memory: read back (S + 1 words, waiting on the
+// stream) and the host-offset build runs on them.
+extern "C" int mphf_build_batched(const uint64_t *d_keys, const uint64_t *d_offsets, uint32_t S,
+                                  double gamma, uint32_t levels, uint64_t seed, void *stream,
+                                  mphf_t **out) {
+  if (!out || !d_offsets || S == 0 || ((uintptr_t)d_offsets & 7)) return MPHF_EINVAL;
+  for (uint32_t s = 0; s < S; s++) out[s] = nullptr;
+  std::vector<uint64_t> off((size_t)S + 1);
+  cudaStream_t st = (cudaStream_t)stream;
+  MPHF_CUDA(cudaMemcpyAsync(off.data(), d_offsets, off.size() * sizeof(uint64_t),
+                            cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  return mphf_build_batched_host_offsets(d_keys, off.data(), S, gamma, levels, seed, stream, out);
 }

@@ -104,15 +104,27 @@ struct LaunchScope {
   ~LaunchScope() { launch_end(s); }
 };
 
-inline int sm_count() {
-  static int v = 0;
-  if (!v) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    if (v <= 0) v = 1;
+// Current device, clamped to the 64 slots of the per-device caches below.
+inline int cur_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = 0;
   }
-  return v;
+  return dev;
+}
+
+// SM count of the current device (cached per device; racing writers store
+// the same value).
+inline int sm_count() {
+  static int cache[64] = {0};
+  const int dev = cur_device();
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
 }
 
 // CTAs of `kernel` (block threads, dynamic smem bytes) that fit on the whole

@@ -204,7 +204,8 @@ static int launch_lookup(const u64 *keys, u64 n, u64 *out, const LookupArgs &a,
                          const LevelTable &t, cudaStream_t s) {
   // one wave of resident CTAs: warps take chunks in a fixed order, so a
   // second wave would only start after the first has drained
-  static unsigned mb = 0;
+  static unsigned mb_dev[64] = {0};  // per device
+  unsigned &mb = mb_dev[cur_device()];
   if (!mb) mb = resident_grid(k_lookup<SLOTS, W, NARROW>, kLookupThreads, 0);
   const u64 csz = lookup_chunk(n, (u64)mb * (kLookupThreads / 32));
   const u64 nwarps_needed = (n + csz - 1) / csz;

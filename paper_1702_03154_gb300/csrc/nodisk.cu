@@ -1,5 +1,5 @@
 // nodisk.cu -- construction without storing the level key sets (Sec. 3.4,
-// second disk strategy; Sec. 4.4's trillion-key run).
+// second disk strategy; Sec. 4.5's trillion-key run).
 //
 // The default build copies F_d and compacts it into F_{d+1} at every level.
 // Here level d instead reads every input key again and asks the levels
@@ -7,9 +7,9 @@
 // up to level d-1); the keys that were not are exactly F_d, and they go
 // through ArrayFill (Algorithm 2) for level d.  No key is stored, so the
 // device holds only the bit arrays: with keys generated on the fly (the
-// SplitMix64 stream key(j) of mphf_keygen, as Sec. 4.4 streams its keys)
+// SplitMix64 stream key(j) of mphf_keygen, as Sec. 4.5 streams its keys)
 // N is bounded by the size of the bit arrays instead of 8 bytes per key.
-// Once |F_d| falls to keep_fraction * N (Sec. 4.4 uses 2%), F_d is collected
+// Once |F_d| falls to keep_fraction * N (Sec. 4.5 uses 2%), F_d is collected
 // once and the remaining levels run on the stored list.
 //
 // ArrayFill uses L2/HBM atomics on an interleaved hit/collision array (bits

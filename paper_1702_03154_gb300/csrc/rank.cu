@@ -350,7 +350,10 @@ static constexpr u64 kNoAllocMaxCtas = 65536;
 static __device__ __align__(256) u64 g_rank_scratch[kNoAllocMaxCtas];
 
 static std::mutex g_noalloc_mu;
-static u64 *g_noalloc_ptr[64] = {nullptr};  // device address of g_rank_scratch, per device
+// Device address of g_rank_scratch, per device, looked up on the first call
+// there.  The cache assumes the device is never reset while the library is
+// loaded (cudaDeviceReset unloads the module that holds the array).
+static u64 *g_noalloc_ptr[64] = {nullptr};
 
 }  // namespace bbh
 

@@ -260,7 +260,8 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total, u64 cs
 
 template <int W, bool NARROW>
 static int launch_multi_wn(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
-  static u64 maxb = 0;  // one wave of resident CTAs
+  static u64 maxb_dev[64] = {0};  // one wave of resident CTAs, per device
+  u64 &maxb = maxb_dev[cur_device()];
   if (!maxb) maxb = resident_grid(k_lookup_multi<W, NARROW>, kMultiThreads, 0);
   const u64 csz = lookup_chunk(total, maxb * (kMultiThreads / 32));
   const u64 chunks = (total + csz - 1) / csz;

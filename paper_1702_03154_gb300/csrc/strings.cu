@@ -1,4 +1,4 @@
-// strings.cu -- byte-string keys (Sec. 4.3, Table 2).
+// strings.cu -- byte-string keys (Sec. 4.4, Table 2).
 //
 // The method takes 64-bit keys; a byte string becomes one by this library's
 // rule: h = mix(seed + (len + 1) G), then for every group of 8 bytes in order

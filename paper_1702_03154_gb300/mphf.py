@@ -70,7 +70,7 @@ def lib():
         "mphf_device_bytes": ([vp], u64),
         "mphf_free": ([vp], None),
         "mphf_num_keys": ([vp], u64),
-        "mphf_num_levels": ([vp], u32),
+        "mphf_num_levels": ([vp, vp], i32),
         "mphf_total_bits": ([vp], u64),
         "mphf_num_rank": ([vp], u64),
         "mphf_num_fallback": ([vp], u64),
@@ -82,6 +82,7 @@ def lib():
         "mphf_build_path": ([vp], i32),
         "mphf_debug_config": ([i32, dbl], i32),
         "mphf_build_batched": ([vp, vp, u32, dbl, u32, u64, vp, vp], i32),
+        "mphf_build_batched_host_offsets": ([vp, vp, u32, dbl, u32, u64, vp, vp], i32),
         "mphf_autotune_batched": ([vp, vp, u32, dbl, u32, u64, vp, ctypes.POINTER(dbl)], i32),
         "mphf_batched_debug_config": ([dbl], i32),
         "mphf_debug_slabs": ([u32, u64], i32),
@@ -215,7 +216,7 @@ class MPHF:
     def build_generated(cls, n: int, key_seed: int, key_start: int = 0, gamma: float = 2.0,
                         levels: int = 25, seed: int = 0, keep_fraction: float = 0.02,
                         stream=None) -> "MPHF":
-        """Build over the SplitMix64 keys key(j), j < n, generated on the fly (Sec. 4.4)."""
+        """Build over the SplitMix64 keys key(j), j < n, generated on the fly (Sec. 4.5)."""
         h = ctypes.c_void_p()
         rc = lib().mphf_build_generated(int(n), int(key_seed) & NOT_FOUND,
                                         int(key_start) & NOT_FOUND, float(gamma), int(levels),
@@ -317,7 +318,9 @@ class MPHF:
 
     @property
     def num_levels(self) -> int:
-        return lib().mphf_num_levels(self._h)
+        v = ctypes.c_uint32()
+        _check(lib().mphf_num_levels(self._h, ctypes.byref(v)), "mphf_num_levels")
+        return v.value
 
     @property
     def total_bits(self) -> int:
@@ -374,6 +377,14 @@ def _host_ptr(orig, arr: np.ndarray) -> Optional[int]:
     return arr.ctypes.data if arr.size else None
 
 
+def _is_cuda_tensor(x) -> bool:
+    try:
+        import torch
+        return isinstance(x, torch.Tensor) and x.is_cuda
+    except ImportError:  # pragma: no cover
+        return False
+
+
 def _offsets(offsets) -> np.ndarray:
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
     if off.ndim != 1 or off.size < 2:
@@ -383,15 +394,28 @@ def _offsets(offsets) -> np.ndarray:
 
 def build_batched(keys, offsets, gamma: float = 2.0, levels: int = 25, seed: int = 0,
                   stream=None) -> list:
-    """One function per key set: set s is keys[offsets[s]:offsets[s+1]]."""
+    """One function per key set: set s is keys[offsets[s]:offsets[s+1]].
+
+    offsets: S + 1 entries, either a CUDA tensor (int64 / uint64; passed to
+    mphf_build_batched) or host integers (mphf_build_batched_host_offsets)."""
     keys = _dev_keys(keys)
+    kp = keys.data_ptr() if keys.numel() else None
+    if _is_cuda_tensor(offsets):
+        if offsets.dim() != 1 or offsets.numel() < 2 or offsets.element_size() != 8:
+            raise ValueError("offsets must hold S + 1 64-bit entries")
+        off_t = offsets.contiguous()
+        S = off_t.numel() - 1
+        arr = (ctypes.c_void_p * S)()
+        rc = lib().mphf_build_batched(kp, off_t.data_ptr(), S, float(gamma), int(levels),
+                                      int(seed) & NOT_FOUND, _stream_ptr(stream), arr)
+        _check(rc, "mphf_build_batched")
+        return [MPHF(ctypes.c_void_p(arr[i])) for i in range(S)]
     off = _offsets(offsets)
     S = off.size - 1
     arr = (ctypes.c_void_p * S)()
-    rc = lib().mphf_build_batched(keys.data_ptr() if keys.numel() else None, off.ctypes.data, S,
-                                  float(gamma), int(levels), int(seed) & NOT_FOUND,
-                                  _stream_ptr(stream), arr)
-    _check(rc, "mphf_build_batched")
+    rc = lib().mphf_build_batched_host_offsets(kp, off.ctypes.data, S, float(gamma), int(levels),
+                                               int(seed) & NOT_FOUND, _stream_ptr(stream), arr)
+    _check(rc, "mphf_build_batched_host_offsets")
     return [MPHF(ctypes.c_void_p(arr[i])) for i in range(S)]
 
 

@@ -43,7 +43,7 @@ def test_error_text_without_gpu(libpath):
     L = mphf.lib()
     assert L.mphf_strerror(mphf.EDUPLICATE) == b"duplicate keys"
     assert L.mphf_strerror(mphf.EINVAL) == b"invalid argument"
-    assert L.mphf_abi_version() == 1
+    assert L.mphf_abi_version() == 2
 
 
 def test_argument_validation_without_gpu(libpath):
@@ -59,6 +59,13 @@ def test_argument_validation_without_gpu(libpath):
     assert L.mphf_lookup(None, 8, 1, 8, None) == mphf.EINVAL
     assert L.mphf_bits_per_key(None) == 0.0
     L.mphf_free(None)
+    lv = ctypes.c_uint32(7)
+    assert L.mphf_num_levels(None, ctypes.byref(lv)) == mphf.EINVAL and lv.value == 7
+    outs = (ctypes.c_void_p * 2)()
+    assert L.mphf_build_batched(8, None, 2, 2.0, 25, 0, None, outs) == mphf.EINVAL
+    assert L.mphf_build_batched(8, 12, 2, 2.0, 25, 0, None, outs) == mphf.EINVAL  # misaligned
+    assert L.mphf_build_batched(8, 16, 0, 2.0, 25, 0, None, outs) == mphf.EINVAL
+    assert L.mphf_build_batched_host_offsets(8, None, 2, 2.0, 25, 0, None, outs) == mphf.EINVAL
 
 
 def test_oracle_and_cuda_sources_share_nothing():

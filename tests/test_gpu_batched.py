@@ -58,6 +58,36 @@ def test_batched_matches_oracle_per_set(M, gamma, levels):
             assert g.build_path in (1, 2, 3)
 
 
+def test_device_offsets_through_the_c_abi(M):
+    # mphf_build_batched takes the S + 1 offsets in device memory; the
+    # functions equal the host-offset call's and the oracle's.
+    import ctypes
+    keys, off = make_sets(20, 1, 50000, 13, extra_sizes=(0, 16385))
+    kd = dev(keys)
+    od = torch.from_numpy(off.view(np.int64)).cuda()
+    L = M.lib()
+    S = off.size - 1
+    arr = (ctypes.c_void_p * S)()
+    rc = L.mphf_build_batched(kd.data_ptr(), od.data_ptr(), S, 2.0, 25, 5,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), arr)
+    assert rc == M.OK
+    hs = [M.MPHF(ctypes.c_void_p(arr[i])) for i in range(S)]
+    hh = M.build_batched(kd, off, gamma=2.0, levels=25, seed=5)
+    hd = M.build_batched(kd, od, gamma=2.0, levels=25, seed=5)
+    for s in range(S):
+        k = keys[off[s]:off[s + 1]]
+        o = oracle.build(k, gamma=2.0, levels=25, seed=5)
+        for g in (hs[s], hh[s], hd[s]):
+            same(g, o)
+    # decreasing offsets are refused, and no handle comes back
+    bad = off.copy()
+    bad[3], bad[4] = bad[4], bad[3]
+    arr2 = (ctypes.c_void_p * S)()
+    rc = L.mphf_build_batched(kd.data_ptr(), torch.from_numpy(bad.view(np.int64)).cuda().data_ptr(),
+                              S, 2.0, 25, 5, None, arr2)
+    assert rc == M.EINVAL and all(arr2[i] is None for i in range(S))
+
+
 def test_batched_equals_plain_builds(M):
     keys, off = make_sets(32, 1000, 300000, 11)
     kd = dev(keys)

@@ -1,4 +1,4 @@
-"""Construction without stored key sets (Sec. 3.4 second strategy, Sec. 4.4).
+"""Construction without stored key sets (Sec. 3.4 second strategy, Sec. 4.5).
 
 Re-reading every key at each level and asking the levels already built
 whether it was placed there yields exactly F_d, so the function must be the

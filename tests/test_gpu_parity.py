@@ -218,9 +218,8 @@ def test_config2_shape_parity_1e7(M, gamma):
 def test_config2_full_size(M, gamma):
     # N = 1e8, L = 25, as the benchmark times it (gamma = 2; 1 and 5 as its
     # sweep does; at gamma = 1 about 1e3 keys reach the fallback): the full
-    # structure (levels, A, rank, fallback) against the oracle, a bijection
-    # check of all 1e8 lookups in shuffled order on the GPU result, and 2e6
-    # sampled lookups against the oracle.
+    # structure (levels, A, rank, fallback) and every one of the 1e8 indices,
+    # queried in shuffled order, against the oracle; 1e6 non-members too.
     N = 10**8
     keys = inputs.splitmix64_keys(N, 2)
     o = oracle.build(keys, gamma=gamma, levels=25, seed=0)
@@ -229,15 +228,15 @@ def test_config2_full_size(M, gamma):
     if gamma == 1.0:
         assert g.num_fallback > 0
     assert_same_structure(g, o)
-    perm = torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
-    q = kd[perm]
-    out = g.lookup(q)
-    hits = torch.zeros(N, dtype=torch.int32, device="cuda")
-    assert int(out.min()) >= 0 and int(out.max()) < N
-    hits.index_add_(0, out, torch.ones_like(out, dtype=torch.int32))
-    assert bool((hits == 1).all())
-    idx = inputs.sample_indices(N, 2 * 10**6, 5)
-    assert np.array_equal(M.to_u64(g.lookup(kd[torch.from_numpy(idx).cuda()])), o.lookup(keys[idx]))
+    del kd
+    q = inputs.shuffled(keys, 3)
+    del keys
+    out = M.to_u64(g.lookup(dev(q)))
+    assert np.array_equal(out, o.lookup(q))
+    assert np.array_equal(np.sort(out), np.arange(N, dtype=np.uint64))
+    del out, q
+    others = inputs.splitmix64_keys(10**6, 103)
+    assert np.array_equal(M.to_u64(g.lookup(dev(others))), o.lookup(others))
 
 
 @pytest.mark.parametrize("n,gamma,levels", [(10**6, 2.0, 25), (300001, 1.0, 25), (300001, 5.0, 25),
@@ -410,19 +409,32 @@ def test_unbucketed_grouping_overflow_redo(M, cap_scale):
 
 def test_unbucketed_slab_grouping_at_scale(M):
     # 1.5e8 keys at gamma 2: level 0's hit/collision array (75 MB) is past the
-    # default threshold, so the unbucketed path groups it into 3 slabs; the
-    # function equals the bucketed build's (itself the oracle's at smaller N).
-    keys = M.keygen(150_000_000, 58)
-    a = M.MPHF.build(keys, gamma=2.0, levels=25, seed=12)
+    # default threshold, so the unbucketed path groups it into 3 slabs and
+    # fills each fine slab in shared memory.  Both paths against the oracle:
+    # levels, A, rank, fallback; every index a bijection on the GPU, and 2e6
+    # sampled members plus non-members against the oracle.
+    N = 150_000_000
+    keys = inputs.splitmix64_keys(N, 58)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=12)
+    kd = dev(keys)
+    a = M.MPHF.build(kd, gamma=2.0, levels=25, seed=12)
     M.debug_config(1, 1.0)
     try:
-        b = M.MPHF.build(keys, gamma=2.0, levels=25, seed=12)
+        b = M.MPHF.build(kd, gamma=2.0, levels=25, seed=12)
     finally:
         M.debug_config(0, 1.0)
     assert a.build_path == 1 and b.build_path == 2
-    assert a.levels() == b.levels()
-    assert np.array_equal(a.bits(), b.bits())
-    assert np.array_equal(a.rank(), b.rank())
-    assert np.array_equal(a.fallback(), b.fallback())
-    sel = keys[::997]
-    assert torch.equal(a.lookup(sel), b.lookup(sel))
+    assert_same_structure(b, o)
+    assert_same_structure(a, o)
+    for g in (a, b):
+        out = g.lookup(kd)
+        hits = torch.zeros(N, dtype=torch.int32, device="cuda")
+        assert int(out.min()) >= 0 and int(out.max()) < N
+        hits.index_add_(0, out, torch.ones_like(out, dtype=torch.int32))
+        assert bool((hits == 1).all())
+        del out, hits
+    idx = inputs.sample_indices(N, 2 * 10**6, 6)
+    q = np.concatenate([keys[idx], inputs.splitmix64_keys(10**5, 104)])
+    want = o.lookup(q)
+    assert np.array_equal(M.to_u64(b.lookup(dev(q))), want)
+    assert np.array_equal(M.to_u64(a.lookup(dev(q))), want)

@@ -1,7 +1,11 @@
 """Serving: multi-function lookups and the continuous-batching server.
 
-Every request's result must be the same alone (mphf_lookup on its own) and
-in the mix (coalesced with other requests, while builds run), exactly.
+Every request's result must equal the oracle's (Algorithm 3, the minimal
+index of Sec. 2.2.3, on the oracle's own function over the same keys), and be
+the same alone (mphf_lookup on its own) and in the mix (coalesced with other
+requests, while builds run), exactly.  The multi-function kernel the server
+runs (32-bit probe arithmetic) is checked against the oracle in all three
+storage layouts, members and non-members.
 """
 import threading
 
@@ -28,18 +32,35 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
 
 
+RESIDENT_SIZES = [1, 37, 4096, 20000, 150001, 600000]
+
+
+def resident_args(i):
+    """gamma, L, seed of resident function i (L = 2 leaves a large fallback)."""
+    return (2.0 if i % 2 else 1.0), (25 if i != 3 else 2), i
+
+
 @pytest.fixture(scope="module")
 def resident(M):
-    sizes = [1, 37, 4096, 20000, 150001, 600000]
     hs, ks = [], []
-    for i, n in enumerate(sizes):
+    for i, n in enumerate(RESIDENT_SIZES):
         k = dev(inputs.splitmix64_keys(n, 300 + i))
-        hs.append(M.MPHF.build(k, gamma=2.0 if i % 2 else 1.0, levels=25 if i != 3 else 2, seed=i))
+        g, L, seed = resident_args(i)
+        hs.append(M.MPHF.build(k, gamma=g, levels=L, seed=seed))
         ks.append(k)
     return hs, ks
 
 
-def test_lookup_multi_equals_alone(M, resident):
+@pytest.fixture(scope="module")
+def oracles():
+    os_ = []
+    for i, n in enumerate(RESIDENT_SIZES):
+        g, L, seed = resident_args(i)
+        os_.append(oracle.build(inputs.splitmix64_keys(n, 300 + i), gamma=g, levels=L, seed=seed))
+    return os_
+
+
+def test_lookup_multi_equals_alone(M, resident, oracles):
     hs, ks = resident
     rng = np.random.default_rng(1)
     reqs = []
@@ -55,10 +76,12 @@ def test_lookup_multi_equals_alone(M, resident):
     for (i, k), o in zip(reqs, outs):
         alone = hs[i].lookup(k) if k.numel() else torch.empty(0, dtype=torch.int64, device="cuda")
         assert torch.equal(o, alone)
+        assert np.array_equal(M.to_u64(o), oracles[i].lookup(M.to_u64(k)))
 
 
-def test_server_results_same_alone_and_in_mix(M, resident):
+def test_server_results_same_alone_and_in_mix(M, resident, oracles):
     hs, ks = resident
+    hk = [M.to_u64(k) for k in ks]
     srv = M.Server(max_batch_keys=1 << 18, max_batch_reqs=256, max_inflight=3, build_workers=2,
                    mem_reserve=1 << 30)
     rng = np.random.default_rng(5)
@@ -102,10 +125,13 @@ def test_server_results_same_alone_and_in_mix(M, resident):
     srv.close()
     for t, (i, o, b) in enumerate(plan):
         assert torch.equal(outs[t], hs[i].lookup(ks[i][o:o + b])), t
-    for bk, h in zip(build_keys, built):
-        ref = oracle.build(M.to_u64(bk), gamma=2.0, levels=25, seed=3)
+        assert np.array_equal(M.to_u64(outs[t]), oracles[i].lookup(hk[i][o:o + b])), t
+    for j, (n, h) in enumerate(zip((1000, 120000), built)):
+        kh = inputs.splitmix64_keys(n, 700 + j)
+        ref = oracle.build(kh, gamma=2.0, levels=25, seed=3)
         assert np.array_equal(h.bits(), ref.bits())
         assert np.array_equal(h.rank(), ref.rank())
+        assert np.array_equal(M.to_u64(h.lookup(dev(kh))), ref.lookup(kh))
 
 
 def test_server_build_waits_for_memory(M):
@@ -130,3 +156,38 @@ def test_server_loadgen_reports_latencies(M, resident):
     assert r["lookups"] > 500
     assert r["latencies"].size == r["lookups"]
     assert np.all(r["latencies"] > 0)
+
+
+@pytest.mark.parametrize("layouts", [(32, 32, 32, 32), (64, 64, 64, 64), (8, 8, 8, 8),
+                                     (32, 64, 8, 64)])
+def test_multi_function_kernel_equals_oracle_every_layout(M, layouts):
+    # The server's kernel: one launch over requests to several functions,
+    # 32-bit probe arithmetic (every function here is far below 2^36 bits),
+    # grouped by storage layout.  Requests are members (shuffled), members
+    # answered by the fallback (L = 2), non-members, empty and tiny batches,
+    # and batches large enough to be cut into warp chunks.
+    specs = [(300000, 2.0, 25), (70001, 1.0, 2), (5000, 5.0, 25), (1_000_003, 2.0, 25)]
+    hs, qs, want = [], [], []
+    for i, ((n, g, L), lay) in enumerate(zip(specs, layouts)):
+        kh = inputs.splitmix64_keys(n, 400 + i)
+        o = oracle.build(kh, gamma=g, levels=L, seed=20 + i)
+        h = M.MPHF.build(dev(kh), gamma=g, levels=L, seed=20 + i)
+        h.set_layout(lay)
+        q = np.concatenate([inputs.shuffled(kh, 30 + i), inputs.splitmix64_keys(3001, 500 + i)])
+        hs.append(h)
+        qs.append(q)
+        want.append(o.lookup(q))
+    assert hs[1].num_fallback > 0
+    # many requests per function, of mixed sizes (0, 1, 17, ..., whole)
+    rng = np.random.default_rng(sum(layouts))
+    rh, rk, rw = [], [], []
+    for t in range(60):
+        i = int(rng.integers(len(hs)))
+        b = int(rng.choice([0, 1, 17, 2048, 40000, qs[i].size]))
+        o = int(rng.integers(0, qs[i].size - b + 1))
+        rh.append(hs[i])
+        rk.append(dev(qs[i][o:o + b]))
+        rw.append(want[i][o:o + b])
+    outs = M.lookup_multi(rh, rk)
+    for o, w in zip(outs, rw):
+        assert np.array_equal(M.to_u64(o), w)

@@ -1,4 +1,4 @@
-"""String keys on the GPU (Sec. 4.3, Table 2) against the oracle, bit for bit.
+"""String keys on the GPU (Sec. 4.4, Table 2) against the oracle, bit for bit.
 
 The device conversion of byte strings to 64-bit keys must equal the oracle's
 for every string: lengths 0 to 40 bytes, strings starting at every byte

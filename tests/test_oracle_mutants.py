@@ -52,7 +52,7 @@ MUTANTS = {
     # Multi-rank merge: a collided position keeps its A bit.
     "merge_keeps_collided_A": ("A1[p] = (unsigned char)((A1[p] | A2[p]) & !c);",
                                "A1[p] = (unsigned char)(A1[p] | A2[p]);"),
-    # String keys (Sec. 4.3): the length left out of the first state.
+    # String keys (Sec. 4.4): the length left out of the first state.
     "string_length_dropped": ("oracle_mix(seed + (len + 1) * 0x9E3779B97F4A7C15ULL)",
                               "oracle_mix(seed + 1 * 0x9E3779B97F4A7C15ULL)"),
     # String keys: groups read big-endian.

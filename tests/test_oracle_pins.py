@@ -336,7 +336,7 @@ def test_non_member_keys_follow_algorithm3():
 
 
 # ---------------------------------------------------------------- string keys
-# Strings become 64-bit keys before the method runs (Sec. 4.3).  The pins tie
+# Strings become 64-bit keys before the method runs (Sec. 4.4).  The pins tie
 # the conversion to the published SplitMix64 outputs: the first state of a
 # string of length len is output len of the generator, and a group equal to
 # that state cancels it (mix(0) = 0), so chosen strings have keys that are
@@ -462,3 +462,75 @@ def test_sharded_level0_equals_the_builds_A0():
     bits = np.unpackbits(words.view(np.uint8), bitorder="little")[:m0]
     assert np.array_equal(A, bits)
     assert int(A.sum()) == n0 - o.level_info(1)[0]
+
+
+# --------------------------------------------------- one window of a level
+# A check of a level too large for the oracle to build whole (1e10 keys)
+# fills one window of its positions from the keys hashed into it.  Pinned to
+# brute-force counting and to the level arrays of a whole build.
+@pytest.mark.parametrize("m,lo,W", [(6000, 0, 6000), (6000, 64, 1024), (6000, 5999, 1),
+                                    (6000, 4000, 2000), (2048, 100, 37)])
+def test_window_fill_is_brute_force_counting(m, lo, W):
+    keys = inputs.splitmix64_keys(3000, 143)
+    s = oracle.level_seed(7, 0)
+    bA, bC = _brute_fill(keys, s, m)
+    A, C = oracle.fill_window(keys, s, m, lo, W)
+    assert np.array_equal(A, bA[lo:lo + W]) and np.array_equal(C, bC[lo:lo + W])
+    sel = oracle.select_window(keys, s, m, lo, W)
+    pos = np.array([oracle.fastrange(oracle.mix(int(k) ^ s), m) for k in keys])
+    assert np.array_equal(sel, keys[(pos >= lo) & (pos < lo + W)])
+    # the selected keys alone give the same window
+    A2, C2 = oracle.fill_window(sel, s, m, lo, W)
+    assert np.array_equal(A2, A) and np.array_equal(C2, C)
+
+
+def test_window_of_level0_equals_the_builds_A0():
+    keys = inputs.splitmix64_keys(30000, 144)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=10)
+    n0, m0, off0, s0 = o.level_info(0)
+    bits = np.unpackbits(o.level_bits_words(0).view(np.uint8), bitorder="little")[:m0]
+    for lo, W in ((0, 640), (1280, 4096), (m0 - 512, 512)):
+        A, _ = oracle.fill_window(oracle.select_window(keys, s0, m0, lo, W), s0, m0, lo, W)
+        assert np.array_equal(A, bits[lo:lo + W])
+
+
+def test_window_ranks_of_the_first_window_are_level0_indices():
+    # For the window at the start of A the rank inside the window is the
+    # index itself: equal to Algorithm 3's answer for every key placed there.
+    keys = inputs.splitmix64_keys(30000, 145)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=11)
+    n0, m0, off0, s0 = o.level_info(0)
+    lvl = np.array([o.key_level(int(k)) for k in keys])
+    for W in (m0, 4096, 64):
+        A, _ = oracle.fill_window(keys, s0, m0, 0, W)
+        r = oracle.window_ranks(keys, s0, m0, 0, A)
+        pos = np.array([oracle.fastrange(oracle.mix(int(k) ^ s0), m0) for k in keys])
+        placed = (lvl == 0) & (pos < W)
+        assert np.array_equal(r[placed], o.lookup(keys[placed]))
+        assert np.all(r[~placed] == np.uint64((1 << 64) - 1))
+    # a later window: ranks are the indices minus the ones before the window
+    lo, W = 2048, 4096
+    A, _ = oracle.fill_window(keys, s0, m0, lo, W)
+    r = oracle.window_ranks(keys, s0, m0, lo, A)
+    pos = np.array([oracle.fastrange(oracle.mix(int(k) ^ s0), m0) for k in keys])
+    placed = (lvl == 0) & (pos >= lo) & (pos < lo + W)
+    base = int(o.rank()[lo // 512])
+    assert np.array_equal(r[placed] + np.uint64(base), o.lookup(keys[placed]))
+
+
+def test_window_selection_over_processes_equals_one_pass():
+    # the helper of the 1e10-key check splits the key stream over spawned
+    # processes; the union of their selections is the single-pass selection
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import oracle_windows
+    n, s, m = 300007, oracle.level_seed(0, 0), oracle.level_bits(300007, 2.0)
+    wins = [(0, 4096), (m // 2 // 64 * 64, 8192), (m - 640, 640)]
+    got = oracle_windows.finish_selection(
+        oracle_windows.start_selection(n, 4, s, m, wins, workers=3))
+    keys = inputs.splitmix64_keys(n, 4)
+    for (lo, W), g in zip(wins, got):
+        assert np.array_equal(g, oracle.select_window(keys, s, m, lo, W))
+    A, _ = oracle.fill_window(keys, s, m, 0, 4096)
+    assert np.array_equal(np.unpackbits(oracle_windows.pack_bits(A).view(np.uint8),
+                                        bitorder="little"), A)
