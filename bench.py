@@ -1,25 +1,33 @@
 """Benchmark: build + lookup of a cascading-bit-array MPHF on one GB300.
 
-Workload (one step): build the function over N = 1e8 distinct 64-bit keys
-(SplitMix64 outputs 0..N-1 of seed 2, resident in HBM), gamma = 2, L = 25,
-then look up all N keys in a uniformly shuffled order.  The keys (800 MB) are
-larger than L2, so no L2 flush is needed between steps.
+Headline workload (one step): build the function over N = 1e10 distinct
+64-bit keys (SplitMix64 outputs 0..N-1 of stream 4, generated on the device:
+80 GB resident in HBM), gamma = 2, L = 25, then answer Q = 1e9 lookups of
+member keys drawn uniformly at random (torch's generator, seed 5).  Keys,
+queries and level arrays are far larger than L2, so no flush is needed
+between steps.
 
-value     = N / (time of one step), Mkeys/s, over all ranks (weak scaling:
-            each rank builds its own function over its own N keys).
-e2e       = the same through the host-buffer C-ABI entry point
-            mphf_build_lookup_host (keys and queries in pinned memory, the
-            indices back to pinned memory), so the host<->device copies are
-            inside the timed region; `two_calls` times mphf_build_host then
-            mphf_lookup_host for comparison.
-roofline  = the dominant kernel's algorithmic bytes / its event-timed duration
-            against the measured HBM copy bandwidth.
+value     = N / (time of one step) in Mkeys/s over all ranks (weak scaling:
+            each rank builds its own function over its own N keys); the
+            step's build and lookup rates are reported beside it.
+e2e       = the same step through the host-buffer C-ABI entry point
+            mphf_build_lookup_host (keys and queries in pinned host memory,
+            the indices back to pinned memory), host<->device copies inside
+            the timed region; measured when the host has the memory for it.
+roofline  = the step's dominant kernel: its algorithmic bytes per launch over
+            its event-timed duration, against the measured HBM copy bandwidth.
+ceilings  = random sector loads and random atomics, measured in this run by
+            the library's ceiling kernels; the lookup and fill bounds use them.
+plain_1e8 = the N = 1e8 configuration (build + all N lookups, shuffled) as a
+            secondary block, with its gamma sweep and storage layouts.
 cpu_baseline / --impl reference = the CPU oracle on a bounded sample.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -31,9 +39,14 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "build+lookup Mkeys/s (N=1e8, gamma=2, L=25)"
-L2_RANDOM_256B_GLOADS = 270.0  # measured ceiling of random 32-byte loads into L2 (G/s)
 UNIT = "Mkeys/s"
+C3_N, C3_Q, C3_KEY_SEED, C3_QUERY_SEED = 10**10, 10**9, 4, 5
+C2_N, C2_KEY_SEED, C2_QUERY_SEED = 10**8, 2, 3
+
+
+def metric_name(N: int, Q: int) -> str:
+    return f"build+lookup Mkeys/s (N={N:.0e} keys built + Q={Q:.0e} member lookups per step, " \
+           f"gamma=2, L=25; value = N / step time)"
 
 
 def parse():
@@ -42,14 +55,17 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=float, default=1e8)
+    p.add_argument("--n", type=float, default=C3_N, help="keys of the headline step")
+    p.add_argument("--q", type=float, default=C3_Q, help="member lookups of the headline step")
     p.add_argument("--gamma", type=float, default=2.0)
     p.add_argument("--levels", type=int, default=25)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-sweep", action="store_true", help="skip timing gamma = 1 and 5")
+    p.add_argument("--no-plain", action="store_true", help="skip the N = 1e8 block")
+    p.add_argument("--no-sweep", action="store_true", help="skip timing gamma = 1 and 5 (1e8)")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-ceilings", action="store_true", help="skip the ceiling kernels")
     p.add_argument("--serve-seconds", type=float, default=3.0)
     p.add_argument("--no-layouts", action="store_true",
                    help="skip timing the lookup in the other storage layouts")
@@ -138,18 +154,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic(kernel: str, n: int):
-    """DRAM bytes per build of `kernel` from the committed ncu summary (a 3e7-key
-    capture scaled by keys), or None if there is none for this workload."""
-    p = os.path.join(ROOT, "profiles", f"{kernel}_n3e7_gamma2.md")
-    if not os.path.exists(p) or n != 10**8:
-        return None
-    for line in open(p):
-        if line.startswith("traffic_bytes_per_build_n1e8:"):
-            return int(line.split(":")[1])
-    return None
-
-
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -181,84 +185,489 @@ def host_cpu() -> dict:
             "machine": platform.machine()}
 
 
-def cpu_baseline(n_sample: int, gamma: float, levels: int):
-    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+def cpu_baseline(n_sample: int, q_sample: int, key_seed: int, gamma: float, levels: int,
+                 what: str):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: a
+    build over the first n_sample keys of the key stream, then q_sample
+    lookups of its members drawn at random."""
     import oracle
     from paper_1702_03154_gb300 import inputs
-    keys = inputs.splitmix64_keys(n_sample, 2)
-    q = inputs.shuffled(keys, 3)
+    keys = inputs.splitmix64_keys(n_sample, key_seed)
+    q = keys[inputs.sample_indices(n_sample, q_sample, 17)]
     t0 = time.perf_counter()
     h = oracle.build(keys, gamma=gamma, levels=levels, seed=0)
     t1 = time.perf_counter()
     h.lookup(q)
     t2 = time.perf_counter()
+    # the sample's step scaled like the workload's: n_sample keys built + q_sample looked up
     return {"value": n_sample / (t2 - t0) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "host": host_cpu(),
-            "sample": f"build over the first {n_sample:.0e} keys of the workload + lookup of all of "
-                      f"them in shuffled order (gamma={gamma}, L={levels}); build {t1 - t0:.2f} s, "
-                      f"lookup {t2 - t1:.2f} s, single-threaded C"}
+            "host": host_cpu(), "seconds": t2 - t0,
+            "sample": f"{what}: build over the first {n_sample:.0e} keys of the key stream + "
+                      f"{q_sample:.0e} random member lookups (gamma={gamma:g}, L={levels}); "
+                      f"build {t1 - t0:.2f} s, lookup {t2 - t1:.2f} s, single-threaded C; "
+                      f"value = keys built / (build + lookup time)"}
 
 
-def workload_config(N: int, gamma: float, L: int, rank: int = 0) -> dict:
+def workload_config(N: int, Q: int, gamma: float, L: int, rank: int = 0) -> dict:
     """The `config` of the bench line (the same for both arms)."""
-    return {"workload": f"plain single MPHF, N={N:.0e} SplitMix64 keys (seed {2 + rank}), "
-                        f"gamma={gamma:g}, L={L}; build + lookup of all N in shuffled order",
-            "N": N, "gamma": gamma, "levels": L,
-            "l2": (f"inputs ({8 * N / 1e6:.0f} MB keys + {8 * N / 1e6:.0f} MB queries) larger "
-                   "than L2; no flush" if 8 * N > 129e6 else
+    seed = C3_KEY_SEED if N == C3_N else C2_KEY_SEED
+    return {"workload": f"plain large MPHF: N={N:.0e} distinct uint64 keys (SplitMix64 outputs "
+                        f"0..N-1 of stream {seed + rank}, generated on the device, "
+                        f"{8 * N / 1e9:.0f} GB in HBM), gamma={gamma:g}, L={L}; build, bits/key, "
+                        f"then Q={Q:.0e} random member lookups",
+            "N": N, "Q": Q, "gamma": gamma, "levels": L,
+            "l2": (f"keys ({8 * N / 1e9:.1f} GB) and queries ({8 * Q / 1e9:.1f} GB) far larger "
+                   "than L2; no flush" if 8 * min(N, Q) > 129e6 else
                    "inputs smaller than L2 (a reduced test size, not the bench workload)")}
 
 
 def run_reference(args):
+    """The oracle, timed on this host's cores on bounded samples of the
+    headline workload (one sample per step)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    n_sample = 2_000_000
-    per_step = []
+    N, Q = int(args.n), int(args.q)
+    n_sample, q_sample = 2_000_000, max(1, int(2_000_000 * Q / N))
+    per_step, r = [], None
     for _ in range(args.warmup):
-        cpu_baseline(n_sample, args.gamma, args.levels)
+        cpu_baseline(n_sample, q_sample, C3_KEY_SEED, args.gamma, args.levels, "warm-up")
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = cpu_baseline(n_sample, args.gamma, args.levels)
-        per_step.append(time.perf_counter() - t0)
+        r = cpu_baseline(n_sample, q_sample, C3_KEY_SEED, args.gamma, args.levels,
+                         "sample of the headline workload")
+        per_step.append(r["seconds"])
     ms = 1e3 * float(np.mean(per_step))
     val = n_sample / (ms / 1e3) / 1e6
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    line = {"impl": "reference", "metric": metric_name(N, Q), "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": workload_config(int(args.n), args.gamma, args.levels),
+            "config": workload_config(N, Q, args.gamma, args.levels),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": r["sample"], "host": r["host"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------- GPU arm
-def algorithmic_bytes(h, name: str) -> int:
-    """Algorithmic DRAM bytes of all launches of one kernel in one build (or lookup).
+# -------------------------------------------------------- algorithmic bytes
+# Unbucketed path: a level whose hit/collision array (2 bits a position)
+# exceeds 64 MiB is grouped by slab before its fill (count pass, coarse and
+# fine multisplit, shared-memory fill); smaller levels fill with L2 atomics.
+GROUP_MIN_AC_BYTES = 64 << 20
 
-    Per key of level d the method reads the key once for ArrayFill and once for
-    the compaction, and writes each survivor once (8 B each); A_d is written
-    once (m_d / 8 B).  Moving F_0 into position buckets costs one read and one
-    write of every key.  A lookup reads its key and writes its index.
-    """
+
+def kernel_bytes(h, name: str, n_queries: int) -> int:
+    """Algorithmic DRAM bytes of all launches of one kernel in one build (or
+    the step's lookup), from the level sizes: every pass over a level's keys
+    reads each key once (8 B) and every pass that moves keys writes each once;
+    A_d is written once (m_d / 8 B).  Moving F_0 into position buckets reads
+    and writes every key; a lookup reads its key and writes its index."""
     sizes = h.level_sizes()          # n_0 .. n_last, n_fb
-    lv = h.levels()
+    lv = h.levels()                  # (n_d, m_d, off_d, s_d)
     nd = sizes[:-1]
-    if name == "partition":
-        return 16 * sizes[0]
-    if name in ("fill_buckets",):
-        return sum(8 * n + m // 8 for (n, m, _, _) in lv)
-    if name in ("compact_buckets", "compact"):
-        return sum(8 * nd[d] + 8 * sizes[d + 1] for d in range(len(nd)))
-    if name == "fill":
-        return 8 * sizes[0]
-    if name == "extract":
-        return sum(m // 8 for (_, m, _, _) in lv)
+    path = h.build_path
     if name == "lookup":
-        return 16 * sizes[0]
+        return 16 * n_queries
+    if path == 1:
+        if name == "partition":
+            return 16 * sizes[0]
+        if name == "fill_buckets":
+            return sum(8 * n + m // 8 for (n, m, _, _) in lv)
+        if name == "compact_buckets":
+            return sum(8 * nd[d] + 8 * sizes[d + 1] for d in range(len(nd)))
+        return 0
+    grouped = [d for d, (n, m, _, _) in enumerate(lv) if m // 4 > GROUP_MIN_AC_BYTES]
+    if name == "slab_count":
+        return sum(8 * nd[d] for d in grouped)
+    if name == "slab_scatter":     # coarse slabs, then fine slabs: read + write twice
+        return sum(32 * nd[d] for d in grouped)
+    if name == "fine_fill":
+        return sum(8 * nd[d] + lv[d][1] // 8 for d in grouped)
+    if name == "compact":
+        return sum(8 * nd[d] + 8 * sizes[d + 1] for d in range(len(nd)))
+    if name == "extract":          # hit/collision array read, A_d written
+        return sum(lv[d][1] // 4 + lv[d][1] // 8 for d in range(len(nd)) if d not in grouped)
     return 0
+
+
+def build_stream_bytes(h) -> int:
+    """The method's streamed bytes for one build (per key-visit: 8 B read by
+    ArrayFill, 8 B read by the compaction, 8 B written per survivor), A
+    written once, and the rank structure (A read, counters written)."""
+    sizes = h.level_sizes()
+    nd = sizes[:-1]
+    M = h.total_bits
+    return sum(16 * n for n in nd) + 8 * sum(sizes[1:-1]) + M // 8 + M // 8 + M // 64
+
+
+# ---------------------------------------------------------------- ceilings
+def measure_ceilings():
+    """Random-access ceilings of this GPU, measured here with the library's
+    ceiling kernels (median of 3 launches after one warm-up): 32-byte and
+    8-byte loads and 64-bit atomic ORs over a 48 MB array (L2-resident), and
+    32-byte loads over an 8 GB array (HBM)."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    out = {}
+    l2buf = torch.zeros(48 << 17, dtype=torch.int64, device="cuda")          # 48 MB
+    hbm = torch.zeros(1 << 30, dtype=torch.int64, device="cuda")              # 8 GB
+    cases = [("l2_loads32", "loads", l2buf, 32, 4 << 30),
+             ("l2_loads8", "loads", l2buf, 8, 4 << 30),
+             ("l2_atomics", "atomics", l2buf, 8, 2 << 30),
+             ("l2_atomics_ret", "atomics_ret", l2buf, 8, 2 << 30),
+             ("hbm_loads32", "loads", hbm, 32, 2 << 30)]
+    for name, kind, buf, width, n in cases:
+        ts, done = [], 0
+        for i in range(4):
+            done, ms = mphf.ceiling(kind, buf, n, seed=i + 1, width=width)
+            if i:
+                ts.append(ms)
+        ms = float(np.median(ts))
+        out[name] = {"g_per_s": round(done / (ms / 1e3) / 1e9, 1), "ops": int(done),
+                     "ms": round(ms, 4), "array_bytes": buf.numel() * 8,
+                     "gbs_accessed": round(done * (width if kind == "loads" else 8)
+                                           / (ms / 1e3) / 1e9, 1)}
+    del l2buf, hbm
+    torch.cuda.empty_cache()
+    out["source"] = "measured in this run (mphf_ceiling_random_loads / _atomics, CUDA events)"
+    return out
+
+
+# ----------------------------------------------------------- timed regions
+def time_steps(step, steps, warmup, stream, world, local, barrier):
+    """Warm-up, then `steps` timed steps bracketed by barrier + synchronize,
+    with the library's per-kernel profile and launch count over the region."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    last = None
+    for _ in range(warmup):
+        if last is not None:
+            last.free()
+        last = step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    mphf.profile_report()
+    mphf.profile_enable(True)
+    launches0 = mphf.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        if last is not None:
+            last.free()
+        last = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = mphf.launch_count() - launches0
+    mphf.profile_enable(False)
+    prof = mphf.profile_report()
+    ms = ev0.elapsed_time(ev1) / steps
+    clk = clocks.stop()
+    return last, ms, prof, launches, clk
+
+
+def kernel_table(h, prof, steps, n_queries):
+    total_ms = sum(v[1] for v in prof.values()) or 1.0
+    kernels = {}
+    for name, (cnt, tot) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        b = kernel_bytes(h, name, n_queries) * steps
+        kernels[name] = {"launches": cnt, "total_ms": round(tot, 4),
+                         "share": round(tot / total_ms, 4),
+                         "gbs": round(b / (tot / 1e3) / 1e9, 1) if tot and b else None}
+    return kernels
+
+
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of
+# work for kernels captured with the commands listed in profiles/, keyed by
+# the kernel's name and the SHA-1 of the source file that holds it: when that
+# file changes the counters no longer describe the kernel and traffic is null.
+NCU_TRAFFIC = {}
+
+
+def traffic_for(name: str, units: float):
+    rec = NCU_TRAFFIC.get(name)
+    if not rec:
+        return None, "no ncu capture of this kernel"
+    src = os.path.join(ROOT, "paper_1702_03154_gb300", "csrc", rec["file"])
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    if sha != rec["sha"]:
+        return None, "kernel changed since its ncu capture"
+    return rec["bytes_per_unit"] * units, rec["note"]
+
+
+def dominant_roofline(h, prof, steps, n_queries, unit_of, peak, peak_kind):
+    """roofline block of the kernel with the most time in the timed region."""
+    if not prof:
+        return None
+    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    b = kernel_bytes(h, name, n_queries) * steps
+    ach = b / (tot / 1e3) / 1e9 if tot else 0.0
+    units = unit_of(name) * steps / cnt
+    tr, tnote = traffic_for(name, units)
+    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach / peak, 4),
+            "traffic": round(tr, 1) if tr else None, "traffic_note": tnote,
+            "per_launch_algorithmic_bytes": round(b / cnt, 1),
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json), of measured",
+            "launches_per_step": cnt / steps, "avg_launch_ms": tot / cnt,
+            "share_of_kernel_time": round(tot / (sum(v[1] for v in prof.values()) or 1), 4)}
+
+
+# ------------------------------------------------------- headline (1e10)
+def host_mem_available() -> int:
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_headline(args, stream, world, rank, local, barrier, ceil):
+    """Build over N keys + Q random member lookups per step (N = 1e10,
+    Q = 1e9 by default).  Returns the fields of the bench line."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    N, Q = int(args.n), int(args.q)
+    gamma, L = args.gamma, args.levels
+    keys = mphf.keygen(N, C3_KEY_SEED + rank)                     # resident in HBM
+    sel = torch.randint(0, N, (Q,), device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(C3_QUERY_SEED))
+    q = keys[sel]
+    del sel
+    out = torch.empty(Q, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    def step():
+        h = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
+        h.lookup(q, out=out)
+        return h
+
+    last, ms, prof, launches, clk = time_steps(step, args.steps, args.warmup, stream, world,
+                                               local, barrier)
+    # build / lookup split (separately timed, outside the main region)
+    tb, tl = [], []
+    for _ in range(2):
+        last.free()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        last = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
+        e1.record(stream)
+        last.lookup(q, out=out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        tl.append(e1.elapsed_time(e2))
+    t_build, t_look = float(np.median(tb)), float(np.median(tl))
+    ms_max = max_over_ranks(ms, world)
+    peak, peak_kind = measured_peaks()
+    sizes = last.level_sizes()
+    probes = sum(last.level_sizes()[:last.num_levels]) * Q / N  # mean levels probed x Q
+
+    def units_of(name):          # keys (or queries) one step's launches of `name` process
+        return Q if name == "lookup" else N
+
+    res = {"ms_max": ms_max, "ms": ms, "launches": launches, "clocks": clk,
+           "build_ms": round(t_build, 3), "lookup_ms": round(t_look, 3),
+           "build_mkeys_s": round(N / (t_build / 1e3) / 1e6, 1),
+           "lookup_mkeys_s": round(Q / (t_look / 1e3) / 1e6, 1),
+           "kernels": kernel_table(last, prof, args.steps, Q),
+           "roofline": dominant_roofline(last, prof, args.steps, Q, units_of, peak, peak_kind),
+           "structure": {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
+                         "level_sizes": sizes[:8], "fallback": last.num_fallback,
+                         "build_path": last.build_path,
+                         "device_bytes_per_key": round(last.device_bytes() / N, 4)}}
+    # The build as a whole against HBM: the method's streamed bytes (survey
+    # model per key-visit) over the build time.
+    sb = build_stream_bytes(last)
+    res["build_roofline"] = {"bound": "hbm", "algorithmic_bytes": sb,
+                             "achieved": round(sb / (t_build / 1e3) / 1e9, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(sb / (t_build / 1e3) / 1e9 / peak, 4),
+                             "model": "per key-visit 8 B fill read + 8 B compaction read + 8 B per "
+                                      "survivor written; A written once; rank structure reads A "
+                                      "and writes its counters"}
+    # The lookup against its own bound: each query streams 16 B and probes
+    # ~e^{1/gamma} random 32-byte sectors of A, HBM-resident at this size.
+    lk = {"bound": "hbm_random_sectors", "probes_per_query": round(probes / Q, 4),
+          "achieved_probes_g_s": round(probes / (t_look / 1e3) / 1e9, 2),
+          "hbm_gbs_sector_bytes": round((16 * Q + 32 * probes) / (t_look / 1e3) / 1e9, 1)}
+    if ceil and "hbm_loads32" in ceil:
+        pk = ceil["hbm_loads32"]["g_per_s"]
+        lk.update({"peak_probes_g_s": pk, "frac": round(probes / (t_look / 1e3) / 1e9 / pk, 4),
+                   "peak_source": "random 32-byte loads over an 8 GB array, measured in this run"})
+    res["lookup_roofline"] = lk
+    res["last"] = last
+    res["keys"], res["q"], res["out"] = keys, q, out
+    return res
+
+
+def e2e_headline(args, res, world, barrier):
+    """The headline step through mphf_build_lookup_host: keys and queries in
+    pinned host memory, indices back to pinned host memory, copies inside
+    the timed region.  Needs ~(8 N + 16 Q) bytes of host memory per rank."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    N, Q = int(args.n), int(args.q)
+    local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+    need = (8 * N + 16 * Q) * local_ranks
+    avail = host_mem_available()
+    if avail < 1.25 * need:
+        return {"value": None, "unit": UNIT,
+                "skipped": f"host memory: {avail / 2**30:.0f} GiB available, "
+                           f"{1.25 * need / 2**30:.0f} GiB needed for pinned keys, queries and "
+                           f"indices of {local_ranks} rank(s)"}
+    keys, q = res.pop("keys"), res.pop("q")
+    res.pop("out")
+    res["last"].free()
+    t0 = time.perf_counter()
+    kh = torch.empty(N, dtype=torch.int64, pin_memory=True)
+    kh.copy_(keys)
+    qh = torch.empty(Q, dtype=torch.int64, pin_memory=True)
+    qh.copy_(q)
+    oh = torch.empty(Q, dtype=torch.int64, pin_memory=True)
+    t_pin = time.perf_counter() - t0
+    del keys, q
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    ov = oh.numpy().view(np.uint64)
+
+    def one_call():
+        h, _ = mphf.MPHF.build_lookup_host(kh, qh, out=ov, gamma=args.gamma, levels=args.levels,
+                                           seed=0)
+        h.free()
+
+    for _ in range(2):   # warm-up: the first calls also fill the allocation pool
+        one_call()
+    torch.cuda.synchronize()
+    barrier()
+    reps = max(3, min(args.steps, 5))
+    per_rep = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        one_call()
+        torch.cuda.synchronize()
+        per_rep.append((time.perf_counter() - t0) * 1e3)
+    barrier()
+    e_max = max_over_ranks(float(np.median(per_rep)), world)
+    del kh, qh, oh
+    return {"value": job_value(N, world, e_max), "unit": UNIT,
+            "h2d_bytes_per_step": 8 * N + 8 * Q, "d2h_bytes_per_step": 8 * Q,
+            "ms_per_step": e_max, "reps": reps, "statistic": "median of the reps (wall clock)",
+            "api": "mphf_build_lookup_host (queries copied while the levels are built), "
+                   "pinned host buffers", "pin_and_fill_s": round(t_pin, 2)}
+
+
+# --------------------------------------------------- secondary: N = 1e8
+def run_plain(args, stream, rank, ceil):
+    """The N = 1e8 configuration: build + lookup of all N keys in shuffled
+    order (median of 5 after 2), its kernels, the lookup against the in-run
+    L2 ceiling, the storage layouts and the gamma sweep."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    N, gamma, L = C2_N, 2.0, 25
+    keys = mphf.keygen(N, C2_KEY_SEED + rank)
+    perm = torch.randperm(N, device="cuda",
+                          generator=torch.Generator(device="cuda").manual_seed(C2_QUERY_SEED))
+    q = keys[perm]
+    del perm
+    out = torch.empty(N, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+
+    def one(g):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        h = mphf.MPHF.build(keys, gamma=g, levels=L, seed=0)
+        ev[1].record(stream)
+        h.lookup(q, out=out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        return h, ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+
+    for _ in range(2):
+        one(gamma)[0].free()
+    mphf.profile_report()
+    mphf.profile_enable(True)
+    tb, tl, reps = [], [], 5
+    for i in range(reps):
+        h, b, lk = one(gamma)
+        tb.append(b)
+        tl.append(lk)
+        if i < reps - 1:
+            h.free()
+    mphf.profile_enable(False)
+    prof = mphf.profile_report()
+    b_ms, l_ms = float(np.median(tb)), float(np.median(tl))
+    peak, peak_kind = measured_peaks()
+    res = {"workload": f"N={N:.0e} SplitMix64 keys (stream {C2_KEY_SEED + rank}), gamma=2, L=25; "
+                       "build + lookup of all N in shuffled order",
+           "build_ms": round(b_ms, 4), "lookup_ms": round(l_ms, 4),
+           "step_mkeys_s": round(N / ((b_ms + l_ms) / 1e3) / 1e6, 1),
+           "build_mkeys_s": round(N / (b_ms / 1e3) / 1e6, 1),
+           "lookup_mkeys_s": round(N / (l_ms / 1e3) / 1e6, 1),
+           "kernels": kernel_table(h, prof, reps, N),
+           "roofline": dominant_roofline(h, prof, reps, N, lambda name: N, peak, peak_kind),
+           "structure": {"levels": h.num_levels, "bits_per_key": round(h.bits_per_key(), 4),
+                         "level_sizes": h.level_sizes()[:8], "fallback": h.num_fallback}}
+    sb = build_stream_bytes(h)
+    res["build_roofline"] = {"bound": "hbm", "achieved": round(sb / (b_ms / 1e3) / 1e9, 1),
+                             "peak": peak, "unit": "GB/s",
+                             "frac": round(sb / (b_ms / 1e3) / 1e9 / peak, 4)}
+    if ceil and "l2_loads32" in ceil:
+        probes = float(sum(h.level_sizes()[:h.num_levels]))
+        ach = probes / (l_ms / 1e3) / 1e9
+        pk = ceil["l2_loads32"]["g_per_s"]
+        res["l2_probe"] = {"kernel": "lookup", "bound": "l2_random_sector_loads",
+                           "achieved": round(ach, 1), "peak": pk, "unit": "G loads/s",
+                           "frac": round(ach / pk, 4), "probes_per_query": round(probes / N, 4),
+                           "peak_source": "random 32-byte loads over a 48 MB array, measured in "
+                                          "this run"}
+    by_layout = {}
+    for nbytes in (() if args.no_layouts else (64, 8, 32)):
+        h.set_layout(nbytes)
+        tt = []
+        for _ in range(3):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            h.lookup(q, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        by_layout[f"{nbytes}B"] = {"lookup_ms": round(float(np.median(tt)), 4),
+                                   "device_bytes_per_key": round(h.device_bytes() / N, 4)}
+    res["lookup_by_layout"] = by_layout
+    h.free()
+    if not args.no_sweep:
+        sweep = {}
+        for g2 in (1.0, 5.0):
+            tb, tl = [], []
+            for i in range(3):
+                h, b, lk = one(g2)
+                if i:
+                    tb.append(b)
+                    tl.append(lk)
+                bpk = h.bits_per_key()
+                h.free()
+            b2, l2 = float(np.median(tb)), float(np.median(tl))
+            sweep[f"gamma={g2:g}"] = {"build_ms": round(b2, 3), "lookup_ms": round(l2, 3),
+                                      "build_mkeys_s": round(N / b2 / 1e3, 1),
+                                      "lookup_mkeys_s": round(N / l2 / 1e3, 1),
+                                      "step_mkeys_s": round(N / (b2 + l2) / 1e3, 1),
+                                      "bits_per_key": round(bpk, 4)}
+        res["gamma_sweep"] = sweep
+    del keys, q, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_batched(args, stream):
@@ -424,11 +833,11 @@ def run_serving(args, stream):
     return res
 
 
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-
-    from paper_1702_03154_gb300 import mphf
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -439,217 +848,44 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    N = int(args.n)
-    gamma, L = args.gamma, args.levels
     stream = torch.cuda.current_stream()
-    keys = mphf.keygen(N, 2 + rank)                       # resident in HBM
-    perm = torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
-    q = keys[perm]
-    del perm
-    out = torch.empty(N, dtype=torch.int64, device="cuda")
-    torch.cuda.synchronize()
-
-    def step():
-        h = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
-        h.lookup(q, out=out)
-        return h
-
-    for _ in range(args.warmup):
-        step().free()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    mphf.profile_enable(True)
-    launches0 = mphf.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    last = None
-    for _ in range(args.steps):
-        if last is not None:
-            last.free()
-        last = step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = mphf.launch_count() - launches0
-    mphf.profile_enable(False)
-    prof = mphf.profile_report()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    clk = clocks.stop()
-
-    # build / lookup split (separately timed, outside the main region)
-    tb, tl = [], []
-    for _ in range(3):
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        h = mphf.MPHF.build(keys, gamma=gamma, levels=L, seed=0)
-        e1.record(stream)
-        h.lookup(q, out=out)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        tb.append(e0.elapsed_time(e1))
-        tl.append(e1.elapsed_time(e2))
-        h.free()
-
-    ms_max = max_over_ranks(ms, world)
-    value = job_value(N, world, ms_max)
-
-    # roofline of the dominant kernel
-    peak, peak_kind = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
-    roof = None
-    kernels = {}
-    total_ms = sum(v[1] for v in prof.values()) or 1.0
-    for name, (cnt, tot) in prof.items():
-        b = algorithmic_bytes(last, name) * args.steps
-        kernels[name] = {"launches": cnt, "total_ms": round(tot, 4),
-                         "share": round(tot / total_ms, 4),
-                         "gbs": round(b / (tot / 1e3) / 1e9, 1) if tot and b else None}
-    if dom:
-        name, (cnt, tot) = dom
-        b = algorithmic_bytes(last, name) * args.steps
-        ach = b / (tot / 1e3) / 1e9
-        tr = profiled_traffic(f"k_{name}", N) if gamma == 2.0 else None
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4),
-                "traffic": round(tr / (cnt / args.steps), 1) if tr else None,
-                "traffic_note": "DRAM read+write per launch (averaged over the kernel's launches "
-                                "in one step), from profiles/ (3e7-key ncu capture scaled to 1e8)",
-                "per_launch_algorithmic_bytes": round(b / cnt, 1),
-                "peak_source": f"{peak_kind} hbm_gbs", "launches_per_step": cnt / args.steps,
-                "avg_launch_ms": tot / cnt}
-    struct = {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
-              "level_sizes": last.level_sizes()[:8], "fallback": last.num_fallback}
-    # the same function's lookup in each storage layout (mphf_set_layout)
-    by_layout = {}
-    for nbytes in (() if args.no_layouts else (64, 8, 32)):
-        last.set_layout(nbytes)
-        tt = []
-        for _ in range(3):
-            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
-            e0.record(stream)
-            last.lookup(q, out=out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tt.append(e0.elapsed_time(e1))
-        by_layout[f"{nbytes}B"] = {"lookup_ms": round(float(np.median(tt)), 4),
-                                   "device_bytes_per_key": round(last.device_bytes() / N, 4)}
-    # The lookup's own bound: its level probes are random 256-bit loads of an
-    # L2-resident sector array (sum of n_d of them for N member queries).
-    l2_probe = None
-    if "lookup" in prof:
-        cnt, tot = prof["lookup"]
-        probes = float(sum(last.level_sizes()[:last.num_levels])) * args.steps
-        ach = probes / (tot / 1e3) / 1e9
-        l2_probe = {"kernel": "lookup", "bound": "l2_random_sector_loads",
-                    "achieved": round(ach, 1), "peak": L2_RANDOM_256B_GLOADS, "unit": "G loads/s",
-                    "frac": round(ach / L2_RANDOM_256B_GLOADS, 4),
-                    "probes_per_query": round(probes / args.steps / N, 4),
-                    "peak_source": "random 256-bit loads over a 53 MB L2-resident array on this "
-                                   "GB300 (microbenchmark; 8-byte loads reach ~600 G/s)"}
-    last.free()
-
-    sweep = {}
-    if not args.no_sweep:
-        # the N = 1e8 workload at the other two gamma of its configuration:
-        # build, then the same shuffled member lookups (median of 3 after 1)
-        for g2 in (1.0, 5.0):
-            tb, tl = [], []
-            for i in range(4):
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                ev[0].record(stream)
-                h = mphf.MPHF.build(keys, gamma=g2, levels=L, seed=0)
-                ev[1].record(stream)
-                h.lookup(q, out=out)
-                ev[2].record(stream)
-                torch.cuda.synchronize()
-                if i:
-                    tb.append(ev[0].elapsed_time(ev[1]))
-                    tl.append(ev[1].elapsed_time(ev[2]))
-                bpk = h.bits_per_key()
-                h.free()
-            b_ms, l_ms = float(np.median(tb)), float(np.median(tl))
-            sweep[f"gamma={g2:g}"] = {"build_ms": round(b_ms, 3), "lookup_ms": round(l_ms, 3),
-                                      "build_mkeys_s": round(N / b_ms / 1e3, 1),
-                                      "lookup_mkeys_s": round(N / l_ms / 1e3, 1),
-                                      "step_mkeys_s": round(N / (b_ms + l_ms) / 1e3, 1),
-                                      "bits_per_key": round(bpk, 4)}
-
+    N, Q = int(args.n), int(args.q)
+    ceil = None if args.no_ceilings else measure_ceilings()
+    res = run_headline(args, stream, world, rank, local, barrier, ceil)
+    value = job_value(N, world, res["ms_max"])
     e2e = None
     if not args.no_e2e:
-        kh = torch.empty(N, dtype=torch.int64, pin_memory=True)
-        kh.copy_(keys)
-        qh = torch.empty(N, dtype=torch.int64, pin_memory=True)
-        qh.copy_(q)
-        oh = torch.empty(N, dtype=torch.int64, pin_memory=True)
-        del q
-        torch.cuda.empty_cache()
-        ov = oh.numpy().view(np.uint64)
+        e2e = e2e_headline(args, res, world, barrier)
+    for k in ("keys", "q", "out"):
+        res.pop(k, None)
+    last = res.pop("last")
+    last.free()
+    del last
+    torch.cuda.empty_cache()
 
-        def one_call():  # host keys in, function built, host queries in, indices out
-            h, _ = mphf.MPHF.build_lookup_host(kh, qh, out=ov, gamma=gamma, levels=L, seed=0)
-            h.free()
-
-        def two_calls():
-            h = mphf.MPHF.build_host(kh, gamma=gamma, levels=L, seed=0)
-            h.lookup_host(qh, out=ov)
-            h.free()
-
-        def timed(fn):
-            for _ in range(2):  # warm-up: the first calls also fill the allocation pool
-                fn()
-            torch.cuda.synchronize()
-            barrier()
-            per_rep = []
-            for _ in range(reps):
-                t0 = time.perf_counter()
-                fn()
-                torch.cuda.synchronize()
-                per_rep.append((time.perf_counter() - t0) * 1e3)
-            barrier()
-            return max_over_ranks(float(np.median(per_rep)), world)
-
-        reps = max(3, min(args.steps, 7))
-        e_max = timed(one_call)
-        sep_max = timed(two_calls)
-        e2e = {"value": job_value(N, world, e_max), "unit": UNIT,
-               "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
-               "ms_per_step": e_max,
-               "reps": reps, "statistic": "median of the reps (wall clock)",
-               "api": "mphf_build_lookup_host (queries copied while the levels are built), "
-                      "pinned host buffers",
-               "two_calls": {"api": "mphf_build_host + mphf_lookup_host",
-                             "value": job_value(N, world, sep_max), "ms_per_step": sep_max}}
-
-    batched = None
-    if not args.no_batched:
-        batched = run_batched(args, stream)
-    serving = None
-    if not args.no_serving:
-        serving = run_serving(args, stream)
-
+    plain = None if args.no_plain else run_plain(args, stream, rank, ceil)
+    batched = None if args.no_batched else run_batched(args, stream)
+    serving = None if args.no_serving else run_serving(args, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(10_000_000, gamma, L)
+        cpu = cpu_baseline(10_000_000, max(1, int(10_000_000 * Q / N)), C3_KEY_SEED, args.gamma,
+                           args.levels, "sample of the headline workload")
+        cpu.pop("seconds", None)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-                "data": "synthetic",
-                "config": workload_config(N, gamma, L, rank),
-                "build_mkeys_s": round(N / (float(np.median(tb)) / 1e3) / 1e6, 1),
-                "lookup_mkeys_s": round(N / (float(np.median(tl)) / 1e3) / 1e6, 1),
-                "build_ms": round(float(np.median(tb)), 4), "lookup_ms": round(float(np.median(tl)), 4),
-                "structure": struct, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roof, "l2_probe": l2_probe, "lookup_by_layout": by_layout,
-                "kernels": kernels, "cpu_baseline": cpu}
-        if sweep:
-            line["gamma_sweep"] = sweep
+        line = {"metric": metric_name(N, Q), "value": round(value, 1), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(res["ms_max"], 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": workload_config(N, Q, args.gamma, args.levels, rank),
+                "build_mkeys_s": res["build_mkeys_s"], "lookup_mkeys_s": res["lookup_mkeys_s"],
+                "build_ms": res["build_ms"], "lookup_ms": res["lookup_ms"],
+                "structure": res["structure"], "clocks": res["clocks"], "e2e": e2e,
+                "gpu_launches": int(res["launches"]), "roofline": res["roofline"],
+                "build_roofline": res["build_roofline"], "lookup_roofline": res["lookup_roofline"],
+                "kernels": res["kernels"], "ceilings": ceil, "cpu_baseline": cpu}
+        if plain:
+            line["plain_1e8"] = plain
         if batched:
             line["batched"] = batched
         if serving:
@@ -672,6 +908,8 @@ def profile_batched():
         hs = mphf.build_batched(keys, off, gamma=2.0, levels=25, seed=0)
         torch.cuda.synchronize()
         del hs
+
+
 
 
 def main():

@@ -438,6 +438,34 @@ uint64_t mphf_launch_count(void);
 int mphf_profile_enable(int on);
 int mphf_profile_report(char *buf, uint64_t buflen);
 
+/*
+ * Ceiling measurements: the throughput the memory system gives the accesses
+ * the method makes, for rooflines taken in the same run as the kernels they
+ * judge.  A lookup probe is one random 32-byte sector load per level
+ * (Algorithm 3 with the ranks of Sec. 3.1 stored beside A); ArrayFill marks
+ * hits and collisions with random atomic ORs (Sec. 3.2: construction is bound
+ * by these random accesses).  Each call launches one kernel on `stream` (time
+ * it with events) doing about n random accesses, 8 independent ones in flight
+ * per thread, 8 blocks of 256 threads per SM; *performed receives the exact
+ * count.  Slot indices come from a per-thread linear congruential stream.
+ *   mphf_ceiling_random_loads    loads of `width` bytes (8 or 32) at random
+ *                                aligned offsets of d_buf (bytes long, 32-byte
+ *                                aligned, at most 2^32 - 1 slots).
+ *   mphf_ceiling_random_atomics  atomicOr of one random bit into a random
+ *                                word of d_buf (words long, < 2^32); with
+ *                                with_return != 0 the old value is used (as
+ *                                ArrayFill's hit test does), else not.
+ *   d_sink                       device array of 1024 words (rarely written;
+ *                                keeps the accesses live).
+ * The buffer decides the level measured: an array of tens of MB stays in L2,
+ * one of many GB exercises HBM.  MPHF_EINVAL for bad sizes or alignment.
+ */
+int mphf_ceiling_random_loads(const void *d_buf, uint64_t bytes, uint32_t width, uint64_t n_loads,
+                              uint64_t seed, uint64_t *d_sink, uint64_t *performed, void *stream);
+int mphf_ceiling_random_atomics(uint64_t *d_buf, uint64_t words, int with_return, uint64_t n_ops,
+                                uint64_t seed, uint64_t *d_sink, uint64_t *performed,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

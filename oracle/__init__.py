@@ -102,6 +102,8 @@ def lib():
         L.oracle_window_ranks.argtypes = [vp, u64, u64, u64, u64, u64, vp, vp]
         L.oracle_window_ranks.restype = ctypes.c_int
         L.oracle_string_keys.argtypes, L.oracle_string_keys.restype = [vp, vp, u64, u64, vp], None
+        L.oracle_part_of.argtypes, L.oracle_part_of.restype = [u64, u32, u64], u32
+        L.oracle_parts.argtypes, L.oracle_parts.restype = [vp, u64, u32, u64, vp], None
         _lib = L
     return _lib
 
@@ -315,6 +317,52 @@ def string_keys(data: np.ndarray, offsets: np.ndarray, seed: int = 0) -> np.ndar
         lib().oracle_string_keys(_ptr(data) if data.size else None, _ptr(off), n, seed & MASK64,
                                  _ptr(out))
     return out
+
+
+def part_of(x: int, K: int, part_seed: int) -> int:
+    """The part of K that key x belongs to."""
+    return lib().oracle_part_of(int(x) & MASK64, int(K), int(part_seed) & MASK64)
+
+
+def parts(keys, K: int, part_seed: int) -> np.ndarray:
+    """Part of every key (uint32 array)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(k.size, dtype=np.uint32)
+    if k.size:
+        lib().oracle_parts(_ptr(k), k.size, int(K), int(part_seed) & MASK64, _ptr(out))
+    return out
+
+
+class PartitionedOracle:
+    """K independent functions, one per part of the keys (each built by the
+    oracle over its part's keys, in input order); a key's global index is
+    the size of the parts before its own plus its index within its part."""
+
+    def __init__(self, keys, K: int, part_seed: int, gamma: float = 2.0, levels: int = 25,
+                 seed: int = 0):
+        keys = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+        self.K, self.part_seed = int(K), int(part_seed)
+        p = parts(keys, K, part_seed)
+        self.functions = [OracleMPHF(keys[p == k], gamma=gamma, levels=levels, seed=seed)
+                          for k in range(self.K)]
+        sizes = np.array([f.N for f in self.functions], dtype=np.uint64)
+        self.offsets = np.zeros(self.K + 1, dtype=np.uint64)
+        np.cumsum(sizes, out=self.offsets[1:])
+        self.N = int(self.offsets[-1])
+
+    def lookup(self, q) -> np.ndarray:
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.uint64))
+        p = parts(q, self.K, self.part_seed)
+        out = np.full(q.size, MASK64, dtype=np.uint64)
+        for k in range(self.K):
+            sel = p == k
+            if not sel.any():
+                continue
+            loc = self.functions[k].lookup(q[sel])
+            hit = loc != np.uint64(MASK64)
+            loc[hit] += self.offsets[k]
+            out[sel] = loc
+        return out
 
 
 def build(keys, gamma: float = 2.0, levels: int = 25, seed: int = 0, pos_hook=None) -> OracleMPHF:

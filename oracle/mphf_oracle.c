@@ -548,3 +548,22 @@ void oracle_merge_fill(unsigned char *A1, unsigned char *C1, const unsigned char
         C1[p] = c;
     }
 }
+
+/*
+ * Partitioned use of the method.  Sec. 4.3 notes that other tools split the
+ * key set into partitions and build one small function per partition, and
+ * that the same split could be put in front of this method.  Here key x goes
+ * to part p = floor(mix(x XOR mix(part_seed)) * K / 2^64) of K parts; part p
+ * gets its own function, built over its keys alone; the global index of a key
+ * is the number of keys of parts 0 .. p-1 plus its index within part p.
+ */
+uint32_t oracle_part_of(uint64_t x, uint32_t K, uint64_t part_seed)
+{
+    return (uint32_t)oracle_fastrange(oracle_mix(x ^ oracle_mix(part_seed)), (uint64_t)K);
+}
+
+void oracle_parts(const uint64_t *keys, uint64_t n, uint32_t K, uint64_t part_seed, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = oracle_part_of(keys[i], K, part_seed);
+}

@@ -111,6 +111,8 @@ def lib():
         "mphf_serialized_size": ([vp, pu64], i32),
         "mphf_serialize": ([vp, vp, u64], i32),
         "mphf_deserialize": ([vp, u64, vp, pvp], i32),
+        "mphf_ceiling_random_loads": ([vp, u64, u32, u64, u64, vp, vp, vp], i32),
+        "mphf_ceiling_random_atomics": ([vp, u64, i32, u64, u64, vp, vp, vp], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -615,6 +617,32 @@ class Server:
         m = int(min(nl.value, lat.size))
         return {"latencies": lat[:m].copy(), "lookups": nl.value, "keys": nk.value,
                 "builds": nb.value, "elapsed": el.value}
+
+
+def ceiling(kind: str, buf, n_ops: int, seed: int = 1, width: int = 32, stream=None) -> tuple:
+    """One ceiling-measurement launch over the device tensor `buf`:
+    kind 'loads' (width 8 or 32 bytes), 'atomics' (result unused) or
+    'atomics_ret' (result used).  Returns (accesses performed, ms) from events
+    around the launch on the stream."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    sink = torch.zeros(1024, dtype=torch.int64, device=buf.device)
+    done = ctypes.c_uint64()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    if kind == "loads":
+        rc = lib().mphf_ceiling_random_loads(buf.data_ptr(), buf.numel() * buf.element_size(),
+                                             int(width), int(n_ops), int(seed), sink.data_ptr(),
+                                             ctypes.byref(done), _stream_ptr(st))
+    else:
+        rc = lib().mphf_ceiling_random_atomics(buf.data_ptr(), buf.numel(),
+                                               1 if kind == "atomics_ret" else 0, int(n_ops),
+                                               int(seed), sink.data_ptr(), ctypes.byref(done),
+                                               _stream_ptr(st))
+    e1.record(st)
+    _check(rc, "mphf_ceiling_" + kind)
+    e1.synchronize()
+    return done.value, e0.elapsed_time(e1)
 
 
 def launch_count() -> int:

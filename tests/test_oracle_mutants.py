@@ -57,6 +57,10 @@ MUTANTS = {
                               "oracle_mix(seed + 1 * 0x9E3779B97F4A7C15ULL)"),
     # String keys: groups read big-endian.
     "string_big_endian": ("w |= byte << (8 * i);", "w |= byte << (8 * (7 - i));"),
+    # Partitioned mode: the part hash keyed by the raw seed.
+    "part_seed_unmixed": ("oracle_mix(x ^ oracle_mix(part_seed))", "oracle_mix(x ^ part_seed)"),
+    # Partitioned mode: the split reduced onto K - 1 parts.
+    "part_range_short": ("(uint64_t)K);\n}", "(uint64_t)K - 1);\n}"),
     # String keys: a group OR-ed into the state instead of XOR-ed.
     "string_group_or": ("h = oracle_mix(h ^ w);", "h = oracle_mix(h | w);"),
 }

@@ -534,3 +534,55 @@ def test_window_selection_over_processes_equals_one_pass():
     A, _ = oracle.fill_window(keys, s, m, 0, 4096)
     assert np.array_equal(np.unpackbits(oracle_windows.pack_bits(A).view(np.uint8),
                                         bitorder="little"), A)
+
+
+# ------------------------------------------------------ partitioned mode
+# K independent functions over a hash split of the keys (the partitioning
+# Sec. 4.3 calls applicable to this method): pinned to the plain build at
+# K = 1, to brute-force bijection, to the per-part index ranges, to the
+# power-of-two closed form of the split, and to the multinomial part sizes.
+def test_one_part_is_the_plain_build():
+    keys = inputs.splitmix64_keys(20011, 150)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=3)
+    P = oracle.PartitionedOracle(keys, 1, 77, gamma=2.0, levels=25, seed=3)
+    assert np.array_equal(P.lookup(keys), o.lookup(keys))
+    assert P.functions[0].levels() == o.levels()
+
+
+@pytest.mark.parametrize("K,n", [(2, 1000), (3, 5003), (7, 777), (16, 20000), (64, 3000)])
+def test_partitioned_indices_are_a_bijection(K, n):
+    keys = inputs.splitmix64_keys(n, 151 + K)
+    P = oracle.PartitionedOracle(keys, K, 5, gamma=1.0, levels=3, seed=1)
+    out = P.lookup(keys)
+    assert np.array_equal(np.sort(out), np.arange(n, dtype=np.uint64))
+    p = oracle.parts(keys, K, 5)
+    sizes = np.bincount(p.astype(np.int64), minlength=K)
+    assert sizes.sum() == n
+    assert np.array_equal(P.offsets[1:] - P.offsets[:-1], sizes.astype(np.uint64))
+    for k in range(K):   # each key's index lies in its part's range
+        sel = p == k
+        assert np.all((out[sel] >= P.offsets[k]) & (out[sel] < P.offsets[k + 1]))
+        # and is its part's own function's index, shifted
+        assert np.array_equal(out[sel] - P.offsets[k], P.functions[k].lookup(keys[sel]))
+    # non-members: either a miss or some index of the part they hash to
+    other = inputs.splitmix64_keys(3000, 152)
+    r = P.lookup(other)
+    po = oracle.parts(other, K, 5)
+    hit = r != np.uint64((1 << 64) - 1)
+    assert np.all((r[hit] >= P.offsets[po[hit]]) & (r[hit] < P.offsets[po[hit] + 1]))
+
+
+def test_part_split_closed_form_for_powers_of_two():
+    # with K = 2^j the part is the top j bits of the part hash
+    xs = inputs.splitmix64_keys(2000, 153)
+    s = oracle.mix(9)
+    for j in (1, 3, 10):
+        for x in xs[:200]:
+            h = oracle.mix(int(x) ^ s)
+            assert oracle.part_of(int(x), 1 << j, 9) == h >> (64 - j)
+    # and the split is close to uniform (multinomial, 6 sigma per part)
+    K, n = 10, 200000
+    c = np.bincount(oracle.parts(inputs.splitmix64_keys(n, 154), K, 9).astype(np.int64),
+                    minlength=K)
+    sd = np.sqrt(n * (1 / K) * (1 - 1 / K))
+    assert np.all(np.abs(c - n / K) < 6 * sd)
