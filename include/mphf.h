@@ -44,6 +44,7 @@ extern "C" {
 
 typedef struct mphf mphf_t;
 typedef struct mphf_server mphf_server_t;
+typedef struct mphf_part mphf_part_t;
 
 #define MPHF_NOT_FOUND UINT64_MAX
 #define MPHF_MAX_LEVELS 64
@@ -417,6 +418,57 @@ int mphf_server_loadgen(mphf_server_t *srv, mphf_t *const *hs, const uint64_t *c
                         double nbmin, double nbmax, double gamma, uint64_t seed, double *lat_out,
                         uint64_t lat_cap, uint64_t *n_lookups_out, uint64_t *n_keys_out,
                         uint64_t *n_builds_out, double *elapsed_out);
+
+/* ---- partitioned functions (one independent function per part) ----------- */
+/*
+ * Sec. 4.3 notes that other tools split the key set into partitions and
+ * build one small function per partition, and that the split applies to this
+ * method too.  Key x belongs to part
+ *   p = floor(mix(x ^ mix(part_seed)) * K / 2^64)      (mix: SplitMix64's finalizer)
+ * of K parts (1 <= K <= 1024).  Part p's function is built over its keys
+ * alone (seed, gamma, L as for mphf_build), and the global index of a key is
+ * the number of keys of parts 0 .. p-1 plus its index within part p: a
+ * bijection onto [0, N) again.  With one part per GPU this is the multi-GPU
+ * form of the method (routing is one all-to-all of keys, the prefix of the
+ * part sizes one all-gather, each part's build needs no exchange); the
+ * routing and scatter steps are exposed for that use.
+ *
+ *   mphf_route        writes d_keys (n, 8-byte aligned) grouped by part into
+ *                     d_routed (n words): part k's keys are
+ *                     d_routed[h_offsets[k] .. h_offsets[k+1]), in no fixed
+ *                     order within the part; d_src (n words, optional) gets
+ *                     each routed key's position in d_keys; h_offsets (host,
+ *                     K + 1) the part boundaries.  Waits for the counts.
+ *   mphf_unroute      d_out[d_src[i]] = d_vals[i] for i < n (the inverse
+ *                     placement of mphf_route's output).  Asynchronous.
+ *   mphf_add_offset   d_vals[i] += offset for every entry that is not
+ *                     MPHF_NOT_FOUND (a part's local indices made global).
+ *   mphf_build_partitioned  routes the keys and builds every part (parts of
+ *                     up to 2^24 keys together by the batched construction,
+ *                     larger ones one by one); the handle owns the K functions.
+ *   mphf_part_lookup  routes the queries, answers every part's queries in one
+ *                     multi-function launch and writes each key's global
+ *                     index (or MPHF_NOT_FOUND) at its own position of d_out.
+ *                     Allocates 24 bytes per query of scratch; waits for the
+ *                     routing counts, the rest is asynchronous on `stream`.
+ *   mphf_part_info    K and the K + 1 global offsets (h_offsets may be NULL).
+ *   mphf_part_function  part k's function (owned by the handle), NULL if k >= K.
+ * Errors: MPHF_EINVAL for K outside [1, 1024], bad gamma / levels, NULL or
+ * misaligned arrays; otherwise as mphf_build and mphf_lookup.
+ */
+int mphf_route(const uint64_t *d_keys, uint64_t n, uint32_t K, uint64_t part_seed,
+               uint64_t *d_routed, uint64_t *d_src, uint64_t *h_offsets, void *stream);
+int mphf_unroute(const uint64_t *d_vals, const uint64_t *d_src, uint64_t n, uint64_t *d_out,
+                 void *stream);
+int mphf_add_offset(uint64_t *d_vals, uint64_t n, uint64_t offset, void *stream);
+int mphf_build_partitioned(const uint64_t *d_keys, uint64_t n, uint32_t K, uint64_t part_seed,
+                           double gamma, uint32_t levels, uint64_t seed, void *stream,
+                           mphf_part_t **out);
+int mphf_part_lookup(const mphf_part_t *p, const uint64_t *d_keys, uint64_t n, uint64_t *d_out,
+                     void *stream);
+int mphf_part_info(const mphf_part_t *p, uint32_t *K, uint64_t *h_offsets);
+const mphf_t *mphf_part_function(const mphf_part_t *p, uint32_t k);
+void mphf_part_free(mphf_part_t *p);
 
 /* ---- synthetic keys ------------------------------------------------------ */
 /*

@@ -113,6 +113,14 @@ def lib():
         "mphf_deserialize": ([vp, u64, vp, pvp], i32),
         "mphf_ceiling_random_loads": ([vp, u64, u32, u64, u64, vp, vp, vp], i32),
         "mphf_ceiling_random_atomics": ([vp, u64, i32, u64, u64, vp, vp, vp], i32),
+        "mphf_route": ([vp, u64, u32, u64, vp, vp, vp, vp], i32),
+        "mphf_unroute": ([vp, vp, u64, vp, vp], i32),
+        "mphf_add_offset": ([vp, u64, u64, vp], i32),
+        "mphf_build_partitioned": ([vp, u64, u32, u64, dbl, u32, u64, vp, pvp], i32),
+        "mphf_part_lookup": ([vp, vp, u64, vp, vp], i32),
+        "mphf_part_info": ([vp, ctypes.POINTER(u32), vp], i32),
+        "mphf_part_function": ([vp, u32], vp),
+        "mphf_part_free": ([vp], None),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -157,8 +165,11 @@ def _host_u64(a) -> np.ndarray:
 class MPHF:
     """A minimal perfect hash function resident in GPU memory."""
 
-    def __init__(self, handle: ctypes.c_void_p):
+    def __init__(self, handle: ctypes.c_void_p, owner=None):
         self._h = handle
+        # a function owned by another object (a part of a PartitionedMPHF)
+        # keeps that object alive and is never freed here
+        self._owner = owner
 
     # -- construction ---------------------------------------------------
     @classmethod
@@ -266,7 +277,7 @@ class MPHF:
             return cls.from_bytes(f.read(), stream)
 
     def free(self):
-        if self._h is not None and self._h.value:
+        if self._owner is None and self._h is not None and self._h.value:
             lib().mphf_free(self._h)
         self._h = None
 
@@ -643,6 +654,100 @@ def ceiling(kind: str, buf, n_ops: int, seed: int = 1, width: int = 32, stream=N
     _check(rc, "mphf_ceiling_" + kind)
     e1.synchronize()
     return done.value, e0.elapsed_time(e1)
+
+
+# ------------------------------------------------- partitioned functions
+def route(keys, K: int, part_seed: int, with_src: bool = True, stream=None):
+    """Keys grouped by part (mphf_route): (routed, src or None, offsets (K + 1,
+    host uint64))."""
+    import torch
+    keys = _dev_keys(keys)
+    n = keys.numel()
+    routed = torch.empty(n, dtype=torch.int64, device=keys.device)
+    src = torch.empty(n, dtype=torch.int64, device=keys.device) if with_src else None
+    off = np.zeros(int(K) + 1, dtype=np.uint64)
+    rc = lib().mphf_route(keys.data_ptr() if n else None, n, int(K), int(part_seed) & NOT_FOUND,
+                          routed.data_ptr() if n else None,
+                          src.data_ptr() if (src is not None and n) else None, off.ctypes.data,
+                          _stream_ptr(stream))
+    _check(rc, "mphf_route")
+    return routed, src, off
+
+
+def unroute(vals, src, out=None, stream=None):
+    """out[src[i]] = vals[i] (mphf_unroute)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(vals)
+    n = vals.numel()
+    rc = lib().mphf_unroute(vals.data_ptr() if n else None, src.data_ptr() if n else None, n,
+                            out.data_ptr() if n else None, _stream_ptr(stream))
+    _check(rc, "mphf_unroute")
+    return out
+
+
+def add_offset(vals, offset: int, stream=None):
+    """vals += offset where vals is not NOT_FOUND (mphf_add_offset), in place."""
+    n = vals.numel()
+    rc = lib().mphf_add_offset(vals.data_ptr() if n else None, n, int(offset) & NOT_FOUND,
+                               _stream_ptr(stream))
+    _check(rc, "mphf_add_offset")
+    return vals
+
+
+class PartitionedMPHF:
+    """K independent functions over a hash split of the keys; global index =
+    keys in the parts before + index within the part (mphf_build_partitioned)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        K = ctypes.c_uint32()
+        _check(lib().mphf_part_info(self._h, ctypes.byref(K), None), "mphf_part_info")
+        self.K = K.value
+        self.offsets = np.zeros(self.K + 1, dtype=np.uint64)
+        _check(lib().mphf_part_info(self._h, ctypes.byref(K), self.offsets.ctypes.data),
+               "mphf_part_info")
+        self.N = int(self.offsets[-1])
+
+    @classmethod
+    def build(cls, keys, K: int, part_seed: int, gamma: float = 2.0, levels: int = 25,
+              seed: int = 0, stream=None) -> "PartitionedMPHF":
+        keys = _dev_keys(keys)
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_partitioned(keys.data_ptr() if keys.numel() else None, keys.numel(),
+                                          int(K), int(part_seed) & NOT_FOUND, float(gamma),
+                                          int(levels), int(seed) & NOT_FOUND, _stream_ptr(stream),
+                                          ctypes.byref(h))
+        _check(rc, "mphf_build_partitioned")
+        return cls(h)
+
+    def function(self, k: int) -> MPHF:
+        p = lib().mphf_part_function(self._h, int(k))
+        if not p:
+            raise IndexError(k)
+        return MPHF(ctypes.c_void_p(p), owner=self)
+
+    def lookup(self, keys, out=None, stream=None):
+        import torch
+        keys = _dev_keys(keys)
+        if out is None:
+            out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+        rc = lib().mphf_part_lookup(self._h, keys.data_ptr() if keys.numel() else None,
+                                    keys.numel(), out.data_ptr() if keys.numel() else None,
+                                    _stream_ptr(stream))
+        _check(rc, "mphf_part_lookup")
+        return out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().mphf_part_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
 
 
 def launch_count() -> int:

@@ -92,3 +92,91 @@ def test_two_gloo_ranks():
         assert got[r]["max_ms"] == 15.0
         assert got[r]["value"] == pytest.approx(2 * 10**8 / 0.015 / 1e6)
         assert got[r]["merge_ok"] and got[r]["same_on_all"]
+
+
+# ------------------------------------------- one part per rank (Sec. 4.3)
+# DistributedMPHF's exchange and offset logic on gloo ranks.  Its device
+# steps (route, build, lookup, offset, scatter back) are stood in for by the
+# oracle on the CPU, so the global indices must equal the oracle's
+# partitioned mode over the union of every rank's keys, with K = world size.
+class _OracleOps:
+    def __init__(self):
+        self.device = torch.device("cpu")
+
+    def empty(self, n):
+        return torch.empty(int(n), dtype=torch.int64)
+
+    def route(self, keys, K, part_seed, with_src):
+        import oracle
+        k = keys.numpy().view(np.uint64)
+        p = oracle.parts(k, K, part_seed)
+        order = np.argsort(p, kind="stable")
+        off = np.zeros(K + 1, dtype=np.uint64)
+        np.cumsum(np.bincount(p.astype(np.int64), minlength=K).astype(np.uint64), out=off[1:])
+        src = torch.from_numpy(order.astype(np.int64)) if with_src else None
+        return torch.from_numpy(k[order].view(np.int64).copy()), src, off
+
+    def build(self, keys, gamma, levels, seed):
+        import oracle
+        return oracle.build(keys.numpy().view(np.uint64), gamma=gamma, levels=levels, seed=seed)
+
+    def lookup(self, f, keys):
+        return torch.from_numpy(f.lookup(keys.numpy().view(np.uint64)).view(np.int64).copy())
+
+    def add_offset(self, vals, offset):
+        v = vals.numpy().view(np.uint64)
+        hit = v != np.uint64((1 << 64) - 1)
+        v[hit] += np.uint64(offset)
+        return vals
+
+    def unroute(self, vals, src):
+        out = torch.empty_like(vals)
+        out[src] = vals
+        return out
+
+
+def _part_worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_1702_03154_gb300 import inputs
+        from paper_1702_03154_gb300.distributed import DistributedMPHF
+        all_keys = inputs.splitmix64_keys(30011, 160)
+        mine = all_keys[rank::world]                       # this rank's share
+        d = DistributedMPHF(torch.from_numpy(mine.view(np.int64).copy()), part_seed=21,
+                            gamma=2.0, levels=25, seed=4, ops=_OracleOps())
+        P = oracle.PartitionedOracle(all_keys, world, 21, gamma=2.0, levels=25, seed=4)
+        res = {"offsets": bool(np.array_equal(d.offsets, P.offsets)), "N": d.N}
+        # queries: another share of the members plus non-members, of a
+        # different size on each rank
+        q = np.concatenate([all_keys[(rank + 1) % world::world][: 5000 + 777 * rank],
+                            inputs.splitmix64_keys(300 + rank, 161 + rank)])
+        got = d.lookup(torch.from_numpy(q.view(np.int64).copy())).numpy().view(np.uint64)
+        res["lookup"] = bool(np.array_equal(got, P.lookup(q)))
+        out.put((rank, res))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_one_part_per_gloo_rank(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_part_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in range(world):
+        r, res = q.get(timeout=240)
+        got[r] = res
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert got[r] == {"offsets": True, "N": 30011, "lookup": True}, got[r]
