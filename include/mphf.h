@@ -478,6 +478,19 @@ void mphf_part_free(mphf_part_t *p);
  */
 int mphf_keygen(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void *stream);
 
+/* ---- device memory -------------------------------------------------------- */
+/*
+ * Scratch and handle memory come from the current device's default
+ * stream-ordered memory pool.  Freed blocks stay in the pool, for the next
+ * build, up to the most memory the library has held at once on that device
+ * (at least 16 GiB): repeated builds over 1e10 keys reuse their ~120 GB of
+ * scratch instead of mapping it again each time.  Memory cached this way is
+ * not available to other allocators of the process (torch's, cudaMalloc);
+ * mphf_pool_trim waits for the device, returns every unused block of the pool
+ * to the driver and sets the limit back to 16 GiB.
+ */
+int mphf_pool_trim(void);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* Number of kernels this library has launched in this process. */
 uint64_t mphf_launch_count(void);

@@ -73,38 +73,79 @@ void launch_end(cudaStream_t s) {
   t_open = -1;
 }
 
+// Device memory comes from the device's default stream-ordered pool.  Freed
+// blocks stay in the pool for the next build as long as the pool's unused
+// memory is below its release threshold; the threshold follows the most
+// memory this library has held at once (at least 16 GiB), so a build that
+// needs 120 GB of scratch (1e10 keys) finds it again on its next call instead
+// of mapping it from the driver anew.  mphf_pool_trim returns the unused part.
+static constexpr u64 kPoolMinKeep = 16ull << 30;
+static std::atomic<long long> g_in_use[64];  // bytes held through dev_alloc
+static std::atomic<u64> g_keep[64];
+
+static void pool_keep(int dev, u64 bytes) {
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    u64 thr = bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  } else {
+    cudaGetLastError();
+  }
+}
+
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
   b.p = nullptr;
   b.bytes = bytes;
   if (bytes == 0) return MPHF_OK;
-  static bool pool_set[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !pool_set[dev]) {
-    // Keep freed blocks in this process's pool for reuse by the next build
-    // (up to 16 GiB), instead of returning them to the driver at every sync.
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      u64 thr = 16ull << 30;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    pool_set[dev] = true;
+  const int dev = cur_device();
+  if (g_keep[dev].load() == 0) {
+    u64 z = 0;
+    if (g_keep[dev].compare_exchange_strong(z, kPoolMinKeep)) pool_keep(dev, kPoolMinKeep);
   }
   cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
   if (e != cudaSuccess) {
     b.p = nullptr;
+    b.bytes = 0;
     cudaGetLastError();
     set_cuda_error(e, "cudaMallocAsync");
     return MPHF_ENOMEM;
+  }
+  const long long used_s = g_in_use[dev].fetch_add((long long)bytes) + (long long)bytes;
+  const u64 used = used_s > 0 ? (u64)used_s : 0;
+  u64 keep = g_keep[dev].load();
+  while (used > keep) {
+    if (g_keep[dev].compare_exchange_weak(keep, used)) {
+      pool_keep(dev, used);
+      break;
+    }
   }
   return MPHF_OK;
 }
 
 void dev_free(DevBuf &b, cudaStream_t s) {
-  if (b.p) cudaFreeAsync(b.p, s);
+  if (b.p) {
+    cudaFreeAsync(b.p, s);
+    g_in_use[cur_device()].fetch_sub((long long)b.bytes);
+  }
   b.p = nullptr;
   b.bytes = 0;
 }
+
+}  // namespace bbh
+
+extern "C" int mphf_pool_trim(void) {
+  using namespace bbh;
+  const int dev = cur_device();
+  cudaMemPool_t pool;
+  MPHF_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  MPHF_CUDA(cudaDeviceSynchronize());
+  g_keep[dev].store(kPoolMinKeep);
+  pool_keep(dev, kPoolMinKeep);
+  MPHF_CUDA(cudaMemPoolTrimTo(pool, 0));
+  return MPHF_OK;
+}
+
+namespace bbh {
 
 // About 16 chunks of at least 2^20 keys: the first chunk's copy is the
 // pipeline's fill time, so chunks stay small next to the whole copy, but each

@@ -121,6 +121,7 @@ def lib():
         "mphf_part_info": ([vp, ctypes.POINTER(u32), vp], i32),
         "mphf_part_function": ([vp, u32], vp),
         "mphf_part_free": ([vp], None),
+        "mphf_pool_trim": ([], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -748,6 +749,11 @@ class PartitionedMPHF:
             self.free()
         except Exception:  # pragma: no cover - interpreter shutdown
             pass
+
+
+def pool_trim() -> None:
+    """Return the library's unused cached device memory to the driver."""
+    _check(lib().mphf_pool_trim(), "mphf_pool_trim")
 
 
 def launch_count() -> int:
