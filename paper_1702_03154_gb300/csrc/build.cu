@@ -10,7 +10,7 @@
 // the concatenated A, counts weight(A_d), and derives |F_{d+1}| = |F_d| -
 // weight(A_d) before any key is moved.  Compaction of level d streams F_d
 // again, keeps the keys whose A_d bit is 0 (they form F_{d+1}, Algorithm 1),
-// packs them with warp ballots + a block scan, and --
+// packs them with warp ballots (each warp reserving its own output run), and --
 // since |A_{d+1}| is already known -- runs level d+1's ArrayFill on the
 // survivors in the same pass, so F_{d+1} is read once less.
 #include <cuda_runtime.h>
@@ -153,14 +153,16 @@ __global__ void k_level_done(BuildMeta *__restrict__ meta, int d, int L, double 
 
 // ---------------------------------------------------------------------------
 // Compaction of level d (+ ArrayFill of level d+1 on the survivors).
-// A tile of kCompactTile keys: each warp packs its surviving keys into its own
-// shared-memory segment with ballots, a block scan of the warp counts places
-// the segments, and one atomicAdd per tile reserves the tile's output range.
-// The output order of F_{d+1} is therefore not the input order; nothing
-// downstream depends on it (ArrayFill is a function of the key set).
+// Warps work independently on warp tiles of 32 * kCompactKPT keys: a warp
+// packs its surviving keys into its own shared-memory segment with ballots,
+// reserves their output range with one atomicAdd and writes them out as one
+// run.  No block barrier: the warps of a block drift apart, so the loads of
+// one overlap the arithmetic of another.  The output order of F_{d+1} is
+// therefore not the input order; nothing downstream depends on it (ArrayFill
+// is a function of the key set).
 // ---------------------------------------------------------------------------
 template <bool VEC>
-__global__ void __launch_bounds__(kCompactThreads)
+__global__ void __launch_bounds__(kCompactThreads, 4)
 k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restrict__ A0,
           const u64 *__restrict__ Aarena, u64 *__restrict__ ACnext, BuildMeta *__restrict__ meta,
           int d, u64 s_d, u64 s_next, int do_fill, u64 cap) {
@@ -172,24 +174,23 @@ k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restri
   const u64 m_next = do_fill ? meta->m[d + 1] : 0;
 
   __shared__ u64 stage[kCompactTile];
-  __shared__ unsigned int wcount[kCompactThreads / 32];
-  __shared__ unsigned int woff[kCompactThreads / 32];
-  __shared__ u64 base_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   u64 *seg = stage + warp * (32 * kCompactKPT);
+  constexpr u64 kWT = 32 * kCompactKPT;  // keys per warp tile
 
-  const u64 ntiles = (n + kCompactTile - 1) / kCompactTile;
-  for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const u64 t0 = tile * kCompactTile;
+  const u64 nwt = (n + kWT - 1) / kWT;
+  const u64 wstride = (u64)gridDim.x * (kCompactThreads / 32);
+  for (u64 wt = (u64)blockIdx.x * (kCompactThreads / 32) + warp; wt < nwt; wt += wstride) {
+    const u64 t0 = wt * kWT;
     u64 x[kCompactKPT];
     bool valid[kCompactKPT];
     if (VEC) {
-      // thread t of warp w reads pairs (t0/2 + w*32*KPT/2 + k*32 + lane), k < KPT/2
+      // lane l reads pairs (t0/2 + k*32 + l), k < KPT/2
       const uint4 *F2 = reinterpret_cast<const uint4 *>(F);
 #pragma unroll
       for (int k = 0; k < kCompactKPT / 2; k++) {
-        u64 i = t0 + (u64)warp * 32 * kCompactKPT + (u64)k * 64 + 2 * lane;
+        u64 i = t0 + (u64)k * 64 + 2 * lane;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (i + 1 < n) {
           v = load_stream(F2 + (i >> 1));
@@ -206,7 +207,7 @@ k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restri
     } else {
 #pragma unroll
       for (int k = 0; k < kCompactKPT; k++) {
-        u64 i = t0 + (u64)warp * 32 * kCompactKPT + (u64)k * 32 + lane;
+        u64 i = t0 + (u64)k * 32 + lane;
         valid[k] = i < n;
         x[k] = valid[k] ? __ldcs(F + i) : 0;
       }
@@ -228,18 +229,10 @@ k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restri
       if (keep[k]) seg[cnt + __popc(b & lt_mask)] = x[k];
       cnt += __popc(b);
     }
-    if (lane == 0) wcount[warp] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned run = 0;
-      for (int w = 0; w < kCompactThreads / 32; w++) {
-        woff[w] = run;
-        run += wcount[w];
-      }
-      base_s = run ? atomicAdd(&meta->out_count[d], (u64)run) : 0;
-    }
-    __syncthreads();
-    const u64 base = base_s + woff[warp];
+    u64 base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(&meta->out_count[d], (u64)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
     if (base + cnt > cap && lane == 0) atomicExch(&meta->status, (unsigned)MPHF_EINTERNAL);
     for (unsigned i = lane; i < cnt; i += 32) {
       u64 y = seg[i];
@@ -247,7 +240,7 @@ k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restri
       Fout[base + i] = y;
       if (m_next) fill_position(ACnext, level_pos(y, s_next, m_next));
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -289,6 +282,10 @@ struct SlabDest {
   }
 };
 
+// The next tile's keys are staged in shared memory by cp.async while the
+// current tile is split (each thread owns kKPT consecutive keys of a tile;
+// ALIGNED: the keys are 16-byte aligned, so they move in 16-byte copies).
+template <bool ALIGNED>
 __global__ void __launch_bounds__(kTT, 2)
 k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
                unsigned nslab, u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
@@ -297,22 +294,55 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
   SplitSmem sm = carve_split(smem, nslab);
   split_clear(sm, nslab);
   __syncthreads();
+  u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes(nslab));
+  auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * kTT + threadIdx.x) + (k & 1); };
   const u64 ntiles = (n + kTile - 1) / kTile;
-  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const unsigned tb = threadIdx.x * kKPT;
+  auto prefetch = [&](u64 t) {
+    if (t < ntiles) {
+      const u64 *src = keys + t * kTile;
+      const u64 rem = n - t * kTile;
+      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
+      if (ALIGNED && tb + kKPT <= nt) {
+#pragma unroll
+        for (int k = 0; k < kKPT; k += 2) cp_async16(slot(k), src + tb + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kKPT; k++)
+          if (tb + k < nt) cp_async8(slot(k), src + tb + k);
+      }
+    }
+    cp_async_commit();
+  };
+  u64 t = blockIdx.x;
+  prefetch(t);
+  for (; t < ntiles; t += gridDim.x) {
+    cp_async_wait0();  // this thread's copies of tile t have landed
+    const u64 rem = n - t * kTile;
+    const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
     u64 x[kKPT];
     unsigned dst[kKPT], lp[kKPT];
     bool ok[kKPT];
 #pragma unroll
+    for (int k = 0; k < kKPT; k += 2) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(slot(k));
+      x[k] = ((u64)v.y << 32) | v.x;
+      x[k + 1] = ((u64)v.w << 32) | v.z;
+    }
+    // the slots are read (into registers) before the next tile's copies are
+    // issued: each thread copies into and reads only its own slots
+    prefetch(t + gridDim.x);
+#pragma unroll
     for (int k = 0; k < kKPT; k++) {
-      const u64 i = t * kTile + (u64)k * kTT + threadIdx.x;
-      ok[k] = i < n;
-      x[k] = ok[k] ? __ldcs(keys + i) : 0;
+      ok[k] = tb + k < nt;
+      if (!ok[k]) x[k] = 0;
       dst[k] = ok[k] ? (unsigned)((level_pos(x[k], s, m) - base) >> shift) : 0u;
       lp[k] = 0;
     }
     multisplit_write<false, false>(x, lp, dst, ok, nslab, sm, out, nullptr,
                                    SlabDest{cursor, end}, status);
   }
+  cp_async_wait0();
 }
 
 // ArrayFill of one fine slab of a grouped level in shared memory: CTA f takes
@@ -337,7 +367,23 @@ k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64
   for (unsigned i = threadIdx.x; i < 2 * kWords; i += kFineThreads) fsm[i] = 0;
   __syncthreads();
   const u64 i1 = min(fend[blockIdx.x], fcap[blockIdx.x]);  // an overflowed range stops at its end
-  for (u64 i = fstart[blockIdx.x] + threadIdx.x; i < i1; i += kFineThreads) {
+  // four keys per thread in flight: their loads are issued before any of
+  // them is hashed
+  constexpr int kU = 4;
+  u64 i = fstart[blockIdx.x] + threadIdx.x;
+  for (; i + (u64)(kU - 1) * kFineThreads < i1; i += (u64)kU * kFineThreads) {
+    u64 x[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) x[u] = __ldcs(T + i + (u64)u * kFineThreads);
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const unsigned q = (unsigned)(level_pos(x[u], s, m) - p0);  // < np
+      const unsigned bit = 1u << (q & 31);
+      const unsigned old = atomicOr(hit + (q >> 5), bit);
+      if (old & bit) atomicOr(col + (q >> 5), bit);
+    }
+  }
+  for (; i < i1; i += kFineThreads) {
     const unsigned q = (unsigned)(level_pos(__ldcs(T + i), s, m) - p0);  // < np
     const unsigned bit = 1u << (q & 31);
     const unsigned old = atomicOr(hit + (q >> 5), bit);
@@ -398,8 +444,10 @@ static unsigned slab_count_for(u64 m) {
 static int slab_attrs() {
   static bool attr = false;
   if (!attr) {
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)split_smem_bytes(kSlabMax)));
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(split_smem_bytes(kSlabMax) + kTile * 8)));
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(split_smem_bytes(kSlabMax) + kTile * 8)));
     MPHF_CUDA(cudaFuncSetAttribute(k_fine_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kFineSmem));
     attr = true;
@@ -435,9 +483,14 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
   MPHF_CUDA(cudaMemcpyAsync(end, se.data() + nslab, nslab * 8, cudaMemcpyHostToDevice, st));
   {
     LaunchScope ls("slab_scatter", st);
-    k_slab_scatter<<<grid_for(n, kTile, (unsigned)sm_count() * 2), kTT,
-                     split_smem_bytes(nslab), st>>>(F, n, s, m, base, shift, nslab, cursor, end,
-                                                    out, status);
+    const unsigned g = grid_for(n, kTile, (unsigned)sm_count() * 2);
+    const size_t sb = split_smem_bytes(nslab) + kTile * 8;
+    if (((uintptr_t)F & 15) == 0)
+      k_slab_scatter<true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end, out,
+                                               status);
+    else
+      k_slab_scatter<false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end, out,
+                                                status);
   }
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
@@ -504,9 +557,14 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
           k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
         }
         LaunchScope ls("slab_scatter", st);
-        k_slab_scatter<<<grid_for(b - a, kTile, (unsigned)sm_count() * 2), kTT,
-                         split_smem_bytes(nf), st>>>(R + a, b - a, s, m, base, kFineShift, nf,
-                                                     cursor, end, T, status);
+        const unsigned g = grid_for(b - a, kTile, (unsigned)sm_count() * 2);
+        const size_t sb = split_smem_bytes(nf) + kTile * 8;
+        if (((uintptr_t)(R + a) & 15) == 0)
+          k_slab_scatter<true><<<g, kTT, sb, st>>>(R + a, b - a, s, m, base, kFineShift, nf,
+                                                   cursor, end, T, status);
+        else
+          k_slab_scatter<false><<<g, kTT, sb, st>>>(R + a, b - a, s, m, base, kFineShift, nf,
+                                                    cursor, end, T, status);
       }
       {
         LaunchScope ls("fine_fill", st);

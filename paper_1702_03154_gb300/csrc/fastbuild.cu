@@ -27,10 +27,6 @@
 
 namespace bbh {
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
 
 // Each thread owns kKPT consecutive keys of a tile, staged by asynchronous
 // copies: a thread takes its keys of tile t into registers, then starts
