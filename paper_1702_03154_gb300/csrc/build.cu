@@ -285,11 +285,13 @@ struct SlabDest {
 // The next tile's keys are staged in shared memory by cp.async while the
 // current tile is split (each thread owns kKPT consecutive keys of a tile;
 // ALIGNED: the keys are 16-byte aligned, so they move in 16-byte copies).
-template <bool ALIGNED>
+// WITH_POS: each key's position within its slab (below 2^20) goes to pout
+// beside it (the fine slabs' fill and compaction then need no hash).
+template <bool ALIGNED, bool WITH_POS>
 __global__ void __launch_bounds__(kTT, 2)
 k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
                unsigned nslab, u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
-               unsigned *__restrict__ status) {
+               unsigned *__restrict__ pout, unsigned *__restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   SplitSmem sm = carve_split(smem, nslab);
   split_clear(sm, nslab);
@@ -336,55 +338,67 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
     for (int k = 0; k < kKPT; k++) {
       ok[k] = tb + k < nt;
       if (!ok[k]) x[k] = 0;
-      dst[k] = ok[k] ? (unsigned)((level_pos(x[k], s, m) - base) >> shift) : 0u;
-      lp[k] = 0;
+      const u64 r = ok[k] ? level_pos(x[k], s, m) - base : 0;
+      dst[k] = (unsigned)(r >> shift);
+      lp[k] = WITH_POS ? (unsigned)r & ((1u << shift) - 1u) : 0u;
     }
-    multisplit_write<false, false>(x, lp, dst, ok, nslab, sm, out, nullptr,
-                                   SlabDest{cursor, end}, status);
+    multisplit_write<WITH_POS, false>(x, lp, dst, ok, nslab, sm, out, pout,
+                                      SlabDest{cursor, end}, status);
   }
   cp_async_wait0();
 }
 
-// ArrayFill of one fine slab of a grouped level in shared memory: CTA f takes
-// the keys T[fstart[f], fend[f]) of positions [p0, min(p0 + 2^kFineShift,
-// lim)), p0 = base + f 2^kFineShift, sets hit and collision bits there (Algorithm 2, the
-// same three implications as fill_position), writes A_d's words of the range
-// and adds their ones to weight(A_d).
+// ArrayFill and compaction of one fine slab of a grouped level, in shared
+// memory: CTA f takes the entries [fstart[f], fend[f]) of T (keys) and TP
+// (their positions within the fine slab) for positions [p0, min(p0 +
+// 2^kFineShift, lim)), p0 = base + f 2^kFineShift.  Pass 1 sets the hit and
+// collision bits from the stored positions (Algorithm 2, the same three
+// implications as fill_position); A_d's words of the range are written and
+// their ones added to weight(A_d).  Every key hashed into these positions is
+// in this CTA, so its bits are final: pass 2 keeps the keys whose A_d bit is
+// 0 (F_{d+1}, Algorithm 1), staged per warp and written to Fout in runs
+// reserved with one atomicAdd on out_count.  A run past `cap` is not written
+// and raises bit 0 of fuse_status.
 static constexpr unsigned kFineShift = 18;
 static constexpr int kFineThreads = 512;
-static constexpr size_t kFineSmem = 2 * ((size_t)1 << kFineShift) / 8;  // hit + collision bits
+static constexpr int kFineStage = 256;  // survivors a warp stages before writing them
+static constexpr size_t kFineSmem =
+    2 * ((size_t)1 << kFineShift) / 8 + (size_t)(kFineThreads / 32) * kFineStage * 8;
 
-__global__ void __launch_bounds__(kFineThreads)
-k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64 *__restrict__ fend,
-            const u64 *__restrict__ fcap, u64 s, u64 m, u64 base, u64 lim,
-            u64 *__restrict__ Alev, u64 *__restrict__ weight) {
+__global__ void __launch_bounds__(kFineThreads, 2)
+k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
+            const u64 *__restrict__ fstart, const u64 *__restrict__ fend,
+            const u64 *__restrict__ fcap, u64 base, u64 lim, u64 *__restrict__ Alev,
+            u64 *__restrict__ weight, u64 *__restrict__ Fout, u64 cap,
+            u64 *__restrict__ out_count, unsigned *__restrict__ fuse_status) {
   extern __shared__ __align__(16) unsigned fsm[];
   __shared__ u64 red[kFineThreads / 32];
   constexpr unsigned kWords = (1u << kFineShift) / 32;
   unsigned *hit = fsm, *col = fsm + kWords;
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64 *stage = reinterpret_cast<u64 *>(fsm + 2 * kWords) + warp * kFineStage;
   const u64 p0 = base + ((u64)blockIdx.x << kFineShift);
   const u64 np = min((u64)1 << kFineShift, lim - p0);  // lim: end of the slab, a multiple of 64
   for (unsigned i = threadIdx.x; i < 2 * kWords; i += kFineThreads) fsm[i] = 0;
   __syncthreads();
+  const u64 i0 = fstart[blockIdx.x];
   const u64 i1 = min(fend[blockIdx.x], fcap[blockIdx.x]);  // an overflowed range stops at its end
-  // four keys per thread in flight: their loads are issued before any of
-  // them is hashed
+  // pass 1: four positions per thread in flight
   constexpr int kU = 4;
-  u64 i = fstart[blockIdx.x] + threadIdx.x;
+  u64 i = i0 + threadIdx.x;
   for (; i + (u64)(kU - 1) * kFineThreads < i1; i += (u64)kU * kFineThreads) {
-    u64 x[kU];
+    unsigned q[kU];
 #pragma unroll
-    for (int u = 0; u < kU; u++) x[u] = __ldcs(T + i + (u64)u * kFineThreads);
+    for (int u = 0; u < kU; u++) q[u] = TP[i + (u64)u * kFineThreads];  // < np
 #pragma unroll
     for (int u = 0; u < kU; u++) {
-      const unsigned q = (unsigned)(level_pos(x[u], s, m) - p0);  // < np
-      const unsigned bit = 1u << (q & 31);
-      const unsigned old = atomicOr(hit + (q >> 5), bit);
-      if (old & bit) atomicOr(col + (q >> 5), bit);
+      const unsigned bit = 1u << (q[u] & 31);
+      const unsigned old = atomicOr(hit + (q[u] >> 5), bit);
+      if (old & bit) atomicOr(col + (q[u] >> 5), bit);
     }
   }
   for (; i < i1; i += kFineThreads) {
-    const unsigned q = (unsigned)(level_pos(__ldcs(T + i), s, m) - p0);  // < np
+    const unsigned q = TP[i];
     const unsigned bit = 1u << (q & 31);
     const unsigned old = atomicOr(hit + (q >> 5), bit);
     if (old & bit) atomicOr(col + (q >> 5), bit);
@@ -398,13 +412,42 @@ k_fine_fill(const u64 *__restrict__ T, const u64 *__restrict__ fstart, const u64
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+  if (lane == 0) red[warp] = wsum;
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 t = 0;
-    for (int i = 0; i < kFineThreads / 32; i++) t += red[i];
+    for (int w = 0; w < kFineThreads / 32; w++) t += red[w];
     if (t) atomicAdd(weight, t);
   }
+  // pass 2: a warp takes 32 consecutive entries at a time
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned cnt = 0;
+  auto flush = [&]() {
+    u64 b0 = 0;
+    if (lane == 0 && cnt) b0 = atomicAdd(out_count, (u64)cnt);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (lane == 0 && b0 + cnt > cap) atomicOr(fuse_status, 1u);
+    __syncwarp();
+    for (unsigned j = lane; j < cnt; j += 32)
+      if (b0 + j < cap) Fout[b0 + j] = stage[j];
+    __syncwarp();
+    cnt = 0;
+  };
+  for (u64 e = i0 + (u64)warp * 32; e < i1; e += kFineThreads) {
+    const u64 k = e + lane;
+    bool keep = false;
+    u64 x = 0;
+    if (k < i1) {
+      const unsigned q = TP[k];
+      keep = !(((hit[q >> 5] & ~col[q >> 5]) >> (q & 31)) & 1u);
+      if (keep) x = __ldcs(T + k);  // only the survivors' keys are read
+    }
+    const unsigned bb = __ballot_sync(0xffffffffu, keep);
+    if (keep) stage[cnt + __popc(bb & lt)] = x;
+    cnt += __popc(bb);
+    if (cnt > (unsigned)(kFineStage - 32)) flush();
+  }
+  flush();
 }
 
 // Fine slab f of a slab takes T[f cap, (f + 1) cap): a cap of mean + 8 sigma
@@ -423,11 +466,11 @@ __global__ void k_fine_ranges(u64 *__restrict__ cursor, u64 *__restrict__ end,
 // Host orchestration.
 // ---------------------------------------------------------------------------
 struct Scratch {
-  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag, R, slab, T;
+  DevBuf meta, AC0, AC1, A0, arena, F1, F2, dupflag, R, slab, T, TP;
   void release(cudaStream_t s) {
     dev_free(meta, s); dev_free(AC0, s); dev_free(AC1, s); dev_free(A0, s);
     dev_free(arena, s); dev_free(F1, s); dev_free(F2, s); dev_free(dupflag, s);
-    dev_free(R, s); dev_free(slab, s); dev_free(T, s);
+    dev_free(R, s); dev_free(slab, s); dev_free(T, s); dev_free(TP, s);
   }
 };
 
@@ -444,10 +487,15 @@ static unsigned slab_count_for(u64 m) {
 static int slab_attrs() {
   static bool attr = false;
   if (!attr) {
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(split_smem_bytes(kSlabMax) + kTile * 8)));
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(split_smem_bytes(kSlabMax) + kTile * 8)));
+    const int sb = (int)(split_smem_bytes(kSlabMax) + kTile * 8);
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
     MPHF_CUDA(cudaFuncSetAttribute(k_fine_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kFineSmem));
     attr = true;
@@ -455,8 +503,34 @@ static int slab_attrs() {
   return MPHF_OK;
 }
 
+// One launch of the slab multisplit: keys F (n) into the ranges cursor[i] ..
+// end[i] of out (and, with pout, their in-slab positions into pout).
+static void launch_slab_scatter(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,
+                                unsigned nslab, u64 *cursor, const u64 *end, u64 *out,
+                                unsigned *pout, unsigned *status, cudaStream_t st) {
+  LaunchScope ls("slab_scatter", st);
+  const unsigned g = grid_for(n, kTile, (unsigned)sm_count() * 2);
+  const size_t sb = split_smem_bytes(nslab) + kTile * 8;
+  const bool al = ((uintptr_t)F & 15) == 0;
+  if (pout) {
+    if (al)
+      k_slab_scatter<true, true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end,
+                                                     out, pout, status);
+    else
+      k_slab_scatter<false, true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
+                                                      end, out, pout, status);
+  } else {
+    if (al)
+      k_slab_scatter<true, false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
+                                                      end, out, nullptr, status);
+    else
+      k_slab_scatter<false, false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
+                                                       end, out, nullptr, status);
+  }
+}
+
 static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,
-                      unsigned nslab, u64 *out, u64 *slab, unsigned *status,
+                      unsigned nslab, u64 *out, unsigned *pout, u64 *slab, unsigned *status,
                       std::vector<u64> &se, cudaStream_t st) {
   int rc0 = slab_attrs();
   if (rc0 != MPHF_OK) return rc0;
@@ -481,28 +555,22 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
   // pageable copies: the host data is staged before each call returns
   MPHF_CUDA(cudaMemcpyAsync(cursor, se.data(), nslab * 8, cudaMemcpyHostToDevice, st));
   MPHF_CUDA(cudaMemcpyAsync(end, se.data() + nslab, nslab * 8, cudaMemcpyHostToDevice, st));
-  {
-    LaunchScope ls("slab_scatter", st);
-    const unsigned g = grid_for(n, kTile, (unsigned)sm_count() * 2);
-    const size_t sb = split_smem_bytes(nslab) + kTile * 8;
-    if (((uintptr_t)F & 15) == 0)
-      k_slab_scatter<true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end, out,
-                                               status);
-    else
-      k_slab_scatter<false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end, out,
-                                                status);
-  }
+  launch_slab_scatter(F, n, s, m, base, shift, nslab, cursor, end, out, pout, status, st);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
 
-// ArrayFill of a level whose keys R are grouped by slab (ranges se):
-// each slab's keys are grouped again into fine slabs of 2^kFineShift positions
-// (into T) and filled in shared memory; A_d and weight(A_d) are written
-// directly, then level d+1 is sized.
+// ArrayFill and compaction of a level whose keys R are grouped by slab
+// (ranges se): each slab's keys are grouped again into fine slabs of
+// 2^kFineShift positions (into T, with their positions in TP), then each fine
+// slab is filled in shared memory and compacted there (k_fine_fill): A_d and
+// weight(A_d) are written, and F_{d+1} goes to Fout (cap keys; out_count[d]
+// counts them; a run past cap raises bit 0 of *fuse_status).  Then level d+1
+// is sized.
 static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::vector<u64> &se,
                         Scratch &sc, u64 *Alev, BuildMeta *meta, int d, int L, double gamma,
-                        unsigned *status, cudaStream_t st) {
+                        u64 *Fout, u64 cap, unsigned *fuse_status, unsigned *status,
+                        cudaStream_t st) {
   int rc0 = slab_attrs();
   if (rc0 != MPHF_OK) return rc0;
   const u64 fine = (u64)1 << kFineShift;
@@ -520,8 +588,8 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
     const u64 cap = (u64)(g_cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));  // scale: tests only
     return (cap + 3) & ~3ull;
   };
-  // T holds one slab's keys in either form: fixed-capacity ranges, or the
-  // exact ranges of a redo
+  // T / TP hold one slab's keys and positions in either form: fixed-capacity
+  // ranges, or the exact ranges of a redo
   u64 need = 0;
   for (unsigned c = 0; c < nslab; c++)
     if (se[nslab + c] > se[c])
@@ -531,7 +599,13 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
     int rc = dev_alloc(sc.T, need * 8, st);
     if (rc != MPHF_OK) return rc;
   }
+  if (sc.TP.bytes < need * 4) {
+    dev_free(sc.TP, st);
+    int rc = dev_alloc(sc.TP, need * 4, st);
+    if (rc != MPHF_OK) return rc;
+  }
   u64 *T = (u64 *)sc.T.p;
+  unsigned *TP = (unsigned *)sc.TP.p;
   u64 *cursor = (u64 *)sc.slab.p + kSlabMax, *end = (u64 *)sc.slab.p + 2 * kSlabMax;
   u64 *fstart = (u64 *)sc.slab.p + 3 * kSlabMax;
   std::vector<u64> fse;
@@ -547,7 +621,7 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
       }
       const unsigned nf = fine_count(c);
       if (exact) {
-        int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, (u64 *)sc.slab.p,
+        int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, TP, (u64 *)sc.slab.p,
                             status, fse, st);
         if (rc != MPHF_OK) return rc;
         MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
@@ -556,31 +630,29 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
           LaunchScope lr("slab_ranges", st);
           k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
         }
-        LaunchScope ls("slab_scatter", st);
-        const unsigned g = grid_for(b - a, kTile, (unsigned)sm_count() * 2);
-        const size_t sb = split_smem_bytes(nf) + kTile * 8;
-        if (((uintptr_t)(R + a) & 15) == 0)
-          k_slab_scatter<true><<<g, kTT, sb, st>>>(R + a, b - a, s, m, base, kFineShift, nf,
-                                                   cursor, end, T, status);
-        else
-          k_slab_scatter<false><<<g, kTT, sb, st>>>(R + a, b - a, s, m, base, kFineShift, nf,
-                                                    cursor, end, T, status);
+        launch_slab_scatter(R + a, b - a, s, m, base, kFineShift, nf, cursor, end, T, TP, status,
+                            st);
       }
       {
         LaunchScope ls("fine_fill", st);
-        k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, fstart, cursor, end, s, m, base,
-                                                         base + range, Alev, &meta->weight[d]);
+        k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, TP, fstart, cursor, end, base,
+                                                         base + range, Alev, &meta->weight[d],
+                                                         Fout, cap, &meta->out_count[d],
+                                                         fuse_status);
       }
       MPHF_CUDA(cudaGetLastError());
     }
     if (exact) break;
-    // a fixed-capacity range overflowed (duplicate-heavy input): redo the level
+    // a fixed-capacity range overflowed (duplicate-heavy input): redo the
+    // level, fill and compaction, from its grouped keys
     unsigned flag = 0;
     MPHF_CUDA(cudaMemcpyAsync(&flag, status, 4, cudaMemcpyDeviceToHost, st));
     MPHF_CUDA(cudaStreamSynchronize(st));
     if (!flag) break;
     MPHF_CUDA(cudaMemsetAsync(status, 0, 4, st));
     MPHF_CUDA(cudaMemsetAsync(&meta->weight[d], 0, 8, st));
+    MPHF_CUDA(cudaMemsetAsync(&meta->out_count[d], 0, 8, st));
+    MPHF_CUDA(cudaMemsetAsync(fuse_status, 0, 4, st));
   }
   {
     LaunchScope ls("extract", st);
@@ -675,7 +747,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   unsigned int *dflag = nullptr;
   unsigned nslab0 = 0;
   unsigned *slab_status = nullptr;
-  const u64 *F0 = keys;
+  unsigned *fuse_status = nullptr;
   std::vector<u64> se;  // slab ranges of the grouped keys
 
 #define TRY(x)                  \
@@ -688,7 +760,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   meta = (BuildMeta *)sc.meta.p;
   TRY(dev_alloc(sc.AC0, m0 / 32 * 8, st));
   TRY(dev_alloc(sc.A0, m0 / 64 * 8, st));
-  TRY(dev_alloc(sc.dupflag, 32, st));  // dup flag, rank total, slab overflow
+  TRY(dev_alloc(sc.dupflag, 32, st));  // dup flag, rank total, slab and F1 overflow
   dflag = (unsigned int *)sc.dupflag.p;
   if ((rc = cudaMemcpyAsync(meta, &hm, sizeof(hm), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     rc = cuda_fail((cudaError_t)rc, "cudaMemcpyAsync(meta)");
@@ -712,25 +784,45 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     }
   }
   slab_status = (unsigned *)((u64 *)sc.dupflag.p + 2);
-  // Level 0: ArrayFill over the caller's keys (grouped by slab: in shared
-  // memory, fine slab by fine slab), then extraction.
+  fuse_status = (unsigned *)((u64 *)sc.dupflag.p + 3);
   if (nslab0) {
-    TRY(group_keys(keys, N, h->s[0], m0, 0, g_slab_shift, nslab0, (u64 *)sc.R.p,
+    // Level 0 grouped: fill and compaction run together, F_1 going to F1,
+    // allocated for a bound on |F_1| (8 standard deviations above its mean).
+    const double mean = (double)N * (1.0 - pow(1.0 - 1.0 / (double)m0, (double)N - 1.0));
+    u64 n1_hi = (u64)(mean + 8.0 * sqrt((double)N) + 1024.0);
+    if (n1_hi > N) n1_hi = N;
+    TRY(dev_alloc(sc.F1, n1_hi * 8, st));
+    TRY(group_keys(keys, N, h->s[0], m0, 0, g_slab_shift, nslab0, (u64 *)sc.R.p, nullptr,
                    (u64 *)sc.slab.p, slab_status, se, st));
-    F0 = (const u64 *)sc.R.p;
-    TRY(fill_grouped(F0, h->s[0], m0, nslab0, se, sc, (u64 *)sc.A0.p, meta, 0, (int)L, gamma,
-                     slab_status, st));
+    TRY(fill_grouped((const u64 *)sc.R.p, h->s[0], m0, nslab0, se, sc, (u64 *)sc.A0.p, meta, 0,
+                     (int)L, gamma, (u64 *)sc.F1.p, n1_hi, fuse_status, slab_status, st));
+    TRY(read_u64(&meta->n[1], &n1, st));
+    u64 fflag = 0;
+    TRY(read_u64((const u64 *)fuse_status, &fflag, st));
+    if ((unsigned)fflag) {
+      // |F_1| above the bound (thousands of equal keys): F1 at its exact size
+      // and the compaction of level 0 again, from the grouped keys in R
+      dev_free(sc.F1, st);
+      TRY(dev_alloc(sc.F1, n1 * 8, st));
+      if (cudaMemsetAsync(&meta->out_count[0], 0, 8, st) != cudaSuccess ||
+          cudaMemsetAsync(fuse_status, 0, 4, st) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+        goto fail;
+      }
+      TRY(launch_compact((const u64 *)sc.R.p, N, (u64 *)sc.F1.p, n1, (const u64 *)sc.A0.p,
+                         nullptr, nullptr, meta, 0, h->s[0], 0, 0, st));
+    }
   } else {
-    TRY(launch_fill0(F0, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
+    TRY(launch_fill0(keys, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
     TRY(launch_extract((u64 *)sc.AC0.p, m0, (u64 *)sc.A0.p, nullptr, meta, 0, (int)L, gamma,
                        st));
+    TRY(read_u64(&meta->n[1], &n1, st));
   }
-  TRY(read_u64(&meta->n[1], &n1, st));
 
   if (n1 > 0) {
     // Every later level holds at most n1 keys, so these bounds are exact worst cases.
     const u64 m1 = level_bits(n1, gamma);
-    TRY(dev_alloc(sc.F1, n1 * 8, st));
+    if (!sc.F1.p) TRY(dev_alloc(sc.F1, n1 * 8, st));
     // with grouped levels, R (N keys) is the second buffer of the level loop
     if (L > 1 && !nslab0) TRY(dev_alloc(sc.F2, n1 * 8, st));
     if (L > 1) {
@@ -744,50 +836,64 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   }
 
   {
-    // Level loop: compaction of d (+ fill of d+1), extraction of d+1.
+    // Level loop.  An ungrouped level d is compacted here (with level d+1's
+    // fill when that level is ungrouped too); a grouped level was compacted
+    // by its fill, F_{d+1} already in F1.  Then level d+1: grouped (group,
+    // fill and compact) or ungrouped (fill unless done, extract).
     u64 n_next = n1;  // |F_{d+1}|
     u64 off_next = 0;
-    const u64 *Fin = F0;
+    const u64 *Fin = keys;          // keys of level d, for a compaction here
+    bool compacted = nslab0 != 0;   // F_{d+1} written by level d's fill
+    u64 *F1 = (u64 *)sc.F1.p;
     int d = 0;
     for (;;) {
       if (n_next == 0) {
         last_level = d;
         break;
       }
-      // F_{d+1} goes to the buffer F_d is not read from: F1 and F2, or F1 and R
-      // (grouped levels, a prefix of the levels, read R and write F1)
-      u64 *other = nslab0 ? (u64 *)sc.R.p : (u64 *)sc.F2.p;
-      u64 *Fout = (Fin == (const u64 *)sc.F1.p) ? other : (u64 *)sc.F1.p;
       const bool to_fallback = (uint32_t)(d + 1) == L;
-      u64 *ACnext = ((d + 1) & 1) ? (u64 *)sc.AC1.p : (u64 *)sc.AC0.p;
-      // a grouped next level is filled after its keys are grouped, not here
       const u64 m_next = to_fallback ? 0 : level_bits(n_next, gamma);
-      const unsigned nslab = (nslab0 && !to_fallback) ? slab_count_for(m_next) : 0u;
-      const int fuse = (to_fallback || nslab) ? 0 : 1;
-      TRY(launch_compact(Fin, d == 0 ? N : n1, Fout, n1, (const u64 *)sc.A0.p,
-                         (const u64 *)sc.arena.p, fuse ? ACnext : nullptr, meta, d, h->s[d],
-                         fuse ? h->s[d + 1] : 0, fuse, st));
+      unsigned nslab = (nslab0 && !to_fallback) ? slab_count_for(m_next) : 0u;
+      u64 *ACnext = ((d + 1) & 1) ? (u64 *)sc.AC1.p : (u64 *)sc.AC0.p;
+      u64 *Fnext;  // F_{d+1}
+      bool filled_next = false;
+      if (compacted) {
+        Fnext = F1;
+      } else {
+        // F_{d+1} goes to the buffer F_d is not read from: F1 and F2, or F1 and R
+        u64 *other = nslab0 ? (u64 *)sc.R.p : (u64 *)sc.F2.p;
+        Fnext = (Fin == F1) ? other : F1;
+        if (Fnext != F1) nslab = 0;  // grouped levels are a prefix: cannot happen
+        const int fuse = (to_fallback || nslab) ? 0 : 1;
+        TRY(launch_compact(Fin, d == 0 ? N : n1, Fnext, n1, (const u64 *)sc.A0.p,
+                           (const u64 *)sc.arena.p, fuse ? ACnext : nullptr, meta, d, h->s[d],
+                           fuse ? h->s[d + 1] : 0, fuse, st));
+        filled_next = fuse != 0;
+      }
       if (to_fallback) {
         last_level = d;
-        Ffb = Fout;
+        Ffb = Fnext;
         n_fb = n_next;
         break;
       }
-      const u64 *Fnext = Fout;
       if (nslab) {
-        TRY(group_keys(Fout, n_next, h->s[d + 1], m_next, 0, g_slab_shift, nslab,
-                       (u64 *)sc.R.p, (u64 *)sc.slab.p, slab_status, se, st));
-        Fnext = (const u64 *)sc.R.p;
+        // level d+1 grouped: F_{d+1} into R by slab, then fill and compaction,
+        // F_{d+2} written back into F1 (read entirely by the grouping)
+        TRY(group_keys(Fnext, n_next, h->s[d + 1], m_next, 0, g_slab_shift, nslab,
+                       (u64 *)sc.R.p, nullptr, (u64 *)sc.slab.p, slab_status, se, st));
         TRY(read_u64(&meta->off[d + 1], &off_next, st));
-        TRY(fill_grouped(Fnext, h->s[d + 1], m_next, nslab, se, sc,
+        TRY(fill_grouped((const u64 *)sc.R.p, h->s[d + 1], m_next, nslab, se, sc,
                          (u64 *)sc.arena.p + ((off_next - m0) >> 6), meta, d + 1, (int)L, gamma,
-                         slab_status, st));
+                         F1, n1, fuse_status, slab_status, st));
+        compacted = true;
       } else {
+        if (!filled_next) TRY(launch_fill0(Fnext, n_next, h->s[d + 1], m_next, ACnext, st));
         TRY(launch_extract(ACnext, level_bits(n1, gamma), (u64 *)sc.A0.p, (u64 *)sc.arena.p,
                            meta, d + 1, (int)L, gamma, st));
+        Fin = Fnext;
+        compacted = false;
       }
       TRY(read_u64(&meta->n[d + 2], &n_next, st));
-      Fin = Fnext;
       d++;
     }
   }
@@ -829,13 +935,13 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     }
   }
   {
-    u64 flags[3] = {0, 0, 0};
-    if (cudaMemcpyAsync(flags, sc.dupflag.p, 24, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    u64 flags[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(flags, sc.dupflag.p, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       rc = cuda_fail(cudaGetLastError(), "dup flag");
       goto fail;
     }
-    if ((unsigned)flags[2]) {  // a grouping overflowed a slab range: cannot happen
+    if ((unsigned)flags[2] || (unsigned)flags[3]) {  // a slab range or F1 overflowed: cannot happen
       rc = MPHF_EINTERNAL;
       goto fail;
     }

@@ -384,6 +384,29 @@ def test_unbucketed_slab_grouping(M, gamma, levels, shift):
     assert np.array_equal(M.to_u64(g.lookup(dev(q))), o.lookup(q))
 
 
+def test_grouped_level0_many_equal_keys(M):
+    # 40000 copies of one key push |F_1| past the bound that the grouped
+    # level 0 sizes F_1 by: the compaction of level 0 runs again into an
+    # exactly sized buffer, and the duplicates are reported; the same keys
+    # without the copies give the oracle's function.
+    keys = inputs.splitmix64_keys(300007, 62)
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=15)
+    dup = np.concatenate([keys, np.full(40000, keys[11], dtype=np.uint64)])
+    M.debug_config(1, 1.0)
+    M.debug_slabs(20, 0)
+    try:
+        with pytest.raises(M.MPHFError) as e:
+            M.MPHF.build(dev(dup), gamma=2.0, levels=25, seed=15)
+        assert e.value.code == M.EDUPLICATE
+        g = M.MPHF.build(dev(keys), gamma=2.0, levels=25, seed=15)
+    finally:
+        M.debug_slabs()
+        M.debug_config(0, 1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(M.to_u64(g.lookup(dev(keys))), o.lookup(keys))
+
+
 @pytest.mark.parametrize("cap_scale", [1.0, 0.3])
 def test_unbucketed_grouping_overflow_redo(M, cap_scale):
     # Fine slabs take fixed-capacity ranges; a range that overflows (capacity
