@@ -163,10 +163,11 @@ __global__ void k_level_done(BuildMeta *__restrict__ meta, int d, int L, double 
 // ---------------------------------------------------------------------------
 template <bool VEC>
 __global__ void __launch_bounds__(kCompactThreads, 4)
-k_compact(const u64 *__restrict__ F, u64 *__restrict__ Fout, const u64 *__restrict__ A0,
+k_compact(const u64 *__restrict__ F, u64 n_in, u64 *__restrict__ Fout, const u64 *__restrict__ A0,
           const u64 *__restrict__ Aarena, u64 *__restrict__ ACnext, BuildMeta *__restrict__ meta,
           int d, u64 s_d, u64 s_next, int do_fill, u64 cap) {
-  const u64 n = meta->n[d];
+  // n_in: keys of F, or ~0 for all of level d (|F_d|, from meta)
+  const u64 n = n_in == ~0ull ? meta->n[d] : n_in;
   const u64 m = meta->m[d];
   if (m == 0 || n == 0 || meta->n[d + 1] == 0) return;
   const u64 m0 = meta->m[0];
@@ -433,19 +434,31 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     __syncwarp();
     cnt = 0;
   };
-  for (u64 e = i0 + (u64)warp * 32; e < i1; e += kFineThreads) {
-    const u64 k = e + lane;
-    bool keep = false;
-    u64 x = 0;
-    if (k < i1) {
-      const unsigned q = TP[k];
-      keep = !(((hit[q >> 5] & ~col[q >> 5]) >> (q & 31)) & 1u);
-      if (keep) x = __ldcs(T + k);  // only the survivors' keys are read
+  // kC chunks of 32 entries per warp step: their position loads, then their
+  // survivors' key loads, are all in flight together
+  constexpr int kC = 4;
+  for (u64 e = i0 + (u64)warp * 32; e < i1; e += (u64)kC * kFineThreads) {
+    unsigned q[kC];
+    bool keep[kC];
+    u64 x[kC];
+#pragma unroll
+    for (int c = 0; c < kC; c++) {
+      const u64 k = e + (u64)c * kFineThreads + lane;
+      q[c] = k < i1 ? TP[k] : 0u;
     }
-    const unsigned bb = __ballot_sync(0xffffffffu, keep);
-    if (keep) stage[cnt + __popc(bb & lt)] = x;
-    cnt += __popc(bb);
-    if (cnt > (unsigned)(kFineStage - 32)) flush();
+#pragma unroll
+    for (int c = 0; c < kC; c++) {
+      const u64 k = e + (u64)c * kFineThreads + lane;
+      keep[c] = k < i1 && !(((hit[q[c] >> 5] & ~col[q[c] >> 5]) >> (q[c] & 31)) & 1u);
+      x[c] = keep[c] ? __ldcs(T + k) : 0;  // only the survivors' keys are read
+    }
+#pragma unroll
+    for (int c = 0; c < kC; c++) {
+      const unsigned bb = __ballot_sync(0xffffffffu, keep[c]);
+      if (keep[c]) stage[cnt + __popc(bb & lt)] = x[c];
+      cnt += __popc(bb);
+      if (cnt > (unsigned)(kFineStage - 32)) flush();
+    }
   }
   flush();
 }
@@ -558,6 +571,65 @@ static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shif
   launch_slab_scatter(F, n, s, m, base, shift, nslab, cursor, end, out, pout, status, st);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
+}
+
+// Capacity of slab c of a level's coarse grouping when n keys spread over m
+// positions: its share of the keys plus 8 standard deviations and 64 keys, a
+// multiple of 4 (so every slab starts 32-byte aligned).
+static u64 slab_cap(u64 n, u64 m, unsigned c) {
+  const u64 lo = (u64)c << g_slab_shift;
+  const u64 range = std::min((u64)1 << g_slab_shift, m - lo);
+  const double mean = (double)n * (double)range / (double)m;
+  const u64 cap = (u64)(g_cap_scale * (mean + 8.0 * sqrt(mean) + 64.0));  // scale: tests only
+  return (cap + 3) & ~3ull;
+}
+
+// Room the coarse grouping of n keys over m positions (nslab slabs) needs:
+// the sum of the slab capacities, and at least n (the exact redo).
+static u64 grouped_room(u64 n, u64 m, unsigned nslab) {
+  u64 t = 0;
+  for (unsigned c = 0; c < nslab; c++) t += slab_cap(n, m, c);
+  return std::max(t, n);
+}
+
+// The coarse grouping of a level (slabs of 2^g_slab_shift positions): keys
+// go to fixed-capacity slab ranges of out (slab_cap), so no count pass is
+// needed; se receives the ranges actually filled.  If a range overflows
+// (thousands of equal keys), the grouping is done again with exact counts.
+static int group_level(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *out, u64 *slab,
+                       unsigned *status, std::vector<u64> &se, cudaStream_t st) {
+  int rc0 = slab_attrs();
+  if (rc0 != MPHF_OK) return rc0;
+  u64 *cursor = slab + kSlabMax, *end = slab + 2 * kSlabMax;
+  std::vector<u64> lo(2 * (size_t)nslab);
+  u64 run = 0;
+  for (unsigned c = 0; c < nslab; c++) {
+    lo[c] = run;
+    run += slab_cap(n, m, c);
+    lo[nslab + c] = run;
+  }
+  // pageable copies: the host data is staged before each call returns
+  MPHF_CUDA(cudaMemcpyAsync(cursor, lo.data(), nslab * 8, cudaMemcpyHostToDevice, st));
+  MPHF_CUDA(cudaMemcpyAsync(end, lo.data() + nslab, nslab * 8, cudaMemcpyHostToDevice, st));
+  launch_slab_scatter(F, n, s, m, 0, g_slab_shift, nslab, cursor, end, out, nullptr, status, st);
+  MPHF_CUDA(cudaGetLastError());
+  std::vector<u64> cur(nslab);
+  unsigned flag = 0;
+  MPHF_CUDA(cudaMemcpyAsync(cur.data(), cursor, nslab * 8, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaMemcpyAsync(&flag, status, 4, cudaMemcpyDeviceToHost, st));
+  MPHF_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    MPHF_CUDA(cudaMemsetAsync(status, 0, 4, st));
+    return group_keys(F, n, s, m, 0, g_slab_shift, nslab, out, nullptr, slab, status, se, st);
+  }
+  se.assign(2 * (size_t)nslab, 0);
+  u64 total = 0;
+  for (unsigned c = 0; c < nslab; c++) {
+    se[c] = lo[c];
+    se[nslab + c] = cur[c];
+    total += cur[c] - lo[c];
+  }
+  return total == n ? MPHF_OK : MPHF_EINTERNAL;
 }
 
 // ArrayFill and compaction of a level whose keys R are grouped by slab
@@ -704,15 +776,15 @@ static int launch_extract(u64 *AC, u64 m_bound, u64 *A0, u64 *arena, BuildMeta *
 
 static int launch_compact(const u64 *F, u64 n_bound, u64 *Fout, u64 cap, const u64 *A0,
                           const u64 *arena, u64 *ACnext, BuildMeta *meta, int d, u64 s_d,
-                          u64 s_next, int do_fill, cudaStream_t st) {
+                          u64 s_next, int do_fill, cudaStream_t st, u64 n_in = ~0ull) {
   unsigned g = grid_for(n_bound, kCompactTile, (unsigned)sm_count() * 4);
   LaunchScope ls("compact", st);
   if (((uintptr_t)F & 15) == 0)
-    k_compact<true><<<g, kCompactThreads, 0, st>>>(F, Fout, A0, arena, ACnext, meta, d, s_d,
-                                                   s_next, do_fill, cap);
+    k_compact<true><<<g, kCompactThreads, 0, st>>>(F, n_in, Fout, A0, arena, ACnext, meta, d,
+                                                   s_d, s_next, do_fill, cap);
   else
-    k_compact<false><<<g, kCompactThreads, 0, st>>>(F, Fout, A0, arena, ACnext, meta, d, s_d,
-                                                    s_next, do_fill, cap);
+    k_compact<false><<<g, kCompactThreads, 0, st>>>(F, n_in, Fout, A0, arena, ACnext, meta, d,
+                                                    s_d, s_next, do_fill, cap);
   MPHF_CUDA(cudaGetLastError());
   return MPHF_OK;
 }
@@ -776,7 +848,8 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   // for it the keys stay in their order.
   nslab0 = slab_count_for(m0);
   if (nslab0) {
-    if (dev_alloc(sc.R, N * 8, st) != MPHF_OK || dev_alloc(sc.slab, 4 * kSlabMax * 8, st) != MPHF_OK) {
+    if (dev_alloc(sc.R, grouped_room(N, m0, nslab0) * 8, st) != MPHF_OK ||
+        dev_alloc(sc.slab, 4 * kSlabMax * 8, st) != MPHF_OK) {
       cudaGetLastError();
       dev_free(sc.R, st);
       dev_free(sc.slab, st);
@@ -792,8 +865,8 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     u64 n1_hi = (u64)(mean + 8.0 * sqrt((double)N) + 1024.0);
     if (n1_hi > N) n1_hi = N;
     TRY(dev_alloc(sc.F1, n1_hi * 8, st));
-    TRY(group_keys(keys, N, h->s[0], m0, 0, g_slab_shift, nslab0, (u64 *)sc.R.p, nullptr,
-                   (u64 *)sc.slab.p, slab_status, se, st));
+    TRY(group_level(keys, N, h->s[0], m0, nslab0, (u64 *)sc.R.p, (u64 *)sc.slab.p, slab_status,
+                    se, st));
     TRY(fill_grouped((const u64 *)sc.R.p, h->s[0], m0, nslab0, se, sc, (u64 *)sc.A0.p, meta, 0,
                      (int)L, gamma, (u64 *)sc.F1.p, n1_hi, fuse_status, slab_status, st));
     TRY(read_u64(&meta->n[1], &n1, st));
@@ -809,8 +882,11 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
         rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
         goto fail;
       }
-      TRY(launch_compact((const u64 *)sc.R.p, N, (u64 *)sc.F1.p, n1, (const u64 *)sc.A0.p,
-                         nullptr, nullptr, meta, 0, h->s[0], 0, 0, st));
+      for (unsigned c = 0; c < nslab0; c++)  // slab by slab: the ranges of R have gaps
+        if (se[nslab0 + c] > se[c])
+          TRY(launch_compact((const u64 *)sc.R.p + se[c], se[nslab0 + c] - se[c],
+                             (u64 *)sc.F1.p, n1, (const u64 *)sc.A0.p, nullptr, nullptr, meta, 0,
+                             h->s[0], 0, 0, st, se[nslab0 + c] - se[c]));
     }
   } else {
     TRY(launch_fill0(keys, N, h->s[0], m0, (u64 *)sc.AC0.p, st));
@@ -879,8 +955,12 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
       if (nslab) {
         // level d+1 grouped: F_{d+1} into R by slab, then fill and compaction,
         // F_{d+2} written back into F1 (read entirely by the grouping)
-        TRY(group_keys(Fnext, n_next, h->s[d + 1], m_next, 0, g_slab_shift, nslab,
-                       (u64 *)sc.R.p, nullptr, (u64 *)sc.slab.p, slab_status, se, st));
+        if (grouped_room(n_next, m_next, nslab) * 8 > sc.R.bytes) {  // cannot happen: n shrinks
+          rc = MPHF_EINTERNAL;
+          goto fail;
+        }
+        TRY(group_level(Fnext, n_next, h->s[d + 1], m_next, nslab, (u64 *)sc.R.p,
+                        (u64 *)sc.slab.p, slab_status, se, st));
         TRY(read_u64(&meta->off[d + 1], &off_next, st));
         TRY(fill_grouped((const u64 *)sc.R.p, h->s[d + 1], m_next, nslab, se, sc,
                          (u64 *)sc.arena.p + ((off_next - m0) >> 6), meta, d + 1, (int)L, gamma,
