@@ -632,31 +632,6 @@ static int group_level(const u64 *F, u64 n, u64 s, u64 m, unsigned nslab, u64 *o
   return total == n ? MPHF_OK : MPHF_EINTERNAL;
 }
 
-// The side stream of the grouped levels' fills, per host thread and device,
-// with the events that order it against the main stream: `ready` (a slab's
-// fine grouping is done) and done[i] (the fill reading buffer i is done).
-struct FillStream {
-  cudaStream_t s;
-  cudaEvent_t ready, done[2];
-};
-static int fill_stream(FillStream *out) {
-  struct Per {
-    FillStream f{};
-    bool made = false;
-  };
-  thread_local Per per[64];
-  Per &p = per[cur_device()];
-  if (!p.made) {
-    MPHF_CUDA(cudaStreamCreateWithFlags(&p.f.s, cudaStreamNonBlocking));
-    MPHF_CUDA(cudaEventCreateWithFlags(&p.f.ready, cudaEventDisableTiming));
-    MPHF_CUDA(cudaEventCreateWithFlags(&p.f.done[0], cudaEventDisableTiming));
-    MPHF_CUDA(cudaEventCreateWithFlags(&p.f.done[1], cudaEventDisableTiming));
-    p.made = true;
-  }
-  *out = p.f;
-  return MPHF_OK;
-}
-
 // ArrayFill and compaction of a level whose keys R are grouped by slab
 // (ranges se): each slab's keys are grouped again into fine slabs of
 // 2^kFineShift positions (into T, with their positions in TP), then each fine
@@ -691,83 +666,23 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
   for (unsigned c = 0; c < nslab; c++)
     if (se[nslab + c] > se[c])
       need = std::max(need, std::max((u64)fine_count(c) * fine_cap(c), se[nslab + c] - se[c]));
-  // two of each: the fill of slab c (side stream) overlaps the grouping of
-  // slab c+1 (main stream)
-  if (sc.T.bytes < 2 * need * 8) {
+  if (sc.T.bytes < need * 8) {
     dev_free(sc.T, st);
-    int rc = dev_alloc(sc.T, 2 * need * 8, st);
+    int rc = dev_alloc(sc.T, need * 8, st);
     if (rc != MPHF_OK) return rc;
   }
-  if (sc.TP.bytes < 2 * need * 4) {
+  if (sc.TP.bytes < need * 4) {
     dev_free(sc.TP, st);
-    int rc = dev_alloc(sc.TP, 2 * need * 4, st);
+    int rc = dev_alloc(sc.TP, need * 4, st);
     if (rc != MPHF_OK) return rc;
   }
   u64 *T = (u64 *)sc.T.p;
   unsigned *TP = (unsigned *)sc.TP.p;
   u64 *cursor = (u64 *)sc.slab.p + kSlabMax, *end = (u64 *)sc.slab.p + 2 * kSlabMax;
   u64 *fstart = (u64 *)sc.slab.p + 3 * kSlabMax;
-  FillStream fsx;
-  rc0 = fill_stream(&fsx);
-  if (rc0 != MPHF_OK) return rc0;
   std::vector<u64> fse;
-  // pass 0: fixed-capacity fine ranges, buffers alternating between slabs,
-  // each slab's fill on the side stream fs
-  {
-    cudaStream_t fs = fsx.s;
-    bool used[2] = {false, false};
-    unsigned k = 0;
-    for (unsigned c = 0; c < nslab; c++) {
-      const u64 a = se[c], b = se[nslab + c];
-      const u64 base = (u64)c << g_slab_shift;
-      const u64 range = std::min((u64)1 << g_slab_shift, m - base);
-      if (a == b) {  // no key in the slab: its stretch of A_d is all zero
-        MPHF_CUDA(cudaMemsetAsync(Alev + (base >> 6), 0, range / 8, st));
-        continue;
-      }
-      const unsigned nf = fine_count(c);
-      const unsigned bi = k++ & 1u;
-      u64 *Tb = T + bi * need;
-      unsigned *TPb = TP + bi * need;
-      u64 *cur_b = cursor + bi * 3 * kSlabMax, *end_b = end + bi * 3 * kSlabMax;
-      u64 *fst_b = fstart + bi * 3 * kSlabMax;
-      if (used[bi]) MPHF_CUDA(cudaStreamWaitEvent(st, fsx.done[bi], 0));
-      {
-        LaunchScope lr("slab_ranges", st);
-        k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cur_b, end_b, fst_b, nf, fine_cap(c));
-      }
-      launch_slab_scatter(R + a, b - a, s, m, base, kFineShift, nf, cur_b, end_b, Tb, TPb, status,
-                          st);
-      MPHF_CUDA(cudaEventRecord(fsx.ready, st));
-      MPHF_CUDA(cudaStreamWaitEvent(fs, fsx.ready, 0));
-      {
-        LaunchScope ls("fine_fill", fs);
-        k_fine_fill<<<nf, kFineThreads, kFineSmem, fs>>>(Tb, TPb, fst_b, cur_b, end_b, base,
-                                                         base + range, Alev, &meta->weight[d],
-                                                         Fout, cap, &meta->out_count[d],
-                                                         fuse_status);
-      }
-      MPHF_CUDA(cudaGetLastError());
-      MPHF_CUDA(cudaEventRecord(fsx.done[bi], fs));
-      used[bi] = true;
-    }
-    for (int i = 0; i < 2; i++)
-      if (used[i]) MPHF_CUDA(cudaStreamWaitEvent(st, fsx.done[i], 0));
-  }
-  // a fixed-capacity range overflowed (duplicate-heavy input): redo the
-  // level, fill and compaction, from its grouped keys, with exact counts
+  // exact = false: fine ranges of a fixed capacity; true: counted first
   for (int exact = 0; exact < 2; exact++) {
-    if (exact == 0) {
-      unsigned flag = 0;
-      MPHF_CUDA(cudaMemcpyAsync(&flag, status, 4, cudaMemcpyDeviceToHost, st));
-      MPHF_CUDA(cudaStreamSynchronize(st));
-      if (!flag) break;
-      MPHF_CUDA(cudaMemsetAsync(status, 0, 4, st));
-      MPHF_CUDA(cudaMemsetAsync(&meta->weight[d], 0, 8, st));
-      MPHF_CUDA(cudaMemsetAsync(&meta->out_count[d], 0, 8, st));
-      MPHF_CUDA(cudaMemsetAsync(fuse_status, 0, 4, st));
-      continue;
-    }
     for (unsigned c = 0; c < nslab; c++) {
       const u64 a = se[c], b = se[nslab + c];
       const u64 base = (u64)c << g_slab_shift;
@@ -777,11 +692,18 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
         continue;
       }
       const unsigned nf = fine_count(c);
-      {
+      if (exact) {
         int rc = group_keys(R + a, b - a, s, m, base, kFineShift, nf, T, TP, (u64 *)sc.slab.p,
                             status, fse, st);
         if (rc != MPHF_OK) return rc;
         MPHF_CUDA(cudaMemcpyAsync(fstart, fse.data(), nf * 8, cudaMemcpyHostToDevice, st));
+      } else {
+        {
+          LaunchScope lr("slab_ranges", st);
+          k_fine_ranges<<<(nf + 255) / 256, 256, 0, st>>>(cursor, end, fstart, nf, fine_cap(c));
+        }
+        launch_slab_scatter(R + a, b - a, s, m, base, kFineShift, nf, cursor, end, T, TP, status,
+                            st);
       }
       {
         LaunchScope ls("fine_fill", st);
@@ -792,6 +714,17 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
       }
       MPHF_CUDA(cudaGetLastError());
     }
+    if (exact) break;
+    // a fixed-capacity range overflowed (duplicate-heavy input): redo the
+    // level, fill and compaction, from its grouped keys
+    unsigned flag = 0;
+    MPHF_CUDA(cudaMemcpyAsync(&flag, status, 4, cudaMemcpyDeviceToHost, st));
+    MPHF_CUDA(cudaStreamSynchronize(st));
+    if (!flag) break;
+    MPHF_CUDA(cudaMemsetAsync(status, 0, 4, st));
+    MPHF_CUDA(cudaMemsetAsync(&meta->weight[d], 0, 8, st));
+    MPHF_CUDA(cudaMemsetAsync(&meta->out_count[d], 0, 8, st));
+    MPHF_CUDA(cudaMemsetAsync(fuse_status, 0, 4, st));
   }
   {
     LaunchScope ls("extract", st);
@@ -916,7 +849,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   nslab0 = slab_count_for(m0);
   if (nslab0) {
     if (dev_alloc(sc.R, grouped_room(N, m0, nslab0) * 8, st) != MPHF_OK ||
-        dev_alloc(sc.slab, 7 * kSlabMax * 8, st) != MPHF_OK) {
+        dev_alloc(sc.slab, 4 * kSlabMax * 8, st) != MPHF_OK) {
       cudaGetLastError();
       dev_free(sc.R, st);
       dev_free(sc.slab, st);
