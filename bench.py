@@ -826,7 +826,9 @@ def run_serving(args, stream):
             "offered_req_s": round(rate, 1), "lookups": r["lookups"], "builds": r["builds"],
             "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "mkeys_s": round(r["keys"] / r["elapsed"] / 1e6, 1)}
+            "mkeys_s": round(r["keys"] / r["elapsed"] / 1e6, 1),
+            "parts_ms": {k: {q: round(v[q] * 1e3, 4) for q in ("p50", "p99")}
+                         for k, v in r["parts"].items()}}
     srv.close()
     del hs, keys, build_keys, out, ring_out
     torch.cuda.empty_cache()

@@ -402,6 +402,13 @@ int mphf_server_wait(mphf_server_t *srv, uint64_t req_id, double timeout_s, int 
                      double *latency_s, mphf_t **built);
 int mphf_server_stats(mphf_server_t *srv, uint64_t *batches, uint64_t *requests, uint64_t *keys,
                       uint64_t *builds);
+/* Where the time of the lookups completed since the last call went: p50[k]
+ * and p99[k] (seconds) of k = 0 the queue wait (submission to the launch of
+ * the request's batch), 1 the batch's GPU time (events around its table copy
+ * and kernel), 2 the rest (launch to completion seen by the scheduler, minus
+ * the GPU time: stream wait behind other work and detection).  Clears the
+ * record. */
+int mphf_server_latency_parts(mphf_server_t *srv, double *p50, double *p99);
 /*
  * Measurement driver: an open-loop Poisson stream of requests at rate_hz for
  * duration_s against the server.  Each lookup picks one of the nh handles

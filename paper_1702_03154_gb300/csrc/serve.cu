@@ -347,6 +347,7 @@ struct Req {
   uint32_t L;
   u64 seed;
   double t_submit = 0, t_done = 0;
+  double t_launch = 0;  // lookups: when the batch holding it was launched
   int status = MPHF_OK;
   mphf_t *built = nullptr;
   bool done = false;
@@ -354,7 +355,8 @@ struct Req {
 
 struct Batch {
   std::vector<Req *> reqs;
-  cudaEvent_t ev;
+  cudaEvent_t ev;       // after the batch (completion)
+  cudaEvent_t ev0;      // before the batch (GPU time of the batch, with ev)
   int slot;
 };
 
@@ -386,6 +388,9 @@ struct mphf_server {
   std::deque<bbh::Batch> inflight;
   // statistics
   std::atomic<uint64_t> batches{0}, batched_reqs{0}, batched_keys{0}, builds_done{0};
+  // per completed lookup: queue wait (submit -> launch of its batch), GPU time
+  // of its batch, and the rest (launch -> completion seen, minus GPU time)
+  std::vector<double> part_queue, part_gpu, part_rest;
 };
 
 namespace bbh {
@@ -408,16 +413,25 @@ static void scheduler(mphf_server *sv) {
       cudaError_t q = cudaEventQuery(b.ev);
       if (q == cudaErrorNotReady) break;
       const double t = now_s();
+      float gpu_ms = 0.f;
+      if (cudaEventElapsedTime(&gpu_ms, b.ev0, b.ev) != cudaSuccess) {
+        cudaGetLastError();
+        gpu_ms = 0.f;
+      }
       {
         std::lock_guard<std::mutex> lk(sv->mu);
         for (Req *r : b.reqs) {
           r->t_done = t;
           r->status = q == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
           r->done = true;
+          sv->part_queue.push_back(r->t_launch - r->t_submit);
+          sv->part_gpu.push_back(gpu_ms * 1e-3);
+          sv->part_rest.push_back(t - r->t_launch - gpu_ms * 1e-3);
         }
       }
       sv->cv_done.notify_all();
       cudaEventDestroy(b.ev);
+      cudaEventDestroy(b.ev0);
       sv->slot_busy[b.slot] = false;
       sv->inflight.pop_front();
       worked = true;
@@ -449,13 +463,17 @@ static void scheduler(mphf_server *sv) {
             [&](size_t i) { return take[i]->keys; }, [&](size_t i) { return take[i]->out; },
             [&](size_t i) { return take[i]->n; });
         cudaStream_t s = sv->lstream[rr++ & 1];
-        cudaMemcpyAsync(sv->dtab[slot].p, ht, sizeof(ReqDev) * take.size(),
-                        cudaMemcpyHostToDevice, s);
-        launch_lookup_multi((const ReqDev *)sv->dtab[slot].p, g, s);
         Batch b;
         b.reqs = take;
         b.slot = slot;
-        cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+        cudaEventCreate(&b.ev0);
+        cudaEventCreate(&b.ev);
+        const double tl = now_s();
+        for (Req *r : take) r->t_launch = tl;
+        cudaEventRecord(b.ev0, s);
+        cudaMemcpyAsync(sv->dtab[slot].p, ht, sizeof(ReqDev) * take.size(),
+                        cudaMemcpyHostToDevice, s);
+        launch_lookup_multi((const ReqDev *)sv->dtab[slot].p, g, s);
         cudaEventRecord(b.ev, s);
         sv->slot_busy[slot] = true;
         sv->inflight.push_back(b);
@@ -669,6 +687,23 @@ int mphf_server_stats(mphf_server_t *sv, uint64_t *batches, uint64_t *requests, 
   if (requests) *requests = sv->batched_reqs.load();
   if (keys) *keys = sv->batched_keys.load();
   if (builds) *builds = sv->builds_done.load();
+  return MPHF_OK;
+}
+
+int mphf_server_latency_parts(mphf_server_t *sv, double *p50, double *p99) {
+  if (!sv || !p50 || !p99) return MPHF_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  std::vector<double> *parts[3] = {&sv->part_queue, &sv->part_gpu, &sv->part_rest};
+  for (int k = 0; k < 3; k++) {
+    std::vector<double> &v = *parts[k];
+    p50[k] = p99[k] = 0.0;
+    if (v.empty()) continue;
+    std::vector<double> w = v;
+    std::sort(w.begin(), w.end());
+    p50[k] = w[(size_t)(0.50 * (w.size() - 1))];
+    p99[k] = w[(size_t)(0.99 * (w.size() - 1))];
+    v.clear();
+  }
   return MPHF_OK;
 }
 

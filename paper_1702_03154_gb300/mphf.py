@@ -122,6 +122,7 @@ def lib():
         "mphf_part_function": ([vp, u32], vp),
         "mphf_part_free": ([vp], None),
         "mphf_pool_trim": ([], i32),
+        "mphf_server_latency_parts": ([vp, vp, vp], i32),
         "mphf_launch_count": ([], u64),
         "mphf_profile_enable": ([i32], i32),
         "mphf_profile_report": ([ctypes.c_char_p, u64], i32),
@@ -618,6 +619,7 @@ class Server:
         C = (ctypes.c_uint64 * n)(*[k.numel() for k in keys_list])
         lat = np.empty(int(lat_cap), dtype=np.float64)
         nl, nk, nb, el = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+        self.latency_parts()  # start the record afresh
         rc = lib().mphf_server_loadgen(
             self._p, H, K, C, n, float(rate_hz), float(duration_s), float(bmin), float(bmax),
             out.data_ptr(), out.numel(), float(build_frac),
@@ -628,7 +630,16 @@ class Server:
         _check(rc, "mphf_server_loadgen")
         m = int(min(nl.value, lat.size))
         return {"latencies": lat[:m].copy(), "lookups": nl.value, "keys": nk.value,
-                "builds": nb.value, "elapsed": el.value}
+                "builds": nb.value, "elapsed": el.value, "parts": self.latency_parts()}
+
+    def latency_parts(self) -> dict:
+        """p50 / p99 seconds of the queue wait, the batch GPU time and the rest
+        for the lookups completed since the last call (mphf_server_latency_parts)."""
+        p50 = (ctypes.c_double * 3)()
+        p99 = (ctypes.c_double * 3)()
+        _check(lib().mphf_server_latency_parts(self._p, p50, p99), "mphf_server_latency_parts")
+        names = ("queue", "gpu", "rest")
+        return {n: {"p50": p50[i], "p99": p99[i]} for i, n in enumerate(names)}
 
 
 def ceiling(kind: str, buf, n_ops: int, seed: int = 1, width: int = 32, stream=None) -> tuple:
