@@ -381,8 +381,10 @@ int mphf_lookup_multi(mphf_t *const *hs, const uint64_t *const *d_keys, uint64_t
  * requests) is answered by one mphf_lookup_multi-style launch; requests that
  * arrive meanwhile join the next launch.  Build requests run on
  * `build_workers` worker threads, each with its own stream, admitted once
- * their memory footprint fits the free device memory minus
- * mem_reserve_bytes.  Handles passed to lookups must stay alive until their
+ * their memory footprint plus that of the builds already running fits the
+ * free device memory minus mem_reserve_bytes (free memory as sampled when
+ * the server was made and after every build: the loop that launches lookups
+ * never waits on a device query).  Handles passed to lookups must stay alive until their
  * requests complete; keys and outputs are device arrays owned by the caller.
  */
 int mphf_server_create(uint64_t max_batch_keys, uint32_t max_batch_reqs, int max_inflight,

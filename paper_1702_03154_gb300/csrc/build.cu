@@ -384,25 +384,43 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
   __syncthreads();
   const u64 i0 = fstart[blockIdx.x];
   const u64 i1 = min(fend[blockIdx.x], fcap[blockIdx.x]);  // an overflowed range stops at its end
-  // pass 1: four positions per thread in flight
-  constexpr int kU = 4;
-  u64 i = i0 + threadIdx.x;
-  for (; i + (u64)(kU - 1) * kFineThreads < i1; i += (u64)kU * kFineThreads) {
-    unsigned q[kU];
-#pragma unroll
-    for (int u = 0; u < kU; u++) q[u] = TP[i + (u64)u * kFineThreads];  // < np
-#pragma unroll
-    for (int u = 0; u < kU; u++) {
-      const unsigned bit = 1u << (q[u] & 31);
-      const unsigned old = atomicOr(hit + (q[u] >> 5), bit);
-      if (old & bit) atomicOr(col + (q[u] >> 5), bit);
-    }
-  }
-  for (; i < i1; i += kFineThreads) {
-    const unsigned q = TP[i];
+  // [ia, ib): the 16-byte aligned part of the range, read four positions at a
+  // time; the at most 3 + 3 entries around it are read one by one
+  const u64 ia = min((i0 + 3) & ~3ull, i1);
+  const u64 ib = max(ia, i1 & ~3ull);
+  auto fill_one = [&](unsigned q) {
     const unsigned bit = 1u << (q & 31);
     const unsigned old = atomicOr(hit + (q >> 5), bit);
     if (old & bit) atomicOr(col + (q >> 5), bit);
+  };
+  // pass 1: ArrayFill, four 16-byte position loads per thread in flight
+  {
+    const uint4 *TP4 = reinterpret_cast<const uint4 *>(TP);
+    const u64 va = ia >> 2, vb = ib >> 2;
+    constexpr int kU = 4;
+    u64 v = va + threadIdx.x;
+    for (; v + (u64)(kU - 1) * kFineThreads < vb; v += (u64)kU * kFineThreads) {
+      uint4 q[kU];
+#pragma unroll
+      for (int u = 0; u < kU; u++) q[u] = TP4[v + (u64)u * kFineThreads];
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        fill_one(q[u].x);
+        fill_one(q[u].y);
+        fill_one(q[u].z);
+        fill_one(q[u].w);
+      }
+    }
+    for (; v < vb; v += kFineThreads) {
+      const uint4 q = TP4[v];
+      fill_one(q.x);
+      fill_one(q.y);
+      fill_one(q.z);
+      fill_one(q.w);
+    }
+    const u64 e = threadIdx.x < ia - i0 ? i0 + threadIdx.x
+                  : (threadIdx.x < (ia - i0) + (i1 - ib) ? ib + (threadIdx.x - (ia - i0)) : i1);
+    if (e < i1) fill_one(TP[e]);
   }
   __syncthreads();
   u64 wsum = 0;
@@ -420,7 +438,9 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     for (int w = 0; w < kFineThreads / 32; w++) t += red[w];
     if (t) atomicAdd(weight, t);
   }
-  // pass 2: a warp takes 32 consecutive entries at a time
+  // pass 2: compaction; a warp step takes kC chunks of 128 entries, each lane
+  // four consecutive entries of a chunk (one 16-byte position load, the
+  // survivors' keys in 16-byte pairs)
   const unsigned lt = (1u << lane) - 1u;
   unsigned cnt = 0;
   auto flush = [&]() {
@@ -434,30 +454,54 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     __syncwarp();
     cnt = 0;
   };
-  // kC chunks of 32 entries per warp step: their position loads, then their
-  // survivors' key loads, are all in flight together
-  constexpr int kC = 4;
-  for (u64 e = i0 + (u64)warp * 32; e < i1; e += (u64)kC * kFineThreads) {
-    unsigned q[kC];
-    bool keep[kC];
-    u64 x[kC];
+  auto kept = [&](unsigned q) { return !(((hit[q >> 5] & ~col[q >> 5]) >> (q & 31)) & 1u); };
+  auto put = [&](bool keep, u64 x) {
+    const unsigned bb = __ballot_sync(0xffffffffu, keep);
+    if (keep) stage[cnt + __popc(bb & lt)] = x;
+    cnt += __popc(bb);
+    if (cnt > (unsigned)(kFineStage - 32)) flush();
+  };
+  {
+    const uint4 *TP4 = reinterpret_cast<const uint4 *>(TP);
+    const uint4 *T4 = reinterpret_cast<const uint4 *>(T);  // T is 16-byte aligned like TP
+    const u64 va = ia >> 2, vb = ib >> 2;
+    constexpr int kC = 2;
+    for (u64 c0 = va + (u64)warp * 32; c0 < vb; c0 += (u64)kC * kFineThreads) {
+      uint4 q[kC];
+      bool ok[kC];
 #pragma unroll
-    for (int c = 0; c < kC; c++) {
-      const u64 k = e + (u64)c * kFineThreads + lane;
-      q[c] = k < i1 ? TP[k] : 0u;
+      for (int c = 0; c < kC; c++) {
+        const u64 v = c0 + (u64)c * kFineThreads + lane;
+        ok[c] = v < vb;
+        q[c] = ok[c] ? TP4[v] : make_uint4(0, 0, 0, 0);
+      }
+      bool k[kC][4];
+      uint4 x01[kC], x23[kC];
+#pragma unroll
+      for (int c = 0; c < kC; c++) {
+        const u64 v = c0 + (u64)c * kFineThreads + lane;
+        k[c][0] = ok[c] && kept(q[c].x);
+        k[c][1] = ok[c] && kept(q[c].y);
+        k[c][2] = ok[c] && kept(q[c].z);
+        k[c][3] = ok[c] && kept(q[c].w);
+        // keys 4v .. 4v+3 are T4[2v], T4[2v + 1]; only pairs with a survivor are read
+        x01[c] = (k[c][0] || k[c][1]) ? __ldcs(T4 + 2 * v) : make_uint4(0, 0, 0, 0);
+        x23[c] = (k[c][2] || k[c][3]) ? __ldcs(T4 + 2 * v + 1) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int c = 0; c < kC; c++) {
+        put(k[c][0], ((u64)x01[c].y << 32) | x01[c].x);
+        put(k[c][1], ((u64)x01[c].w << 32) | x01[c].z);
+        put(k[c][2], ((u64)x23[c].y << 32) | x23[c].x);
+        put(k[c][3], ((u64)x23[c].w << 32) | x23[c].z);
+      }
     }
-#pragma unroll
-    for (int c = 0; c < kC; c++) {
-      const u64 k = e + (u64)c * kFineThreads + lane;
-      keep[c] = k < i1 && !(((hit[q[c] >> 5] & ~col[q[c] >> 5]) >> (q[c] & 31)) & 1u);
-      x[c] = keep[c] ? __ldcs(T + k) : 0;  // only the survivors' keys are read
-    }
-#pragma unroll
-    for (int c = 0; c < kC; c++) {
-      const unsigned bb = __ballot_sync(0xffffffffu, keep[c]);
-      if (keep[c]) stage[cnt + __popc(bb & lt)] = x[c];
-      cnt += __popc(bb);
-      if (cnt > (unsigned)(kFineStage - 32)) flush();
+    // the entries around the aligned part (at most 6): warp 0, one per lane
+    if (warp == 0) {
+      const u64 nh = ia - i0, nt = i1 - ib;
+      const u64 e = lane < nh ? i0 + lane : (lane < nh + nt ? ib + (lane - nh) : i1);
+      const bool keep = e < i1 && kept(TP[e]);
+      put(keep, keep ? T[e] : 0);
     }
   }
   flush();

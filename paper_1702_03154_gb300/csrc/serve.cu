@@ -6,7 +6,8 @@
 // launch slot is free (continuous batching: requests that arrive while other
 // batches run join the next batch, up to kMaxInflight batches on two
 // alternating lookup streams).  Build requests are admitted when their memory
-// footprint fits the free device memory minus a reserve, and run on their own
+// footprint fits the free device memory (sampled by the build workers, not by
+// the scheduler) minus a reserve, and run on their own
 // streams in worker threads, so they overlap the lookups.  Completion times
 // are taken when the scheduler sees a batch's event complete; latency is
 // submit -> completion on the host clock.
@@ -385,6 +386,10 @@ struct mphf_server {
   std::vector<bbh::DevBuf> dtab;           // request tables, one per launch slot
   std::vector<bbh::ReqDev *> htab;         // pinned staging
   std::vector<bool> slot_busy;
+  std::vector<cudaEvent_t> slot_ev0, slot_ev;  // timing events of each launch slot, made once
+  // free device memory, sampled by the build workers (never by the scheduler,
+  // whose loop must not wait on a device query)
+  std::atomic<uint64_t> free_mem{0};
   std::deque<bbh::Batch> inflight;
   // statistics
   std::atomic<uint64_t> batches{0}, batched_reqs{0}, batched_keys{0}, builds_done{0};
@@ -430,8 +435,6 @@ static void scheduler(mphf_server *sv) {
         }
       }
       sv->cv_done.notify_all();
-      cudaEventDestroy(b.ev);
-      cudaEventDestroy(b.ev0);
       sv->slot_busy[b.slot] = false;
       sv->inflight.pop_front();
       worked = true;
@@ -466,8 +469,8 @@ static void scheduler(mphf_server *sv) {
         Batch b;
         b.reqs = take;
         b.slot = slot;
-        cudaEventCreate(&b.ev0);
-        cudaEventCreate(&b.ev);
+        b.ev0 = sv->slot_ev0[slot];
+        b.ev = sv->slot_ev[slot];
         const double tl = now_s();
         for (Req *r : take) r->t_launch = tl;
         cudaEventRecord(b.ev0, s);
@@ -483,16 +486,16 @@ static void scheduler(mphf_server *sv) {
         worked = true;
       }
     }
-    // 3. build admission by free device memory
+    // 3. build admission by free device memory (as last sampled: at start
+    // and after every build)
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       while (!sv->pending_builds.empty()) {
         Req *r = sv->pending_builds.front();
-        size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
+        const u64 free_b = sv->free_mem.load();
         const u64 need = build_footprint(r->n, r->gamma);
         const u64 held = sv->build_reserved.load();
-        if ((u64)free_b < held + need + sv->mem_reserve) break;  // wait for memory
+        if (free_b < held + need + sv->mem_reserve) break;  // wait for memory
         sv->build_reserved += need;
         sv->pending_builds.pop_front();
         sv->build_queue.push_back(r);
@@ -524,6 +527,11 @@ static void build_worker(mphf_server *sv) {
     mphf_t *h = nullptr;
     int rc = mphf_build((const uint64_t *)r->keys, r->n, r->gamma, r->L, r->seed, s, &h);
     const double t = now_s();
+    {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) sv->free_mem.store(free_b);
+      else cudaGetLastError();
+    }
     sv->build_reserved -= build_footprint(r->n, r->gamma);
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -570,6 +578,17 @@ int mphf_server_create(uint64_t max_batch_keys, uint32_t max_batch_reqs, int max
   sv->dtab.resize(max_inflight);
   sv->htab.resize(max_inflight, nullptr);
   sv->slot_busy.assign(max_inflight, false);
+  sv->slot_ev0.assign(max_inflight, nullptr);
+  sv->slot_ev.assign(max_inflight, nullptr);
+  for (int i = 0; i < max_inflight && rc == MPHF_OK; i++)
+    if (cudaEventCreate(&sv->slot_ev0[i]) != cudaSuccess ||
+        cudaEventCreate(&sv->slot_ev[i]) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "server events");
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) sv->free_mem.store(free_b);
+    else cudaGetLastError();
+  }
   for (int i = 0; i < max_inflight && rc == MPHF_OK; i++) {
     if (cudaMalloc(&sv->dtab[i].p, sizeof(ReqDev) * max_batch_reqs) != cudaSuccess ||
         cudaMallocHost((void **)&sv->htab[i], sizeof(ReqDev) * max_batch_reqs) != cudaSuccess)
@@ -592,10 +611,11 @@ void mphf_server_destroy(mphf_server_t *sv) {
   if (sv->sched.joinable()) sv->sched.join();
   for (auto &t : sv->workers)
     if (t.joinable()) t.join();
-  for (auto &b : sv->inflight) {
-    cudaEventSynchronize(b.ev);
-    cudaEventDestroy(b.ev);
-  }
+  for (auto &b : sv->inflight) cudaEventSynchronize(b.ev);
+  for (auto e : sv->slot_ev0)
+    if (e) cudaEventDestroy(e);
+  for (auto e : sv->slot_ev)
+    if (e) cudaEventDestroy(e);
   for (auto &kv : sv->reqs) {  // requests never waited for: their builds are released
     if (kv.second->built) mphf_free(kv.second->built);
     delete kv.second;
