@@ -816,6 +816,11 @@ def run_serving(args, stream):
     srv = mphf.Server(max_batch_keys=1 << 22, max_batch_reqs=4096, max_inflight=3,
                       build_workers=1, mem_reserve=8 << 30)
     ring_out = torch.empty(1 << 24, dtype=torch.int64, device="cuda")
+    # warm-up (not reported): first-use work of the server and of the build
+    # path (lookup descriptors, pool growth) stays out of the measured loads
+    srv.loadgen(hs, ks, rate_hz=0.5 / per_arrival, duration_s=min(1.0, args.serve_seconds),
+                bmin=1, bmax=1e6, out=ring_out, build_frac=0.01, build_keys=build_keys, nbmin=1e5,
+                nbmax=1e7, gamma=2.0, seed=7)
     for load in (0.5, 0.9):
         rate = load / per_arrival
         r = srv.loadgen(hs, ks, rate_hz=rate, duration_s=args.serve_seconds, bmin=1, bmax=1e6,
