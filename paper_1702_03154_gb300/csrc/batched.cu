@@ -1121,7 +1121,11 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   unsigned gstat[4] = {0, 0, 0, 0};
   MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaMemcpyAsync(gstat, c.status, 16, cudaMemcpyDeviceToHost, st));
+  // the level histogram too, in the same round trip (read again below if
+  // levels had to be added)
+  MPHF_CUDA(cudaMemcpyAsync(hist, c.hist, sizeof(FLevel) * n_hist, cudaMemcpyDeviceToHost, st));
   MPHF_CUDA(cudaStreamSynchronize(st));
+  bool extended = false;
   // sets whose loop did not finish within D levels (prediction short): run the
   // remaining levels unrecorded
   for (int extra = 0; extra < 64; extra++) {
@@ -1154,11 +1158,14 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     MPHF_CUDA(cudaMemcpyAsync(rs, c.sets, sizeof(BSet) * S, cudaMemcpyDeviceToHost, st));
     MPHF_CUDA(cudaStreamSynchronize(st));
     gc.D = -1;  // the recorded graph no longer matches this build
+    extended = true;
   }
   for (unsigned s = 0; s < S; s++)
     if (rs[s].status & ST_DUPLICATE) return MPHF_EDUPLICATE;
-  MPHF_CUDA(cudaMemcpyAsync(hist, c.hist, sizeof(FLevel) * n_hist, cudaMemcpyDeviceToHost, st));
-  MPHF_CUDA(cudaStreamSynchronize(st));
+  if (extended) {
+    MPHF_CUDA(cudaMemcpyAsync(hist, c.hist, sizeof(FLevel) * n_hist, cudaMemcpyDeviceToHost, st));
+    MPHF_CUDA(cudaStreamSynchronize(st));
+  }
   // ---- output layout
   std::vector<BOut> bo(S);
   std::vector<char> okset(S, 0);
