@@ -384,32 +384,74 @@ def kernel_table(h, prof, steps, n_queries):
 
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of
-# work for kernels captured with the commands listed in profiles/, keyed by
-# the kernel's name and the SHA-1 of the source file that holds it: when that
-# file changes the counters no longer describe the kernel and traffic is null.
-NCU_TRAFFIC = {}
+# work, from the captures summarised in profiles/ (traffic_n3e8_n3e7.md),
+# keyed by the kernel and, for the lookup, by where A lives (HBM or L2).
+# `src` lists the source files the kernel is built from and `sha` their SHA-1
+# at capture time: when any of them changes the counters no longer describe
+# the kernel and traffic is null.  Units: a "grouped key-visit" is one key of
+# a level grouped by slab (the unbucketed path's levels past 64 MiB of
+# hit/collision bits); a "query" one looked-up key; a "key" one key of F_0.
+_HDR = ["common.cuh", "fastbuild.cuh", "sector.cuh"]
+NCU_TRAFFIC = {
+    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "8ff0086b3b15", "unit": "grouped key-visit",
+                     "bytes_per_unit": 35.07,
+                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.07 GB "
+                             "over 1.2e9 grouped key-visits), scaled by grouped key-visits"},
+    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "8ff0086b3b15", "unit": "grouped key-visit",
+                  "bytes_per_unit": 19.09,
+                  "note": "3e8-key capture (20 launches of 4 builds, 22.91 GB over 1.2e9 "
+                          "grouped key-visits), scaled by grouped key-visits"},
+    "lookup@hbm": {"src": ["lookup.cu"] + _HDR, "sha": "7154cc30723b", "unit": "query",
+                   "bytes_per_unit": 106.4,
+                   "note": "3e8-key function (A 140 MB, above L2), 3e7 random member queries x 4 "
+                           "launches, 13.77 GB"},
+    "lookup@l2": {"src": ["lookup.cu"] + _HDR, "sha": "7154cc30723b", "unit": "query",
+                  "bytes_per_unit": 16.3,
+                  "note": "3e7-key function (A 14 MB, in L2), 3e7 random member queries x 2 "
+                          "launches, 0.978 GB"},
+    "partition": {"src": ["fastbuild.cu"] + _HDR, "sha": "a95370586c9d", "unit": "key",
+                  "bytes_per_unit": 18.2, "note": "3e7-key builds (3 launches, 1.639 GB)"},
+    "compact_buckets": {"src": ["fastbuild.cu"] + _HDR, "sha": "a95370586c9d", "unit": "key",
+                        "bytes_per_unit": 23.3,
+                        "note": "3e7-key builds (3 builds, 26 launches, 2.100 GB), per key of F_0"},
+}
+L2_BYTES = 126 << 20
 
 
-def traffic_for(name: str, units: float):
-    rec = NCU_TRAFFIC.get(name)
+def traffic_units(h, name: str, n_queries: int):
+    """(key into NCU_TRAFFIC, units one step's launches of `name` process)."""
+    if name == "lookup":
+        return ("lookup@hbm" if h.device_bytes() > L2_BYTES else "lookup@l2"), n_queries
+    if name in ("slab_scatter", "fine_fill"):
+        lv = h.levels()
+        return name, sum(n for (n, m, _, _) in lv if m // 4 > GROUP_MIN_AC_BYTES)
+    return name, h.level_sizes()[0]
+
+
+def traffic_for(h, name: str, n_queries: int, launches_per_step: float):
+    key, units = traffic_units(h, name, n_queries)
+    rec = NCU_TRAFFIC.get(key)
     if not rec:
         return None, "no ncu capture of this kernel"
-    src = os.path.join(ROOT, "paper_1702_03154_gb300", "csrc", rec["file"])
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    if sha != rec["sha"]:
-        return None, "kernel changed since its ncu capture"
-    return rec["bytes_per_unit"] * units, rec["note"]
+    hsh = hashlib.sha1()
+    for f in rec["src"]:
+        hsh.update(open(os.path.join(ROOT, "paper_1702_03154_gb300", "csrc", f), "rb").read())
+    if hsh.hexdigest()[:12] != rec["sha"]:
+        return None, "kernel source changed since its ncu capture"
+    per_launch = rec["bytes_per_unit"] * units / launches_per_step
+    return per_launch, (f"DRAM read+write per launch: {rec['bytes_per_unit']} B per "
+                        f"{rec['unit']} x {units:.4g} a step / {launches_per_step:g} launches; "
+                        f"{rec['note']}")
 
 
-def dominant_roofline(h, prof, steps, n_queries, unit_of, peak, peak_kind):
+def dominant_roofline(h, prof, steps, n_queries, peak, peak_kind):
     """roofline block of the kernel with the most time in the timed region."""
     if not prof:
         return None
     name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
     b = kernel_bytes(h, name, n_queries) * steps
     ach = b / (tot / 1e3) / 1e9 if tot else 0.0
-    units = unit_of(name) * steps / cnt
-    tr, tnote = traffic_for(name, units)
+    tr, tnote = traffic_for(h, name, n_queries, cnt / steps)
     return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
             "unit": "GB/s", "frac": round(ach / peak, 4),
             "traffic": round(tr, 1) if tr else None, "traffic_note": tnote,
@@ -473,15 +515,12 @@ def run_headline(args, stream, world, rank, local, barrier, ceil):
     sizes = last.level_sizes()
     probes = sum(last.level_sizes()[:last.num_levels]) * Q / N  # mean levels probed x Q
 
-    def units_of(name):          # keys (or queries) one step's launches of `name` process
-        return Q if name == "lookup" else N
-
     res = {"ms_max": ms_max, "ms": ms, "launches": launches, "clocks": clk,
            "build_ms": round(t_build, 3), "lookup_ms": round(t_look, 3),
            "build_mkeys_s": round(N / (t_build / 1e3) / 1e6, 1),
            "lookup_mkeys_s": round(Q / (t_look / 1e3) / 1e6, 1),
            "kernels": kernel_table(last, prof, args.steps, Q),
-           "roofline": dominant_roofline(last, prof, args.steps, Q, units_of, peak, peak_kind),
+           "roofline": dominant_roofline(last, prof, args.steps, Q, peak, peak_kind),
            "structure": {"levels": last.num_levels, "bits_per_key": round(last.bits_per_key(), 4),
                          "level_sizes": sizes[:8], "fallback": last.num_fallback,
                          "build_path": last.build_path,
@@ -616,7 +655,7 @@ def run_plain(args, stream, rank, ceil):
            "build_mkeys_s": round(N / (b_ms / 1e3) / 1e6, 1),
            "lookup_mkeys_s": round(N / (l_ms / 1e3) / 1e6, 1),
            "kernels": kernel_table(h, prof, reps, N),
-           "roofline": dominant_roofline(h, prof, reps, N, lambda name: N, peak, peak_kind),
+           "roofline": dominant_roofline(h, prof, reps, N, peak, peak_kind),
            "structure": {"levels": h.num_levels, "bits_per_key": round(h.bits_per_key(), 4),
                          "level_sizes": h.level_sizes()[:8], "fallback": h.num_fallback}}
     sb = build_stream_bytes(h)
