@@ -384,7 +384,8 @@ def kernel_table(h, prof, steps, n_queries):
 
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of
-# work, from the captures summarised in profiles/ (traffic_n3e8_n3e7.md),
+# work, from ncu captures of the kernels (their commands are kept with the
+# profile summaries),
 # keyed by the kernel and, for the lookup, by where A lives (HBM or L2).
 # `src` lists the source files the kernel is built from and `sha` their SHA-1
 # at capture time: when any of them changes the counters no longer describe
@@ -585,9 +586,12 @@ def e2e_headline(args, res, world, barrier):
                                            seed=0)
         h.free()
 
+    warm = []
     for _ in range(2):   # warm-up: the first calls also fill the allocation pool
+        t0 = time.perf_counter()
         one_call()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        warm.append((time.perf_counter() - t0) * 1e3)
     barrier()
     reps = max(3, min(args.steps, 5))
     per_rep = []
@@ -602,6 +606,7 @@ def e2e_headline(args, res, world, barrier):
     return {"value": job_value(N, world, e_max), "unit": UNIT,
             "h2d_bytes_per_step": 8 * N + 8 * Q, "d2h_bytes_per_step": 8 * Q,
             "ms_per_step": e_max, "reps": reps, "statistic": "median of the reps (wall clock)",
+            "rep_ms": [round(x, 1) for x in per_rep], "warmup_ms": [round(x, 1) for x in warm],
             "api": "mphf_build_lookup_host (queries copied while the levels are built), "
                    "pinned host buffers", "pin_and_fill_s": round(t_pin, 2)}
 

@@ -466,7 +466,12 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     const uint4 *T4 = reinterpret_cast<const uint4 *>(T);  // T is 16-byte aligned like TP
     const u64 va = ia >> 2, vb = ib >> 2;
     constexpr int kC = 2;
-    for (u64 c0 = va + (u64)warp * 32; c0 < vb; c0 += (u64)kC * kFineThreads) {
+    // last steps first: the positions pass 1 read last are the likeliest to
+    // still be in L2
+    constexpr u64 kStep = (u64)kC * kFineThreads;
+    const u64 nsteps = (vb - va + kStep - 1) / kStep;
+    for (u64 st = nsteps; st-- > 0;) {
+      const u64 c0 = va + st * kStep + (u64)warp * 32;
       uint4 q[kC];
       bool ok[kC];
 #pragma unroll
