@@ -903,6 +903,8 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    from paper_1702_03154_gb300 import mphf
+
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -926,6 +928,7 @@ def run_ours(args):
     last.free()
     del last
     torch.cuda.empty_cache()
+    mphf.pool_trim()  # the 1e10 scratch cached by the library, back for the blocks below
 
     plain = None if args.no_plain else run_plain(args, stream, rank, ceil)
     batched = None if args.no_batched else run_batched(args, stream)

@@ -490,13 +490,12 @@ int mphf_keygen(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void
 /* ---- device memory -------------------------------------------------------- */
 /*
  * Scratch and handle memory come from the current device's default
- * stream-ordered memory pool.  Freed blocks stay in the pool, for the next
- * build, up to the most memory the library has held at once on that device
- * (at least 16 GiB): repeated builds over 1e10 keys reuse their ~120 GB of
- * scratch instead of mapping it again each time.  Memory cached this way is
- * not available to other allocators of the process (torch's, cudaMalloc);
- * mphf_pool_trim waits for the device, returns every unused block of the pool
- * to the driver and sets the limit back to 16 GiB.
+ * stream-ordered memory pool, which keeps the blocks it has mapped (the
+ * library sets its release threshold to unlimited): repeated builds over 1e10
+ * keys reuse their ~125 GB of scratch instead of mapping it again each time.
+ * Memory cached this way is not available to other allocators of the process
+ * (torch's, cudaMalloc); mphf_pool_trim waits for the device and returns every
+ * unused block of the pool to the driver.
  */
 int mphf_pool_trim(void);
 

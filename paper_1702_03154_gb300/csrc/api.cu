@@ -73,15 +73,15 @@ void launch_end(cudaStream_t s) {
   t_open = -1;
 }
 
-// Device memory comes from the device's default stream-ordered pool.  Freed
-// blocks stay in the pool for the next build as long as the pool's unused
-// memory is below its release threshold; the threshold follows the most
-// memory this library has held at once (at least 16 GiB), so a build that
-// needs 120 GB of scratch (1e10 keys) finds it again on its next call instead
-// of mapping it from the driver anew.  mphf_pool_trim returns the unused part.
-static constexpr u64 kPoolMinKeep = 16ull << 30;
-static std::atomic<long long> g_in_use[64];  // bytes held through dev_alloc
-static std::atomic<u64> g_keep[64];
+// Device memory comes from the device's default stream-ordered pool, which
+// keeps every block it has mapped once the library has used it (release
+// threshold: unlimited), so a build that needs 120 GB of scratch (1e10 keys)
+// finds it again on its next call instead of mapping it from the driver anew.
+// A threshold at the most memory held at once is not enough: the cached
+// blocks of one workload do not match the sizes another asks for, the pool
+// then holds more than that peak and releases (and re-maps) tens of GB at
+// every synchronisation.  mphf_pool_trim returns the unused part.
+static std::atomic<int> g_pool_set[64];
 
 static void pool_keep(int dev, u64 bytes) {
   cudaMemPool_t pool;
@@ -98,9 +98,9 @@ int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
   b.bytes = bytes;
   if (bytes == 0) return MPHF_OK;
   const int dev = cur_device();
-  if (g_keep[dev].load() == 0) {
-    u64 z = 0;
-    if (g_keep[dev].compare_exchange_strong(z, kPoolMinKeep)) pool_keep(dev, kPoolMinKeep);
+  if (g_pool_set[dev].load() == 0) {
+    int z = 0;
+    if (g_pool_set[dev].compare_exchange_strong(z, 1)) pool_keep(dev, ~0ull);
   }
   cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
   if (e != cudaSuccess) {
@@ -110,23 +110,11 @@ int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
     set_cuda_error(e, "cudaMallocAsync");
     return MPHF_ENOMEM;
   }
-  const long long used_s = g_in_use[dev].fetch_add((long long)bytes) + (long long)bytes;
-  const u64 used = used_s > 0 ? (u64)used_s : 0;
-  u64 keep = g_keep[dev].load();
-  while (used > keep) {
-    if (g_keep[dev].compare_exchange_weak(keep, used)) {
-      pool_keep(dev, used);
-      break;
-    }
-  }
   return MPHF_OK;
 }
 
 void dev_free(DevBuf &b, cudaStream_t s) {
-  if (b.p) {
-    cudaFreeAsync(b.p, s);
-    g_in_use[cur_device()].fetch_sub((long long)b.bytes);
-  }
+  if (b.p) cudaFreeAsync(b.p, s);
   b.p = nullptr;
   b.bytes = 0;
 }
@@ -139,8 +127,6 @@ extern "C" int mphf_pool_trim(void) {
   cudaMemPool_t pool;
   MPHF_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
   MPHF_CUDA(cudaDeviceSynchronize());
-  g_keep[dev].store(kPoolMinKeep);
-  pool_keep(dev, kPoolMinKeep);
   MPHF_CUDA(cudaMemPoolTrimTo(pool, 0));
   return MPHF_OK;
 }

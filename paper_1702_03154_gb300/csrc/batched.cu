@@ -1242,8 +1242,12 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     for (unsigned s = 0; s < S; s++)
       if (okset[s] && rs[s].n0 && totals[s] != rs[s].n0 - bo[s].n_fb) okset[s] = 0;
   }
-  // ---- handles
+  // ---- handles (the device and the level seeds are the same for every set)
   int live = 0;
+  int device = 0;
+  cudaGetDevice(&device);
+  u64 seeds[MPHF_MAX_LEVELS];
+  for (uint32_t d = 0; d < L; d++) seeds[d] = level_seed(seed, d);
   for (unsigned s = 0; s < S; s++) {
     if (!okset[s]) continue;
     mphf_t *h = new (std::nothrow) mphf_t();
@@ -1251,13 +1255,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       rc = MPHF_ENOMEM;
       break;
     }
-    cudaGetDevice(&h->device);
+    h->device = device;
     const BSet &b = rs[s];
     h->N = b.n0;
     h->gamma = gamma;
     h->L = L;
     h->seed = seed;
-    for (uint32_t d = 0; d < L; d++) h->s[d] = level_seed(seed, d);
+    memcpy(h->s, seeds, L * sizeof(u64));
     h->path = 3;
     if (b.n0) {
       const FLevel *hl = &hist[(u64)s * (L + 1)];
