@@ -394,13 +394,13 @@ def kernel_table(h, prof, steps, n_queries):
 # hit/collision bits); a "query" one looked-up key; a "key" one key of F_0.
 _HDR = ["common.cuh", "fastbuild.cuh", "sector.cuh"]
 NCU_TRAFFIC = {
-    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "8ff0086b3b15", "unit": "grouped key-visit",
-                     "bytes_per_unit": 35.07,
-                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.07 GB "
+    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "a9bb7191c25d", "unit": "grouped key-visit",
+                     "bytes_per_unit": 35.05,
+                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.06 GB "
                              "over 1.2e9 grouped key-visits), scaled by grouped key-visits"},
-    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "8ff0086b3b15", "unit": "grouped key-visit",
-                  "bytes_per_unit": 19.09,
-                  "note": "3e8-key capture (20 launches of 4 builds, 22.91 GB over 1.2e9 "
+    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "a9bb7191c25d", "unit": "grouped key-visit",
+                  "bytes_per_unit": 17.74,
+                  "note": "3e8-key capture (20 launches of 4 builds, 21.28 GB over 1.2e9 "
                           "grouped key-visits), scaled by grouped key-visits"},
     "lookup@hbm": {"src": ["lookup.cu"] + _HDR, "sha": "7154cc30723b", "unit": "query",
                    "bytes_per_unit": 106.4,
