@@ -328,9 +328,22 @@ def measure_ceilings():
                      "ms": round(ms, 4), "array_bytes": buf.numel() * 8,
                      "gbs_accessed": round(done * (width if kind == "loads" else 8)
                                            / (ms / 1e3) / 1e9, 1)}
-    del l2buf, hbm
+    # streaming copy HBM -> HBM over 2 x 8 GB (read + write bytes counted)
+    dst = torch.empty_like(hbm)
+    ts = []
+    for i in range(4):
+        ms = mphf.ceiling_copy(hbm, dst)
+        if i:
+            ts.append(ms)
+    ms = float(np.median(ts))
+    out["hbm_copy"] = {"gbs": round(2 * hbm.numel() * 8 / (ms / 1e3) / 1e9, 1),
+                       "ms": round(ms, 4), "array_bytes": hbm.numel() * 8,
+                       "note": "cross-check of the roofline peak, which is MEASURED_PEAKS.json's "
+                               "hbm_gbs"}
+    del l2buf, hbm, dst
     torch.cuda.empty_cache()
-    out["source"] = "measured in this run (mphf_ceiling_random_loads / _atomics, CUDA events)"
+    out["source"] = ("measured in this run (mphf_ceiling_random_loads / _atomics / _copy, "
+                     "CUDA events)")
     return out
 
 

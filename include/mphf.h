@@ -538,6 +538,10 @@ int mphf_ceiling_random_loads(const void *d_buf, uint64_t bytes, uint32_t width,
 int mphf_ceiling_random_atomics(uint64_t *d_buf, uint64_t words, int with_return, uint64_t n_ops,
                                 uint64_t seed, uint64_t *d_sink, uint64_t *performed,
                                 void *stream);
+/* Streaming copy of `bytes` (a multiple of 16, both arrays 16-byte aligned)
+ * from d_src to d_dst: the HBM bandwidth a kernel streaming its keys reaches
+ * (read + write bytes over the launch's time).  One launch on `stream`. */
+int mphf_ceiling_copy(const void *d_src, void *d_dst, uint64_t bytes, void *stream);
 
 #ifdef __cplusplus
 }

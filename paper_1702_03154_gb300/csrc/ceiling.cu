@@ -78,9 +78,40 @@ k_ceiling_atomics(u64 *__restrict__ buf, unsigned words, u64 rounds, u64 seed,
   if (RET && acc == 0x9E3779B97F4A7C15ull) sink[tid & 1023] = acc;
 }
 
+// Streaming copy, 16 bytes a thread per step, four steps in flight: the
+// HBM bandwidth that a kernel streaming its keys can reach.
+__global__ void __launch_bounds__(kCeilThreads)
+k_ceiling_copy(const uint4 *__restrict__ src, uint4 *__restrict__ dst, u64 n16) {
+  const u64 stride = (u64)gridDim.x * kCeilThreads;
+  u64 i = (u64)blockIdx.x * kCeilThreads + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = __ldcs(src + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; u++) __stcs(dst + i + u * stride, v[u]);
+  }
+  for (; i < n16; i += stride) __stcs(dst + i, __ldcs(src + i));
+}
+
 }  // namespace bbh
 
 using namespace bbh;
+
+extern "C" int mphf_ceiling_copy(const void *d_src, void *d_dst, uint64_t bytes, void *stream) {
+  if (!d_src || !d_dst || ((uintptr_t)d_src & 15) || ((uintptr_t)d_dst & 15) || (bytes & 15))
+    return MPHF_EINVAL;
+  const u64 n16 = bytes / 16;
+  if (n16 == 0) return MPHF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    LaunchScope ls("ceiling_copy", s);
+    k_ceiling_copy<<<(unsigned)sm_count() * 8, kCeilThreads, 0, s>>>((const uint4 *)d_src,
+                                                                      (uint4 *)d_dst, n16);
+  }
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
 
 // Grid for a ceiling launch: `ops` accesses spread over whole rounds of
 // kCeilUnroll per thread, 8 CTAs per SM (enough warps to cover latency).

@@ -113,6 +113,7 @@ def lib():
         "mphf_deserialize": ([vp, u64, vp, pvp], i32),
         "mphf_ceiling_random_loads": ([vp, u64, u32, u64, u64, vp, vp, vp], i32),
         "mphf_ceiling_random_atomics": ([vp, u64, i32, u64, u64, vp, vp, vp], i32),
+        "mphf_ceiling_copy": ([vp, vp, u64, vp], i32),
         "mphf_route": ([vp, u64, u32, u64, vp, vp, vp, vp], i32),
         "mphf_unroute": ([vp, vp, u64, vp, vp], i32),
         "mphf_add_offset": ([vp, u64, u64, vp], i32),
@@ -765,6 +766,21 @@ class PartitionedMPHF:
 def pool_trim() -> None:
     """Return the library's unused cached device memory to the driver."""
     _check(lib().mphf_pool_trim(), "mphf_pool_trim")
+
+
+def ceiling_copy(src, dst, stream=None) -> float:
+    """One streaming-copy launch src -> dst (device tensors of equal bytes);
+    returns its event-timed milliseconds."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    nb = src.numel() * src.element_size()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rc = lib().mphf_ceiling_copy(src.data_ptr(), dst.data_ptr(), nb, _stream_ptr(st))
+    e1.record(st)
+    _check(rc, "mphf_ceiling_copy")
+    e1.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def launch_count() -> int:
