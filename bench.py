@@ -791,6 +791,14 @@ def run_batched(args, stream):
     paths = {}
     for h in hs:
         paths[h.build_path] = paths.get(h.build_path, 0) + 1
+    # the method's streamed bytes of all sets (the same model as the plain
+    # build's build_roofline) over the batched build's time
+    peak, peak_kind = measured_peaks()
+    sb = sum(build_stream_bytes(h) for h in hs if h.N)
+    roof = {"bound": "hbm", "algorithmic_bytes": sb,
+            "achieved": round(sb / (t_b / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(sb / (t_b / 1e3) / 1e9 / peak, 4),
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json), of measured"}
     res = {"sets": S, "keys": total, "gamma": 2.0, "levels": 25,
            "batched_build_ms": round(t_b, 3), "batched_build_mkeys_s": round(total / t_b / 1e3, 1),
            "batched_build_api": "mphf_build_batched_host_offsets (C ABI), CUDA events around the call",
@@ -800,7 +808,7 @@ def run_batched(args, stream):
            "lookup_all_ms": round(t_l, 3), "lookup_mkeys_s": round(total / t_l / 1e3, 1),
            "autotune_best_ms": round(tune_ms, 3),
            "autotune_choice": mphf.batched_tuning(S, total),
-           "kernels_per_batched_build": int(launches),
+           "kernels_per_batched_build": int(launches), "build_roofline": roof,
            "handles_by_path": {str(k): v for k, v in sorted(paths.items())}}
     del hs, keys, out
     torch.cuda.empty_cache()
