@@ -8,6 +8,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -111,6 +112,46 @@ int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
     return MPHF_ENOMEM;
   }
   return MPHF_OK;
+}
+
+static std::mutex g_handle_mu;
+static const size_t kHandleFreeMax = 1u << 16;
+static mphf *g_handle_free[kHandleFreeMax];
+static size_t g_handle_nfree = 0;
+
+mphf *handle_new() {
+  mphf *h = nullptr;
+  if (!handle_new_n(1, &h)) return nullptr;
+  return h;
+}
+
+bool handle_new_n(unsigned n, mphf **out) {
+  unsigned got = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_handle_mu);
+    while (got < n && g_handle_nfree) out[got++] = g_handle_free[--g_handle_nfree];
+  }
+  for (unsigned i = 0; i < got; i++) new (out[i]) mphf();
+  for (; got < n; got++) {
+    out[got] = new (std::nothrow) mphf();
+    if (!out[got]) {
+      for (unsigned i = 0; i < got; i++) handle_delete(out[i]);
+      return false;
+    }
+  }
+  return true;
+}
+
+void handle_delete(mphf *h) {
+  if (!h) return;
+  {
+    std::lock_guard<std::mutex> lk(g_handle_mu);
+    if (g_handle_nfree < kHandleFreeMax) {
+      g_handle_free[g_handle_nfree++] = h;
+      return;
+    }
+  }
+  delete h;
 }
 
 void dev_free(DevBuf &b, cudaStream_t s) {
@@ -241,7 +282,7 @@ void mphf_free(mphf_t *h) {
     dev_free(h->fb, 0);
   }
   if (prev != h->device) cudaSetDevice(prev);
-  delete h;
+  handle_delete(h);
 }
 
 // Sec. 3.1's size with one 64-bit counter per 512 bits of A, or per 1024

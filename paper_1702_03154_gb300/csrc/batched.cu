@@ -1248,13 +1248,21 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   cudaGetDevice(&device);
   u64 seeds[MPHF_MAX_LEVELS];
   for (uint32_t d = 0; d < L; d++) seeds[d] = level_seed(seed, d);
+  std::vector<mphf_t *> recs;
+  {
+    unsigned n_ok = 0;
+    for (unsigned s = 0; s < S; s++) n_ok += okset[s] ? 1 : 0;
+    recs.resize(n_ok);
+    if (n_ok && !handle_new_n(n_ok, recs.data())) {
+      rc = MPHF_ENOMEM;
+      recs.clear();
+      for (unsigned s = 0; s < S; s++) okset[s] = 0;
+    }
+  }
+  unsigned next_rec = 0;
   for (unsigned s = 0; s < S; s++) {
     if (!okset[s]) continue;
-    mphf_t *h = new (std::nothrow) mphf_t();
-    if (!h) {
-      rc = MPHF_ENOMEM;
-      break;
-    }
+    mphf_t *h = recs[next_rec++];
     h->device = device;
     const BSet &b = rs[s];
     h->N = b.n0;

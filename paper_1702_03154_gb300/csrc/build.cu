@@ -788,7 +788,7 @@ static void release_handle(mphf_t *h, cudaStream_t s) {
   dev_free(h->S, s);
   dev_free(h->SB, s);
   dev_free(h->fb, s);
-  delete h;
+  handle_delete(h);
 }
 
 static int launch_fill0(const u64 *keys, u64 n, u64 s0, u64 m0, u64 *AC, cudaStream_t st) {
@@ -1104,7 +1104,7 @@ int g_build_path = 0;  // 0: bucketed, unbucketed on overflow; 1: unbucketed onl
 // consumes them chunk by chunk, every other step waits for all of them.
 static int build_impl(const u64 *keys, u64 N, double gamma, uint32_t L, u64 seed, cudaStream_t st,
                       mphf_t **out, KeyFeed *feed = nullptr) {
-  mphf_t *h = new (std::nothrow) mphf_t();
+  mphf_t *h = handle_new();
   if (!h) return MPHF_ENOMEM;
   cudaGetDevice(&h->device);
   h->N = N;

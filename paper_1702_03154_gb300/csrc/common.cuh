@@ -250,4 +250,13 @@ inline bool narrow_positions(const mphf *h) {
   for (uint32_t d = 0; d < h->L_used; d++) narrow = narrow && (h->m[d] >> 32) == 0;
   return narrow;
 }
+
+// Handle records come from a process-wide free list: a batched build makes
+// thousands at once, and fresh heap pages for them (each record is ~2 KB of
+// level tables) cost a page fault per page.  handle_new returns a zeroed
+// record or nullptr; handle_new_n fills out[0..n) under one lock (all or
+// none); handle_delete takes back a record whose device memory is released.
+mphf *handle_new();
+bool handle_new_n(unsigned n, mphf **out);
+void handle_delete(mphf *h);
 }  // namespace bbh

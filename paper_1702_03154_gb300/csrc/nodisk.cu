@@ -149,7 +149,7 @@ k_nd_collect(NdSrc src, const NdLevel *__restrict__ lvs, int hi, u64 *__restrict
 
 static int nd_build(NdSrc src0, u64 N, double gamma, uint32_t L, u64 seed, double keep,
                     cudaStream_t st, mphf_t **out) {
-  mphf_t *h = new (std::nothrow) mphf_t();
+  mphf_t *h = handle_new();
   if (!h) return MPHF_ENOMEM;
   cudaGetDevice(&h->device);
   h->N = N;
@@ -321,7 +321,7 @@ fail:
   dev_free(h->SB, st);
   dev_free(h->fb, st);
   cudaStreamSynchronize(st);
-  delete h;
+  handle_delete(h);
   return rc;
 #undef NTRY
 #undef NCUDA

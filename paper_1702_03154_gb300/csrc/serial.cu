@@ -156,7 +156,7 @@ extern "C" int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream,
     const uint64_t left = lv[3 * hd.L_used];
     if (left != hd.n_fb || (hd.n_fb && hd.L_used != hd.L)) return MPHF_EINVAL;
   }
-  mphf_t *h = new (std::nothrow) mphf_t();
+  mphf_t *h = handle_new();
   if (!h) return MPHF_ENOMEM;
   cudaGetDevice(&h->device);
   h->N = hd.N;
@@ -200,7 +200,7 @@ extern "C" int mphf_deserialize(const void *h_buf, uint64_t bytes, void *stream,
     dev_free(h->SB, st);
     dev_free(h->fb, st);
     cudaStreamSynchronize(st);
-    delete h;
+    handle_delete(h);
     return rc;
   }
   *out = h;
