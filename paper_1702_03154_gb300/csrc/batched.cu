@@ -207,8 +207,8 @@ k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
         }
       }
     }
-    multisplit_write<true, false>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
-                           PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], t_gb0}, c.status);
+    multisplit_write<true>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
+                     PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], t_gb0}, c.status);
   }
 }
 
@@ -482,10 +482,10 @@ __global__ void __launch_bounds__(kTT, 2) k_bcompact(int d, BCfg c) {
     }
     __syncthreads();  // the staging area is reused by the writer
     if (flat)
-      multisplit_write<false, false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
+      multisplit_write<false>(x, lp, dst, ok, 1u, sm, c.flat, nullptr,
                               SetFlatDest{&st->n_flat, st->flat_off, st->flat_cap}, &st->status);
     else
-      multisplit_write<true, false>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
+      multisplit_write<true>(x, lp, dst, ok, (unsigned)nx.B, sm, c.X[nl], c.XP[nl],
                              SetBucketDest{c.cnt[nl], nx.bbase, nx.aoff, nx.cap}, &st->status);
   };
 

@@ -287,8 +287,9 @@ struct SlabDest {
 // current tile is split (each thread owns kKPT consecutive keys of a tile;
 // ALIGNED: the keys are 16-byte aligned, so they move in 16-byte copies).
 // WITH_POS: each key's position within its slab (below 2^20) goes to pout
-// beside it (the fine slabs' fill and compaction then need no hash).
-template <bool ALIGNED, bool WITH_POS>
+// beside it (the fine slabs' fill and compaction then need no hash).  ONE: at
+// most kTT slabs, one per thread in the multisplit.
+template <bool ALIGNED, bool WITH_POS, bool ONE>
 __global__ void __launch_bounds__(kTT, 2)
 k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
                unsigned nslab, u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
@@ -343,8 +344,12 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
       dst[k] = (unsigned)(r >> shift);
       lp[k] = WITH_POS ? (unsigned)r & ((1u << shift) - 1u) : 0u;
     }
-    multisplit_write<WITH_POS, false>(x, lp, dst, ok, nslab, sm, out, pout,
-                                      SlabDest{cursor, end}, status);
+    if (ONE)
+      multisplit_write_one<WITH_POS>(x, lp, dst, ok, nslab, sm, out, pout, SlabDest{cursor, end},
+                                     status);
+    else
+      multisplit_write<WITH_POS>(x, lp, dst, ok, nslab, sm, out, pout, SlabDest{cursor, end},
+                                 status);
   }
   cp_async_wait0();
 }
@@ -543,6 +548,17 @@ static unsigned slab_count_for(u64 m) {
   return ns <= kSlabMax ? (unsigned)ns : 0u;
 }
 
+using SlabScatterFn = void (*)(const u64 *, u64, u64, u64, u64, unsigned, unsigned, u64 *,
+                               const u64 *, u64 *, unsigned *, unsigned *);
+static SlabScatterFn slab_scatter_fn(bool al, bool pos, bool one) {
+  if (one) {
+    if (pos) return al ? k_slab_scatter<true, true, true> : k_slab_scatter<false, true, true>;
+    return al ? k_slab_scatter<true, false, true> : k_slab_scatter<false, false, true>;
+  }
+  if (pos) return al ? k_slab_scatter<true, true, false> : k_slab_scatter<false, true, false>;
+  return al ? k_slab_scatter<true, false, false> : k_slab_scatter<false, false, false>;
+}
+
 // out <- the n keys of F grouped by slab: position p of level (s, m) goes to
 // slab (p - base) >> shift, nslab slabs; se[i], se[nslab + i] receive slab i's
 // range of out.  slab: 4 * kSlabMax u64 of device scratch.
@@ -550,14 +566,9 @@ static int slab_attrs() {
   static bool attr = false;
   if (!attr) {
     const int sb = (int)(split_smem_bytes(kSlabMax) + kTile * 8);
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true, false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false, false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<true, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    MPHF_CUDA(cudaFuncSetAttribute(k_slab_scatter<false, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
+    for (int v = 0; v < 8; v++)
+      MPHF_CUDA(cudaFuncSetAttribute(slab_scatter_fn(v & 1, v & 2, v & 4),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
     MPHF_CUDA(cudaFuncSetAttribute(k_fine_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kFineSmem));
     attr = true;
@@ -574,21 +585,8 @@ static void launch_slab_scatter(const u64 *F, u64 n, u64 s, u64 m, u64 base, uns
   const unsigned g = grid_for(n, kTile, (unsigned)sm_count() * 2);
   const size_t sb = split_smem_bytes(nslab) + kTile * 8;
   const bool al = ((uintptr_t)F & 15) == 0;
-  if (pout) {
-    if (al)
-      k_slab_scatter<true, true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor, end,
-                                                     out, pout, status);
-    else
-      k_slab_scatter<false, true><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
-                                                      end, out, pout, status);
-  } else {
-    if (al)
-      k_slab_scatter<true, false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
-                                                      end, out, nullptr, status);
-    else
-      k_slab_scatter<false, false><<<g, kTT, sb, st>>>(F, n, s, m, base, shift, nslab, cursor,
-                                                       end, out, nullptr, status);
-  }
+  slab_scatter_fn(al, pout != nullptr, nslab <= (unsigned)kTT)<<<g, kTT, sb, st>>>(
+      F, n, s, m, base, shift, nslab, cursor, end, out, pout, status);
 }
 
 static int group_keys(const u64 *F, u64 n, u64 s, u64 m, u64 base, unsigned shift,

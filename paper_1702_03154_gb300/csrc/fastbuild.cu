@@ -92,7 +92,7 @@ k_partition0(const u64 *__restrict__ keys, u64 n, FastMeta *__restrict__ meta, F
       dst[k] = (unsigned)(p >> sh);
       lp[k] = (unsigned)p & mask;
     }
-    multisplit_write<true, true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
+    multisplit_write<true>(x, lp, dst, ok, nb, sm, cfg.X, cfg.XP, UniformDest{cfg.cntX, lv.cap},
                            &meta->status);
   }
   cp_async_wait0();
@@ -332,10 +332,10 @@ k_compact_buckets(FastMeta *__restrict__ meta, int d, FastCfg cfg) {
     }
     __syncthreads();  // the staging area is reused by the writer
     if (flat)
-      multisplit_write<false, true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+      multisplit_write<false>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                               &meta->status);
     else
-      multisplit_write<true, true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
+      multisplit_write<true>(x, lp, dst, ok, nb, sm, out, pout, UniformDest{ocnt, ocap},
                              &meta->status);
   };
 

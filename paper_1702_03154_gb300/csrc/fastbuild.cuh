@@ -181,9 +181,11 @@ __device__ __forceinline__ unsigned block_scan_u32_fenced(unsigned v, unsigned *
 
 // Shared memory of the multisplit writer.
 struct SplitSmem {
-  unsigned *cnt;         // [nb] entries per destination in this tile, then their local start
-  unsigned *lim;         // [nb] local index past which the destination bucket is full
-  u64 *dbase;            // [nb] arena index of local entry 0 of each destination
+  unsigned *cnt;         // [nb] entries per destination in this tile (zero between calls)
+  unsigned short *start; // [nb] multisplit_write_one: local index of each destination's
+                         // first entry; multisplit_write: its local limit
+  u64 *run;              // [nb] multisplit_write_one: (local limit << 44) | (arena index of
+                         // local entry 0, mod 2^44); multisplit_write: that arena index
   u64 *sorted;           // [kTile] keys in destination order (also the survivor staging area)
   unsigned *stag;        // [kTile] (destination << 20) | in-bucket position
   unsigned *red;         // [kTT / 32 + 2]
@@ -205,78 +207,160 @@ struct UniformDest {
   }
 };
 
+static constexpr unsigned kRunShift = 44;  // arena indices below 2^44
+static constexpr u64 kRunMask = (1ull << kRunShift) - 1;
+
 // Write the valid entries of a tile into their destination buckets: key to
 // arena[base_b + slot] and (WITH_POS) its in-bucket position lp (< 2^20) to
 // parena[base_b + slot], where dest(b) gives the bucket's counter, base and
 // capacity.  Slots are reserved with one atomicAdd per non-empty destination;
 // the entries of one destination leave as one contiguous run.  Entries past a
-// bucket's capacity are dropped and ST_OVERFLOW is raised.
-template <bool WITH_POS, bool GROUPED, class Dest>
-__device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
-                                 const unsigned (&dst)[kKPT], const bool (&ok)[kKPT], unsigned nb,
-                                 const SplitSmem &sm, u64 *__restrict__ arena,
-                                 unsigned *__restrict__ parena, const Dest &dest,
-                                 unsigned *__restrict__ status) {
-  // sm.cnt[0, nb) is zero on entry (split_clear before the first call; every
-  // call clears what it used while writing out, behind its last barrier)
+// bucket's capacity are dropped and ST_OVERFLOW is raised.  sm.cnt[0, nb) is
+// zero on entry and on return (split_clear before a kernel's first call).
+//
+// Up to kTT destinations (one per thread): four block barriers a call (after
+// the rank atomics, in the scan, before the scatter into destination order,
+// before the write-out), the reservation atomics in flight during the
+// scatter, and no barrier at the end: the owner zeroes a destination's count
+// as soon as the scan has read it, and the next call writes `start`,
+// `sorted`, `stag`, `run` and `red` only after barriers that every thread
+// reaches after its write-out.  A caller that itself writes `sorted` (a
+// survivor stage) right after the call puts a block barrier in between.
+template <bool WITH_POS, class Dest>
+__device__ __forceinline__ void multisplit_write_one(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
+                                                     const unsigned (&dst)[kKPT], const bool (&ok)[kKPT],
+                                                     unsigned nb, const SplitSmem &sm,
+                                                     u64 *__restrict__ arena,
+                                                     unsigned *__restrict__ parena, const Dest &dest,
+                                                     unsigned *__restrict__ status) {
+  const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned rk[kKPT], tag[kKPT];
+#pragma unroll
+  for (int k = 0; k < kKPT; k++) {
+    tag[k] = (dst[k] << 20) | lp[k];
+    rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
+  }
+  __syncthreads();
+  const unsigned i0 = threadIdx.x;  // the destination this thread owns
+  unsigned c = 0;
+  if (i0 < nb) {
+    c = sm.cnt[i0];
+    sm.cnt[i0] = 0;
+  }
+  // exclusive scan of the counts: each warp scans its own, lane 31 posts the
+  // warp's total, and every warp scans the posted totals itself
+  unsigned incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) sm.red[warp] = incl;
+  __syncthreads();
+  unsigned wv = lane < kTT / 32 ? sm.red[lane] : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, wv, o);
+    if (lane >= (unsigned)o) wv += y;
+  }
+  const unsigned wbefore = __shfl_sync(0xffffffffu, wv, (warp + 31) & 31);
+  const unsigned total = __shfl_sync(0xffffffffu, wv, kTT / 32 - 1);
+  const unsigned pre = (warp ? wbefore : 0u) + incl - c;
+  const u64 b0 = c ? atomicAdd(dest(i0).counter, (u64)c) : 0;  // waited for after the scatter
+  if (i0 < nb) sm.start[i0] = (unsigned short)pre;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kKPT; k++)
+    if (ok[k]) {
+      const unsigned pos = sm.start[tag[k] >> 20] + rk[k];
+      sm.sorted[pos] = x[k];
+      sm.stag[pos] = tag[k];
+    }
+  // the write-out's limit and arena index of this thread's destination
+  if (c) {
+    const DestRun r = dest(i0);
+    const u64 room = b0 < r.cap ? r.cap - b0 : 0;
+    const unsigned lim = pre + (unsigned)(room < c ? room : c);
+    sm.run[i0] = ((u64)lim << kRunShift) | ((r.base + b0 - pre) & kRunMask);
+  }
+  __syncthreads();
+  // write-out, four entries a thread at a time: a group's loads are issued
+  // before its stores
+#pragma unroll
+  for (int k0 = 0; k0 < kKPT; k0 += 4) {
+    unsigned tg[4];
+    u64 v[4], rr[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
+      tg[u] = 0;
+      v[u] = 0;
+      if (i < total) {
+        tg[u] = sm.stag[i];
+        v[u] = sm.sorted[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
+      rr[u] = i < total ? sm.run[tg[u] >> 20] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
+      if (i < total) {
+        if (i < (unsigned)(rr[u] >> kRunShift)) {
+          const u64 j = (rr[u] + i) & kRunMask;
+          arena[j] = v[u];
+          if (WITH_POS) parena[j] = tg[u] & 0xfffffu;
+        } else {
+          atomicOr(status, ST_OVERFLOW);
+        }
+      }
+    }
+  }
+}
+
+// Any number of destinations up to kBmax: each thread owns up to kBmax / kTT
+// consecutive ones and issues their reservations together.  Here `start`
+// holds each destination's local limit and `run` the arena index of its local
+// entry 0; the counts hold the local starts until the write-out, which clears
+// them behind a final barrier.
+template <bool WITH_POS, class Dest>
+__device__ __forceinline__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
+                                                 const unsigned (&dst)[kKPT], const bool (&ok)[kKPT],
+                                                 unsigned nb, const SplitSmem &sm, u64 *__restrict__ arena,
+                                                 unsigned *__restrict__ parena, const Dest &dest,
+                                                 unsigned *__restrict__ status) {
+  constexpr unsigned kPer = (unsigned)(kBmax / kTT);
+  static_assert(kBmax % kTT == 0, "destinations per thread");
   unsigned rk[kKPT];
 #pragma unroll
   for (int k = 0; k < kKPT; k++) rk[k] = ok[k] ? atomicAdd(&sm.cnt[dst[k]], 1u) : 0u;
   __syncthreads();
-  // exclusive scan of the counts (each thread owns a run of entries), then
-  // reserve each destination's slots and precompute where its run goes; sm.red
-  // is only touched by this scan, and the barriers below separate its reads
-  // from the next call's writes
-  // GROUPED: nb <= kBmax, so a thread owns at most kBmax / kTT destinations,
-  // and their reservations are issued together instead of one round trip
-  // after another (more registers: kernels already at their register limit
-  // take the plain loop)
   const unsigned per = (nb + kTT - 1) / kTT;
   const unsigned lo = threadIdx.x * per;
   const unsigned hi = min(lo + per, nb);
+  unsigned c[kPer], s = 0;
+#pragma unroll
+  for (unsigned k = 0; k < kPer; k++) {
+    c[k] = lo + k < hi ? sm.cnt[lo + k] : 0u;
+    s += c[k];
+  }
   unsigned total;
-  if (GROUPED) {
-    constexpr unsigned kPer = (unsigned)(kBmax / kTT);
-    static_assert(kBmax % kTT == 0, "destinations per thread");
-    unsigned c[kPer], s = 0;
+  unsigned pre = block_scan_u32_fenced<kTT>(s, sm.red, &total);
+  u64 b0[kPer];
 #pragma unroll
-    for (unsigned k = 0; k < kPer; k++) {
-      c[k] = lo + k < hi ? sm.cnt[lo + k] : 0u;
-      s += c[k];
-    }
-    unsigned pre = block_scan_u32_fenced<kTT>(s, sm.red, &total);
-    u64 b0[kPer];
+  for (unsigned k = 0; k < kPer; k++) b0[k] = c[k] ? atomicAdd(dest(lo + k).counter, (u64)c[k]) : 0;
 #pragma unroll
-    for (unsigned k = 0; k < kPer; k++)
-      b0[k] = c[k] ? atomicAdd(dest(lo + k).counter, (u64)c[k]) : 0;
-#pragma unroll
-    for (unsigned k = 0; k < kPer; k++) {
-      if (lo + k < hi) {
-        const DestRun r = dest(lo + k);
-        const u64 room = c[k] && b0[k] < r.cap ? r.cap - b0[k] : 0;
-        sm.cnt[lo + k] = pre;
-        sm.lim[lo + k] = pre + (unsigned)(room < c[k] ? room : c[k]);
-        sm.dbase[lo + k] = (c[k] ? r.base + b0[k] : 0) - pre;
-        pre += c[k];
-      }
-    }
-  } else {
-    unsigned s = 0;
-    for (unsigned i = lo; i < hi; i++) s += sm.cnt[i];
-    unsigned pre = block_scan_u32_fenced<kTT>(s, sm.red, &total);
-    for (unsigned i = lo; i < hi; i++) {
-      const unsigned c = sm.cnt[i];
-      u64 b0 = 0, room = 0, base = 0;
-      if (c) {
-        const DestRun r = dest(i);
-        b0 = atomicAdd(r.counter, (u64)c);
-        room = b0 < r.cap ? r.cap - b0 : 0;
-        base = r.base;
-      }
-      sm.cnt[i] = pre;
-      sm.lim[i] = pre + (unsigned)(room < c ? room : c);
-      sm.dbase[i] = base + b0 - pre;
-      pre += c;
+  for (unsigned k = 0; k < kPer; k++) {
+    if (lo + k < hi) {
+      const DestRun r = dest(lo + k);
+      const u64 room = c[k] && b0[k] < r.cap ? r.cap - b0[k] : 0;
+      sm.cnt[lo + k] = pre;
+      sm.start[lo + k] = (unsigned short)(pre + (unsigned)(room < c[k] ? room : c[k]));
+      sm.run[lo + k] = (c[k] ? r.base + b0[k] : 0) - pre;
+      pre += c[k];
     }
   }
   __syncthreads();
@@ -292,8 +376,8 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   for (unsigned i = threadIdx.x; i < total; i += kTT) {
     const unsigned tg = sm.stag[i];
     const unsigned b = tg >> 20;
-    if (i < sm.lim[b]) {
-      const u64 j = sm.dbase[b] + i;
+    if (i < sm.start[b]) {
+      const u64 j = sm.run[b] + i;
       arena[j] = sm.sorted[i];
       if (WITH_POS) parena[j] = tg & 0xfffffu;
     } else {
@@ -303,7 +387,6 @@ __device__ void multisplit_write(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT
   for (unsigned i = threadIdx.x; i < nb; i += kTT) sm.cnt[i] = 0;  // last read before the scatter
   __syncthreads();
 }
-
 // Zero the destination counts before a kernel's first multisplit_write (the
 // caller synchronises the block before that call).
 __device__ __forceinline__ void split_clear(const SplitSmem &sm, unsigned nb_cap) {
@@ -316,17 +399,18 @@ __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned n
                                                  unsigned sorted_cap = kTile) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
-  s.dbase = s.sorted + sorted_cap;
-  s.stag = reinterpret_cast<unsigned *>(s.dbase + nb_cap);
+  s.run = s.sorted + sorted_cap;
+  s.stag = reinterpret_cast<unsigned *>(s.run + nb_cap);
   s.cnt = s.stag + kTile;
-  s.lim = s.cnt + nb_cap;
-  s.red = s.lim + nb_cap;
+  s.red = s.cnt + nb_cap;
+  s.start = reinterpret_cast<unsigned short *>(s.red + kTT / 32 + 2);
   return s;
 }
 
 static constexpr size_t split_smem_bytes(unsigned nb_cap, unsigned sorted_cap = kTile) {
-  return (size_t)sorted_cap * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 +
-         2 * (size_t)nb_cap * 4 + (kTT / 32 + 2) * 4 + 8;
+  // a multiple of 16 bytes: callers place 16-byte staging buffers after it
+  return ((size_t)sorted_cap * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 + (size_t)nb_cap * 4 +
+          (kTT / 32 + 2) * 4 + (size_t)nb_cap * 2 + 8 + 15) & ~(size_t)15;
 }
 
 // ---------------------------------------------------------------------------
