@@ -53,6 +53,18 @@ struct BSet {     // per set
   unsigned levels_used, status, small, tail_level;
 };
 
+// Tile t of the partition (keys [t kTile, (t + 1) kTile) of the concatenated
+// sets): the sets it overlaps, the global buckets their keys can go to, and,
+// when the whole tile lies in one bucketed set, that set's level-0 parameters.
+struct BTile {
+  u64 gb0;        // first global bucket of the tile's bucketed sets
+  u64 m, base;    // one-set tile: the set's m_0 and its first bucket - gb0
+  unsigned sa;    // first set overlapping the tile
+  unsigned nb;    // destination buckets (0: no bucketed key in the tile)
+  unsigned sh;    // one-set tile: log2 of the set's bucket width
+  unsigned one;   // 1: the tile lies in one bucketed set
+};
+
 struct BCfg {
   double gamma;
   uint32_t L;
@@ -76,6 +88,7 @@ struct BCfg {
   double cap_scale;
   unsigned *status;                  // global (any overflow of a shared bound)
   unsigned *upre;                    // [bcap + 1] compaction units before each bucket of level d
+  BTile *tiles;                      // [ceil(total / kTile)] partition tile headers
 };
 
 __host__ __device__ inline void size_set_level(BLvl &lv, u64 n, const BCfg &c) {
@@ -115,101 +128,130 @@ struct PartDest {
   }
 };
 
+// One thread per tile (the headers the partition reads, so that no thread of
+// it searches the set offsets while the others wait).
+__global__ void k_btiles(const u64 *__restrict__ key_off, u64 total, BCfg c,
+                         BTile *__restrict__ tiles) {
+  const u64 ntiles = ceil_div(total, kTile);
+  const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const u64 t0 = t * kTile, t1 = min(t0 + kTile, total);
+  // sets overlapping [t0, t1): key_off is non-decreasing with S + 1 entries
+  unsigned lo = 0, hi = c.S;  // first s with key_off[s + 1] > t0
+  while (lo < hi) {
+    const unsigned mid = (lo + hi) >> 1;
+    if (key_off[mid + 1] > t0) hi = mid;
+    else lo = mid + 1;
+  }
+  unsigned sb = lo;
+  while (sb + 1 < c.S && key_off[sb + 1] < t1) sb++;
+  // global buckets of the large sets in [sa, sb] are consecutive
+  u64 g0 = ~0ull, g1 = 0;
+  for (unsigned s = lo; s <= sb; s++) {
+    const BLvl &lv = c.lvl[0][s];
+    if (lv.mode == LM_BUCKETED) {
+      g0 = min(g0, lv.bbase);
+      g1 = max(g1, lv.bbase + lv.B);
+    }
+  }
+  BTile h;
+  h.sa = lo;
+  h.gb0 = g0 == ~0ull ? 0 : g0;
+  h.nb = g0 == ~0ull ? 0u : (unsigned)(g1 - g0);
+  if (g0 != ~0ull && g1 - g0 > kBmax) {
+    for (unsigned s = lo; s <= sb; s++)
+      if (c.lvl[0][s].mode == LM_BUCKETED) fail_set(&c.sets[s]);
+    h.nb = 0;
+  }
+  h.one = (lo == sb && c.lvl[0][lo].mode == LM_BUCKETED) ? 1u : 0u;
+  h.m = h.one ? c.lvl[0][lo].m : 0;
+  h.sh = h.one ? c.lvl[0][lo].sh : 0;
+  h.base = h.one ? c.lvl[0][lo].bbase - h.gb0 : 0;
+  tiles[t] = h;
+}
+
+// Each thread owns kKPT consecutive keys of a tile, staged by asynchronous
+// copies while the previous tile is split (the layout of k_partition0).
+template <bool ALIGNED>
 __global__ void __launch_bounds__(kTT, 2)
 k_bpartition0(const u64 *__restrict__ key_off, u64 total, BCfg c) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned t_sa;
-  __shared__ u64 t_gb0;
-  __shared__ unsigned t_nb;
-  __shared__ u64 t_m, t_base;  // one bucketed set in the tile: its m and first bucket - gb0
-  __shared__ unsigned t_sh, t_one;
   SplitSmem sm = carve_split(smem, (unsigned)kBmax);
-  split_clear(sm, (unsigned)kBmax);  // ordered by the first tile's barrier
+  split_clear(sm, (unsigned)kBmax);
+  __syncthreads();
+  u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes((unsigned)kBmax));
+  auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * kTT + threadIdx.x) + (k & 1); };
   const u64 s0 = level_seed(c.seed, 0);
   const u64 ntiles = ceil_div(total, kTile);
-  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const u64 t0 = t * kTile, t1 = min(t0 + kTile, total);
-    if (threadIdx.x == 0) {
-      // sets overlapping [t0, t1): key_off is non-decreasing with S + 1 entries
-      unsigned lo = 0, hi = c.S;  // first s with key_off[s + 1] > t0
-      while (lo < hi) {
-        unsigned mid = (lo + hi) >> 1;
-        if (key_off[mid + 1] > t0) hi = mid;
-        else lo = mid + 1;
-      }
-      unsigned sb = lo;
-      while (sb + 1 < c.S && key_off[sb + 1] < t1) sb++;
-      t_sa = lo;
-      // global buckets of the large sets in [sa, sb] are consecutive
-      u64 g0 = ~0ull, g1 = 0;
-      for (unsigned s = lo; s <= sb; s++) {
-        const BLvl &lv = c.lvl[0][s];
-        if (lv.mode == LM_BUCKETED) {
-          g0 = min(g0, lv.bbase);
-          g1 = max(g1, lv.bbase + lv.B);
-        }
-      }
-      t_gb0 = g0 == ~0ull ? 0 : g0;
-      t_nb = g0 == ~0ull ? 0u : (unsigned)(g1 - g0);
-      if (g0 != ~0ull && g1 - g0 > kBmax) {
-        for (unsigned s = lo; s <= sb; s++)
-          if (c.lvl[0][s].mode == LM_BUCKETED) fail_set(&c.sets[s]);
-        t_nb = 0;
-      }
-      // the common case: the whole tile lies in one bucketed set
-      t_one = (lo == sb && c.lvl[0][lo].mode == LM_BUCKETED) ? 1u : 0u;
-      if (t_one) {
-        t_m = c.lvl[0][lo].m;
-        t_sh = c.lvl[0][lo].sh;
-        t_base = c.lvl[0][lo].bbase - t_gb0;
+  const unsigned tb = threadIdx.x * kKPT;
+  auto prefetch = [&](u64 t) {
+    if (t < ntiles) {
+      const u64 *src = c.keys + t * kTile;
+      const u64 rem = total - t * kTile;
+      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
+      if (ALIGNED && tb + kKPT <= nt) {
+#pragma unroll
+        for (int k = 0; k < kKPT; k += 2) cp_async16(slot(k), src + tb + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kKPT; k++)
+          if (tb + k < nt) cp_async8(slot(k), src + tb + k);
       }
     }
-    __syncthreads();
-    const unsigned nb = t_nb;
-    if (nb == 0) {
-      __syncthreads();
-      continue;
-    }
+    cp_async_commit();
+  };
+  u64 t = blockIdx.x;
+  prefetch(t);
+  for (; t < ntiles; t += gridDim.x) {
+    const BTile hd = c.tiles[t];
+    cp_async_wait0();  // this thread's copies of tile t have landed
+    const u64 t0 = t * kTile;
+    const unsigned nt = (unsigned)min((u64)kTile, total - t0);
     u64 x[kKPT];
+#pragma unroll
+    for (int k = 0; k < kKPT; k += 2) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(slot(k));
+      x[k] = ((u64)v.y << 32) | v.x;
+      x[k + 1] = ((u64)v.w << 32) | v.z;
+    }
+    // the slots are read before the next tile's copies into them are issued
+    prefetch(t + gridDim.x);
+    if (hd.nb == 0) continue;  // the same in every thread
     unsigned dst[kKPT], lp[kKPT];
     bool ok[kKPT];
-    if (t_one) {  // one set: its parameters for every key, no per-key set search
-      const u64 m = t_m, base = t_base;
-      const unsigned sh = t_sh, mask = (1u << sh) - 1u;
+    if (hd.one) {  // one set: its parameters for every key, no per-key set search
+      const unsigned mask = (1u << hd.sh) - 1u;
 #pragma unroll
       for (int k = 0; k < kKPT; k++) {
-        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
-        ok[k] = i < t1;
-        x[k] = ok[k] ? __ldcs(c.keys + i) : 0;
-        const u64 p = level_pos(x[k], s0, m);
-        dst[k] = (unsigned)(base + (p >> sh));
+        ok[k] = tb + k < nt;
+        const u64 p = level_pos(x[k], s0, hd.m);
+        dst[k] = (unsigned)(hd.base + (p >> hd.sh));
         lp[k] = (unsigned)p & mask;
       }
     } else {
-      unsigned s = t_sa;
+      unsigned s = hd.sa;
 #pragma unroll
       for (int k = 0; k < kKPT; k++) {
-        const u64 i = t0 + (u64)k * kTT + threadIdx.x;
+        const u64 i = t0 + tb + k;
         ok[k] = false;
-        x[k] = 0;
         dst[k] = 0;
         lp[k] = 0;
-        if (i < t1) {
+        if (tb + k < nt) {
           while (key_off[s + 1] <= i) s++;  // monotone in k
           const BLvl &lv = c.lvl[0][s];
           if (lv.mode == LM_BUCKETED) {
-            x[k] = __ldcs(c.keys + i);
             const u64 p = level_pos(x[k], s0, lv.m);
-            dst[k] = (unsigned)(lv.bbase + (p >> lv.sh) - t_gb0);
+            dst[k] = (unsigned)(lv.bbase + (p >> lv.sh) - hd.gb0);
             lp[k] = (unsigned)(p & (lv.P - 1));
             ok[k] = true;
           }
         }
       }
     }
-    multisplit_write<true>(x, lp, dst, ok, nb, sm, c.X[0], c.XP[0],
-                     PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], t_gb0}, c.status);
+    multisplit_write<true>(x, lp, dst, ok, hd.nb, sm, c.X[0], c.XP[0],
+                           PartDest{c.bset[0], c.bidx[0], c.lvl[0], c.cnt[0], hd.gb0}, c.status);
   }
+  cp_async_wait0();
 }
 
 // ---------------------------------------------------------------------------
@@ -889,8 +931,12 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   mcap = level_bits(T, gamma);
   const size_t tail_b = tail_smem_bytes(mcap, tune.tail_keys);
   if (!attr) {
-    MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)split_b));
+    MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(split_b + kTile * 8)));
+    MPHF_CUDA(cudaFuncSetAttribute(k_bpartition0<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(split_b + kTile * 8)));
     MPHF_CUDA(cudaFuncSetAttribute(k_bcompact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)comp_max));
     MPHF_CUDA(cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1007,6 +1053,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   WS(19, sizeof(u64) * (S + 1), &p);
   u64 *d_koff = (u64 *)p;
   WS(20, 4 * (bcap + 1), &c.upre);
+  WS(21, sizeof(BTile) * (ceil_div(total, kTile) + 1), &c.tiles);
 #undef WS
   c.keys = d_keys;
   // ---- level-0 bucket descriptors on the host
@@ -1049,8 +1096,13 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   unsigned nk_rec = 0;
   auto record = [&](int Dl) -> int {
     if (nbk) {
-      k_bpartition0<<<grid2, kTT, split_b, st>>>(d_koff, total, c);
-      nk_rec++;
+      const u64 ntiles = ceil_div(total, kTile);
+      k_btiles<<<(unsigned)ceil_div(ntiles, 256), 256, 0, st>>>(d_koff, total, c, c.tiles);
+      if (((uintptr_t)c.keys & 15) == 0)
+        k_bpartition0<true><<<grid2, kTT, split_b + kTile * 8, st>>>(d_koff, total, c);
+      else
+        k_bpartition0<false><<<grid2, kTT, split_b + kTile * 8, st>>>(d_koff, total, c);
+      nk_rec += 2;
     }
     for (int d = 0; d <= Dl && d < (int)L; d++) {
       if (nbk) {
