@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <atomic>
@@ -125,13 +126,17 @@ mphf *handle_new() {
   return h;
 }
 
-bool handle_new_n(unsigned n, mphf **out) {
+bool handle_new_n(unsigned n, mphf **out, bool zero_tables) {
+  static const mphf proto;
   unsigned got = 0;
   {
     std::lock_guard<std::mutex> lk(g_handle_mu);
     while (got < n && g_handle_nfree) out[got++] = g_handle_free[--g_handle_nfree];
   }
-  for (unsigned i = 0; i < got; i++) new (out[i]) mphf();
+  for (unsigned i = 0; i < got; i++) {
+    if (zero_tables) new (out[i]) mphf();
+    else memcpy((void *)out[i], (const void *)&proto, offsetof(mphf, n));
+  }
   for (; got < n; got++) {
     out[got] = new (std::nothrow) mphf();
     if (!out[got]) {

@@ -1305,7 +1305,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     unsigned n_ok = 0;
     for (unsigned s = 0; s < S; s++) n_ok += okset[s] ? 1 : 0;
     recs.resize(n_ok);
-    if (n_ok && !handle_new_n(n_ok, recs.data())) {
+    if (n_ok && !handle_new_n(n_ok, recs.data(), false)) {
       rc = MPHF_ENOMEM;
       recs.clear();
       for (unsigned s = 0; s < S; s++) okset[s] = 0;
@@ -1323,6 +1323,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     h->seed = seed;
     memcpy(h->s, seeds, L * sizeof(u64));
     h->path = 3;
+    h->n[0] = 0;  // an empty set: no level; the tables are written below otherwise
     if (b.n0) {
       const FLevel *hl = &hist[(u64)s * (L + 1)];
       h->L_used = b.levels_used;

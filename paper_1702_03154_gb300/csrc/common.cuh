@@ -222,10 +222,6 @@ struct mphf {
   uint32_t L = 25;
   uint64_t seed = 0;
   uint32_t L_used = 0;
-  uint64_t n[MPHF_MAX_LEVELS + 1] = {0};
-  uint64_t m[MPHF_MAX_LEVELS] = {0};
-  uint64_t off[MPHF_MAX_LEVELS] = {0};
-  uint64_t s[MPHF_MAX_LEVELS] = {0};
   uint64_t M = 0;        // total bits
   uint64_t n_rank = 0;   // ceil(M / 512)
   uint64_t n_fb = 0;
@@ -238,6 +234,12 @@ struct mphf {
   int path = 0;          // 1 bucketed, 2 unbucketed, 3 batched, 4 loaded, 5 without stored F_d
   mphf_shared *shared = nullptr;  // set: S/SB/fb live in a batched arena
   bbh::DevBuf ldesc;     // device descriptor for multi-function lookups (made on first use)
+  // level tables (last, so that a record can be reset without them): entries
+  // past L_used (n: past L_used + 1; s: past L) are never read
+  uint64_t n[MPHF_MAX_LEVELS + 1] = {0};
+  uint64_t m[MPHF_MAX_LEVELS] = {0};
+  uint64_t off[MPHF_MAX_LEVELS] = {0};
+  uint64_t s[MPHF_MAX_LEVELS] = {0};
 };
 
 namespace bbh {
@@ -255,8 +257,10 @@ inline bool narrow_positions(const mphf *h) {
 // thousands at once, and fresh heap pages for them (each record is ~2 KB of
 // level tables) cost a page fault per page.  handle_new returns a zeroed
 // record or nullptr; handle_new_n fills out[0..n) under one lock (all or
-// none); handle_delete takes back a record whose device memory is released.
+// none; zero_tables = false leaves a reused record's level tables as they
+// were, for a caller that writes every entry it reads); handle_delete takes
+// back a record whose device memory is released.
 mphf *handle_new();
-bool handle_new_n(unsigned n, mphf **out);
+bool handle_new_n(unsigned n, mphf **out, bool zero_tables = true);
 void handle_delete(mphf *h);
 }  // namespace bbh
