@@ -407,27 +407,27 @@ def kernel_table(h, prof, steps, n_queries):
 # hit/collision bits); a "query" one looked-up key; a "key" one key of F_0.
 _HDR = ["common.cuh", "fastbuild.cuh", "sector.cuh"]
 NCU_TRAFFIC = {
-    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "a9bb7191c25d", "unit": "grouped key-visit",
-                     "bytes_per_unit": 35.05,
-                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.06 GB "
+    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "a42013b72b0c", "unit": "grouped key-visit",
+                     "bytes_per_unit": 35.18,
+                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.22 GB "
                              "over 1.2e9 grouped key-visits), scaled by grouped key-visits"},
-    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "a9bb7191c25d", "unit": "grouped key-visit",
+    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "a42013b72b0c", "unit": "grouped key-visit",
                   "bytes_per_unit": 17.74,
                   "note": "3e8-key capture (20 launches of 4 builds, 21.28 GB over 1.2e9 "
                           "grouped key-visits), scaled by grouped key-visits"},
-    "lookup@hbm": {"src": ["lookup.cu"] + _HDR, "sha": "7154cc30723b", "unit": "query",
-                   "bytes_per_unit": 106.4,
+    "lookup@hbm": {"src": ["lookup.cu"] + _HDR, "sha": "590bc6e40776", "unit": "query",
+                   "bytes_per_unit": 114.8,
                    "note": "3e8-key function (A 140 MB, above L2), 3e7 random member queries x 4 "
-                           "launches, 13.77 GB"},
-    "lookup@l2": {"src": ["lookup.cu"] + _HDR, "sha": "7154cc30723b", "unit": "query",
-                  "bytes_per_unit": 16.3,
+                           "launches, 13.78 GB"},
+    "lookup@l2": {"src": ["lookup.cu"] + _HDR, "sha": "590bc6e40776", "unit": "query",
+                  "bytes_per_unit": 16.25,
                   "note": "3e7-key function (A 14 MB, in L2), 3e7 random member queries x 2 "
-                          "launches, 0.978 GB"},
-    "partition": {"src": ["fastbuild.cu"] + _HDR, "sha": "a95370586c9d", "unit": "key",
-                  "bytes_per_unit": 18.2, "note": "3e7-key builds (3 launches, 1.639 GB)"},
-    "compact_buckets": {"src": ["fastbuild.cu"] + _HDR, "sha": "a95370586c9d", "unit": "key",
-                        "bytes_per_unit": 23.3,
-                        "note": "3e7-key builds (3 builds, 26 launches, 2.100 GB), per key of F_0"},
+                          "launches, 0.975 GB"},
+    "partition": {"src": ["fastbuild.cu"] + _HDR, "sha": "5f73b2a05ed5", "unit": "key",
+                  "bytes_per_unit": 18.21, "note": "3e7-key builds (3 launches, 1.639 GB)"},
+    "compact_buckets": {"src": ["fastbuild.cu"] + _HDR, "sha": "5f73b2a05ed5", "unit": "key",
+                        "bytes_per_unit": 23.34,
+                        "note": "3e7-key builds (3 builds, 26 launches, 2.101 GB), per key of F_0"},
 }
 L2_BYTES = 126 << 20
 
