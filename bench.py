@@ -539,8 +539,9 @@ def run_headline(args, stream, world, rank, local, barrier, ceil):
                          "level_sizes": sizes[:8], "fallback": last.num_fallback,
                          "build_path": last.build_path,
                          "device_bytes_per_key": round(last.device_bytes() / N, 4)}}
-    # The build as a whole against HBM: the method's streamed bytes (survey
-    # model per key-visit) over the build time.
+    # The build as a whole against HBM: the method's streamed bytes per
+    # key-visit (read for the fill, read for the compaction, survivors
+    # written) over the build time.
     sb = build_stream_bytes(last)
     res["build_roofline"] = {"bound": "hbm", "algorithmic_bytes": sb,
                              "achieved": round(sb / (t_build / 1e3) / 1e9, 1), "peak": peak,
