@@ -360,11 +360,13 @@ def test_build_lookup_host_edges(M):
 
 
 @pytest.mark.parametrize("gamma,levels,shift", [(2.0, 25, 12), (1.0, 25, 10), (5.0, 25, 14),
-                                                (1.0, 3, 12), (2.0, 25, 6)])
+                                                (1.0, 3, 12), (2.0, 25, 8), (2.0, 25, 6)])
 def test_unbucketed_slab_grouping(M, gamma, levels, shift):
     # The unbucketed path groups a level's keys by slabs of 2^shift positions
-    # before filling it (all levels here: threshold 0); shift 6 gives more
-    # slabs than a multisplit takes, so level 0 is left ungrouped.
+    # before filling it (all levels here: threshold 0).  Shift 8 gives levels
+    # 0 and 1 more slabs than threads (the multisplit whose threads own
+    # several slabs) and the later levels fewer (one slab per thread); shift 6
+    # gives more slabs than a multisplit takes, so level 0 is left ungrouped.
     keys = inputs.splitmix64_keys(200001, 56)
     q = np.concatenate([inputs.shuffled(keys, 7), inputs.splitmix64_keys(5000, 57)])
     o = oracle.build(keys, gamma=gamma, levels=levels, seed=11)
