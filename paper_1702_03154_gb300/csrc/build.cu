@@ -867,6 +867,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
   unsigned nslab0 = 0;
   unsigned *slab_status = nullptr;
   unsigned *fuse_status = nullptr;
+  u64 ac_cap = 0;       // bytes of each hit/collision array
   std::vector<u64> se;  // slab ranges of the grouped keys
 
 #define TRY(x)                  \
@@ -877,7 +878,6 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
 
   TRY(dev_alloc(sc.meta, sizeof(BuildMeta), st));
   meta = (BuildMeta *)sc.meta.p;
-  TRY(dev_alloc(sc.AC0, m0 / 32 * 8, st));
   TRY(dev_alloc(sc.A0, m0 / 64 * 8, st));
   TRY(dev_alloc(sc.dupflag, 32, st));  // dup flag, rank total, slab and F1 overflow
   dflag = (unsigned int *)sc.dupflag.p;
@@ -885,8 +885,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     rc = cuda_fail((cudaError_t)rc, "cudaMemcpyAsync(meta)");
     goto fail;
   }
-  if (cudaMemsetAsync(sc.AC0.p, 0, sc.AC0.bytes, st) != cudaSuccess ||
-      cudaMemsetAsync(dflag, 0, 32, st) != cudaSuccess) {
+  if (cudaMemsetAsync(dflag, 0, 32, st) != cudaSuccess) {
     rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
     goto fail;
   }
@@ -902,6 +901,16 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
       dev_free(sc.slab, st);
       nslab0 = 0;
     }
+  }
+  // The hit/collision arrays (2 bits a position) serve the ungrouped levels
+  // only.  Once level 0 is grouped, a level is ungrouped only when its array
+  // is at most g_slab_min_ac bytes (or it is the fallback), so that bounds
+  // both arrays.  The extraction zeroes an array behind it: one memset here.
+  ac_cap = nslab0 ? std::min(m0 / 32 * 8, ((g_slab_min_ac + 15) & ~(u64)15) + 16) : m0 / 32 * 8;
+  TRY(dev_alloc(sc.AC0, ac_cap, st));
+  if (cudaMemsetAsync(sc.AC0.p, 0, sc.AC0.bytes, st) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+    goto fail;
   }
   slab_status = (unsigned *)((u64 *)sc.dupflag.p + 2);
   fuse_status = (unsigned *)((u64 *)sc.dupflag.p + 3);
@@ -949,7 +958,7 @@ static int robust_build(const u64 *keys, u64 N, double gamma, uint32_t L, u64 se
     // with grouped levels, R (N keys) is the second buffer of the level loop
     if (L > 1 && !nslab0) TRY(dev_alloc(sc.F2, n1 * 8, st));
     if (L > 1) {
-      TRY(dev_alloc(sc.AC1, m1 / 32 * 8, st));
+      TRY(dev_alloc(sc.AC1, std::min(m1 / 32 * 8, ac_cap), st));
       TRY(dev_alloc(sc.arena, (u64)(L - 1) * (m1 / 64) * 8, st));
       if (cudaMemsetAsync(sc.AC1.p, 0, sc.AC1.bytes, st) != cudaSuccess) {
         rc = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
