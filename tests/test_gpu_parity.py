@@ -193,6 +193,28 @@ def test_host_build_chunked_unbucketed_path(M, path, cap_scale):
     assert_same_structure(g, o)
 
 
+@pytest.mark.parametrize("cap_scale", [1.0, 0.3])
+def test_host_build_grouped_level0(M, cap_scale):
+    # Keys streamed from host memory into a build whose level 0 is grouped by
+    # slab (with the slab capacities scaled down the ranges overflow and level
+    # 0 is grouped again with exact counts): the function and the indices of
+    # the oracle.
+    n = (1 << 22) + 777
+    keys = inputs.splitmix64_keys(n, 63)
+    q = np.concatenate([inputs.shuffled(keys, 9), inputs.splitmix64_keys(5000, 64)])
+    o = oracle.build(keys, gamma=2.0, levels=25, seed=16)
+    M.debug_config(1, cap_scale)
+    M.debug_slabs(16, 0)
+    try:
+        g, out = M.MPHF.build_lookup_host(keys, q, gamma=2.0, levels=25, seed=16)
+    finally:
+        M.debug_slabs()
+        M.debug_config(0, 1.0)
+    assert g.build_path == 2
+    assert_same_structure(g, o)
+    assert np.array_equal(out, o.lookup(q))
+
+
 def test_host_lookup_chunked_empty_function(M):
     g = M.MPHF.build_host(np.empty(0, dtype=np.uint64))
     q = inputs.splitmix64_keys((1 << 22) + 5, 51)
