@@ -8,7 +8,8 @@
 //   * larger sets are kept in position-range buckets (global bucket list:
 //     bucket = (set, index)); one launch per phase and level processes the
 //     buckets of all sets: ArrayFill in shared memory (k_bfill), sizing of the
-//     next level of every set (k_bfinish, one CTA, scans over sets) and the
+//     next level of every set (k_bfin_sets / k_bfin_scan / k_bfin_desc: per set,
+//     one CTA's scans over the sets, per set again) and the
 //     compaction of the survivors into their next-level buckets (k_bcompact);
 //     a set whose level has at most T keys moves to its flat range and joins
 //     the single-CTA tail.
@@ -89,6 +90,8 @@ struct BCfg {
   unsigned *status;                  // global (any overflow of a shared bound)
   unsigned *upre;                    // [bcap + 1] compaction units before each bucket of level d
   BTile *tiles;                      // [ceil(total / kTile)] partition tile headers
+  u64 *fin;                          // [3 S] level finish: per-set counts, then their prefixes
+  unsigned *fit;                     // [2] level finish: the next level's buckets fit, by d & 1
 };
 
 __host__ __device__ inline void size_set_level(BLvl &lv, u64 n, const BCfg &c) {
@@ -324,133 +327,167 @@ __global__ void __launch_bounds__(kTT, 2) k_bfill(int d, BCfg c) {
 }
 
 // ---------------------------------------------------------------------------
-// Next-level sizing for every set (one CTA): records level d, decides where
-// level d+1 lives, lays out its buckets and flat ranges, zeroes counters.
+// Next-level sizing for every set, in three launches: per set (one thread a
+// set) record level d, decide where level d+1 lives and count its buckets,
+// arena slots and level d's compaction units; one CTA scans those counts over
+// the sets; per set again, lay out level d+1's buckets, zero their counters
+// and turn level d's unit counts into the prefix the compaction reads.
 // ---------------------------------------------------------------------------
+static constexpr int kFinSetThreads = 256;
 static constexpr int kFinishThreads = 1024;
 
-__global__ void __launch_bounds__(kFinishThreads, 1) k_bfinish(int d, BCfg c) {
-  __shared__ unsigned red32[kFinishThreads / 32 + 2];
-  __shared__ u64 red64[kFinishThreads / 32 + 2];
+// 1. one thread per set
+__global__ void __launch_bounds__(kFinSetThreads) k_bfin_sets(int d, BCfg c) {
+  const unsigned s = blockIdx.x * kFinSetThreads + threadIdx.x;
+  if (s >= c.S) return;
   const int sl = d & 1, nl = (d + 1) & 1;
+  BSet *st = &c.sets[s];
+  const BLvl cur = c.lvl[sl][s];
+  BLvl nx = cur;
+  if (cur.mode == LM_BUCKETED && !st->status) {
+    FLevel &h = c.hist[(u64)s * (c.L + 1) + d];
+    h.n = cur.n;
+    h.m = cur.m;
+    h.off = cur.off;
+    h.weight = cur.weight;
+    if (cur.weight > cur.n) atomicOr(&st->status, ST_INTERNAL);
+    const u64 nn = cur.weight > cur.n ? 0 : cur.n - cur.weight;
+    memset(&nx, 0, sizeof(nx));
+    nx.n = nn;
+    nx.off = cur.off + cur.m;
+    if (nn == 0) {
+      nx.mode = LM_DONE;
+      st->levels_used = d + 1;
+    } else if ((uint32_t)(d + 1) == c.L) {
+      nx.mode = LM_FLAT;
+      st->tail_level = d + 1;
+      if (nn > st->flat_cap) fail_set(st);
+    } else if (nn <= c.T) {
+      nx.mode = LM_FLAT;
+      nx.m = level_bits(nn, c.gamma);
+      st->tail_level = d + 1;
+    } else {
+      size_set_level(nx, nn, c);
+      nx.off = cur.off + cur.m;
+      nx.mode = LM_BUCKETED;
+    }
+  } else if (cur.mode == LM_BUCKETED) {
+    nx.mode = LM_FAILED;
+  }
+  u64 nb = 0, ns = 0;
+  if (nx.mode == LM_BUCKETED && !st->status) {
+    nb = nx.B;
+    ns = nx.B * nx.cap;
+  } else if (nx.mode == LM_BUCKETED) {
+    nx.mode = LM_FAILED;
+  }
+  nx.weight = 0;
+  c.lvl[nl][s] = nx;
+  // level d's compaction units (kIn entries) of this set's buckets, parked in
+  // upre until the prefix over sets is known
+  u64 nu = 0;
+  if (cur.mode == LM_BUCKETED) {
+    for (u64 j = 0; j < cur.B; j++) {
+      const u64 g = cur.bbase + j;
+      const u64 nk = c.cnt[sl][g] < cur.cap ? c.cnt[sl][g] : cur.cap;
+      const unsigned u = (unsigned)((nk + kIn - 1) / kIn);
+      c.upre[g] = u;
+      nu += u;
+    }
+  }
+  c.fin[3 * (u64)s] = nb;
+  c.fin[3 * (u64)s + 1] = ns;
+  c.fin[3 * (u64)s + 2] = nu;
+}
+
+// 2. one CTA: exclusive scans of the three counts over the sets (in place),
+// the fit check of level d+1's buckets and slots, the totals
+__global__ void __launch_bounds__(kFinishThreads, 1) k_bfin_scan(int d, BCfg c) {
+  __shared__ u64 red[3][kFinishThreads / 32];
+  const int sl = d & 1, nl = (d + 1) & 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned per = (c.S + kFinishThreads - 1) / kFinishThreads;
   const unsigned lo = threadIdx.x * per, hi = min(lo + per, c.S);
-  // 1. decide each set's next state; count its buckets and arena slots
-  u64 nbk = 0, nslots = 0;
-  for (unsigned s = lo; s < hi; s++) {
-    BSet *st = &c.sets[s];
-    const BLvl cur = c.lvl[sl][s];
-    BLvl nx = cur;
-    if (cur.mode == LM_BUCKETED && !st->status) {
-      FLevel &h = c.hist[(u64)s * (c.L + 1) + d];
-      h.n = cur.n;
-      h.m = cur.m;
-      h.off = cur.off;
-      h.weight = cur.weight;
-      if (cur.weight > cur.n) atomicOr(&st->status, ST_INTERNAL);
-      const u64 nn = cur.weight > cur.n ? 0 : cur.n - cur.weight;
-      memset(&nx, 0, sizeof(nx));
-      nx.n = nn;
-      nx.off = cur.off + cur.m;
-      if (nn == 0) {
-        nx.mode = LM_DONE;
-        st->levels_used = d + 1;
-      } else if ((uint32_t)(d + 1) == c.L) {
-        nx.mode = LM_FLAT;
-        st->tail_level = d + 1;
-        if (nn > st->flat_cap) fail_set(st);
-      } else if (nn <= c.T) {
-        nx.mode = LM_FLAT;
-        nx.m = level_bits(nn, c.gamma);
-        st->tail_level = d + 1;
-      } else {
-        size_set_level(nx, nn, c);
-        nx.off = cur.off + cur.m;
-        nx.mode = LM_BUCKETED;
-      }
-    } else if (cur.mode == LM_BUCKETED) {
-      nx.mode = LM_FAILED;
-    }
-    if (nx.mode == LM_BUCKETED && !st->status) {
-      nbk += nx.B;
-      nslots += nx.B * nx.cap;
-    } else if (nx.mode == LM_BUCKETED) {
-      nx.mode = LM_FAILED;
-    }
-    nx.weight = 0;
-    c.lvl[nl][s] = nx;
-  }
-  // 2. exclusive scans over sets: bucket bases and arena offsets
-  auto scan64 = [&](u64 v, u64 *total) -> u64 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u64 x = v;
+  u64 v[3] = {0, 0, 0};
+  for (unsigned s = lo; s < hi; s++)
+    for (int k = 0; k < 3; k++) v[k] += c.fin[3 * (u64)s + k];
+  u64 x[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    x[k] = v[k];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      u64 y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const u64 y = __shfl_up_sync(0xffffffffu, x[k], o);
+      if (lane >= o) x[k] += y;
     }
-    __syncthreads();
-    if (lane == 31) red64[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      u64 w = lane < kFinishThreads / 32 ? red64[lane] : 0;
+    if (lane == 31) red[k][warp] = x[k];
+  }
+  __syncthreads();
+  u64 pre[3], tot[3];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        u64 y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      if (lane < kFinishThreads / 32) red64[lane] = w;
+  for (int k = 0; k < 3; k++) {
+    u64 w = lane < kFinishThreads / 32 ? red[k][lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    __syncthreads();
-    u64 before = warp ? red64[warp - 1] : 0;
-    *total = red64[kFinishThreads / 32 - 1];
-    __syncthreads();
-    return before + x - v;
-  };
-  u64 tb, ts;
-  u64 gb = scan64(nbk, &tb);
-  u64 ao = scan64(nslots, &ts);
-  const bool fit = tb <= c.bcap && ts <= c.acap[nl];
-  for (unsigned s = lo; s < hi; s++) {
-    BLvl &nx = c.lvl[nl][s];
-    if (nx.mode != LM_BUCKETED) continue;
-    if (!fit) {
-      fail_set(&c.sets[s]);
-      nx.mode = LM_FAILED;
-      continue;
-    }
-    nx.bbase = gb;
-    nx.aoff = ao;
-    for (u64 j = 0; j < nx.B; j++) {
-      c.bset[nl][gb + j] = s;
-      c.bidx[nl][gb + j] = (unsigned)j;
-      c.cnt[nl][gb + j] = 0;
-    }
-    gb += nx.B;
-    ao += nx.B * nx.cap;
+    const u64 before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);
+    tot[k] = __shfl_sync(0xffffffffu, w, kFinishThreads / 32 - 1);
+    pre[k] = (warp ? before : 0) + x[k] - v[k];
   }
-  if (threadIdx.x == 0) c.btotal[nl] = fit ? tb : 0;
-  // 3. compaction units (kIn entries) before each bucket of level d, so that
-  //    the compaction hands every CTA the same number of units
-  {
-    const u64 nbk_d = c.btotal[sl];
-    const u64 bper = (nbk_d + kFinishThreads - 1) / kFinishThreads;
-    const u64 b0 = threadIdx.x * bper, b1 = b0 + bper < nbk_d ? b0 + bper : nbk_d;
-    auto units = [&](u64 g) -> unsigned {
-      const u64 cap = c.lvl[sl][c.bset[sl][g]].cap;
-      const u64 nk = c.cnt[sl][g] < cap ? c.cnt[sl][g] : cap;
-      return (unsigned)((nk + kIn - 1) / kIn);
-    };
-    unsigned su = 0;
-    for (u64 g = b0; g < b1; g++) su += units(g);
-    unsigned total;
-    unsigned pre = block_scan_u32<kFinishThreads>(su, red32, &total);
-    for (u64 g = b0; g < b1; g++) {
+  for (unsigned s = lo; s < hi; s++)
+    for (int k = 0; k < 3; k++) {
+      const u64 t = c.fin[3 * (u64)s + k];
+      c.fin[3 * (u64)s + k] = pre[k];
+      pre[k] += t;
+    }
+  if (threadIdx.x == 0) {
+    const bool fit = tot[0] <= c.bcap && tot[1] <= c.acap[nl];
+    c.btotal[nl] = fit ? tot[0] : 0;
+    c.fit[nl] = fit ? 1u : 0u;
+    c.upre[c.btotal[sl]] = (unsigned)tot[2];
+  }
+}
+
+// 3. one thread per set: level d+1's bucket layout, level d's unit prefix
+__global__ void __launch_bounds__(kFinSetThreads) k_bfin_desc(int d, BCfg c) {
+  const unsigned s = blockIdx.x * kFinSetThreads + threadIdx.x;
+  if (s >= c.S) return;
+  const int sl = d & 1, nl = (d + 1) & 1;
+  const BLvl cur = c.lvl[sl][s];
+  if (cur.mode == LM_BUCKETED) {
+    unsigned pre = (unsigned)c.fin[3 * (u64)s + 2];
+    for (u64 j = 0; j < cur.B; j++) {
+      const u64 g = cur.bbase + j;
+      const unsigned u = c.upre[g];
       c.upre[g] = pre;
-      pre += units(g);
+      pre += u;
     }
-    if (threadIdx.x == 0) c.upre[nbk_d] = total;
   }
+  BLvl &nx = c.lvl[nl][s];
+  if (nx.mode != LM_BUCKETED) return;
+  if (!c.fit[nl]) {
+    fail_set(&c.sets[s]);
+    nx.mode = LM_FAILED;
+    return;
+  }
+  const u64 gb = c.fin[3 * (u64)s], ao = c.fin[3 * (u64)s + 1];
+  nx.bbase = gb;
+  nx.aoff = ao;
+  for (u64 j = 0; j < nx.B; j++) {
+    c.bset[nl][gb + j] = s;
+    c.bidx[nl][gb + j] = (unsigned)j;
+    c.cnt[nl][gb + j] = 0;
+  }
+}
+
+// The three launches of level d's finish.
+static void launch_bfinish(int d, const BCfg &c, cudaStream_t st) {
+  const unsigned gs = (c.S + kFinSetThreads - 1) / kFinSetThreads;
+  k_bfin_sets<<<gs, kFinSetThreads, 0, st>>>(d, c);
+  k_bfin_scan<<<1, kFinishThreads, 0, st>>>(d, c);
+  k_bfin_desc<<<gs, kFinSetThreads, 0, st>>>(d, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -1054,6 +1091,8 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
   u64 *d_koff = (u64 *)p;
   WS(20, 4 * (bcap + 1), &c.upre);
   WS(21, sizeof(BTile) * (ceil_div(total, kTile) + 1), &c.tiles);
+  WS(22, 24 * (u64)S, &c.fin);
+  WS(23, 16, &c.fit);
 #undef WS
   c.keys = d_keys;
   // ---- level-0 bucket descriptors on the host
@@ -1107,9 +1146,9 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
     for (int d = 0; d <= Dl && d < (int)L; d++) {
       if (nbk) {
         k_bfill<<<grid2, kTT, kPmax / 4, st>>>(d, c);
-        k_bfinish<<<1, kFinishThreads, 0, st>>>(d, c);
+        launch_bfinish(d, c, st);
         k_bcompact<<<grid2, kTT, comp_b, st>>>(d, c);
-        nk_rec += 3;
+        nk_rec += 5;
       }
     }
     nk_rec++;
@@ -1195,7 +1234,7 @@ static int batched_impl(const u64 *d_keys, const u64 *h_off, unsigned S, double 
       }
       {
         LaunchScope ls("bfinish", st);
-        k_bfinish<<<1, kFinishThreads, 0, st>>>(d, c);
+        launch_bfinish(d, c, st);
       }
       {
         LaunchScope ls("bcompact", st);
