@@ -289,26 +289,24 @@ struct SlabDest {
 // WITH_POS: each key's position within its slab (below 2^20) goes to pout
 // beside it (the fine slabs' fill and compaction then need no hash).  ONE: at
 // most kTT slabs, one per thread in the multisplit.
-template <bool ALIGNED, bool WITH_POS, bool ONE, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+template <bool ALIGNED, bool WITH_POS, bool ONE>
+__global__ void __launch_bounds__(kTT, 2)
 k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsigned shift,
                unsigned nslab, u64 *__restrict__ cursor, const u64 *__restrict__ end, u64 *__restrict__ out,
                unsigned *__restrict__ pout, unsigned *__restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int kT = NT * kKPT;  // keys a tile
-  static_assert(ONE || NT == kTT, "destinations beyond the threads: kTT-thread blocks only");
-  SplitSmem sm = carve_split(smem, nslab, kT, kT);
+  SplitSmem sm = carve_split(smem, nslab);
   split_clear(sm, nslab);
   __syncthreads();
-  u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes(nslab, kT, kT));
-  auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * NT + threadIdx.x) + (k & 1); };
-  const u64 ntiles = (n + kT - 1) / kT;
+  u64 *inbuf = reinterpret_cast<u64 *>(smem + split_smem_bytes(nslab));
+  auto slot = [&](int k) -> u64 * { return inbuf + 2 * ((k >> 1) * kTT + threadIdx.x) + (k & 1); };
+  const u64 ntiles = (n + kTile - 1) / kTile;
   const unsigned tb = threadIdx.x * kKPT;
   auto prefetch = [&](u64 t) {
     if (t < ntiles) {
-      const u64 *src = keys + t * kT;
-      const u64 rem = n - t * kT;
-      const unsigned nt = rem < (u64)kT ? (unsigned)rem : (unsigned)kT;
+      const u64 *src = keys + t * kTile;
+      const u64 rem = n - t * kTile;
+      const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
       if (ALIGNED && tb + kKPT <= nt) {
 #pragma unroll
         for (int k = 0; k < kKPT; k += 2) cp_async16(slot(k), src + tb + k);
@@ -324,8 +322,8 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
   prefetch(t);
   for (; t < ntiles; t += gridDim.x) {
     cp_async_wait0();  // this thread's copies of tile t have landed
-    const u64 rem = n - t * kT;
-    const unsigned nt = rem < (u64)kT ? (unsigned)rem : (unsigned)kT;
+    const u64 rem = n - t * kTile;
+    const unsigned nt = rem < (u64)kTile ? (unsigned)rem : (unsigned)kTile;
     u64 x[kKPT];
     unsigned dst[kKPT], lp[kKPT];
     bool ok[kKPT];
@@ -347,8 +345,8 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
       lp[k] = WITH_POS ? (unsigned)r & ((1u << shift) - 1u) : 0u;
     }
     if (ONE)
-      multisplit_write_one<WITH_POS, NT>(x, lp, dst, ok, nslab, sm, out, pout,
-                                         SlabDest{cursor, end}, status);
+      multisplit_write_one<WITH_POS>(x, lp, dst, ok, nslab, sm, out, pout, SlabDest{cursor, end},
+                                     status);
     else
       multisplit_write<WITH_POS>(x, lp, dst, ok, nslab, sm, out, pout, SlabDest{cursor, end},
                                  status);
@@ -552,16 +550,13 @@ static unsigned slab_count_for(u64 m) {
 
 using SlabScatterFn = void (*)(const u64 *, u64, u64, u64, u64, unsigned, unsigned, u64 *,
                                const u64 *, u64 *, unsigned *, unsigned *);
-static constexpr int kSmallNT = 256;  // coarse passes of at most kSmallNT slabs: 2048-key tiles
-static SlabScatterFn slab_scatter_fn(bool al, bool pos, bool one, bool small) {
-  if (small && !pos) return al ? k_slab_scatter<true, false, true, kSmallNT>
-                               : k_slab_scatter<false, false, true, kSmallNT>;
+static SlabScatterFn slab_scatter_fn(bool al, bool pos, bool one) {
   if (one) {
-    if (pos) return al ? k_slab_scatter<true, true, true, kTT> : k_slab_scatter<false, true, true, kTT>;
-    return al ? k_slab_scatter<true, false, true, kTT> : k_slab_scatter<false, false, true, kTT>;
+    if (pos) return al ? k_slab_scatter<true, true, true> : k_slab_scatter<false, true, true>;
+    return al ? k_slab_scatter<true, false, true> : k_slab_scatter<false, false, true>;
   }
-  if (pos) return al ? k_slab_scatter<true, true, false, kTT> : k_slab_scatter<false, true, false, kTT>;
-  return al ? k_slab_scatter<true, false, false, kTT> : k_slab_scatter<false, false, false, kTT>;
+  if (pos) return al ? k_slab_scatter<true, true, false> : k_slab_scatter<false, true, false>;
+  return al ? k_slab_scatter<true, false, false> : k_slab_scatter<false, false, false>;
 }
 
 // out <- the n keys of F grouped by slab: position p of level (s, m) goes to
@@ -572,13 +567,8 @@ static int slab_attrs() {
   if (!attr) {
     const int sb = (int)(split_smem_bytes(kSlabMax) + kTile * 8);
     for (int v = 0; v < 8; v++)
-      MPHF_CUDA(cudaFuncSetAttribute(slab_scatter_fn(v & 1, v & 2, v & 4, false),
+      MPHF_CUDA(cudaFuncSetAttribute(slab_scatter_fn(v & 1, v & 2, v & 4),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sb));
-    const int sbs = (int)(split_smem_bytes(kSmallNT, kSmallNT * kKPT, kSmallNT * kKPT) +
-                          kSmallNT * kKPT * 8);
-    for (int v = 0; v < 2; v++)
-      MPHF_CUDA(cudaFuncSetAttribute(slab_scatter_fn(v & 1, false, true, true),
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sbs));
     MPHF_CUDA(cudaFuncSetAttribute(k_fine_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kFineSmem));
     attr = true;
@@ -592,12 +582,10 @@ static void launch_slab_scatter(const u64 *F, u64 n, u64 s, u64 m, u64 base, uns
                                 unsigned nslab, u64 *cursor, const u64 *end, u64 *out,
                                 unsigned *pout, unsigned *status, cudaStream_t st) {
   LaunchScope ls("slab_scatter", st);
+  const unsigned g = grid_for(n, kTile, (unsigned)sm_count() * 2);
+  const size_t sb = split_smem_bytes(nslab) + kTile * 8;
   const bool al = ((uintptr_t)F & 15) == 0;
-  const bool small = !pout && nslab <= (unsigned)kSmallNT;
-  const unsigned nt = small ? kSmallNT : kTT, tile = nt * kKPT;
-  const unsigned g = grid_for(n, tile, (unsigned)sm_count() * (1024 / nt));
-  const size_t sb = split_smem_bytes(nslab, tile, tile) + (size_t)tile * 8;
-  slab_scatter_fn(al, pout != nullptr, nslab <= (unsigned)kTT, small)<<<g, nt, sb, st>>>(
+  slab_scatter_fn(al, pout != nullptr, nslab <= (unsigned)kTT)<<<g, kTT, sb, st>>>(
       F, n, s, m, base, shift, nslab, cursor, end, out, pout, status);
 }
 

@@ -226,7 +226,7 @@ static constexpr u64 kRunMask = (1ull << kRunShift) - 1;
 // `sorted`, `stag`, `run` and `red` only after barriers that every thread
 // reaches after its write-out.  A caller that itself writes `sorted` (a
 // survivor stage) right after the call puts a block barrier in between.
-template <bool WITH_POS, int NT = kTT, class Dest>
+template <bool WITH_POS, class Dest>
 __device__ __forceinline__ void multisplit_write_one(const u64 (&x)[kKPT], const unsigned (&lp)[kKPT],
                                                      const unsigned (&dst)[kKPT], const bool (&ok)[kKPT],
                                                      unsigned nb, const SplitSmem &sm,
@@ -257,14 +257,14 @@ __device__ __forceinline__ void multisplit_write_one(const u64 (&x)[kKPT], const
   }
   if (lane == 31) sm.red[warp] = incl;
   __syncthreads();
-  unsigned wv = lane < NT / 32 ? sm.red[lane] : 0u;
+  unsigned wv = lane < kTT / 32 ? sm.red[lane] : 0u;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const unsigned y = __shfl_up_sync(0xffffffffu, wv, o);
     if (lane >= (unsigned)o) wv += y;
   }
   const unsigned wbefore = __shfl_sync(0xffffffffu, wv, (warp + 31) & 31);
-  const unsigned total = __shfl_sync(0xffffffffu, wv, NT / 32 - 1);
+  const unsigned total = __shfl_sync(0xffffffffu, wv, kTT / 32 - 1);
   const unsigned pre = (warp ? wbefore : 0u) + incl - c;
   const u64 b0 = c ? atomicAdd(dest(i0).counter, (u64)c) : 0;  // waited for after the scatter
   if (i0 < nb) sm.start[i0] = (unsigned short)pre;
@@ -292,7 +292,7 @@ __device__ __forceinline__ void multisplit_write_one(const u64 (&x)[kKPT], const
     u64 v[4], rr[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * NT;
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
       tg[u] = 0;
       v[u] = 0;
       if (i < total) {
@@ -302,12 +302,12 @@ __device__ __forceinline__ void multisplit_write_one(const u64 (&x)[kKPT], const
     }
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * NT;
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
       rr[u] = i < total ? sm.run[tg[u] >> 20] : 0;
     }
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * NT;
+      const unsigned i = threadIdx.x + (unsigned)(k0 + u) * kTT;
       if (i < total) {
         if (i < (unsigned)(rr[u] >> kRunShift)) {
           const u64 j = (rr[u] + i) & kRunMask;
@@ -390,28 +390,26 @@ __device__ __forceinline__ void multisplit_write(const u64 (&x)[kKPT], const uns
 // Zero the destination counts before a kernel's first multisplit_write (the
 // caller synchronises the block before that call).
 __device__ __forceinline__ void split_clear(const SplitSmem &sm, unsigned nb_cap) {
-  for (unsigned i = threadIdx.x; i < nb_cap; i += blockDim.x) sm.cnt[i] = 0;
+  for (unsigned i = threadIdx.x; i < nb_cap; i += kTT) sm.cnt[i] = 0;
 }
 
 // sorted_cap >= kTile entries of `sorted` (a caller may stage more keys there
 // than one multisplit takes; the multisplit itself uses the first kTile).
 __device__ __forceinline__ SplitSmem carve_split(unsigned char *smem, unsigned nb_cap,
-                                                 unsigned sorted_cap = kTile,
-                                                 unsigned tile = kTile) {
+                                                 unsigned sorted_cap = kTile) {
   SplitSmem s;
   s.sorted = reinterpret_cast<u64 *>(smem);
   s.run = s.sorted + sorted_cap;
   s.stag = reinterpret_cast<unsigned *>(s.run + nb_cap);
-  s.cnt = s.stag + tile;
+  s.cnt = s.stag + kTile;
   s.red = s.cnt + nb_cap;
   s.start = reinterpret_cast<unsigned short *>(s.red + kTT / 32 + 2);
   return s;
 }
 
-static constexpr size_t split_smem_bytes(unsigned nb_cap, unsigned sorted_cap = kTile,
-                                        unsigned tile = kTile) {
+static constexpr size_t split_smem_bytes(unsigned nb_cap, unsigned sorted_cap = kTile) {
   // a multiple of 16 bytes: callers place 16-byte staging buffers after it
-  return ((size_t)sorted_cap * 8 + (size_t)nb_cap * 8 + (size_t)tile * 4 + (size_t)nb_cap * 4 +
+  return ((size_t)sorted_cap * 8 + (size_t)nb_cap * 8 + (size_t)kTile * 4 + (size_t)nb_cap * 4 +
           (kTT / 32 + 2) * 4 + (size_t)nb_cap * 2 + 8 + 15) & ~(size_t)15;
 }
 
