@@ -361,10 +361,12 @@ k_slab_scatter(const u64 *__restrict__ keys, u64 n, u64 s, u64 m, u64 base, unsi
 // collision bits from the stored positions (Algorithm 2, the same three
 // implications as fill_position); A_d's words of the range are written and
 // their ones added to weight(A_d).  Every key hashed into these positions is
-// in this CTA, so its bits are final: pass 2 keeps the keys whose A_d bit is
-// 0 (F_{d+1}, Algorithm 1), staged per warp and written to Fout in runs
-// reserved with one atomicAdd on out_count.  A run past `cap` is not written
-// and raises bit 0 of fuse_status.
+// in this CTA, so its bits are final: pass 2 reads the keys, hashes each to
+// its position again (level seed s_d, size m_d: one memory round trip a step
+// instead of a position load and then a key load) and keeps those whose A_d
+// bit is 0 (F_{d+1}, Algorithm 1), staged per warp and written to Fout in
+// runs reserved with one atomicAdd on out_count.  A run past `cap` is not
+// written and raises bit 0 of fuse_status.
 static constexpr unsigned kFineShift = 18;
 static constexpr int kFineThreads = 512;
 static constexpr int kFineStage = 256;  // survivors a warp stages before writing them
@@ -376,7 +378,7 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
             const u64 *__restrict__ fstart, const u64 *__restrict__ fend,
             const u64 *__restrict__ fcap, u64 base, u64 lim, u64 *__restrict__ Alev,
             u64 *__restrict__ weight, u64 *__restrict__ Fout, u64 cap,
-            u64 *__restrict__ out_count, unsigned *__restrict__ fuse_status) {
+            u64 *__restrict__ out_count, unsigned *__restrict__ fuse_status, u64 s_d, u64 m_d) {
   extern __shared__ __align__(16) unsigned fsm[];
   __shared__ u64 red[kFineThreads / 32];
   constexpr unsigned kWords = (1u << kFineShift) / 32;
@@ -444,8 +446,7 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     if (t) atomicAdd(weight, t);
   }
   // pass 2: compaction; a warp step takes kC chunks of 128 entries, each lane
-  // four consecutive entries of a chunk (one 16-byte position load, the
-  // survivors' keys in 16-byte pairs)
+  // four consecutive entries of a chunk (its keys in two 16-byte loads)
   const unsigned lt = (1u << lane) - 1u;
   unsigned cnt = 0;
   auto flush = [&]() {
@@ -467,43 +468,33 @@ k_fine_fill(const u64 *__restrict__ T, const unsigned *__restrict__ TP,
     if (cnt > (unsigned)(kFineStage - 32)) flush();
   };
   {
-    const uint4 *TP4 = reinterpret_cast<const uint4 *>(TP);
     const uint4 *T4 = reinterpret_cast<const uint4 *>(T);  // T is 16-byte aligned like TP
     const u64 va = ia >> 2, vb = ib >> 2;
     constexpr int kC = 2;
-    // last steps first: the positions pass 1 read last are the likeliest to
-    // still be in L2
+    // each lane's four keys of a chunk in two 16-byte loads; their positions
+    // in the fine slab come from the level hash (no second read of TP)
+    auto qpos = [&](u64 x) { return (unsigned)(level_pos(x, s_d, m_d) - p0); };
     constexpr u64 kStep = (u64)kC * kFineThreads;
     const u64 nsteps = (vb - va + kStep - 1) / kStep;
-    for (u64 st = nsteps; st-- > 0;) {
+    for (u64 st = 0; st < nsteps; st++) {
       const u64 c0 = va + st * kStep + (u64)warp * 32;
-      uint4 q[kC];
+      uint4 x01[kC], x23[kC];
       bool ok[kC];
 #pragma unroll
       for (int c = 0; c < kC; c++) {
         const u64 v = c0 + (u64)c * kFineThreads + lane;
         ok[c] = v < vb;
-        q[c] = ok[c] ? TP4[v] : make_uint4(0, 0, 0, 0);
-      }
-      bool k[kC][4];
-      uint4 x01[kC], x23[kC];
-#pragma unroll
-      for (int c = 0; c < kC; c++) {
-        const u64 v = c0 + (u64)c * kFineThreads + lane;
-        k[c][0] = ok[c] && kept(q[c].x);
-        k[c][1] = ok[c] && kept(q[c].y);
-        k[c][2] = ok[c] && kept(q[c].z);
-        k[c][3] = ok[c] && kept(q[c].w);
-        // keys 4v .. 4v+3 are T4[2v], T4[2v + 1]; only pairs with a survivor are read
-        x01[c] = (k[c][0] || k[c][1]) ? __ldcs(T4 + 2 * v) : make_uint4(0, 0, 0, 0);
-        x23[c] = (k[c][2] || k[c][3]) ? __ldcs(T4 + 2 * v + 1) : make_uint4(0, 0, 0, 0);
+        x01[c] = ok[c] ? __ldcs(T4 + 2 * v) : make_uint4(0, 0, 0, 0);
+        x23[c] = ok[c] ? __ldcs(T4 + 2 * v + 1) : make_uint4(0, 0, 0, 0);
       }
 #pragma unroll
       for (int c = 0; c < kC; c++) {
-        put(k[c][0], ((u64)x01[c].y << 32) | x01[c].x);
-        put(k[c][1], ((u64)x01[c].w << 32) | x01[c].z);
-        put(k[c][2], ((u64)x23[c].y << 32) | x23[c].x);
-        put(k[c][3], ((u64)x23[c].w << 32) | x23[c].z);
+        const u64 y0 = ((u64)x01[c].y << 32) | x01[c].x, y1 = ((u64)x01[c].w << 32) | x01[c].z;
+        const u64 y2 = ((u64)x23[c].y << 32) | x23[c].x, y3 = ((u64)x23[c].w << 32) | x23[c].z;
+        put(ok[c] && kept(qpos(y0)), y0);
+        put(ok[c] && kept(qpos(y1)), y1);
+        put(ok[c] && kept(qpos(y2)), y2);
+        put(ok[c] && kept(qpos(y3)), y3);
       }
     }
     // the entries around the aligned part (at most 6): warp 0, one per lane
@@ -757,7 +748,7 @@ static int fill_grouped(const u64 *R, u64 s, u64 m, unsigned nslab, const std::v
         k_fine_fill<<<nf, kFineThreads, kFineSmem, st>>>(T, TP, fstart, cursor, end, base,
                                                          base + range, Alev, &meta->weight[d],
                                                          Fout, cap, &meta->out_count[d],
-                                                         fuse_status);
+                                                         fuse_status, s, m);
       }
       MPHF_CUDA(cudaGetLastError());
     }
