@@ -407,13 +407,13 @@ def kernel_table(h, prof, steps, n_queries):
 # hit/collision bits); a "query" one looked-up key; a "key" one key of F_0.
 _HDR = ["common.cuh", "fastbuild.cuh", "sector.cuh"]
 NCU_TRAFFIC = {
-    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "a2f470193f6a", "unit": "grouped key-visit",
-                     "bytes_per_unit": 35.20,
-                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.24 GB "
+    "slab_scatter": {"src": ["build.cu"] + _HDR, "sha": "3e970480a42b", "unit": "grouped key-visit",
+                     "bytes_per_unit": 35.19,
+                     "note": "3e8-key capture (level 0 grouped: 24 launches of 4 builds, 42.23 GB "
                              "over 1.2e9 grouped key-visits), scaled by grouped key-visits"},
-    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "a2f470193f6a", "unit": "grouped key-visit",
-                  "bytes_per_unit": 17.73,
-                  "note": "3e8-key capture (20 launches of 4 builds, 21.27 GB over 1.2e9 "
+    "fine_fill": {"src": ["build.cu"] + _HDR, "sha": "3e970480a42b", "unit": "grouped key-visit",
+                  "bytes_per_unit": 14.52,
+                  "note": "3e8-key capture (20 launches of 4 builds, 17.43 GB over 1.2e9 "
                           "grouped key-visits), scaled by grouped key-visits"},
     "lookup@hbm": {"src": ["lookup.cu"] + _HDR, "sha": "590bc6e40776", "unit": "query",
                    "bytes_per_unit": 114.8,
