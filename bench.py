@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--no-sweep", action="store_true", help="skip timing gamma = 1 and 5 (1e8)")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-set batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-partitioned", action="store_true",
+                   help="skip the partitioned-form block (1e9 keys in 8 parts)")
     p.add_argument("--no-ceilings", action="store_true", help="skip the ceiling kernels")
     p.add_argument("--serve-seconds", type=float, default=3.0)
     p.add_argument("--no-layouts", action="store_true",
@@ -827,6 +829,50 @@ def run_batched(args, stream):
     return res
 
 
+def run_partitioned(args, stream):
+    """The partitioned form on this GPU: 1e9 keys (stream 13) routed by a
+    seeded hash into K = 8 parts, one function a part built one after
+    another (mphf_build_partitioned; with one part per rank this is the
+    8-GPU form, each rank building one part), then the 1e9 keys looked up in
+    shuffled order through the routing (mphf_part_lookup).  Median of 3."""
+    import torch
+
+    from paper_1702_03154_gb300 import mphf
+    N, K = 10**9, 8
+    keys = mphf.keygen(N, 13)
+    q = keys[torch.randperm(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(14))]
+    out = torch.empty_like(q)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tb, tl = [], []
+    last = None
+    for rep in range(4):
+        if last is not None:
+            del last
+        ev[0].record(stream)
+        last = mphf.PartitionedMPHF.build(keys, K, 21, gamma=2.0, levels=25, seed=0)
+        ev[1].record(stream)
+        last.lookup(q, out=out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            tb.append(ev[0].elapsed_time(ev[1]))
+            tl.append(ev[1].elapsed_time(ev[2]))
+    b_ms, l_ms = float(np.median(tb)), float(np.median(tl))
+    sizes = np.diff(last.offsets.astype(np.int64))
+    res = {"workload": f"N=1e9 SplitMix64 keys (stream 13), K={K} parts by a seeded hash "
+                       "(one function a part, built one after another on this GPU; the "
+                       "8-GPU form gives each rank one part), gamma=2, L=25; then all keys "
+                       "looked up in shuffled order through the routing",
+           "build_ms": round(b_ms, 3), "build_mkeys_s": round(N / b_ms / 1e3, 1),
+           "lookup_ms": round(l_ms, 3), "lookup_mkeys_s": round(N / l_ms / 1e3, 1),
+           "part_keys_min_max": [int(sizes.min()), int(sizes.max())],
+           "statistic": "median of 3 after one warm-up, CUDA events"}
+    del last, keys, q, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_serving(args, stream):
     """256 resident functions, sizes log-uniform in [1e4, 1e7] (seed 11), gamma = 2;
     open-loop Poisson lookups (batch sizes log-uniform in [1, 1e6] of member keys)
@@ -966,6 +1012,7 @@ def run_ours(args):
     plain = None if args.no_plain else run_plain(args, stream, rank, ceil)
     batched = None if args.no_batched else run_batched(args, stream)
     serving = None if args.no_serving else run_serving(args, stream)
+    partitioned = None if args.no_partitioned else run_partitioned(args, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(10_000_000, max(1, int(10_000_000 * Q / N)), C3_KEY_SEED, args.gamma,
@@ -990,6 +1037,8 @@ def run_ours(args):
             line["batched"] = batched
         if serving:
             line["serving"] = serving
+        if partitioned:
+            line["partitioned"] = partitioned
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
