@@ -253,8 +253,9 @@ def run_reference(args):
 
 # -------------------------------------------------------- algorithmic bytes
 # Unbucketed path: a level whose hit/collision array (2 bits a position)
-# exceeds 64 MiB is grouped by slab before its fill (count pass, coarse and
-# fine multisplit, shared-memory fill); smaller levels fill with L2 atomics.
+# exceeds 64 MiB is grouped by slab before its fill (coarse and fine
+# multisplit into fixed-capacity ranges, shared-memory fill and compaction);
+# smaller levels fill with L2 atomics.
 GROUP_MIN_AC_BYTES = 64 << 20
 
 
