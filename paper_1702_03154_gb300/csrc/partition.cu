@@ -27,7 +27,7 @@ static constexpr int kPartTile = kPartThreads * kPartPerThread;
 static constexpr uint32_t kMaxParts = 1024;
 
 __device__ __forceinline__ uint32_t part_of(u64 x, u64 sp, uint32_t K) {
-  return (uint32_t)__umul64hi(mix64(x ^ sp), (u64)K);
+  return part_index(x, sp, K);
 }
 
 __global__ void __launch_bounds__(kPartThreads)
@@ -263,6 +263,11 @@ extern "C" int mphf_part_lookup(const mphf_part_t *p, const uint64_t *d_keys, ui
   if (n == 0) return MPHF_OK;
   if (!d_keys || !d_out || ((uintptr_t)d_keys & 7) || ((uintptr_t)d_out & 7)) return MPHF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  // one pass: each key's part from its hash, no routing (when the parts share
+  // a layout and none is empty)
+  if (lookup_parts_direct(p->f.data(), p->K, mix64(p->part_seed), (const u64 *)p->d_off.p,
+                          (const u64 *)d_keys, n, (u64 *)d_out, s) == MPHF_OK)
+    return MPHF_OK;
   DevBuf buf;
   int rc = dev_alloc(buf, 3 * n * sizeof(u64), s);
   if (rc != MPHF_OK) return rc;

@@ -259,6 +259,172 @@ k_lookup_multi(const ReqDev *__restrict__ reqs, unsigned nreq, u64 total, u64 cs
   }
 }
 
+// Lookups against the K functions of a split, without routing the keys: a
+// refilled slot takes its key's part from the part hash, that part's
+// function, and adds the part's offset to the answer.  Slots and probes as in
+// k_lookup_multi (one index space: the n keys).
+template <int W, bool NARROW>
+__global__ void __launch_bounds__(kMultiThreads)
+k_lookup_parts(const u64 *__restrict__ keys, u64 n, u64 csz, u64 *__restrict__ out,
+               const LookupDev *const *__restrict__ fns, const u64 *__restrict__ prefix,
+               uint32_t K, u64 sp) {
+  using LW = Lay<W>;
+  const unsigned lane = threadIdx.x & 31;
+  const u64 nchunks = (n + csz - 1) / csz;
+  const u64 nwarps = ((u64)gridDim.x * kMultiThreads) >> 5;
+  u64 chunk = ((u64)blockIdx.x * kMultiThreads + threadIdx.x) >> 5;
+  u64 cursor = chunk * csz;
+  u64 cend = chunk < nchunks ? min(cursor + csz, n) : cursor;
+  bool more = chunk < nchunks;
+  const unsigned lt = (1u << lane) - 1u;
+  u64 x[kMultiSlots], idx[kMultiSlots];
+  const LookupDev *hd[kMultiSlots];
+  unsigned part[kMultiSlots], lvl[kMultiSlots];
+  bool act[kMultiSlots];
+#pragma unroll
+  for (int s = 0; s < kMultiSlots; s++) {
+    act[s] = false;
+    lvl[s] = 0;
+    x[s] = 0;
+    idx[s] = 0;
+    part[s] = 0;
+    hd[s] = nullptr;
+  }
+  auto take = [&](int s, u64 i) {
+    x[s] = __ldcs(keys + i);
+    idx[s] = i;
+    part[s] = part_index(x[s], sp, K);
+    hd[s] = fns[part[s]];
+    lvl[s] = 0;
+    act[s] = true;
+  };
+  for (;;) {
+#pragma unroll
+    for (int s = 0; s < kMultiSlots; s++) {
+      unsigned need = __ballot_sync(0xffffffffu, !act[s]);
+      while (need && more) {
+        if (cursor >= cend) {
+          chunk += nwarps;
+          if (chunk >= nchunks) {
+            more = false;
+            break;
+          }
+          cursor = chunk * csz;
+          cend = min(cursor + csz, n);
+        }
+        const u64 avail = cend - cursor;
+        const unsigned r = __popc(need & lt);
+        const bool mine = ((need >> lane) & 1u) && (u64)r < avail;
+        if (mine) take(s, cursor + r);
+        const unsigned taken = __ballot_sync(0xffffffffu, mine);
+        need &= ~taken;
+        cursor += __popc(taken);
+      }
+    }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < kMultiSlots; s++) any |= act[s];
+    if (!__any_sync(0xffffffffu, any)) break;
+    typename LW::Pos p[kMultiSlots];
+    typename LW::Data v[kMultiSlots];
+#pragma unroll
+    for (int s = 0; s < kMultiSlots; s++) {
+      if (act[s]) {
+        const unsigned d = lvl[s];
+        const LookupDev *h = hd[s];
+        if (NARROW) {
+          const u64 hh = mix64(x[s] ^ __ldg(h->s + d));
+          const unsigned m32 = __ldg(h->m32 + d);
+          const u64 lo = ((u64)(unsigned)hh * m32) >> 32;
+          const unsigned pd = (unsigned)(((u64)(unsigned)(hh >> 32) * m32 + lo) >> 32);
+          p[s] = LW::pos_q(__ldg(h->oq + d) + (pd >> LW::kQShift),
+                           pd & ((1u << LW::kQShift) - 1u));
+        } else {
+          p[s] = LW::pos(__ldg(h->off + d) + level_pos(x[s], __ldg(h->s + d), __ldg(h->m + d)));
+        }
+        v[s] = LW::load(h->S, p[s]);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kMultiSlots; s++) {
+      if (act[s]) {
+        const LookupDev *h = hd[s];
+        unsigned w = 0;
+        u64 r = MPHF_NOT_FOUND;
+        bool done = false;
+        if (LW::hit(v[s], p[s], w)) {
+          r = LW::rank(v[s], p[s], w, h->SB);
+          done = true;
+        } else if (++lvl[s] >= h->L_used) {
+          r = h->n_fb ? fallback_index_m(h, x[s]) : MPHF_NOT_FOUND;
+          done = true;
+        }
+        if (done) {
+          __stcs(out + idx[s], r == MPHF_NOT_FOUND ? r : r + __ldg(prefix + part[s]));
+          act[s] = false;
+        }
+      }
+    }
+  }
+}
+
+template <int W, bool NARROW>
+static int launch_parts_wn(const LookupDev *const *d_fns, const u64 *prefix, uint32_t K, u64 sp,
+                           const u64 *keys, u64 n, u64 *out, cudaStream_t s) {
+  static u64 maxb_dev[64] = {0};  // one wave of resident CTAs, per device
+  u64 &maxb = maxb_dev[cur_device()];
+  if (!maxb) maxb = resident_grid(k_lookup_parts<W, NARROW>, kMultiThreads, 0);
+  const u64 csz = lookup_chunk(n, maxb * (kMultiThreads / 32));
+  const u64 chunks = (n + csz - 1) / csz;
+  u64 grid = (chunks + (kMultiThreads / 32) - 1) / (kMultiThreads / 32);
+  if (grid > maxb) grid = maxb;
+  if (grid < 1) grid = 1;
+  LaunchScope ls("lookup_parts", s);
+  k_lookup_parts<W, NARROW><<<(unsigned)grid, kMultiThreads, 0, s>>>(keys, n, csz, out, d_fns,
+                                                                      prefix, K, sp);
+  MPHF_CUDA(cudaGetLastError());
+  return MPHF_OK;
+}
+
+template <int W>
+static int launch_parts_w(const LookupDev *const *d_fns, const u64 *prefix, uint32_t K, u64 sp,
+                          const u64 *keys, u64 n, u64 *out, bool narrow, cudaStream_t s) {
+  return narrow ? launch_parts_wn<W, true>(d_fns, prefix, K, sp, keys, n, out, s)
+                : launch_parts_wn<W, false>(d_fns, prefix, K, sp, keys, n, out, s);
+}
+
+int lookup_parts_direct(mphf *const *fs, uint32_t K, u64 sp, const u64 *d_prefix,
+                        const u64 *keys, u64 n, u64 *out, cudaStream_t s) {
+  if (K == 0 || !fs[0]) return MPHF_EINVAL;
+  const unsigned sw = fs[0]->sw;
+  bool narrow = true;
+  for (uint32_t k = 0; k < K; k++) {
+    if (!fs[k] || fs[k]->sw != sw || fs[k]->L_used == 0) return MPHF_EINVAL;
+    narrow = narrow && narrow_positions(fs[k]);
+  }
+  std::vector<const LookupDev *> t(K);
+  for (uint32_t k = 0; k < K; k++) {
+    int rc = ensure_lookup_desc(fs[k]);
+    if (rc != MPHF_OK) return rc;
+    t[k] = (const LookupDev *)fs[k]->ldesc.p;
+  }
+  DevBuf d;
+  int rc = dev_alloc(d, sizeof(void *) * K, s);
+  if (rc != MPHF_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(d.p, t.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    dev_free(d, s);
+    return cuda_fail(e, "cudaMemcpyAsync(part functions)");
+  }
+  const LookupDev *const *dt = (const LookupDev *const *)d.p;
+  if (sw == kSectWords) rc = launch_parts_w<kSectWords>(dt, d_prefix, K, sp, keys, n, out, narrow, s);
+  else if (sw == kSectWordsMini)
+    rc = launch_parts_w<kSectWordsMini>(dt, d_prefix, K, sp, keys, n, out, narrow, s);
+  else rc = launch_parts_w<kUnitBits>(dt, d_prefix, K, sp, keys, n, out, narrow, s);
+  dev_free(d, s);  // stream-ordered: released after the kernel (the pageable copy has taken t)
+  return rc;
+}
+
 template <int W, bool NARROW>
 static int launch_multi_wn(const ReqDev *d_reqs, unsigned nreq, u64 total, cudaStream_t s) {
   static u64 maxb_dev[64] = {0};  // one wave of resident CTAs, per device
