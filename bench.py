@@ -835,7 +835,8 @@ def run_partitioned(args, stream):
     seeded hash into K = 8 parts, one function a part built one after
     another (mphf_build_partitioned; with one part per rank this is the
     8-GPU form, each rank building one part), then the 1e9 keys looked up in
-    shuffled order through the routing (mphf_part_lookup).  Median of 3."""
+    shuffled order (mphf_part_lookup: each key's function from its part
+    hash).  Median of 3."""
     import torch
 
     from paper_1702_03154_gb300 import mphf
@@ -864,7 +865,7 @@ def run_partitioned(args, stream):
     res = {"workload": f"N=1e9 SplitMix64 keys (stream 13), K={K} parts by a seeded hash "
                        "(one function a part, built one after another on this GPU; the "
                        "8-GPU form gives each rank one part), gamma=2, L=25; then all keys "
-                       "looked up in shuffled order through the routing",
+                       "looked up in shuffled order, each with its part's function",
            "build_ms": round(b_ms, 3), "build_mkeys_s": round(N / b_ms / 1e3, 1),
            "lookup_ms": round(l_ms, 3), "lookup_mkeys_s": round(N / l_ms / 1e3, 1),
            "part_keys_min_max": [int(sizes.min()), int(sizes.max())],

@@ -455,11 +455,15 @@ int mphf_server_loadgen(mphf_server_t *srv, mphf_t *const *hs, const uint64_t *c
  *   mphf_build_partitioned  routes the keys and builds every part (parts of
  *                     up to 2^24 keys together by the batched construction,
  *                     larger ones one by one); the handle owns the K functions.
- *   mphf_part_lookup  routes the queries, answers every part's queries in one
- *                     multi-function launch and writes each key's global
- *                     index (or MPHF_NOT_FOUND) at its own position of d_out.
- *                     Allocates 24 bytes per query of scratch; waits for the
- *                     routing counts, the rest is asynchronous on `stream`.
+ *   mphf_part_lookup  writes each key's global index (or MPHF_NOT_FOUND) at
+ *                     its own position of d_out.  When the K functions share
+ *                     one storage layout and none is empty, one launch
+ *                     answers every key with the function of its part (part
+ *                     hash per key, no routing; asynchronous on `stream`).
+ *                     Otherwise it routes the queries (24 bytes per query of
+ *                     scratch; waits for the routing counts), answers every
+ *                     part's queries in one multi-function launch and scatters
+ *                     the answers back.
  *   mphf_part_info    K and the K + 1 global offsets (h_offsets may be NULL).
  *   mphf_part_function  part k's function (owned by the handle), NULL if k >= K.
  * Errors: MPHF_EINVAL for K outside [1, 1024], bad gamma / levels, NULL or
