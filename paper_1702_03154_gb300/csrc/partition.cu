@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "parts.cuh"
 
 namespace bbh {
 

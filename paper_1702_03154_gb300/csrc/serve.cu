@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "parts.cuh"
 #include "sector.cuh"
 
 namespace bbh {
