@@ -579,11 +579,15 @@ static void scheduler(mphf_server *sv) {
   int rr = 0;
   while (!sv->stop.load()) {
     bool worked = false;
-    // 1. completions
-    while (!sv->inflight.empty()) {
-      Batch &b = sv->inflight.front();
+    // 1. completions, in any order: batches alternate between two streams,
+    // so a short batch may finish behind a longer one launched before it
+    for (auto it = sv->inflight.begin(); it != sv->inflight.end();) {
+      Batch &b = *it;
       cudaError_t q = cudaEventQuery(b.ev);
-      if (q == cudaErrorNotReady) break;
+      if (q == cudaErrorNotReady) {
+        ++it;
+        continue;
+      }
       const double t = now_s();
       float gpu_ms = 0.f;
       if (cudaEventElapsedTime(&gpu_ms, b.ev0, b.ev) != cudaSuccess) {
@@ -603,7 +607,7 @@ static void scheduler(mphf_server *sv) {
       }
       sv->cv_done.notify_all();
       sv->slot_busy[b.slot] = false;
-      sv->inflight.pop_front();
+      it = sv->inflight.erase(it);
       worked = true;
     }
     // 2. a new lookup batch from everything pending (continuous batching)
